@@ -91,6 +91,14 @@ void orc_window_stats_twopass(const float *x, int64_t n, int64_t m,
     for (int64_t i = 0; i < N; ++i) orc_stats_twopass(x + i, m, &mu[i], &sigma[i]);
 }
 
+/* Compensated summation (Neumaier): s + c carries the sum to about one ulp. */
+static void comp_add(double *s, double *c, double v)
+{
+    double t = *s + v;
+    *c += fabs(*s) >= fabs(v) ? (*s - t) + v : (v - t) + *s;
+    *s = t;
+}
+
 /* Sum over [bB, e) of block b's anchored terms, for bB < e <= end of block b:
    the block total when e is the block's end, else the prefix entry P[e]. */
 static double block_upto(const double *P, const double *T, int64_t n, int64_t B,
@@ -108,8 +116,10 @@ static double block_upto(const double *P, const double *T, int64_t n, int64_t B,
  * most two blocks; the second block's sums are moved to anchor a_b0 with
  *   sum(x - a0)   = sum(x - a1) + k (a1 - a0)
  *   sum(x - a0)^2 = sum(x - a1)^2 + 2 (a1 - a0) sum(x - a1) + k (a1 - a0)^2.
- * Then mu = a0 + S1/m and var = S2/m - (S1/m)^2, and R2 applies.  When the
- * subtraction cancels (var <= 1e-6 * S2/m) the window is evaluated two-pass.
+ * Then mu = a0 + S1/m and var = S2/m - (S1/m)^2, and R2 applies.  The block
+ * sums are compensated, and when the subtraction cancels (var <= 1e-6*S2/m)
+ * or m*var <= 1e-9 times the block's sum of squares, the window is evaluated
+ * two-pass instead.
  * Returns 0, or -1 when B < m or memory is short.
  */
 int orc_window_stats_anchored(const float *x, int64_t n, int64_t m, int64_t B,
@@ -130,17 +140,17 @@ int orc_window_stats_anchored(const float *x, int64_t n, int64_t m, int64_t B,
     }
     for (int64_t b = 0; b < nb; ++b) {
         int64_t t0 = b * B, t1 = t0 + B < n ? t0 + B : n;
-        double a = (double)x[t0], s1 = 0.0, s2 = 0.0;
+        double a = (double)x[t0], s1 = 0.0, c1 = 0.0, s2 = 0.0, c2 = 0.0;
         A[b] = a;
         for (int64_t t = t0; t < t1; ++t) {
-            P1[t] = s1;
-            P2[t] = s2;
+            P1[t] = s1 + c1;
+            P2[t] = s2 + c2;
             double d = (double)x[t] - a;
-            s1 += d;
-            s2 += d * d;
+            comp_add(&s1, &c1, d);
+            comp_add(&s2, &c2, d * d);
         }
-        T1[b] = s1;
-        T2[b] = s2;
+        T1[b] = s1 + c1;
+        T2[b] = s2 + c2;
     }
     int64_t N = n - m + 1;
     for (int64_t i = 0; i < N; ++i) {
@@ -159,9 +169,11 @@ int orc_window_stats_anchored(const float *x, int64_t n, int64_t m, int64_t B,
         }
         double mr = S1 / (double)m;
         double v = S2 / (double)m - mr * mr;
-        if (v <= 1e-6 * (S2 / (double)m)) {
-            /* the shifted sums cancelled to fewer than ~10 significant
-               digits: evaluate Eq. 5 two-pass for this window instead */
+        double M2 = T2[b0] + (e > (b0 + 1) * B ? T2[b0 + 1] + S2 : 0.0);
+        if (v <= 1e-6 * (S2 / (double)m) || v * (double)m <= 1e-9 * M2) {
+            /* the shifted sums cancelled, or var is not far above the
+               rounding of the block sums: evaluate Eq. 5 two-pass for this
+               window instead */
             orc_stats_twopass(x + i, m, &mu[i], &sigma[i]);
             continue;
         }

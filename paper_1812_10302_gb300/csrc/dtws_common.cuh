@@ -1,0 +1,188 @@
+// dtws_common.cuh -- device helpers shared by the dtws kernels (sm_103a).
+//
+// * packed top-k keys: (float bits of a non-negative distance << 32) | offset,
+//   so unsigned order is (distance, offset) order, the tie rule of the search
+//   (lowest offset wins);
+// * a lock-free bounded top-k list built from atomicMin on such keys;
+// * inline-PTX wrappers for mbarriers and 1-D bulk (TMA) copies;
+// * bounded waits that record DTWS_ETIMEOUT instead of spinning forever.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace dtws {
+
+// ---------------------------------------------------------------- limits
+constexpr int kBlockB = 8192;       // anchored prefix block length (= DTWS_M_MAX)
+constexpr int kMMax = 8192;
+constexpr int kKMax = 64;
+constexpr int kListMax = 128;       // result list capacity (k + near-tie margin)
+constexpr int kSeedMax = 128;       // random seeds + proxy proposals
+constexpr int kPropMax = 64;
+constexpr int kTile = 2048;         // windows per lower-bound tile
+constexpr int kBins = 1024;         // survivor ordering bins
+constexpr uint64_t kEmptyKey = ~0ull;
+
+// status bits (device word in the handle)
+constexpr int kStNonFinite = 1;
+constexpr int kStTimeout = 2;
+constexpr int kStOverflow = 4;
+
+// per-query counters (QueryState::ctr)
+enum Ctr {
+    kCtrKim = 0, kCtrKeoghQ = 1, kCtrKeoghS = 2, kCtrDtwStarted = 3,
+    kCtrDtwAbandoned = 4, kCtrCells = 5, kCtrRescored = 6, kCtrN = 8
+};
+
+// Device-resident state of one query (one per handle; queries of a batch
+// reuse it in stream order).
+struct QueryState {
+    unsigned long long seed_keys[kKMax];   // k smallest seed distances
+    unsigned long long res_keys[kListMax]; // smallest survivor distances
+    unsigned long long prop_keys[kPropMax];// proxy-scan proposals
+    unsigned int seed_off[kSeedMax];       // offsets whose DTW seeds bsf
+    int n_seeds;
+    int n_cand;                            // survivors of the lower bounds
+    int work;                              // work cursor (seeds, *_at, re-score)
+    int work2;                             // work cursor of the survivor DTW
+    int n_margin;                          // candidates to re-score in FP64
+    unsigned int margin_idx[kListMax];
+    double margin_d64[kListMax];
+    unsigned long long ctr[kCtrN];
+    float thr_scan;                        // threshold the LB scan used
+    int valid;                             // 0 when the query is non-finite
+    int hist[kBins];
+    int bin_off[kBins];
+};
+
+// Scalars of one query, passed by value to every kernel.
+struct QueryArgs {
+    int64_t N;          // windows
+    int m, r, k;
+    int list_cap;       // result list slots in use (k + margin)
+    float delta, alpha; // prune when LB > bsf*(1+delta) + alpha
+    float qgrid;        // key grid: a power of two <= alpha/4
+};
+
+// ---------------------------------------------------------------- keys
+__device__ __forceinline__ unsigned long long make_key(float d, unsigned int idx) {
+    return ((unsigned long long)__float_as_uint(d) << 32) | idx;
+}
+// Distance as stored in a key: rounded DOWN to a grid coarser than FP32
+// noise -- multiples of g below 2048 g, 11 mantissa bits above (the same
+// spacing at the seam, so the map is monotone).  Windows whose distances
+// differ only by rounding (e.g. bit-identical windows whose statistics came
+// from different prefix sums) share a key distance and are ordered by
+// offset, as exact ties must be.  Rounding down keeps every threshold built
+// from keys within the pruning margin: with delta >= 2^-10 > 2^-11 and
+// alpha >= 4 g the bound bsf*(1+delta)+alpha still covers the FP32 error.
+__device__ __forceinline__ float key_quantize(float d, float g) {
+    if (d < g * 2048.0f) return floorf(d / g) * g;
+    return __uint_as_float(__float_as_uint(d) & ~0xfffu);
+}
+__device__ __forceinline__ float key_dist(unsigned long long key) {
+    return key == kEmptyKey ? __int_as_float(0x7f800000) : __uint_as_float((unsigned)(key >> 32));
+}
+__device__ __forceinline__ unsigned int key_idx(unsigned long long key) {
+    return (unsigned)(key & 0xffffffffu);
+}
+
+// Insert a unique key into a sorted list of `cap` slots that holds the cap
+// smallest keys offered so far.  Slot j keeps the minimum of what reaches it
+// and hands the larger value on to slot j+1; since every atomicMin keeps one
+// value and emits one, slot j ends as the (j+1)-th smallest key offered,
+// whatever the interleaving.  Slots already below the key are skipped: an
+// atomicMin there would return a smaller value and emit the key unchanged.
+__device__ __forceinline__ void list_insert(unsigned long long *slots, int cap,
+                                            unsigned long long key) {
+    for (int j = 0; j < cap && key != kEmptyKey; ++j) {
+        unsigned long long cur = *((volatile unsigned long long *)&slots[j]);
+        if (cur < key) continue;
+        unsigned long long old = atomicMin(&slots[j], key);
+        key = old > key ? old : key;
+    }
+}
+
+__device__ __forceinline__ float list_kth(const unsigned long long *slots, int k) {
+    return key_dist(*((volatile const unsigned long long *)&slots[k - 1]));
+}
+
+// Current pruning threshold: bsf*(1+delta)+alpha, bsf = the k-th best of the
+// seeds and of the survivors found so far (+inf while fewer than k exist).
+__device__ __forceinline__ float current_thr(const QueryState *st, const QueryArgs &a) {
+    float b = fminf(list_kth(st->seed_keys, a.k), list_kth(st->res_keys, a.k));
+    if (!(b < __int_as_float(0x7f800000))) return __int_as_float(0x7f800000);
+    return fmaf(b, 1.0f + a.delta, a.alpha);
+}
+
+// ---------------------------------------------------------------- timers
+__device__ __forceinline__ long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return (long long)t;
+}
+
+// ---------------------------------------------------------------- mbarrier / bulk copy
+__device__ __forceinline__ unsigned smem_u32(const void *p) {
+    return (unsigned)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t *bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
+                 : "memory");
+}
+__device__ __forceinline__ void mbar_fence_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, unsigned parity) {
+    unsigned ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Wait for phase `parity` of the barrier for at most limit_ns; false on timeout.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, unsigned parity, long long limit_ns) {
+    if (mbar_try_wait(bar, parity)) return true;
+    long long t0 = global_ns();
+    while (!mbar_try_wait(bar, parity)) {
+        if (global_ns() - t0 > limit_ns) return false;
+    }
+    return true;
+}
+// 1-D bulk copy global -> shared through the TMA unit; completes `bytes`
+// transaction bytes on the barrier.  dst, src 16-byte aligned, bytes % 16 == 0.
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, unsigned bytes, uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+
+// ---------------------------------------------------------------- warp helpers
+__device__ __forceinline__ unsigned lane_id() { return threadIdx.x & 31; }
+
+// Append `pass` lanes' values to a shared or global array through one atomic
+// per warp.  All lanes of `mask` must call it.
+__device__ __forceinline__ int warp_append(int *counter, bool pass, unsigned mask) {
+    unsigned bal = __ballot_sync(mask, pass);
+    if (bal == 0) return -1;
+    int leader = __ffs(bal) - 1;
+    int base = 0;
+    if ((int)lane_id() == leader) base = atomicAdd(counter, __popc(bal));
+    base = __shfl_sync(mask, base, leader);
+    unsigned lt = bal & ((1u << lane_id()) - 1u);
+    return pass ? base + __popc(lt) : -1;
+}
+
+}  // namespace dtws

@@ -1,0 +1,358 @@
+"""Thin ctypes binding of ``include/dtws.h`` (libdtws.so).
+
+Argument marshalling only: every step of the search runs in the library's
+CUDA kernels.  Functions keep the C names (``dtws_create``, ``dtws_query``,
+...) and take plain pointers; :class:`Index` is a convenience wrapper that
+accepts torch tensors (device or host) and NumPy arrays and uses torch only
+for device memory and the current CUDA stream.
+
+There is no CPU fallback: if the library is not built or cannot be loaded,
+every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+_lock = threading.Lock()
+_lib = None
+
+DTWS_OK = 0
+DTWS_EINVAL = 1
+DTWS_ENOMEM = 2
+DTWS_ECUDA = 3
+DTWS_ENONFINITE = 4
+DTWS_ETIMEOUT = 5
+DTWS_ENOTIMPL = 6
+DTWS_EOVERFLOW = 7
+DTWS_M_MAX = 8192
+DTWS_K_MAX = 64
+
+
+class DtwsError(RuntimeError):
+    def __init__(self, status: int, where: str, detail: str = ""):
+        self.status = status
+        msg = f"{where}: {strerror(status)} ({status})"
+        if detail:
+            msg += f": {detail}"
+        super().__init__(msg)
+
+
+class dtws_options(ctypes.Structure):
+    _fields_ = [
+        ("delta", ctypes.c_float),
+        ("alpha_per_m", ctypes.c_float),
+        ("seed_random", ctypes.c_int32),
+        ("seed_proposals", ctypes.c_int32),
+        ("proxy_terms", ctypes.c_int32),
+        ("ordering", ctypes.c_int32),
+        ("timing", ctypes.c_int32),
+        ("reserved0", ctypes.c_int32),
+        ("wait_limit_ns", ctypes.c_int64),
+        ("rng_seed", ctypes.c_uint64),
+    ]
+
+
+class dtws_query_stats(ctypes.Structure):
+    _fields_ = [
+        ("windows", ctypes.c_int64),
+        ("pass_kim", ctypes.c_int64),
+        ("pass_keogh_q", ctypes.c_int64),
+        ("pass_keogh_s", ctypes.c_int64),
+        ("dtw_started", ctypes.c_int64),
+        ("dtw_abandoned", ctypes.c_int64),
+        ("dtw_cells", ctypes.c_int64),
+        ("rescored", ctypes.c_int64),
+        ("seed_bsf", ctypes.c_float),
+        ("phase_ms", ctypes.c_float * 8),
+        ("kernel_launches", ctypes.c_int64),
+    ]
+
+    def as_dict(self) -> dict:
+        d = {f: getattr(self, f) for f, _ in self._fields_ if f != "phase_ms"}
+        d["phase_ms"] = list(self.phase_ms)
+        return d
+
+
+PHASES = ["qprep", "seeds", "lb_scan", "order", "dtw", "finalize", "window_stats", "envelope"]
+
+_P = ctypes.c_void_p
+_I32 = ctypes.c_int32
+_I64 = ctypes.c_int64
+_S = ctypes.c_int
+_SIGS = {
+    "dtws_default_options": (None, [_P]),
+    "dtws_create": (_S, [_P, _I64, _P, _P]),
+    "dtws_destroy": (_S, [_P]),
+    "dtws_set_options": (_S, [_P, _P]),
+    "dtws_get_options": (_S, [_P, _P]),
+    "dtws_query": (_S, [_P, _P, _I32, _I32, _I32, _P, _P, _P]),
+    "dtws_query_batch": (_S, [_P, _P, _P, _P, _P, _I32, _I32, _P, _P, _P]),
+    "dtws_sync_status": (_S, [_P, _P]),
+    "dtws_last_stats": (_S, [_P, _P]),
+    "dtws_clear_cache": (_S, [_P]),
+    "dtws_strerror": (ctypes.c_char_p, [_S]),
+    "dtws_last_error_detail": (ctypes.c_char_p, []),
+    "dtws_debug_fail_next_allocs": (None, [ctypes.c_int]),
+    "dtws_window_stats": (_S, [_P, _I32, _P, _P, _P, _P]),
+    "dtws_series_envelope": (_S, [_P, _I32, _P, _P, _P]),
+    "dtws_dtw_at": (_S, [_P, _P, _I32, _I32, _P, _I64, _P, _P]),
+    "dtws_dtw_at_f64": (_S, [_P, _P, _I32, _I32, _P, _I64, _P, _P]),
+    "dtws_lower_bounds_at": (_S, [_P, _P, _I32, _I32, _P, _I64, _P, _P, _P, _P]),
+}
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = False) -> ctypes.CDLL:
+    """Load libdtws.so (optionally building it first).  Raises if absent."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = _build.LIB
+        if build_if_missing:
+            path = _build.build()
+        if not os.path.exists(path):
+            raise RuntimeError(
+                f"libdtws.so not found at {path}: build it with "
+                "`python -c 'import __graft_entry__ as g; g.build()'` (needs nvcc)")
+        lib = ctypes.CDLL(path)
+        for name, (res, args) in _SIGS.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+        return lib
+
+
+def exported_symbols() -> list[str]:
+    return sorted(_SIGS)
+
+
+def strerror(status: int) -> str:
+    try:
+        return load().dtws_strerror(status).decode()
+    except RuntimeError:
+        return f"status {status}"
+
+
+def _check(status: int, where: str):
+    if status != DTWS_OK:
+        detail = load().dtws_last_error_detail().decode(errors="replace")
+        raise DtwsError(status, where, detail)
+
+
+# ------------------------------------------------------------------ C names
+def dtws_default_options() -> dtws_options:
+    o = dtws_options()
+    load().dtws_default_options(ctypes.byref(o))
+    return o
+
+
+def dtws_create(series_ptr: int, n: int, stream: int = 0) -> ctypes.c_void_p:
+    h = ctypes.c_void_p()
+    _check(load().dtws_create(series_ptr, n, stream, ctypes.byref(h)), "dtws_create")
+    return h
+
+
+def dtws_destroy(h) -> None:
+    _check(load().dtws_destroy(h), "dtws_destroy")
+
+
+def dtws_set_options(h, opt: dtws_options) -> None:
+    _check(load().dtws_set_options(h, ctypes.byref(opt)), "dtws_set_options")
+
+
+def dtws_get_options(h) -> dtws_options:
+    o = dtws_options()
+    _check(load().dtws_get_options(h, ctypes.byref(o)), "dtws_get_options")
+    return o
+
+
+def dtws_query(h, Q_ptr, m, r, k, idx_ptr, dist_ptr, stream=0) -> None:
+    _check(load().dtws_query(h, Q_ptr, m, r, k, idx_ptr, dist_ptr, stream), "dtws_query")
+
+
+def dtws_query_batch(h, Q_ptr, q_off_ptr, m_ptr, r_ptr, nq, k, idx_ptr, dist_ptr, stream=0) -> None:
+    _check(load().dtws_query_batch(h, Q_ptr, q_off_ptr, m_ptr, r_ptr, nq, k, idx_ptr, dist_ptr, stream),
+           "dtws_query_batch")
+
+
+def dtws_sync_status(h, stream=0) -> int:
+    return load().dtws_sync_status(h, stream)
+
+
+def dtws_last_stats(h) -> dtws_query_stats:
+    s = dtws_query_stats()
+    _check(load().dtws_last_stats(h, ctypes.byref(s)), "dtws_last_stats")
+    return s
+
+
+def dtws_clear_cache(h) -> None:
+    _check(load().dtws_clear_cache(h), "dtws_clear_cache")
+
+
+def dtws_debug_fail_next_allocs(count: int) -> None:
+    load().dtws_debug_fail_next_allocs(count)
+
+
+# ------------------------------------------------------------------ wrapper
+def _torch():
+    import torch  # torch is plumbing here: device memory and streams
+    return torch
+
+
+def _stream_ptr(stream) -> int:
+    if stream is None:
+        torch = _torch()
+        return int(torch.cuda.current_stream().cuda_stream) if torch.cuda.is_available() else 0
+    if isinstance(stream, int):
+        return stream
+    return int(stream.cuda_stream)
+
+
+class _Arg:
+    """Pointer to an array's data: a contiguous torch tensor (any device) or
+    a NumPy array kept alive for the call."""
+
+    def __init__(self, a, dtype):
+        torch = _torch()
+        if isinstance(a, torch.Tensor):
+            want = {np.float32: torch.float32, np.float64: torch.float64, np.int64: torch.int64,
+                    np.int32: torch.int32}[dtype]
+            if a.dtype != want:
+                a = a.to(want)
+            self.obj = a.contiguous()
+            self.ptr = self.obj.data_ptr()
+            self.size = self.obj.numel()
+        else:
+            self.obj = np.ascontiguousarray(a, dtype=dtype)
+            self.ptr = self.obj.ctypes.data
+            self.size = self.obj.size
+
+
+class Index:
+    """A search handle over one series (``dtws_create`` / ``dtws_destroy``)."""
+
+    def __init__(self, series, stream=None, options: dict | None = None):
+        self._lib = load()
+        a = _Arg(series, np.float32)
+        self.n = a.size
+        self.h = dtws_create(a.ptr, a.size, _stream_ptr(stream))
+        if options:
+            self.set_options(**options)
+
+    def close(self):
+        if getattr(self, "h", None):
+            dtws_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def set_options(self, **kw):
+        o = dtws_get_options(self.h)
+        for k, v in kw.items():
+            setattr(o, k, v)
+        dtws_set_options(self.h, o)
+
+    def options(self) -> dict:
+        o = dtws_get_options(self.h)
+        return {f: getattr(o, f) for f, _ in o._fields_}
+
+    # -------------------------------------------------------------- search
+    def query(self, Q, r: int, k: int = 1, out=None, stream=None):
+        """Top-k (offsets int64, squared DTW float32).  ``out`` = (idx, dist)
+        tensors to write into (device or host); default: host NumPy arrays."""
+        q = _Arg(Q, np.float32)
+        if out is None:
+            idx = np.empty(k, np.int64)
+            dist = np.empty(k, np.float32)
+            ip, dp = idx.ctypes.data, dist.ctypes.data
+        else:
+            idx, dist = out
+            ip, dp = idx.data_ptr(), dist.data_ptr()
+        dtws_query(self.h, q.ptr, q.size, r, k, ip, dp, _stream_ptr(stream))
+        return idx, dist
+
+    def query_batch(self, queries, rs, k: int = 1, stream=None):
+        """Many queries; returns ([nq, k] offsets, [nq, k] distances), host."""
+        ms = np.array([len(q) for q in queries], np.int32)
+        off = np.zeros(len(queries) + 1, np.int64)
+        off[1:] = np.cumsum(ms)
+        cat = np.concatenate([np.asarray(q, np.float32) for q in queries]) \
+            if not hasattr(queries, "data_ptr") else queries
+        rr = np.ascontiguousarray(rs, dtype=np.int32)
+        c = _Arg(cat, np.float32)
+        nq = len(queries)
+        idx = np.empty((nq, k), np.int64)
+        dist = np.empty((nq, k), np.float32)
+        dtws_query_batch(self.h, c.ptr, off.ctypes.data, ms.ctypes.data, rr.ctypes.data, nq, k,
+                         idx.ctypes.data, dist.ctypes.data, _stream_ptr(stream))
+        return idx, dist
+
+    def sync_status(self, stream=None) -> int:
+        return dtws_sync_status(self.h, _stream_ptr(stream))
+
+    def last_stats(self) -> dict:
+        return dtws_last_stats(self.h).as_dict()
+
+    def clear_cache(self):
+        dtws_clear_cache(self.h)
+
+    # -------------------------------------------------------------- building blocks
+    def window_stats(self, m: int, stream=None):
+        N = self.n - m + 1
+        mh, ml, inv = (np.empty(N, np.float32) for _ in range(3))
+        _check(self._lib.dtws_window_stats(self.h, m, mh.ctypes.data, ml.ctypes.data, inv.ctypes.data,
+                                           _stream_ptr(stream)), "dtws_window_stats")
+        return mh, ml, inv
+
+    def series_envelope(self, r: int, stream=None):
+        U = np.empty(self.n, np.float32)
+        L = np.empty(self.n, np.float32)
+        _check(self._lib.dtws_series_envelope(self.h, r, U.ctypes.data, L.ctypes.data, _stream_ptr(stream)),
+               "dtws_series_envelope")
+        return U, L
+
+    def dtw_at(self, Q, r: int, offsets, stream=None) -> np.ndarray:
+        q = _Arg(Q, np.float32)
+        o = _Arg(offsets, np.int64)
+        out = np.empty(o.size, np.float32)
+        _check(self._lib.dtws_dtw_at(self.h, q.ptr, q.size, r, o.ptr, o.size, out.ctypes.data,
+                                     _stream_ptr(stream)), "dtws_dtw_at")
+        return out
+
+    def dtw_at_f64(self, Q, r: int, offsets, stream=None) -> np.ndarray:
+        q = _Arg(Q, np.float32)
+        o = _Arg(offsets, np.int64)
+        out = np.empty(o.size, np.float64)
+        _check(self._lib.dtws_dtw_at_f64(self.h, q.ptr, q.size, r, o.ptr, o.size, out.ctypes.data,
+                                         _stream_ptr(stream)), "dtws_dtw_at_f64")
+        return out
+
+    def lower_bounds_at(self, Q, r: int, offsets, stream=None):
+        q = _Arg(Q, np.float32)
+        o = _Arg(offsets, np.int64)
+        kim, kq, ks = (np.empty(o.size, np.float32) for _ in range(3))
+        _check(self._lib.dtws_lower_bounds_at(self.h, q.ptr, q.size, r, o.ptr, o.size, kim.ctypes.data,
+                                              kq.ctypes.data, ks.ctypes.data, _stream_ptr(stream)),
+               "dtws_lower_bounds_at")
+        return kim, kq, ks

@@ -1,0 +1,189 @@
+"""End-to-end parity of dtws_query / dtws_query_batch with the FP64 oracle:
+identical top-k offsets, distances within 1e-4 relative (absolute 1e-6*m
+near zero), plus the degenerate cases of the method."""
+import numpy as np
+import pytest
+
+import oracle
+from oracle import fragments
+from paper_1812_10302_gb300 import dtws, synth
+
+pytestmark = pytest.mark.gpu
+
+
+def _close(got, want, m):
+    np.testing.assert_allclose(got, want, rtol=1e-4, atol=1e-6 * m)
+
+
+@pytest.fixture(scope="module")
+def walk():
+    return synth.random_walk(50_003, 17)
+
+
+@pytest.fixture(scope="module")
+def index(walk):
+    dtws.load(build_if_missing=True)
+    ix = dtws.Index(walk)
+    yield ix
+    ix.close()
+
+
+@pytest.mark.parametrize("m,w,k,noise", [
+    (16, 0.0, 1, 0.5), (32, 0.1, 10, 0.5), (64, 0.05, 1, 0.2), (128, 0.05, 1, 0.1),
+    (128, 0.2, 10, 1.0), (256, 0.1, 3, 0.3), (512, 0.1, 1, 0.1), (100, 1.0, 5, 0.5),
+    (1024, 0.1, 10, 0.2), (40, 0.5, 64, 2.0)])
+def test_query_matches_oracle(walk, index, m, w, k, noise):
+    q, _ = synth.noisy_copy(walk, m, 100 + m, 200 + k, noise=noise)
+    r = synth.band(w, m)
+    idx, dist = index.query(q, r, k)
+    assert index.sync_status() == dtws.DTWS_OK
+    oi, od = fragments.search_fragments(walk, q, r, k)
+    np.testing.assert_array_equal(idx, oi)
+    _close(dist, od, m)
+
+
+def test_random_query_not_a_copy(walk, index):
+    """A query unrelated to the series: loose seeds, many survivors."""
+    q = synth.random_walk(128, 999)
+    idx, dist = index.query(q, 12, 4)
+    oi, od = fragments.search_fragments(walk, q, 12, 4)
+    np.testing.assert_array_equal(idx, oi)
+    _close(dist, od, 128)
+
+
+def test_planted_exact_copy(walk, index):
+    o = 31_337
+    q = walk[o:o + 200].copy()
+    idx, dist = index.query(q, 20, 1)
+    assert idx[0] == o and dist[0] <= 1e-6 * 200
+
+
+def test_exact_ties_lowest_index():
+    pat = np.random.default_rng(5).standard_normal(97).astype(np.float32)
+    x = np.tile(pat, 80)                       # 7760 samples, period 97
+    q = x[50:50 + 150].copy()
+    with dtws.Index(x) as ix:
+        idx, dist = ix.query(q, 15, 5)
+    oi, od = oracle.search_cascade(x, q, 15, 5)
+    np.testing.assert_array_equal(idx, oi)
+    assert idx.tolist() == [50 + 97 * t for t in range(5)]
+    assert np.all(dist <= 1e-6 * 150)
+
+
+def test_constant_windows_and_query():
+    x = synth.random_walk(12_000, 6)
+    x[4000:4600] = 7.0
+    with dtws.Index(x) as ix:
+        # constant query: normalises to zeros; constant windows also to zeros
+        q = np.full(64, 3.0, np.float32)
+        idx, dist = ix.query(q, 6, 3)
+        oi, od = oracle.search_cascade(x, q, 6, 3)
+        np.testing.assert_array_equal(idx, oi)
+        _close(dist, od, 64)
+        assert idx[0] == 4000 and dist[0] == 0.0
+        q2, _ = synth.noisy_copy(x, 64, 3, 4)
+        idx, dist = ix.query(q2, 6, 2)
+        oi, od = oracle.search_cascade(x, q2, 6, 2)
+        np.testing.assert_array_equal(idx, oi)
+        _close(dist, od, 64)
+
+
+def test_k_equals_all_windows_and_m_equals_n():
+    x = synth.random_walk(300, 8)
+    q, _ = synth.noisy_copy(x, 250, 9, 10, noise=0.5)
+    with dtws.Index(x) as ix:
+        idx, dist = ix.query(q, 25, 51)           # N = 51: every window
+        oi, od = oracle.search_brute(x, q, 25, 51)
+        np.testing.assert_array_equal(idx, oi)
+        _close(dist, od, 250)
+        q3 = synth.random_walk(300, 11)
+        idx, dist = ix.query(q3, 30, 1)           # m = n: one window
+        assert idx[0] == 0
+        _close(dist, oracle.dtw_at(x, q3, 30, [0]), 300)
+
+
+def test_band_wider_than_query(walk, index):
+    q, _ = synth.noisy_copy(walk, 60, 12, 13, noise=0.5)
+    idx, dist = index.query(q, 500, 3)
+    oi, od = oracle.search_cascade(walk, q, 59, 3)
+    np.testing.assert_array_equal(idx, oi)
+    _close(dist, od, 60)
+
+
+def test_nonfinite_query_reported(index):
+    q = np.ones(64, np.float32)
+    q[10] = np.nan
+    idx, dist = index.query(q, 5, 2)
+    assert index.sync_status() == dtws.DTWS_ENONFINITE
+    assert np.all(idx == -1) and np.all(np.isinf(dist))
+    assert index.sync_status() == dtws.DTWS_OK     # cleared
+
+
+def test_nonfinite_series_rejected():
+    x = synth.random_walk(1000, 1)
+    x[500] = np.inf
+    with pytest.raises(dtws.DtwsError) as e:
+        dtws.Index(x)
+    assert e.value.status == dtws.DTWS_ENONFINITE
+
+
+def test_bad_arguments_rejected(index):
+    q = np.zeros(10, np.float32)
+    for m, r, k in ((1, 1, 1), (10, -1, 1), (10, 1, 0), (10, 1, 65)):
+        with pytest.raises(dtws.DtwsError) as e:
+            index.query(q[:m], r, k)
+        assert e.value.status == dtws.DTWS_EINVAL
+
+
+def test_allocation_failure_is_reported_and_recoverable():
+    x = synth.random_walk(5000, 2)
+    dtws.dtws_debug_fail_next_allocs(1)
+    with pytest.raises(dtws.DtwsError) as e:
+        dtws.Index(x)
+    assert e.value.status == dtws.DTWS_ENOMEM
+    with dtws.Index(x) as ix:           # the hook is spent: works again
+        q, _ = synth.noisy_copy(x, 50, 1, 2)
+        dtws.dtws_debug_fail_next_allocs(1)
+        with pytest.raises(dtws.DtwsError):
+            ix.query(q, 5, 1)            # workspace allocation fails
+        idx, dist = ix.query(q, 5, 1)    # and completes on the next call
+        oi, od = oracle.search_cascade(x, q, 5, 1)
+        np.testing.assert_array_equal(idx, oi)
+
+
+def test_batch_matches_single_queries(walk, index):
+    qs, rs, _ = synth.batch_queries(walk, 12, 77, m_range=(20, 700), w_range=(0.0, 0.3), noise=0.3)
+    bi, bd = index.query_batch(qs, rs, k=3)
+    for t, (q, r) in enumerate(zip(qs, rs)):
+        oi, od = fragments.search_fragments(walk, q, r, 3)
+        np.testing.assert_array_equal(bi[t], oi)
+        _close(bd[t], od, len(q))
+
+
+def test_device_outputs_and_repeatability(walk, index):
+    import torch
+    q, _ = synth.noisy_copy(walk, 300, 55, 56, noise=0.3)
+    qd = torch.from_numpy(q).cuda()
+    outs = []
+    for _ in range(5):
+        idx = torch.empty(10, dtype=torch.int64, device="cuda")
+        dist = torch.empty(10, dtype=torch.float32, device="cuda")
+        index.query(qd, 30, 10, out=(idx, dist))
+        outs.append((idx.cpu().numpy(), dist.cpu().numpy()))
+    for a in outs[1:]:
+        np.testing.assert_array_equal(a[0], outs[0][0])
+        np.testing.assert_array_equal(a[1], outs[0][1])
+    hi, hd = index.query(q, 30, 10)
+    np.testing.assert_array_equal(hi, outs[0][0])
+
+
+def test_stats_counters(walk, index):
+    q, _ = synth.noisy_copy(walk, 128, 60, 61, noise=0.1)
+    index.set_options(timing=1)
+    index.query(q, 6, 1)
+    s = index.last_stats()
+    index.set_options(timing=0)
+    assert s["windows"] == walk.size - 128 + 1
+    assert s["pass_kim"] >= s["pass_keogh_q"] >= s["pass_keogh_s"] >= 1
+    assert s["dtw_started"] >= 1 and s["rescored"] >= 1
+    assert all(v >= 0 for v in s["phase_ms"])

@@ -211,6 +211,35 @@ dtws_status dtws_lower_bounds_at(dtws_t h, const float *Q, int32_t m, int32_t r,
                                  const int64_t *offsets, int64_t count, float *kim,
                                  float *keogh_q, float *keogh_s, void *stream);
 
+/* ---- allocation-free variant (the paper has no counterpart) ---- */
+
+/* Longest query dtws_dtw_at_noalloc accepts: the size of its fixed scratch. */
+#define DTWS_NOALLOC_M_MAX 8192
+
+/*
+ * dtws_dtw_at without a handle and without any device allocation, for
+ * callers that cannot let a library call cudaMalloc (it synchronises the
+ * device and stalls other work, a host framework may own all device memory
+ * through its own pool, or the deployment fixes its memory at start-up).
+ * Inputs and outputs are the caller's DEVICE arrays: series FP32 [n],
+ * Q FP32 [m] (raw), offsets int64 [count] (each in [0, n-m]), out FP32
+ * [count]; nothing is staged.  Result: the FP32 banded DTW (Eq. 1 + band) of
+ * the z-normalised query against each z-normalised window, each window's
+ * statistics computed two-pass in FP64; an offset out of range, or a
+ * non-finite query, gives NaN.
+ * Working memory is one fixed device array inside the library (about 33 KB,
+ * held by every GPU that loads the library until the process exits).  Its
+ * device address is looked up on the first call made on each device, so
+ * that first call should come before any stream capture.  Calls share the
+ * array: each call resets what it uses, and calls whose work overlaps on the
+ * GPU race, so do not run two at once.
+ * Errors (synchronous): DTWS_EINVAL for null or host pointers, n or r out of
+ * range, or m beyond DTWS_NOALLOC_M_MAX (the scratch size); DTWS_ECUDA.
+ */
+dtws_status dtws_dtw_at_noalloc(const float *series, int64_t n, const float *Q, int32_t m,
+                                int32_t r, const int64_t *offsets, int64_t count, float *out,
+                                void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -54,6 +54,13 @@ constexpr int kCacheSlots = 8;
 
 }  // namespace
 
+void dtws::set_error_detail(const char *fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof g_err, fmt, ap);
+    va_end(ap);
+}
+
 struct dtws_ctx {
     int device = 0, num_sms = 0;
     int64_t n = 0, n_alloc = 0;

@@ -10,6 +10,9 @@
 
 namespace dtws {
 
+// Record the text returned by dtws_last_error_detail() (printf format).
+void set_error_detail(const char *fmt, ...);
+
 // ---- series level (series_kernels.cu)
 cudaError_t launch_check_finite(const float *x, int64_t n, int *flag, cudaStream_t s);
 cudaError_t launch_prefix(const float *x, int64_t n, double *P1, double *P2, double *T1,

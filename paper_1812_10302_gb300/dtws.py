@@ -32,6 +32,7 @@ DTWS_ENOTIMPL = 6
 DTWS_EOVERFLOW = 7
 DTWS_M_MAX = 8192
 DTWS_K_MAX = 64
+DTWS_NOALLOC_M_MAX = 8192
 
 
 class DtwsError(RuntimeError):
@@ -104,6 +105,7 @@ _SIGS = {
     "dtws_dtw_at": (_S, [_P, _P, _I32, _I32, _P, _I64, _P, _P]),
     "dtws_dtw_at_f64": (_S, [_P, _P, _I32, _I32, _P, _I64, _P, _P]),
     "dtws_lower_bounds_at": (_S, [_P, _P, _I32, _I32, _P, _I64, _P, _P, _P, _P]),
+    "dtws_dtw_at_noalloc": (_S, [_P, _I64, _P, _I32, _I32, _P, _I64, _P, _P]),
 }
 
 

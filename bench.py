@@ -44,6 +44,7 @@ from paper_1812_10302_gb300 import synth  # noqa: E402
 
 SPECS = {
     "rw100m": dict(n=100_000_000, m=512, w=0.10, k=1),
+    "rw30m": dict(n=30_000_000, m=512, w=0.10, k=1),
     "rw1m": dict(n=1_000_000, m=128, w=0.05, k=1),
 }
 
@@ -121,7 +122,7 @@ def make_workload(name: str, rank: int = 0, world: int = 1):
     r = synth.band(spec["w"], m)
 
     def frag(k):
-        if name == "rw100m":
+        if name in ("rw100m", "rw30m"):
             return synth.walk_with_bursts(n, 0 + 101 * k, 3 + 101 * k, 5 + 101 * k)
         return synth.random_walk(n, 101 * k)
 

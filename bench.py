@@ -248,6 +248,9 @@ def gpu_arm(args):
     if world > 1:
         torch.distributed.barrier()
     clocks = clk.stop()
+    status = ix.sync_status()
+    if status != dtws.DTWS_OK:
+        raise RuntimeError(f"device-side error during the timed steps: {dtws.strerror(status)}")
     ms = e0.elapsed_time(e1) / args.steps
     st = ix.last_stats()
     launches = int(st["kernel_launches"]) * args.steps

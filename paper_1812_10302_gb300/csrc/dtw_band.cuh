@@ -67,9 +67,17 @@ __device__ __forceinline__ float tail_term(const TailCtx &c, int i) {
     return d * d;
 }
 
+// Candidate sample j of the window, normalised: from the group's staged copy
+// in shared memory (cs != nullptr) or from the series with the window's
+// normalisation (x - na) * nb - nc.
+template <typename T>
+__device__ __forceinline__ T cand_value(const T *cs, const float *xw, T na, T nb, T nc, int j) {
+    return cs ? cs[j] : tfma((T)xw[j] - na, nb, -nc);
+}
+
 template <typename T, int L, bool ABANDON>
-__device__ T dtw_band(const T *__restrict__ qs, const float *__restrict__ xw, T na, T nb, T nc,
-                      const TailCtx *tail, T *ring, int m, int r, T thr, unsigned gmask, int lane,
+__device__ T dtw_band(const T *__restrict__ qs, const float *__restrict__ xw, const T *cs, T na, T nb,
+                      T nc, const TailCtx *tail, T *ring, int m, int r, T thr, unsigned gmask, int lane,
                       int &cells) {
     const T INF = tinf<T>();
     const int W = 2 * r + 1;
@@ -93,24 +101,34 @@ __device__ T dtw_band(const T *__restrict__ qs, const float *__restrict__ xw, T 
     T qi = i < m ? qs[i] : (T)0;
     T out = INF, upPrev = INF, rmin = INF, res = INF;
     bool stop = false;
-    for (int s = 0; s < total; ++s) {
-        T upIn = __shfl_up_sync(gmask, out, 1, L);
+    // operands of the current step, loaded one step ahead: lane 0's ring
+    // cells (written by lane L-1 at least two steps earlier, since L <= r)
+    // and the candidate sample of this lane's cell
+    T rk0 = INF, rk1 = INF, cj = (T)0;
+    bool valid = false;
+    {
         const bool act = (k >= 0) && (i < m);
-        const int kk = act ? k : 0;
+        const int kk = act ? k : 0, j = i - r + k;
+        if (lane == 0) { rk0 = ring[kk]; rk1 = ring[kk + 1]; }
+        valid = act && j >= 0 && j < m;
+        if (valid) cj = cand_value(cs, xw, na, nb, nc, j);
+    }
+    for (int s = 0; s < total; ++s) {
+        const T upIn = __shfl_up_sync(gmask, out, 1, L);
+        const bool act = (k >= 0) && (i < m);
         T up, diag;
         if (lane == 0) {
-            up = ring[kk + 1];
-            diag = ring[kk];
+            up = rk1;
+            diag = rk0;
         } else {
             up = (k + 1 < W) ? upIn : INF;
             diag = upPrev;
         }
         upPrev = upIn;
         const T left = (k > 0) ? out : INF;
-        const int j = i - r + k;
         T v = INF;
-        if (act && j >= 0 && j < m) {
-            T c = qi - tfma((T)xw[j] - na, nb, -nc);
+        if (valid) {
+            const T c = qi - cj;
             v = tfma(c, c, tmin(tmin(up, diag), left));
             ++cells;
         }
@@ -121,9 +139,9 @@ __device__ T dtw_band(const T *__restrict__ qs, const float *__restrict__ xw, T 
         if (ABANDON && tail) {
             if (++wcount == W) {  // all lanes together: prefix of the next block's rows
                 wcount = 0;
-                int row = ((s + 1) / W) * L + lane;
-                float e = row < m ? tail_term(*tail, row) : 0.0f;
-                float inc = group_incl_scan<L>(e, gmask, lane);
+                const int row = ((s + 1) / W) * L + lane;
+                const float e = row < m ? tail_term(*tail, row) : 0.0f;
+                const float inc = group_incl_scan<L>(e, gmask, lane);
                 pref_next = carry + inc;
                 carry += __shfl_sync(gmask, inc, L - 1, L);
             }
@@ -140,6 +158,13 @@ __device__ T dtw_band(const T *__restrict__ qs, const float *__restrict__ xw, T 
             qi = i < m ? qs[i] : (T)0;
             pref_cur = pref_next;
         }
+        {  // next step's operands
+            const bool nact = (k >= 0) && (i < m);
+            const int kk = nact ? k : 0, j = i - r + k;
+            if (lane == 0) { rk0 = ring[kk]; rk1 = ring[kk + 1]; }
+            valid = nact && j >= 0 && j < m;
+            if (valid) cj = cand_value(cs, xw, na, nb, nc, j);
+        }
         __syncwarp(gmask);
         if (ABANDON && (s & 15) == 15) {
             if (__any_sync(gmask, stop)) return INF;
@@ -147,6 +172,261 @@ __device__ T dtw_band(const T *__restrict__ qs, const float *__restrict__ xw, T 
     }
     return __shfl_sync(gmask, res, (m - 1) % L, L);
 }
+
+// ------------------------------------------------------------------ anti-diagonal DTW
+// The same recurrence (Eq. 1 on the band |i - j| <= r) evaluated along
+// anti-diagonals a = i + j.  On anti-diagonal a the band holds the cells
+// e = j - i in [-r, r] with e = a (mod 2); cell p (0-based) has
+// e = e_min(a) + 2p, e_min(a) = -r + ((a + r) & 1), i = (a - e)/2,
+// j = (a + e)/2.  Its neighbours are (i, j-1) and (i-1, j) on anti-diagonal
+// a-1 and (i-1, j-1) on a-2; in cell indices that is
+//   even (a + r):  left = prev1[p-1], up = prev1[p],   diag = prev2[p]
+//   odd  (a + r):  left = prev1[p],   up = prev1[p+1], diag = prev2[p].
+// A group of L lanes holds the r+1 cells of an anti-diagonal, K consecutive
+// cells per lane in registers; the one neighbour held by the adjacent lane
+// arrives by one shuffle per anti-diagonal.  2m - 1 steps, K independent
+// cells per lane per step.  The base d(-1,-1) = 0 sits on anti-diagonal -2.
+//
+// Early abandon (ABANDON): every warping path visits anti-diagonal a or a+1,
+// so min over the cells of two consecutive anti-diagonals of d(cell) plus a
+// lower bound of the rows after the cell's row bounds DTW from below.  The
+// rows' bound is cbs[i] = sum_{i' >= i} of the row's LB_Keogh term (q_hat_i'
+// against the window's envelope), in shared memory; tested every 16 steps.
+// cp: the group's normalised window (nullptr: read and normalise from xw).
+// Padding on each side of the query / window arrays the anti-diagonal kernel
+// reads: cell indices run r/2 + L*K past either end.  The query is padded
+// with +inf and the window with -inf, so every cell outside [0, m)^2 costs
+// +inf (never NaN) and needs no bounds test.
+__host__ __device__ inline int diag_pad(int r, int L, int K) { return (r >> 1) + L * K + 4; }
+
+template <typename T, int L, int K, bool ABANDON, int ODD>
+__device__ __forceinline__ void diag_step(const T *qp, const T *cp, T (&p1)[K], T (&p2)[K], int bi, int bj,
+                                          int lane, int r, unsigned gmask, int &cells) {
+    const T INF = tinf<T>();
+    // the one neighbour held by the adjacent lane: p-1 (even) / p+1 (odd)
+    T nb = __shfl_sync(gmask, ODD ? p1[0] : p1[K - 1], ODD ? ((lane + 1) & (L - 1)) : ((lane - 1) & (L - 1)), L);
+    if (ODD ? (lane == L - 1) : (lane == 0)) nb = INF;
+    T cur[K];
+#pragma unroll
+    for (int t = 0; t < K; ++t) {
+        const int p = lane * K + t;
+        const T left = ODD ? p1[t] : (t == 0 ? nb : p1[t > 0 ? t - 1 : 0]);
+        const T up = ODD ? (t == K - 1 ? nb : p1[t < K - 1 ? t + 1 : 0]) : p1[t];
+        const T d = qp[bi - p] - cp[bj + p];
+        T v = tfma(d, d, tmin(tmin(left, up), p2[t]));
+        if (ODD ? (p >= r) : (p > r)) v = INF;  // past the band's cells on this anti-diagonal
+        cells += v < INF;
+        cur[t] = v;
+    }
+#pragma unroll
+    for (int t = 0; t < K; ++t) {
+        p2[t] = p1[t];
+        p1[t] = cur[t];
+    }
+}
+
+// qp, cp: the query and the group's normalised window, each padded by
+// diag_pad(r, L, K) elements (+inf / -inf) on both sides, pointing at
+// element 0.  cbs: the rows' tail bound for ABANDON (or nullptr).
+template <typename T, int L, int K, bool ABANDON>
+__device__ T dtw_diag(const T *__restrict__ qp, const T *__restrict__ cp, const float *cbs, int m, int r, T thr,
+                      unsigned gmask, int lane, int &cells) {
+    const T INF = tinf<T>();
+    const int p0 = (r - (r & 1)) >> 1;
+    T p1[K], p2[K];
+#pragma unroll
+    for (int t = 0; t < K; ++t) {
+        p1[t] = INF;
+        p2[t] = (lane * K + t == p0) ? (T)0 : INF;
+    }
+    const int last = 2 * m - 2;
+    // anti-diagonal a has e_min = -r + ((a + r) & 1); its first cell is
+    // (bi, bj) = ((a - e_min)/2, (a + e_min)/2).  Along an (even, odd) pair
+    // bi stays and bj grows by one; from pair to pair both grow by one.
+    int a = 0, bi, bj;
+    if (r & 1) {  // a = 0 is odd: e_min = 1 - r
+        diag_step<T, L, K, ABANDON, 1>(qp, cp, p1, p2, (r - 1) >> 1, (1 - r) >> 1, lane, r, gmask, cells);
+        a = 1;
+    }
+    bi = (a + r) >> 1;
+    bj = (a - r) >> 1;
+    for (; a + 1 <= last; a += 2, ++bi, ++bj) {
+        diag_step<T, L, K, ABANDON, 0>(qp, cp, p1, p2, bi, bj, lane, r, gmask, cells);
+        diag_step<T, L, K, ABANDON, 1>(qp, cp, p1, p2, bi, bj + 1, lane, r, gmask, cells);
+        if (ABANDON && ((a >> 1) & 7) == 7) {
+            // p1: anti-diagonal a+1 (rows bi - p), p2: a (rows bi - p)
+            float low = __int_as_float(0x7f800000);
+#pragma unroll
+            for (int t = 0; t < K; ++t) {
+                const int i = bi - (lane * K + t);
+                const float tail = (cbs && i >= 0 && i < m) ? cbs[i + 1] : 0.0f;
+                low = fminf(low, fminf((float)p1[t], (float)p2[t]) + tail);
+            }
+#pragma unroll
+            for (int o = L / 2; o > 0; o >>= 1) low = fminf(low, __shfl_xor_sync(gmask, low, o, L));
+            if (low > (float)thr) return INF;
+        }
+    }
+    if (a == last) diag_step<T, L, K, ABANDON, 0>(qp, cp, p1, p2, bi, bj, lane, r, gmask, cells);
+    // d(m-1, m-1): e = 0 on the last anti-diagonal
+    const int pe = (r - ((last + r) & 1)) >> 1;
+    T res = INF;
+#pragma unroll
+    for (int t = 0; t < K; ++t)
+        if (lane * K + t == pe) res = p1[t];
+    return __shfl_sync(gmask, res, pe / K, L);
+}
+
+// ------------------------------------------------------------------ double-float DTW
+// Re-scoring in double-float arithmetic: a value is an unevaluated sum
+// hi + lo of two floats (about 48 significant bits), built from Dekker's and
+// Knuth's error-free transformations (TwoSum, FastTwoSum, FMA-based
+// products).  It runs on the FP32 pipes, which on this part issue far more
+// than its FP64 units; accumulated relative error over a DTW is ~1e-14.
+struct dfloat {
+    float hi, lo;
+};
+__device__ __forceinline__ dfloat df_from(double v) {
+    const float h = (float)v;
+    return dfloat{h, (float)(v - (double)h)};
+}
+__device__ __forceinline__ dfloat df_two_sum(float a, float b) {
+    const float s = a + b, bb = s - a;
+    return dfloat{s, (a - (s - bb)) + (b - bb)};
+}
+__device__ __forceinline__ dfloat df_fast_two_sum(float a, float b) {
+    const float s = a + b;
+    return dfloat{s, b - (s - a)};
+}
+// x + y for x, y >= 0 (all DTW partial sums are)
+__device__ __forceinline__ dfloat df_add_pos(dfloat x, dfloat y) {
+    const dfloat s = df_two_sum(x.hi, y.hi);
+    return df_fast_two_sum(s.hi, (s.lo + x.lo) + y.lo);
+}
+__device__ __forceinline__ dfloat df_sub(dfloat x, dfloat y) {
+    const dfloat s = df_two_sum(x.hi, -y.hi);
+    return df_fast_two_sum(s.hi, s.lo + (x.lo - y.lo));
+}
+__device__ __forceinline__ dfloat df_sqr(dfloat d) {
+    const float p = d.hi * d.hi;
+    float e = fmaf(d.hi, d.hi, -p);
+    e = fmaf(2.0f * d.hi, d.lo, e);
+    return df_fast_two_sum(p, e);
+}
+__device__ __forceinline__ dfloat df_min(dfloat x, dfloat y) {
+    return (y.hi < x.hi || (y.hi == x.hi && y.lo < x.lo)) ? y : x;
+}
+__device__ __forceinline__ dfloat df_shfl(unsigned mask, dfloat v, int src, int width) {
+    return dfloat{__shfl_sync(mask, v.hi, src, width), __shfl_sync(mask, v.lo, src, width)};
+}
+
+template <int L, int K, int ODD>
+__device__ __forceinline__ void diag_step_df(const dfloat *qs, const dfloat *cs, dfloat (&p1)[K], dfloat (&p2)[K],
+                                             int bi, int bj, int lane, int r, unsigned gmask) {
+    // a large finite stand-in for +inf: sums of such values stay finite
+    const dfloat INF = dfloat{1e30f, 0.0f};
+    dfloat nb = df_shfl(gmask, ODD ? p1[0] : p1[K - 1], ODD ? ((lane + 1) & (L - 1)) : ((lane - 1) & (L - 1)), L);
+    if (ODD ? (lane == L - 1) : (lane == 0)) nb = INF;
+    dfloat cur[K];
+#pragma unroll
+    for (int t = 0; t < K; ++t) {
+        const int p = lane * K + t;
+        const dfloat left = ODD ? p1[t] : (t == 0 ? nb : p1[t > 0 ? t - 1 : 0]);
+        const dfloat up = ODD ? (t == K - 1 ? nb : p1[t < K - 1 ? t + 1 : 0]) : p1[t];
+        // qs / cs are padded with finite poison values (+/-1e15): a cell
+        // outside [0, m)^2 costs ~4e30, far above any DTW and far below
+        // FP32 overflow over 2m steps, and never turns TwoSum into NaN
+        const dfloat best = df_min(df_min(left, up), p2[t]);
+        dfloat v = df_add_pos(df_sqr(df_sub(qs[bi - p], cs[bj + p])), best);
+        if (ODD ? (p >= r) : (p > r)) v = INF;  // past the band's cells
+        cur[t] = v;
+    }
+#pragma unroll
+    for (int t = 0; t < K; ++t) {
+        p2[t] = p1[t];
+        p1[t] = cur[t];
+    }
+}
+
+// Double-float counterpart of dtw_diag (no abandon).  qs, cs point at
+// element 0 of arrays padded by diag_pad(r, L, K) on both sides with
+// +1e15 (query) and -1e15 (window).
+template <int L, int K>
+__device__ double dtw_diag_df(const dfloat *__restrict__ qs, const dfloat *__restrict__ cs, int m, int r,
+                              unsigned gmask, int lane) {
+    const dfloat INF = dfloat{1e30f, 0.0f};
+    const int p0 = (r - (r & 1)) >> 1;
+    dfloat p1[K], p2[K];
+#pragma unroll
+    for (int t = 0; t < K; ++t) {
+        p1[t] = INF;
+        p2[t] = (lane * K + t == p0) ? dfloat{0.0f, 0.0f} : INF;
+    }
+    const int last = 2 * m - 2;
+    int a = 0, bi, bj;
+    if (r & 1) {
+        diag_step_df<L, K, 1>(qs, cs, p1, p2, (r - 1) >> 1, (1 - r) >> 1, lane, r, gmask);
+        a = 1;
+    }
+    bi = (a + r) >> 1;
+    bj = (a - r) >> 1;
+    for (; a + 1 <= last; a += 2, ++bi, ++bj) {
+        diag_step_df<L, K, 0>(qs, cs, p1, p2, bi, bj, lane, r, gmask);
+        diag_step_df<L, K, 1>(qs, cs, p1, p2, bi, bj + 1, lane, r, gmask);
+    }
+    if (a == last) diag_step_df<L, K, 0>(qs, cs, p1, p2, bi, bj, lane, r, gmask);
+    const int pe = (r - ((last + r) & 1)) >> 1;
+    dfloat res = INF;
+#pragma unroll
+    for (int t = 0; t < K; ++t)
+        if (lane * K + t == pe) res = p1[t];
+    res = df_shfl(gmask, res, pe / K, L);
+    return (double)res.hi + (double)res.lo;
+}
+
+// Suffix sums of the rows' LB_Keogh terms for the abandon test of dtw_diag:
+// cbs[i] = sum_{i' >= i} (q_hat_i' against the window's normalised envelope
+// interval at i')^2, cbs[m] = 0, shrunk by 1e-5 of the total so FP32
+// rounding of the sums can only weaken the bound.  Rows are taken L at a
+// time (coalesced loads), from the last chunk to the first, with a suffix
+// scan across the group per chunk.
+template <int L>
+__device__ void tail_suffix(const TailCtx &tc, float *cbs, int m, unsigned gmask, int lane) {
+    const int chunks = (m + L - 1) / L;
+    float carry = 0.0f;
+    for (int c = chunks - 1; c >= 0; --c) {
+        const int i = c * L + lane;
+        float v = i < m ? tail_term(tc, i) : 0.0f;
+#pragma unroll
+        for (int o = 1; o < L; o <<= 1) {
+            const float u = __shfl_down_sync(gmask, v, o, L);
+            if (lane + o < L) v += u;
+        }
+        if (i < m) cbs[i] = carry + v;
+        carry += __shfl_sync(gmask, v, 0, L);
+    }
+    const float slack = 1e-5f * carry;
+    for (int i = lane; i < m; i += L) cbs[i] = fmaxf(0.0f, cbs[i] - slack);
+    if (lane == 0) cbs[m] = 0.0f;
+    __syncwarp(gmask);
+}
+
+// Cells per lane for the anti-diagonal kernel: r+1 cells over L lanes.
+__host__ __device__ inline void diag_shape(int r, int *L, int *K) {
+    const int need = r + 1;
+    if (need <= 32) {
+        int l = 1;
+        while (l < need) l *= 2;
+        *L = l;
+        *K = 1;
+        return;
+    }
+    *L = 32;
+    int k = 1;
+    while (32 * k < need) k *= 2;
+    *K = k;  // 0 < K <= 16 for r <= 511
+}
+constexpr int kDiagRMax = 511;
 
 // Lanes per group for band half-width r: the largest power of two <= r
 // (<= 32), 1 for r = 0.

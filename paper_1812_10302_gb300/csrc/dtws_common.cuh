@@ -20,7 +20,8 @@ constexpr int kKMax = 64;
 constexpr int kListMax = 128;       // result list capacity (k + near-tie margin)
 constexpr int kSeedMax = 128;       // random seeds + proxy proposals
 constexpr int kPropMax = 64;
-constexpr int kTile = 2048;         // windows per lower-bound tile
+constexpr int kTile = 1024;         // windows per lower-bound tile
+constexpr int kStages = 4;          // shared-memory stages of the scan pipeline
 constexpr int kBins = 1024;         // survivor ordering bins
 constexpr uint64_t kEmptyKey = ~0ull;
 
@@ -51,6 +52,7 @@ struct QueryState {
     double margin_d64[kListMax];
     unsigned long long ctr[kCtrN];
     float thr_scan;                        // threshold the LB scan used
+    unsigned long long tile_ctr[2];        // dynamic tile cursors: proxy scan, LB scan
     int valid;                             // 0 when the query is non-finite
     int hist[kBins];
     int bin_off[kBins];
@@ -138,6 +140,9 @@ __device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, unsigned by
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
                  "r"(bytes)
                  : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, unsigned parity) {
     unsigned ok;

@@ -127,7 +127,7 @@ __global__ void __launch_bounds__(256) k_noalloc_dtw(const float *__restrict__ x
         const double inv = zero ? 0.0 : 1.0 / sqrt(var);
         const float mh = (float)mu, is = (float)inv, ls = (float)(mu - (double)mh) * is;
         int cells = 0;
-        const float d = dtw_band<float, L, false>(qs, xw, mh, is, ls, nullptr, ring, m, r,
+        const float d = dtw_band<float, L, false>(qs, xw, (const float *)nullptr, mh, is, ls, nullptr, ring, m, r,
                                                   __int_as_float(0x7f800000), gmask, lane, cells);
         if (lane == 0) out[c] = d;
         __syncwarp(gmask);

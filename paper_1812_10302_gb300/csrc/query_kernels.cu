@@ -43,6 +43,8 @@ __global__ void k_query_reset(QueryState *st) {
         st->n_margin = 0;
         st->thr_scan = DINF;
         st->valid = 1;
+        st->tile_ctr[0] = 0;
+        st->tile_ctr[1] = 0;
     }
 }
 
@@ -51,26 +53,11 @@ cudaError_t launch_query_reset(const QueryBufs &b, const QueryArgs &, cudaStream
     return cudaGetLastError();
 }
 
-// ------------------------------------------------------------------ block reductions
-template <typename T>
-__device__ T block_sum(T v, T *red) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    const int w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    __syncthreads();
-    if (lane_id() == 0) red[w] = v;
-    __syncthreads();
-    T s = 0;
-    for (int i = 0; i < nw; ++i) s += red[i];
-    return s;
-}
-
 // ------------------------------------------------------------------ query prep
 // One CTA of 1024 threads.  Dynamic smem: q_hat FP32 [m] + sort keys u64 [P],
 // P = next power of two >= m.
 __global__ void __launch_bounds__(1024) k_qprep(const float *__restrict__ Q, QueryBufs b, QueryArgs a) {
     extern __shared__ __align__(16) unsigned char smraw[];
-    __shared__ double red[32];
     __shared__ int bad;
     const int m = a.m, r = a.r;
     int P = 1;
@@ -91,23 +78,38 @@ __global__ void __launch_bounds__(1024) k_qprep(const float *__restrict__ Q, Que
         }
         return;
     }
-    // Eq. 5, two-pass in FP64: mu, then sum (x - mu)^2 / m (population)
-    double s = 0.0;
-    for (int j = threadIdx.x; j < m; j += blockDim.x) s += (double)Q[j];
-    const double mu = block_sum(s, red) / (double)m;
-    double v = 0.0;
-    for (int j = threadIdx.x; j < m; j += blockDim.x) {
-        double d = (double)Q[j] - mu;
-        v = fma(d, d, v);
-    }
-    const double var = block_sum(v, red) / (double)m;
-    const double mm = mu * mu;
-    const bool zero = var <= 1e-24 * (mm > 1.0 ? mm : 1.0);
-    const double sg = zero ? 0.0 : sqrt(var);
-    for (int j = threadIdx.x; j < m; j += blockDim.x) {
-        double qh = zero ? 0.0 : ((double)Q[j] - mu) / sg;
-        b.qh64[j] = qh;
-        qs[j] = (float)qh;
+    // Eq. 5, two-pass in FP64: mu, then sum (x - mu)^2 / m (population).
+    // One warp does the FP64 work: this part's FP64 units retire about one
+    // lane operation per cycle per SM, so FP64 shuffle reductions in every
+    // warp of the block would cost far more than the sums themselves.
+    __shared__ double mu_s, isg_s;
+    if (threadIdx.x < 32) {
+        double s = 0.0;
+        for (int j = threadIdx.x; j < m; j += 32) s += (double)Q[j];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (threadIdx.x == 0) mu_s = s / (double)m;  // one division
+        __syncwarp();
+        const double mu = mu_s;
+        double v = 0.0;
+        for (int j = threadIdx.x; j < m; j += 32) {
+            const double d = (double)Q[j] - mu;
+            v = fma(d, d, v);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (threadIdx.x == 0) {
+            const double var = v / (double)m, mm = mu * mu;
+            // one square root and reciprocal
+            isg_s = var <= 1e-24 * (mm > 1.0 ? mm : 1.0) ? 0.0 : 1.0 / sqrt(var);
+        }
+        __syncwarp();
+        const double isg = isg_s;
+        for (int j = threadIdx.x; j < m; j += 32) {
+            const double qh = ((double)Q[j] - mu) * isg;
+            b.qh64[j] = qh;
+            qs[j] = (float)qh;
+        }
     }
     __syncthreads();
     // envelope of q_hat, half-width r, clipped (Eq. 9)
@@ -164,95 +166,173 @@ cudaError_t launch_qprep(const float *Q, const QueryBufs &b, const QueryArgs &a,
     return cudaGetLastError();
 }
 
-// ------------------------------------------------------------------ tile staging
+// ------------------------------------------------------------------ tile pipeline
 // A tile is kTile consecutive windows [i0, i0 + kTile).  Its samples
 // x[i0, i0 + kTile + m - 1) and its window statistics are staged in shared
-// memory by 1-D bulk copies (the TMA engine) on one mbarrier.  The padded
-// series and the statistics arrays are allocated so that every full tile is
-// in bounds (the library rounds both up to whole tiles plus kMMax).
+// memory by 1-D bulk copies (the TMA engine) completing on an mbarrier.  The
+// padded series and the statistics arrays are allocated so that every full
+// tile is in bounds (the library rounds both up to whole tiles plus kMMax).
+//
+// Scan kernels are persistent and warp-specialised.  The last warp is the
+// producer: it takes the next tile from a device-wide cursor (so CTAs that
+// meet expensive windows simply take fewer tiles), writes its index into a
+// free shared-memory stage and issues the stage's copies; a stage is free
+// once its "empty" barrier shows that every consumer warp has released it.
+// The other warps are consumers: each waits for the stage's "full" barrier
+// (the copies landed), processes its own share of the tile and releases the
+// stage with one arrive.  There is no CTA-wide barrier in the loop, so a warp
+// held up by a rare expensive window delays only the refill of one stage.
+// Use u of a stage waits for phase u & 1 of its barriers.  The end is a stage
+// whose tile index is -1, completed without copies.
 struct Tile {
     float *xs, *mh, *ml, *is;
-    uint64_t *bar;
+    uint64_t *full, *empty;
+    long long *tile;
 };
 
-__device__ __forceinline__ unsigned tile_x_floats(int m) { return (unsigned)((kTile + m - 1 + 3) & ~3); }
+constexpr int kStageHeader = 32;  // full, empty barriers and the tile index
 
-__device__ __forceinline__ Tile carve_tile(unsigned char *sm, int m) {
+__host__ __device__ __forceinline__ unsigned tile_x_floats(int m) {
+    return (unsigned)((kTile + m - 1 + 3) & ~3);
+}
+__host__ __device__ __forceinline__ size_t stage_bytes(int m) {
+    return kStageHeader + (size_t)3 * kTile * 4 + (size_t)tile_x_floats(m) * 4;
+}
+
+__device__ __forceinline__ Tile carve_stage(unsigned char *sm, int m, int stage) {
     Tile t;
-    t.bar = (uint64_t *)sm;
-    t.mh = (float *)(sm + 16);
+    unsigned char *base = sm + stage * stage_bytes(m);
+    t.full = (uint64_t *)base;
+    t.empty = (uint64_t *)(base + 8);
+    t.tile = (long long *)(base + 16);
+    t.mh = (float *)(base + kStageHeader);
     t.ml = t.mh + kTile;
     t.is = t.ml + kTile;
     t.xs = t.is + kTile;
     return t;
 }
 
-// Returns false (and records a timeout) if the copies did not land in time.
-__device__ bool stage_tile(const Tile &t, const QueryBufs &b, int64_t i0, int m) {
+__device__ __forceinline__ void issue_tile(const Tile &t, const QueryBufs &b, int64_t i0, int m) {
     const unsigned xb = tile_x_floats(m) * 4u;
+    mbar_arrive_expect_tx(t.full, xb + 3u * kTile * 4u);
+    bulk_g2s(t.xs, b.x + i0, xb, t.full);
+    bulk_g2s(t.mh, b.mu_hi + i0, kTile * 4u, t.full);
+    bulk_g2s(t.ml, b.mu_lo + i0, kTile * 4u, t.full);
+    bulk_g2s(t.is, b.inv_sigma + i0, kTile * 4u, t.full);
+}
+
+constexpr int kScanConsumers = 8;                       // consumer warps
+constexpr int kScanThreads = (kScanConsumers + 1) * 32;  // + one producer warp
+
+// Runs process(tile, i0) in every consumer warp for each tile this CTA takes
+// from *cursor.  A wait that runs past the bound records DTWS_ETIMEOUT and
+// ends the loop for that warp (the other warps' waits then run out too).
+template <typename F>
+__device__ void tile_pipeline(unsigned char *sm, const QueryBufs &b, int m, int64_t ntiles,
+                              unsigned long long *cursor, F &&process) {
+    const int warp = threadIdx.x >> 5, lane = lane_id();
     if (threadIdx.x == 0) {
-        mbar_init(t.bar, 1);
+        for (int q = 0; q < kStages; ++q) {
+            const Tile t = carve_stage(sm, m, q);
+            mbar_init(t.full, 1);
+            mbar_init(t.empty, kScanConsumers);
+        }
         mbar_fence_init();
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
-        mbar_arrive_expect_tx(t.bar, xb + 3u * kTile * 4u);
-        bulk_g2s(t.xs, b.x + i0, xb, t.bar);
-        bulk_g2s(t.mh, b.mu_hi + i0, kTile * 4u, t.bar);
-        bulk_g2s(t.ml, b.mu_lo + i0, kTile * 4u, t.bar);
-        bulk_g2s(t.is, b.inv_sigma + i0, kTile * 4u, t.bar);
+    bool ok = true;
+    if (warp == kScanConsumers) {
+        if (lane == 0) {
+            int64_t u = 0;
+            for (;; ++u) {
+                const Tile t = carve_stage(sm, m, (int)(u % kStages));
+                if (u >= kStages &&
+                    !mbar_wait_bounded(t.empty, (unsigned)(((u / kStages) - 1) & 1), b.wait_ns)) {
+                    ok = false;
+                    break;
+                }
+                const long long tile = (long long)atomicAdd(cursor, 1ull);
+                if (tile >= ntiles) {
+                    *t.tile = -1;
+                    mbar_arrive(t.full);  // completes the phase with no copies
+                    break;
+                }
+                *t.tile = tile;
+                issue_tile(t, b, tile * kTile, m);
+            }
+            // On the normal path every issued copy is observed landing by the
+            // consumers before they reach the end marker.  After a timeout,
+            // let the copies that may still be in flight (uses u-S+1 .. u-1;
+            // use u-S was confirmed released) land before the CTA leaves.
+            if (!ok)
+                for (int64_t v = u - kStages + 1 > 0 ? u - kStages + 1 : 0; v < u; ++v)
+                    mbar_wait_bounded(carve_stage(sm, m, (int)(v % kStages)).full,
+                                      (unsigned)((v / kStages) & 1), b.wait_ns);
+        }
+    } else {
+        for (int64_t j = 0;; ++j) {
+            const Tile t = carve_stage(sm, m, (int)(j % kStages));
+            if (!mbar_wait_bounded(t.full, (unsigned)((j / kStages) & 1), b.wait_ns)) {
+                ok = false;
+                break;
+            }
+            const long long tile = *(volatile long long *)t.tile;
+            if (tile < 0) break;
+            process(t, (int64_t)tile * kTile);
+            __syncwarp();
+            if (lane == 0) mbar_arrive(t.empty);
+        }
     }
-    bool ok = mbar_wait_bounded(t.bar, 0, b.wait_ns);
-    if (!ok) {
-        atomicOr(b.status, kStTimeout);
-        // give the copies in flight one more bounded chance before leaving
-        mbar_wait_bounded(t.bar, 0, b.wait_ns);
-    }
-    return __syncthreads_and(ok) != 0;
+    if (!ok) atomicOr(b.status, kStTimeout);
 }
 
-__host__ __device__ inline size_t tile_smem_bytes(int m) {
-    return 16 + (size_t)3 * kTile * 4 + (size_t)(((kTile + m - 1 + 3) & ~3)) * 4;
+static int scan_grid(const void *kernel, int threads, size_t smem, int num_sms, int64_t ntiles) {
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem) != cudaSuccess ||
+        per_sm < 1)
+        per_sm = 1;
+    int64_t g = (int64_t)num_sms * per_sm;
+    return (int)(g < ntiles ? g : ntiles);
 }
 
 // ------------------------------------------------------------------ proxy scan
-// Per window: the squared distance on the `terms` query positions of largest
+// Per window: the squared distance on the TERMS query positions of largest
 // |q_hat| (not a lower bound: it only proposes windows whose exact DTW seeds
-// the best-so-far).  Each tile proposes its best window.
-__global__ void __launch_bounds__(256) k_seed_scan(QueryBufs b, QueryArgs a, int proposals, int terms) {
+// the best-so-far).  Each thread keeps its best window over all the tiles it
+// scans; each CTA proposes its best.
+template <int TERMS>
+__global__ void __launch_bounds__(kScanThreads) k_seed_scan(QueryBufs b, QueryArgs a, int proposals) {
     extern __shared__ __align__(16) unsigned char smraw[];
-    __shared__ unsigned long long wbest[8];
+    __shared__ unsigned long long wbest[kScanConsumers + 1];
     if (!b.st->valid) return;
     const int m = a.m;
-    Tile t = carve_tile(smraw, m);
-    const int64_t i0 = (int64_t)blockIdx.x * kTile;
-    if (!stage_tile(t, b, i0, m)) return;
-    int pos[16];
-    float qv[16];
+    int pos[TERMS];
+    float qv[TERMS];
 #pragma unroll
-    for (int u = 0; u < 16; ++u) {
-        pos[u] = u < terms ? (int)b.ord[u] : 0;
-        qv[u] = u < terms ? b.sq[u] : 0.0f;
+    for (int u = 0; u < TERMS; ++u) {
+        pos[u] = (int)b.ord[u];
+        qv[u] = b.sq[u];
     }
     unsigned long long best = kEmptyKey;
-    for (int w = threadIdx.x; w < kTile; w += blockDim.x) {
-        int64_t i = i0 + w;
-        if (i >= a.N) break;
-        float mh = t.mh[w], is = t.is[w], ls = t.ml[w] * is;
-        float acc = 0.0f;
+    const int64_t ntiles = (a.N + kTile - 1) / kTile;
+    tile_pipeline(smraw, b, m, ntiles, &b.st->tile_ctr[0], [&](const Tile &t, int64_t i0) {
+        for (int w = threadIdx.x; w < kTile; w += kScanConsumers * 32) {
+            const int64_t i = i0 + w;
+            if (i >= a.N) break;
+            const float mh = t.mh[w], is = t.is[w], ls = t.ml[w] * is;
+            float acc = 0.0f;
 #pragma unroll
-        for (int u = 0; u < 16; ++u) {
-            if (u < terms) {
-                float c = qv[u] - fmaf(t.xs[w + pos[u]] - mh, is, -ls);
+            for (int u = 0; u < TERMS; ++u) {
+                const float c = qv[u] - fmaf(t.xs[w + pos[u]] - mh, is, -ls);
                 acc = fmaf(c, c, acc);
             }
+            const unsigned long long key = make_key(acc, (unsigned)i);
+            best = key < best ? key : best;
         }
-        unsigned long long key = make_key(acc, (unsigned)i);
-        best = key < best ? key : best;
-    }
+    });
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
-        unsigned long long v = __shfl_xor_sync(0xffffffffu, best, o);
+        const unsigned long long v = __shfl_xor_sync(0xffffffffu, best, o);
         best = v < best ? v : best;
     }
     if (lane_id() == 0) wbest[threadIdx.x >> 5] = best;
@@ -260,23 +340,31 @@ __global__ void __launch_bounds__(256) k_seed_scan(QueryBufs b, QueryArgs a, int
     if (threadIdx.x == 0) {
         for (int w = 1; w < (int)(blockDim.x >> 5); ++w) best = wbest[w] < best ? wbest[w] : best;
         if (best != kEmptyKey) {
-            unsigned long long last = *((volatile unsigned long long *)&b.st->prop_keys[proposals - 1]);
+            const unsigned long long last = *((volatile unsigned long long *)&b.st->prop_keys[proposals - 1]);
             if (best < last) list_insert(b.st->prop_keys, proposals, best);
         }
     }
 }
 
+template <int TERMS>
+static cudaError_t launch_seed_scan_t(const QueryBufs &b, const QueryArgs &a, int proposals, cudaStream_t s) {
+    const size_t smem = kStages * stage_bytes(a.m);
+    cudaError_t e = cudaFuncSetAttribute(k_seed_scan<TERMS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const int64_t tiles = (a.N + kTile - 1) / kTile;
+    const int grid = scan_grid((const void *)k_seed_scan<TERMS>, kScanThreads, smem, b.num_sms, tiles);
+    k_seed_scan<TERMS><<<grid, kScanThreads, smem, s>>>(b, a, proposals);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_seed_scan(const QueryBufs &b, const QueryArgs &a, int proposals, int terms,
                              cudaStream_t s) {
     if (proposals <= 0) return cudaSuccess;
-    size_t smem = tile_smem_bytes(a.m);
-    cudaError_t e = cudaFuncSetAttribute(k_seed_scan, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    int64_t tiles = (a.N + kTile - 1) / kTile;
-    int t = terms > 16 ? 16 : terms;
-    t = t > a.m ? a.m : t;  // positions are taken from the query's order
-    k_seed_scan<<<(unsigned)tiles, 256, smem, s>>>(b, a, proposals, t);
-    return cudaGetLastError();
+    // positions are taken from the query's order, so never more than m
+    if (terms >= 16 && a.m >= 16) return launch_seed_scan_t<16>(b, a, proposals, s);
+    if (terms >= 8 && a.m >= 8) return launch_seed_scan_t<8>(b, a, proposals, s);
+    if (terms >= 4 && a.m >= 4) return launch_seed_scan_t<4>(b, a, proposals, s);
+    return launch_seed_scan_t<2>(b, a, proposals, s);
 }
 
 // splitmix64 (Steele, Lea & Flood, 2014) as the counter-based generator of
@@ -290,23 +378,41 @@ __device__ __forceinline__ unsigned long long splitmix64(unsigned long long z) {
 
 __global__ void k_seed_gather(QueryBufs b, QueryArgs a, int n_random, int proposals,
                               unsigned long long rng) {
-    if (threadIdx.x != 0 || !b.st->valid) return;
     // distinct offsets only: a repeated seed would fill two of the k seed
     // slots with one window and understate the k-th seed distance
-    int n = 0;
-    auto add = [&](unsigned o) {
-        for (int t = 0; t < n; ++t)
-            if (b.st->seed_off[t] == o) return;
-        if (n < kSeedMax) b.st->seed_off[n++] = o;
-    };
-    for (int j = 0; j < n_random; ++j)
-        add((unsigned)(splitmix64(rng + (unsigned long long)j) % (unsigned long long)a.N));
-    for (int p = 0; p < proposals; ++p) {
-        unsigned long long key = b.st->prop_keys[p];
-        if (key != kEmptyKey) add(key_idx(key));
+    __shared__ unsigned cand[2 * kPropMax];
+    __shared__ int nc;
+    if (!b.st->valid) return;
+    const int lane = threadIdx.x;  // one warp
+    if (lane == 0) nc = 0;
+    __syncwarp();
+    for (int j = lane; j < n_random; j += 32)
+        cand[j] = (unsigned)(splitmix64(rng + (unsigned long long)j) % (unsigned long long)a.N);
+    for (int p = lane; p < proposals; p += 32) {
+        const unsigned long long key = b.st->prop_keys[p];
+        cand[n_random + p] = key != kEmptyKey ? key_idx(key) : 0xffffffffu;
     }
-    b.st->n_seeds = n;
-    b.st->work = 0;
+    __syncwarp();
+    const int total = n_random + proposals;
+    // keep candidate t if it is valid and no earlier candidate equals it
+    for (int base = 0; base < total; base += 32) {
+        const int t = base + lane;
+        bool keep = false;
+        if (t < total && cand[t] != 0xffffffffu) {
+            keep = true;
+            for (int u = 0; u < t; ++u) keep &= cand[u] != cand[t];
+        }
+        const unsigned bal = __ballot_sync(0xffffffffu, keep);
+        const int pos = nc + __popc(bal & ((1u << lane) - 1u));
+        if (keep && pos < kSeedMax) b.st->seed_off[pos] = cand[t];
+        __syncwarp();
+        if (lane == 0) nc += __popc(bal);
+        __syncwarp();
+    }
+    if (lane == 0) {
+        b.st->n_seeds = nc < kSeedMax ? nc : kSeedMax;
+        b.st->work = 0;
+    }
 }
 
 cudaError_t launch_seed_gather(const QueryBufs &b, const QueryArgs &a, int n_random, int proposals,
@@ -318,28 +424,85 @@ cudaError_t launch_seed_gather(const QueryBufs &b, const QueryArgs &a, int n_ran
 // ------------------------------------------------------------------ DTW kernels
 enum DtwMode { kModeSeed = 0, kModeSurv = 1, kModeOut = 2 };
 
-// FP32 DTW over a candidate list.  Groups of L lanes pull candidates from a
-// device cursor.  Shared memory: q_hat [m] + one ring of W+1 per group.
-template <int L, int MODE>
+// Shared memory of a DTW CTA: the query [pad + m + pad] then, per group,
+// its staged normalised window [pad + m + pad] (when staged), the rows' tail
+// bound [m4 + 4] (FP32; anti-diagonal kernel with abandon) and the ring
+// [W + 1] (row-systolic kernel, K == 0).  pad = diag_pad(r, L, K) for the
+// anti-diagonal kernel, 0 for the row-systolic one.
+template <typename T>
+struct DtwSmem {
+    int m, m4, W, pad;
+    bool staged, tail, ring;
+    __host__ __device__ size_t span() const { return (size_t)((m + 2 * pad + 3) & ~3); }
+    __host__ __device__ size_t group_bytes() const {
+        return (staged ? span() * sizeof(T) : 0) + (tail ? (size_t)(m4 + 4) * 4 : 0) +
+               (ring ? (size_t)(W + 1) * sizeof(T) : 0);
+    }
+    __host__ __device__ size_t q_bytes() const { return span() * sizeof(T); }
+};
+
+template <typename T, int L, int K>
+__host__ __device__ inline DtwSmem<T> dtw_smem(int m, int r, bool staged, bool tail) {
+    DtwSmem<T> d;
+    d.m = m;
+    d.m4 = (m + 3) & ~3;
+    d.W = 2 * r + 1;
+    d.pad = K > 0 ? diag_pad(r, L, K) : 0;
+    d.staged = staged;
+    d.tail = staged && tail && K > 0;
+    d.ring = K == 0;
+    return d;
+}
+
+// Fill [base, base + pad) and [base + pad + m, base + 2 pad + m) with v.
+template <typename T>
+__device__ __forceinline__ void fill_pads(T *base, int m, int pad, T v, int tid, int nthreads) {
+    for (int t = tid; t < 2 * pad; t += nthreads) base[t < pad ? t : m + t] = v;
+}
+
+// FP32 DTW over a candidate list (MODE: seeds, survivors, or given offsets).
+// Groups of L lanes pull candidates from a device cursor.  K > 0: the
+// anti-diagonal kernel with K cells per lane (window staged in shared
+// memory); K == 0: the row-systolic kernel (staged when it fits).
+template <int L, int K, int MODE>
 __global__ void __launch_bounds__(256) k_dtw(QueryBufs b, QueryArgs a, const int64_t *offsets,
-                                             int64_t count_host, float *out) {
+                                             int64_t count_host, float *out, int staged) {
     extern __shared__ __align__(16) unsigned char smraw[];
     QueryState *st = b.st;
     if (!st->valid) return;
-    const int m = a.m, r = a.r, W = 2 * r + 1;
-    float *qs = (float *)smraw;
+    const int m = a.m, r = a.r;
+    const DtwSmem<float> lay = dtw_smem<float, L, K>(m, r, staged != 0, MODE == kModeSurv && b.U != nullptr);
+    const float INF = DINF;
+    float *qbase = (float *)smraw, *qs = qbase + lay.pad;
     for (int t = threadIdx.x; t < m; t += blockDim.x) qs[t] = b.qh32[t];
-    __syncthreads();
+    fill_pads(qbase, m, lay.pad, INF, threadIdx.x, blockDim.x);
     const int warp = threadIdx.x >> 5, ln = lane_id();
     const int g = ln / L, lane = ln % L;
     const int gid = warp * (32 / L) + g;
     const unsigned gmask = (L == 32) ? 0xffffffffu : (((1u << L) - 1u) << (g * L));
-    float *ring = qs + ((m + 3) & ~3) + gid * (W + 1);
+    unsigned char *gbase = smraw + lay.q_bytes() + (size_t)gid * lay.group_bytes();
+    float *cbuf = nullptr;
+    if (lay.staged) {
+        fill_pads((float *)gbase, m, lay.pad, -INF, lane, L);
+        cbuf = (float *)gbase + lay.pad;
+    }
+    float *cbs = lay.tail ? (float *)(gbase + (lay.staged ? lay.span() * 4 : 0)) : nullptr;
+    float *ring = lay.ring ? (float *)(gbase + (lay.staged ? lay.span() * 4 : 0) +
+                                       (lay.tail ? (size_t)(lay.m4 + 4) * 4 : 0))
+                           : nullptr;
+    // survivor pass: the seeds' offsets (already evaluated by the seed pass)
+    __shared__ unsigned seeds_s[kSeedMax];
+    __shared__ int n_seeds_s;
+    if (MODE == kModeSurv) {
+        if (threadIdx.x == 0) n_seeds_s = st->n_seeds;
+        for (int t = threadIdx.x; t < st->n_seeds; t += blockDim.x) seeds_s[t] = st->seed_off[t];
+    }
+    __syncthreads();
     int *cursor = MODE == kModeSurv ? &st->work2 : &st->work;
     const int64_t count = MODE == kModeSeed ? (int64_t)st->n_seeds
                         : MODE == kModeSurv ? (int64_t)st->n_cand : count_host;
     long long cells_acc = 0;
-    int started = 0, abandoned = 0;
+    int started = 0, abandoned = 0, passed_s = 0;
     while (true) {
         int c = 0;
         if (lane == 0) c = atomicAdd(cursor, 1);
@@ -361,29 +524,53 @@ __global__ void __launch_bounds__(256) k_dtw(QueryBufs b, QueryArgs a, const int
         // 0) so every lane of the group takes the same branches
         float thr = DINF;
         if (MODE == kModeSeed) {
-            float kth = list_kth(st->seed_keys, a.k);
+            const float kth = list_kth(st->seed_keys, a.k);
             thr = kth < DINF ? fmaf(kth, 1.0f + a.delta, a.alpha) : DINF;
         } else if (MODE == kModeSurv) {
             thr = current_thr(st, a);
         }
         thr = __shfl_sync(gmask, thr, 0, L);
         if (MODE == kModeSurv && lb > thr) continue;
+        if (MODE == kModeSurv) {
+            bool seen = false;
+            for (int t = lane; t < n_seeds_s; t += L) seen |= seeds_s[t] == idx;
+            if (__any_sync(gmask, seen)) continue;
+        }
         const float mh = b.mu_hi[idx], is = b.inv_sigma[idx], ls = b.mu_lo[idx] * is;
+        const float *xw = b.x + idx;
+        if (cbuf) {  // the group's normalised copy of the window
+            for (int j = lane; j < m; j += L) cbuf[j] = fmaf(xw[j] - mh, is, -ls);
+        }
+        TailCtx tc;
+        tc.Uw = b.U ? b.U + idx : nullptr;
+        tc.Lw = b.L ? b.L + idx : nullptr;
+        tc.qs = qs;
+        tc.mh = mh;
+        tc.is = is;
+        tc.ls = ls;
+        if (cbs) {
+            tail_suffix<L>(tc, cbs, m, gmask, lane);
+            // cbs[0] is LB_Keogh of q_hat against the window's envelope
+            // (Eq. 10 with the series-wide envelope): the third bound
+            if (cbs[0] > thr) continue;
+            if (lane == 0) ++passed_s;
+        }
+        __syncwarp(gmask);
         int cells = 0;
         float d;
-        if (MODE == kModeOut) {
-            d = dtw_band<float, L, false>(qs, b.x + idx, mh, is, ls, nullptr, ring, m, r, thr, gmask,
-                                          lane, cells);
+        if constexpr (K == 0) {
+            if (MODE == kModeOut)
+                d = dtw_band<float, L, false>(qs, xw, cbuf, mh, is, ls, nullptr, ring, m, r, thr, gmask, lane,
+                                              cells);
+            else
+                d = dtw_band<float, L, true>(qs, xw, cbuf, mh, is, ls,
+                                             (b.U && MODE == kModeSurv) ? &tc : nullptr, ring, m, r, thr,
+                                             gmask, lane, cells);
         } else {
-            TailCtx tc;
-            tc.Uw = b.U ? b.U + idx : nullptr;
-            tc.Lw = b.L ? b.L + idx : nullptr;
-            tc.qs = qs;
-            tc.mh = mh;
-            tc.is = is;
-            tc.ls = ls;
-            d = dtw_band<float, L, true>(qs, b.x + idx, mh, is, ls, (b.U && MODE == kModeSurv) ? &tc : nullptr,
-                                         ring, m, r, thr, gmask, lane, cells);
+            if (MODE == kModeOut)
+                d = dtw_diag<float, L, K, false>(qs, cbuf, nullptr, m, r, thr, gmask, lane, cells);
+            else
+                d = dtw_diag<float, L, K, true>(qs, cbuf, cbs, m, r, thr, gmask, lane, cells);
         }
         cells_acc += cells;
         if (lane == 0) {
@@ -391,7 +578,13 @@ __global__ void __launch_bounds__(256) k_dtw(QueryBufs b, QueryArgs a, const int
             if (!(d < DINF)) ++abandoned;
             if (MODE == kModeOut) out[c] = d;
             else if (MODE == kModeSeed) {
-                if (d < DINF) list_insert(st->seed_keys, a.k, make_key(key_quantize(d, a.qgrid), idx));
+                if (d < DINF) {
+                    // a finished seed is also a result candidate; the survivor
+                    // pass skips the seeds, so each window enters once
+                    const unsigned long long key = make_key(key_quantize(d, a.qgrid), idx);
+                    list_insert(st->seed_keys, a.k, key);
+                    list_insert(st->res_keys, a.list_cap, key);
+                }
             } else if (d <= thr) {
                 list_insert(st->res_keys, a.list_cap, make_key(key_quantize(d, a.qgrid), idx));
             }
@@ -403,38 +596,56 @@ __global__ void __launch_bounds__(256) k_dtw(QueryBufs b, QueryArgs a, const int
         unsigned long long cs = (unsigned long long)cells_acc;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) cs += __shfl_xor_sync(0xffffffffu, cs, o);
-        int ns = started, na = abandoned;
+        int ns = started, na = abandoned, np = passed_s;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
             ns += __shfl_xor_sync(0xffffffffu, ns, o);
             na += __shfl_xor_sync(0xffffffffu, na, o);
+            np += __shfl_xor_sync(0xffffffffu, np, o);
         }
         if (ln == 0) {
             atomicAdd(&st->ctr[kCtrCells], cs);
             atomicAdd(&st->ctr[kCtrDtwStarted], (unsigned long long)ns);
             atomicAdd(&st->ctr[kCtrDtwAbandoned], (unsigned long long)na);
+            if (np) atomicAdd(&st->ctr[kCtrKeoghS], (unsigned long long)np);
         }
     }
 }
 
-// FP64 re-score: per window two-pass FP64 statistics (Eq. 5) and FP64 banded
-// DTW, no pruning.  Candidates: the margin list (offsets == null) or offsets.
-template <int L>
+// Re-score: per window two-pass FP64 statistics (Eq. 5), the normalised
+// values formed in FP64, and the banded DTW in double-float arithmetic
+// (about 48 significant bits; FP64 itself for bands wider than kDiagRMax).
+// No pruning.  Candidates: the margin list (offsets == null) or offsets.
+template <int L, int K>
 __global__ void __launch_bounds__(256) k_dtw64(QueryBufs b, QueryArgs a, const int64_t *offsets,
-                                               int64_t count_host, double *out) {
+                                               int64_t count_host, double *out, int staged) {
     extern __shared__ __align__(16) unsigned char smraw[];
     QueryState *st = b.st;
     if (!st->valid) return;
-    const int m = a.m, r = a.r, W = 2 * r + 1;
-    double *qs = (double *)smraw;
-    for (int t = threadIdx.x; t < m; t += blockDim.x) qs[t] = b.qh64[t];
-    __syncthreads();
+    const int m = a.m, r = a.r;
+    const DtwSmem<double> lay = dtw_smem<double, L, K>(m, r, staged != 0, false);
+    // K > 0: double-float arrays (8 B per element, as for a double), padded
+    // with finite poison values (+1e15 query, -1e15 window)
+    double *qbase = (double *)smraw;
+    dfloat *qd = (dfloat *)smraw + lay.pad;
+    double *qs = qbase + lay.pad;
+    for (int t = threadIdx.x; t < m; t += blockDim.x) {
+        if (K > 0) qd[t] = df_from(b.qh64[t]);
+        else qs[t] = b.qh64[t];
+    }
+    if (K > 0) fill_pads((dfloat *)smraw, m, lay.pad, dfloat{1e15f, 0.0f}, threadIdx.x, blockDim.x);
     const int warp = threadIdx.x >> 5, ln = lane_id();
     const int g = ln / L, lane = ln % L;
     const int gid = warp * (32 / L) + g;
     const unsigned gmask = (L == 32) ? 0xffffffffu : (((1u << L) - 1u) << (g * L));
-    double *ring = qs + ((m + 3) & ~3) + gid * (W + 1);
+    unsigned char *gbase = smraw + lay.q_bytes() + (size_t)gid * lay.group_bytes();
+    double *cbuf = lay.staged ? (double *)gbase + lay.pad : nullptr;
+    dfloat *cd = (dfloat *)gbase + lay.pad;
+    if (K > 0) fill_pads((dfloat *)gbase, m, lay.pad, dfloat{-1e15f, 0.0f}, lane, L);
+    double *ring = lay.ring ? (double *)(gbase + (lay.staged ? lay.span() * 8 : 0)) : nullptr;
+    __syncthreads();
     const int64_t count = offsets ? count_host : (int64_t)st->n_margin;
+    __shared__ double bc[2 * 8 * 32];  // per group: mu, 1/sigma
     while (true) {
         int c = 0;
         if (lane == 0) c = atomicAdd(&st->work, 1);
@@ -456,20 +667,36 @@ __global__ void __launch_bounds__(256) k_dtw64(QueryBufs b, QueryArgs a, const i
         for (int j = lane; j < m; j += L) s += (double)xw[j];
 #pragma unroll
         for (int o = L / 2; o > 0; o >>= 1) s += __shfl_xor_sync(gmask, s, o, L);
-        const double mu = s / (double)m;
         double v = 0.0;
+        const double mu0 = s * (1.0 / (double)m);
         for (int j = lane; j < m; j += L) {
-            double d = (double)xw[j] - mu;
+            const double d = (double)xw[j] - mu0;
             v = fma(d, d, v);
         }
 #pragma unroll
         for (int o = L / 2; o > 0; o >>= 1) v += __shfl_xor_sync(gmask, v, o, L);
-        const double var = v / (double)m, mm = mu * mu;
-        const bool zero = var <= 1e-24 * (mm > 1.0 ? mm : 1.0);
-        const double inv = zero ? 0.0 : 1.0 / sqrt(var);
-        int cells = 0;
-        double d = dtw_band<double, L, false>(qs, xw, mu, inv, 0.0, nullptr, ring, m, r, tinf<double>(),
-                                              gmask, lane, cells);
+        // one division and square root per group (long FP64 sequences)
+        if (lane == 0) {
+            const double mu = s / (double)m, var = v / (double)m, mm = mu * mu;
+            bc[2 * gid] = mu;
+            bc[2 * gid + 1] = var <= 1e-24 * (mm > 1.0 ? mm : 1.0) ? 0.0 : 1.0 / sqrt(var);
+        }
+        __syncwarp(gmask);
+        const double mu = bc[2 * gid], inv = bc[2 * gid + 1];
+        double d;
+        if constexpr (K > 0) {
+            for (int j = lane; j < m; j += L) cd[j] = df_from(((double)xw[j] - mu) * inv);
+            __syncwarp(gmask);
+            d = dtw_diag_df<L, K>(qd, cd, m, r, gmask, lane);
+        } else {
+            if (cbuf) {
+                for (int j = lane; j < m; j += L) cbuf[j] = ((double)xw[j] - mu) * inv;
+            }
+            __syncwarp(gmask);
+            int cells = 0;
+            d = dtw_band<double, L, false>(qs, xw, cbuf, mu, inv, 0.0, nullptr, ring, m, r, tinf<double>(), gmask,
+                                           lane, cells);
+        }
         if (lane == 0) {
             if (offsets) out[c] = d;
             else st->margin_d64[c] = d;
@@ -478,70 +705,97 @@ __global__ void __launch_bounds__(256) k_dtw64(QueryBufs b, QueryArgs a, const i
     }
 }
 
+// Kernel choice and CTA shape.  The anti-diagonal kernel (K > 0) is used
+// when r <= kDiagRMax and one warp's groups can stage their windows;
+// otherwise the row-systolic kernel (K == 0), staged when it fits.  Warps
+// per CTA shrink until the CTA fits in ~100 KB (two CTAs per SM).
+struct DtwPlan {
+    int L, K, staged, warps;
+    size_t smem;
+};
+
+template <typename T, int L, int K>
+static bool plan_fits(int m, int r, bool tail, DtwPlan *p) {
+    const size_t budget = 100 * 1024, hard = 200 * 1024;
+    for (int staged = 1; staged >= (K > 0 ? 1 : 0); --staged) {
+        const DtwSmem<T> lay = dtw_smem<T, L, K>(m, r, staged != 0, tail);
+        auto total = [&](int w) { return lay.q_bytes() + (size_t)w * (32 / L) * lay.group_bytes(); };
+        int warps = 8;
+        while (warps > 1 && total(warps) > budget) --warps;
+        if (total(warps) <= hard) {
+            *p = DtwPlan{L, K, staged, warps, total(warps)};
+            return true;
+        }
+    }
+    return false;
+}
+
 template <typename T>
-static void dtw_launch_shape(int m, int r, int L, int num_sms, int64_t count, int *blocks,
-                             int *threads, size_t *smem) {
-    const int W = 2 * r + 1;
-    const size_t qbytes = (size_t)((m + 3) & ~3) * sizeof(T);
-    const size_t per_warp = (size_t)(32 / L) * (W + 1) * sizeof(T);
-    int warps = 8;
-    while (warps > 1 && qbytes + warps * per_warp > 100 * 1024) --warps;
-    *threads = warps * 32;
-    *smem = qbytes + warps * per_warp;
-    const int groups = warps * (32 / L);
+static bool plan_dtw(int m, int r, bool tail, DtwPlan *p) {
+    if (r <= kDiagRMax) {
+        int L, K;
+        diag_shape(r, &L, &K);
+#define DTWS_TRY(LL, KK) \
+    if (L == LL && K == KK && plan_fits<T, LL, KK>(m, r, tail, p)) return true;
+        DTWS_TRY(1, 1) DTWS_TRY(2, 1) DTWS_TRY(4, 1) DTWS_TRY(8, 1) DTWS_TRY(16, 1)
+        DTWS_TRY(32, 1) DTWS_TRY(32, 2) DTWS_TRY(32, 4) DTWS_TRY(32, 8) DTWS_TRY(32, 16)
+#undef DTWS_TRY
+    }
+    const int L = lanes_for(r);
+#define DTWS_TRY(LL) \
+    if (L == LL) return plan_fits<T, LL, 0>(m, r, tail, p);
+    DTWS_TRY(1) DTWS_TRY(2) DTWS_TRY(4) DTWS_TRY(8) DTWS_TRY(16) DTWS_TRY(32)
+#undef DTWS_TRY
+    return false;
+}
+
+static int dtw_blocks(const DtwPlan &p, int num_sms, int64_t count) {
+    const int groups = p.warps * (32 / p.L);
     int64_t want = (count + groups - 1) / groups;
-    int64_t cap = (int64_t)num_sms * 4;
+    const int64_t cap = (int64_t)num_sms * 4;
     if (want < 1) want = 1;
-    *blocks = (int)(want < cap ? want : cap);
+    return (int)(want < cap ? want : cap);
 }
 
 template <int MODE>
 static cudaError_t dtw_dispatch(const QueryBufs &b, const QueryArgs &a, const int64_t *offsets,
                                 int64_t count, float *out, int64_t count_for_grid, cudaStream_t s) {
-    int L = lanes_for(a.r), blocks, threads;
-    size_t smem;
-    dtw_launch_shape<float>(a.m, a.r, L, b.num_sms, count_for_grid, &blocks, &threads, &smem);
-#define DTWS_LAUNCH(LL)                                                                             \
-    {                                                                                                \
-        cudaError_t e = cudaFuncSetAttribute(k_dtw<LL, MODE>,                                        \
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
-        if (e != cudaSuccess) return e;                                                              \
-        k_dtw<LL, MODE><<<blocks, threads, smem, s>>>(b, a, offsets, count, out);                    \
-        return cudaGetLastError();                                                                   \
+    DtwPlan p;
+    if (!plan_dtw<float>(a.m, a.r, MODE == kModeSurv && b.U != nullptr, &p)) return cudaErrorInvalidValue;
+    const int blocks = dtw_blocks(p, b.num_sms, count_for_grid);
+#define DTWS_CASE(LL, KK)                                                                                     \
+    if (p.L == LL && p.K == KK) {                                                                             \
+        cudaError_t e = cudaFuncSetAttribute(k_dtw<LL, KK, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                                             (int)p.smem);                                                    \
+        if (e != cudaSuccess) return e;                                                                       \
+        k_dtw<LL, KK, MODE><<<blocks, p.warps * 32, p.smem, s>>>(b, a, offsets, count, out, p.staged);        \
+        return cudaGetLastError();                                                                            \
     }
-    switch (L) {
-    case 1: DTWS_LAUNCH(1)
-    case 2: DTWS_LAUNCH(2)
-    case 4: DTWS_LAUNCH(4)
-    case 8: DTWS_LAUNCH(8)
-    case 16: DTWS_LAUNCH(16)
-    default: DTWS_LAUNCH(32)
-    }
-#undef DTWS_LAUNCH
+    DTWS_CASE(1, 1) DTWS_CASE(2, 1) DTWS_CASE(4, 1) DTWS_CASE(8, 1) DTWS_CASE(16, 1)
+    DTWS_CASE(32, 1) DTWS_CASE(32, 2) DTWS_CASE(32, 4) DTWS_CASE(32, 8) DTWS_CASE(32, 16)
+    DTWS_CASE(1, 0) DTWS_CASE(2, 0) DTWS_CASE(4, 0) DTWS_CASE(8, 0) DTWS_CASE(16, 0) DTWS_CASE(32, 0)
+#undef DTWS_CASE
+    return cudaErrorInvalidValue;
 }
 
 static cudaError_t dtw64_dispatch(const QueryBufs &b, const QueryArgs &a, const int64_t *offsets,
                                   int64_t count, double *out, int64_t count_for_grid, cudaStream_t s) {
-    int L = lanes_for(a.r), blocks, threads;
-    size_t smem;
-    dtw_launch_shape<double>(a.m, a.r, L, b.num_sms, count_for_grid, &blocks, &threads, &smem);
-#define DTWS_LAUNCH(LL)                                                                             \
-    {                                                                                                \
-        cudaError_t e = cudaFuncSetAttribute(k_dtw64<LL>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
-                                             (int)smem);                                             \
-        if (e != cudaSuccess) return e;                                                              \
-        k_dtw64<LL><<<blocks, threads, smem, s>>>(b, a, offsets, count, out);                        \
-        return cudaGetLastError();                                                                   \
+    DtwPlan p;
+    if (!plan_dtw<double>(a.m, a.r, false, &p)) return cudaErrorInvalidValue;
+    const int blocks = dtw_blocks(p, b.num_sms, count_for_grid);
+#define DTWS_CASE(LL, KK)                                                                                     \
+    if (p.L == LL && p.K == KK) {                                                                             \
+        cudaError_t e = cudaFuncSetAttribute(k_dtw64<LL, KK>, cudaFuncAttributeMaxDynamicSharedMemorySize,     \
+                                             (int)p.smem);                                                    \
+        if (e != cudaSuccess) return e;                                                                       \
+        k_dtw64<LL, KK><<<blocks, p.warps * 32, p.smem, s>>>(b, a, offsets, count, out, p.staged);            \
+        return cudaGetLastError();                                                                            \
     }
-    switch (L) {
-    case 1: DTWS_LAUNCH(1)
-    case 2: DTWS_LAUNCH(2)
-    case 4: DTWS_LAUNCH(4)
-    case 8: DTWS_LAUNCH(8)
-    case 16: DTWS_LAUNCH(16)
-    default: DTWS_LAUNCH(32)
-    }
-#undef DTWS_LAUNCH
+    DTWS_CASE(1, 1) DTWS_CASE(2, 1) DTWS_CASE(4, 1) DTWS_CASE(8, 1) DTWS_CASE(16, 1)
+    DTWS_CASE(32, 1) DTWS_CASE(32, 2) DTWS_CASE(32, 4) DTWS_CASE(32, 8) DTWS_CASE(32, 16)
+    DTWS_CASE(1, 0) DTWS_CASE(2, 0) DTWS_CASE(4, 0) DTWS_CASE(8, 0) DTWS_CASE(16, 0) DTWS_CASE(32, 0)
+#undef DTWS_CASE
+    return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_dtw_seeds(const QueryBufs &b, const QueryArgs &a, cudaStream_t s) {
@@ -567,149 +821,112 @@ cudaError_t launch_dtw_at_f64(const QueryBufs &b, const QueryArgs &a, const int6
 }
 
 // ------------------------------------------------------------------ LB scan
-// Fused cascade over one tile of windows (Sec. 2.2, Eqs. 6-10, prune when a
-// bound exceeds thr).  Stage 1: LB_KimFL (Eq. 7, squared) for every window;
-// the survivors are compacted into a shared queue so that stage 2 keeps all
-// lanes busy: LB_Keogh of the window against the query envelope (Eq. 8),
-// terms taken in |q_hat|-descending order with early abandon every 8 terms.
-// Stage 3 on stage 2's survivors: LB_Keogh of the query against the
-// window's envelope (Eq. 10), the envelope read from the series-wide
-// envelope and normalised with the window's statistics (looser than the
-// window-clipped envelope, still admissible).  Survivors (lb = max of the
-// three bounds, offset) are appended to the global survivor list.
-constexpr int kLbThreads = 256;
+// Cascade over tiles of windows (Sec. 2.2, Eqs. 6-8, prune when a bound
+// exceeds thr): LB_KimFL (Eq. 7, squared) for every window, then LB_Keogh of
+// the window against the query envelope (Eq. 8), terms in |q_hat|-descending
+// order with early abandon.  Survivors (lb = max of the two, offset) are
+// appended to the global survivor list.  The third bound, LB_Keogh of the
+// query against the window's envelope (Eq. 10, from the series-wide envelope
+// normalised with the window's statistics: looser than the window-clipped
+// envelope, still admissible), is evaluated for each survivor by the DTW
+// kernel, whose tail bound consists of exactly its per-row terms.
+constexpr int kEqChunks = 2;
 
 __device__ __forceinline__ float keogh_term(float v, float u, float l) {
-    float d = fmaxf(v - u, 0.0f) + fmaxf(l - v, 0.0f);
+    const float d = fmaxf(v - u, 0.0f) + fmaxf(l - v, 0.0f);
     return d * d;
 }
 
-__global__ void __launch_bounds__(kLbThreads) k_lb_scan(QueryBufs b, QueryArgs a) {
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Each warp scans 32 windows at a time with LB_KimFL (one window per lane);
+// the rare windows that pass are then bounded by the whole warp, one at a
+// time: lanes take 32 consecutive terms of the |q_hat|-ordered LB_Keogh sums
+// and the warp abandons as soon as a chunk's running total exceeds thr.  No
+// thread waits on another warp's survivors.
+__global__ void __launch_bounds__(kScanThreads) k_lb_scan(QueryBufs b, QueryArgs a) {
     extern __shared__ __align__(16) unsigned char smraw[];
-    __shared__ int n1, n2;
-    __shared__ unsigned short q1[kTile], q2[kTile];
-    __shared__ float l1[kTile], l2[kTile];
     QueryState *st = b.st;
     if (!st->valid) return;
     const int m = a.m;
-    Tile t = carve_tile(smraw, m);
-    const int64_t i0 = (int64_t)blockIdx.x * kTile;
     const float thr = current_thr(st, a);
     if (blockIdx.x == 0 && threadIdx.x == 0) st->thr_scan = thr;
-    if (threadIdx.x == 0) { n1 = 0; n2 = 0; }
-    if (!stage_tile(t, b, i0, m)) return;
     const float qf = b.qh32[0], ql = b.qh32[m - 1];
-
-    // stage 1: LB_KimFL
-    for (int w = threadIdx.x; w < kTile; w += blockDim.x) {
-        const int64_t i = i0 + w;
-        bool pass = false;
-        float kim = 0.0f;
-        if (i < a.N) {
-            const float mh = t.mh[w], is = t.is[w], ls = t.ml[w] * is;
-            const float c0 = fmaf(t.xs[w] - mh, is, -ls);
-            const float c1 = fmaf(t.xs[w + m - 1] - mh, is, -ls);
-            const float d0 = qf - c0, d1 = ql - c1;
-            kim = fmaf(d0, d0, d1 * d1);
-            pass = !(kim > thr);
-        }
-        int pos = warp_append(&n1, pass, 0xffffffffu);
-        if (pass) { q1[pos] = (unsigned short)w; l1[pos] = kim; }
+    const int lane = lane_id(), warp = threadIdx.x >> 5;
+    constexpr int kPerWarp = kTile / kScanConsumers;
+    // the ordered query terms the scan uses, in shared memory
+    __shared__ int o_s[kEqChunks * 32];
+    __shared__ float u_s[kEqChunks * 32], l_s[kEqChunks * 32];
+    for (int j = threadIdx.x; j < kEqChunks * 32; j += blockDim.x) {
+        o_s[j] = j < m ? (int)b.ord[j] : 0;
+        u_s[j] = j < m ? b.sU[j] : 0.0f;
+        l_s[j] = j < m ? b.sL[j] : 0.0f;
     }
-    __syncthreads();
-    const int c1n = n1;
-    // stage 2: LB_Keogh, window vs query envelope
-    for (int base = 0; base < c1n; base += blockDim.x) {
-        const int e = base + threadIdx.x;
-        bool pass = false;
-        float lb = 0.0f;
-        int w = 0;
-        if (e < c1n) {
-            w = q1[e];
-            const float mh = t.mh[w], is = t.is[w], ls = t.ml[w] * is;
-            const float *xw = t.xs + w;
-            float s = 0.0f;
-            int j = 0;
-            for (; j + 8 <= m; j += 8) {
-#pragma unroll
-                for (int u = 0; u < 8; ++u) {
-                    const int p = b.ord[j + u];
-                    const float c = fmaf(xw[p] - mh, is, -ls);
-                    s += keogh_term(c, b.sU[j + u], b.sL[j + u]);
-                }
-                if (s > thr) break;
+    unsigned long long c1 = 0, c2 = 0;
+    const int64_t ntiles = (a.N + kTile - 1) / kTile;
+    tile_pipeline(smraw, b, m, ntiles, &st->tile_ctr[1], [&](const Tile &t, int64_t i0) {
+#pragma unroll 1
+        for (int u = 0; u < kPerWarp / 32; ++u) {
+            const int w = warp * kPerWarp + u * 32 + lane;
+            bool pass = false;
+            float kim = 0.0f;
+            if (i0 + w < a.N) {
+                const float mh = t.mh[w], is = t.is[w], ls = t.ml[w] * is;
+                const float d0 = qf - fmaf(t.xs[w] - mh, is, -ls);
+                const float d1 = ql - fmaf(t.xs[w + m - 1] - mh, is, -ls);
+                kim = fmaf(d0, d0, d1 * d1);
+                pass = !(kim > thr);
             }
-            if (!(s > thr)) {
-                for (; j < m; ++j) {
-                    const int p = b.ord[j];
-                    const float c = fmaf(xw[p] - mh, is, -ls);
-                    s += keogh_term(c, b.sU[j], b.sL[j]);
+            unsigned bal = __ballot_sync(0xffffffffu, pass);
+            c1 += __popc(bal);
+            while (bal) {
+                const int src = __ffs(bal) - 1;
+                bal &= bal - 1;
+                const int ws = warp * kPerWarp + u * 32 + src;
+                const int64_t i = i0 + ws;
+                const float mh = t.mh[ws], is = t.is[ws], ls = t.ml[ws] * is;
+                const float *xw = t.xs + ws;
+                // LB_Keogh, window vs query envelope (Eq. 8), at most kEqChunks
+                // chunks of 32 terms here: a window that survives them (the
+                // neighbourhood of a match) goes to the DTW stage with the
+                // partial sum, itself a lower bound, rather than holding
+                // this warp for the full sum
+                float s2 = 0.0f;
+                for (int base = 0; base < m && base < kEqChunks * 32; base += 32) {
+                    const int j = base + lane;
+                    float term = 0.0f;
+                    if (j < m) term = keogh_term(fmaf(xw[o_s[j]] - mh, is, -ls), u_s[j], l_s[j]);
+                    s2 += warp_sum(term);
+                    if (s2 > thr) break;
+                }
+                if (s2 > thr) continue;
+                ++c2;
+                const float kim_s = __shfl_sync(0xffffffffu, kim, src);
+                if (lane == 0) {
+                    const int pos = atomicAdd(&st->n_cand, 1);
+                    b.cand_lb[pos] = fmaxf(kim_s, s2);
+                    b.cand_idx[pos] = (unsigned)i;
                 }
             }
-            pass = !(s > thr);
-            lb = fmaxf(l1[e], s);
         }
-        int pos = warp_append(&n2, pass, 0xffffffffu);
-        if (pass) { q2[pos] = (unsigned short)w; l2[pos] = lb; }
-    }
-    __syncthreads();
-    const int c2n = n2;
-    // stage 3: LB_Keogh, query vs the window's series-wide envelope
-    int n3 = 0;
-    for (int base = 0; base < c2n; base += blockDim.x) {
-        const int e = base + threadIdx.x;
-        bool pass = false;
-        float lb = 0.0f;
-        int64_t i = 0;
-        if (e < c2n) {
-            const int w = q2[e];
-            i = i0 + w;
-            const float mh = t.mh[w], is = t.is[w], ls = t.ml[w] * is;
-            const float *Uw = b.U + i, *Lw = b.L + i;
-            float s = 0.0f;
-            int j = 0;
-            for (; j + 8 <= m; j += 8) {
-#pragma unroll
-                for (int u = 0; u < 8; ++u) {
-                    const int p = b.ord[j + u];
-                    const float uu = fmaf(Uw[p] - mh, is, -ls), ll = fmaf(Lw[p] - mh, is, -ls);
-                    s += keogh_term(b.sq[j + u], uu, ll);
-                }
-                if (s > thr) break;
-            }
-            if (!(s > thr)) {
-                for (; j < m; ++j) {
-                    const int p = b.ord[j];
-                    const float uu = fmaf(Uw[p] - mh, is, -ls), ll = fmaf(Lw[p] - mh, is, -ls);
-                    s += keogh_term(b.sq[j], uu, ll);
-                }
-            }
-            pass = !(s > thr);
-            lb = fmaxf(l2[e], s);
-        }
-        int pos = warp_append(&st->n_cand, pass, 0xffffffffu);
-        if (pass) {
-            b.cand_lb[pos] = lb;
-            b.cand_idx[pos] = (unsigned)i;
-            ++n3;
-        }
-    }
-    // counters
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) n3 += __shfl_xor_sync(0xffffffffu, n3, o);
-    if (lane_id() == 0 && n3) atomicAdd(&st->ctr[kCtrKeoghS], (unsigned long long)n3);
-    if (threadIdx.x == 0) {
-        if (c1n) atomicAdd(&st->ctr[kCtrKim], (unsigned long long)c1n);
-        if (c2n) atomicAdd(&st->ctr[kCtrKeoghQ], (unsigned long long)c2n);
+    });
+    if (lane == 0) {
+        if (c1) atomicAdd(&st->ctr[kCtrKim], c1);
+        if (c2) atomicAdd(&st->ctr[kCtrKeoghQ], c2);
     }
 }
 
 cudaError_t launch_lb_scan(const QueryBufs &b, const QueryArgs &a, cudaStream_t s) {
-    size_t smem = tile_smem_bytes(a.m);
+    const size_t smem = kStages * stage_bytes(a.m);
     cudaError_t e = cudaFuncSetAttribute(k_lb_scan, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    int64_t tiles = (a.N + kTile - 1) / kTile;
-    k_lb_scan<<<(unsigned)tiles, kLbThreads, smem, s>>>(b, a);
+    const int64_t tiles = (a.N + kTile - 1) / kTile;
+    const int grid = scan_grid((const void *)k_lb_scan, kScanThreads, smem, b.num_sms, tiles);
+    k_lb_scan<<<grid, kScanThreads, smem, s>>>(b, a);
     return cudaGetLastError();
 }
 

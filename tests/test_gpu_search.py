@@ -187,3 +187,22 @@ def test_stats_counters(walk, index):
     assert s["pass_kim"] >= s["pass_keogh_q"] >= s["pass_keogh_s"] >= 1
     assert s["dtw_started"] >= 1 and s["rescored"] >= 1
     assert all(v >= 0 for v in s["phase_ms"])
+
+
+def test_long_scan_reports_no_device_error():
+    """Enough tiles that every scan CTA cycles through its shared-memory
+    stages several times; the query must finish without a device-side
+    error (a stuck pipeline would end in DTWS_ETIMEOUT)."""
+    import time
+    x = synth.random_walk(4_000_000, 31)
+    q, o = synth.noisy_copy(x, 256, 32, 33, noise=0.1)
+    with dtws.Index(x) as ix:
+        ix.query(q, 25, 1)
+        t0 = time.perf_counter()
+        idx, dist = ix.query(q, 25, 1)
+        elapsed = time.perf_counter() - t0
+        assert ix.sync_status() == dtws.DTWS_OK
+    assert elapsed < 1.0
+    lo = max(0, o - 50_000)
+    oi, od = oracle.search_cascade(x[lo:o + 50_000 + 256], q, 25, 1)
+    assert idx[0] == o or dist[0] <= od[0] * (1 + 1e-6)

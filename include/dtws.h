@@ -76,7 +76,9 @@ typedef struct {
     float alpha_per_m;      /* absolute margin per query sample, default 1e-6 */
     int32_t seed_random;    /* random seed windows, default 4 (0..64) */
     int32_t seed_proposals; /* proxy-scan proposals, default 16 (0..64) */
-    int32_t proxy_terms;    /* query positions in the proxy distance, default 8 */
+    int32_t proxy_terms;    /* query positions in the proxy distance: 16, 8, 4
+                               (other values round down to one of them, or 2),
+                               default 8 */
     int32_t ordering;       /* dtws_ordering, default DTWS_ORDER_PLAIN */
     int32_t timing;         /* 1: record per-phase CUDA events (small cost) */
     int32_t reserved0;
@@ -86,19 +88,21 @@ typedef struct {
 
 /* Per-query counters of the last dtws_query() (reset by each call; read
    after the stream has completed).  Phases: 0 query prep, 1 proxy scan +
-   seeds, 2 lower-bound scan, 3 survivor ordering, 4 DTW, 5 finalise (FP64
-   re-score), 6 window statistics (when computed by this call), 7 series
-   envelope (when computed by this call). */
+   seeds, 2 lower-bound scan, 3 survivor ordering, 4 DTW, 5 finalise
+   (extended-precision re-score), 6 window statistics (when computed by this
+   call), 7 series envelope (when computed by this call). */
 typedef struct {
     int64_t windows;          /* N */
     int64_t pass_kim;         /* windows whose LB_KimFL did not prune */
     int64_t pass_keogh_q;     /* ... whose LB_Keogh vs the query envelope did not */
     int64_t pass_keogh_s;     /* ... whose LB_Keogh vs the series envelope did not
-                                 (= survivors handed to DTW ordering) */
+                                 (checked by the DTW stage, so counted among
+                                 the windows it examined before its threshold
+                                 ended the pass) */
     int64_t dtw_started;      /* DTW computations begun (seeds + survivors) */
     int64_t dtw_abandoned;    /* ... abandoned early */
     int64_t dtw_cells;        /* band cells evaluated by the FP32 DTW */
-    int64_t rescored;         /* candidates re-scored in FP64 */
+    int64_t rescored;         /* candidates re-scored in extended precision */
     float seed_bsf;           /* smallest seed distance (inf if no seed) */
     float phase_ms[8];        /* valid when options.timing == 1 */
     int64_t kernel_launches;  /* kernels this library launched for the query */
@@ -132,7 +136,9 @@ dtws_status dtws_get_options(dtws_t h, dtws_options *opt);
  * k: 1 <= k <= min(N, DTWS_K_MAX).
  * out_idx: int64 [k], offsets ascending by (distance, offset).
  * out_dist: FP32 [k], squared banded DTW of the z-normalised query and
- *   window, re-scored in FP64 and rounded to FP32.
+ *   window, re-scored in extended precision (FP64 statistics, DTW in
+ *   double-float arithmetic, ~48 significant bits) and rounded to FP32.
+ *   The offsets are ordered by that re-scored distance, then by offset.
  * A window (or query) whose variance is <= 1e-24*max(1, mean^2) normalises
  * to all zeros.  Per-series data for this m (window statistics) and r
  * (series envelope) are computed on first use and cached in the handle.
@@ -196,8 +202,10 @@ dtws_status dtws_series_envelope(dtws_t h, int32_t r, float *U, float *L, void *
 dtws_status dtws_dtw_at(dtws_t h, const float *Q, int32_t m, int32_t r,
                         const int64_t *offsets, int64_t count, float *out, void *stream);
 
-/* Same, evaluated in FP64 with per-window two-pass statistics: the
-   re-score kernel.  out: FP64 [count]. */
+/* Same, in extended precision: per-window two-pass FP64 statistics (Eq. 5),
+   normalised values formed in FP64 and the DTW in double-float arithmetic
+   (~48 significant bits; plain FP64 for bands wider than 511): the re-score
+   kernel of dtws_query.  out: FP64 [count]. */
 dtws_status dtws_dtw_at_f64(dtws_t h, const float *Q, int32_t m, int32_t r,
                             const int64_t *offsets, int64_t count, double *out,
                             void *stream);

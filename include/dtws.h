@@ -76,9 +76,9 @@ typedef struct {
     float alpha_per_m;      /* absolute margin per query sample, default 1e-6 */
     int32_t seed_random;    /* random seed windows, default 4 (0..64) */
     int32_t seed_proposals; /* proxy-scan proposals, default 16 (0..64) */
-    int32_t proxy_terms;    /* query positions in the proxy distance: 16, 8, 4
-                               (other values round down to one of them, or 2),
-                               default 8 */
+    int32_t proxy_terms;    /* evenly spaced query positions in the proxy
+                               distance: 16, 8, 4 (other values round down to
+                               one of them, or 2), default 16 */
     int32_t ordering;       /* dtws_ordering, default DTWS_ORDER_PLAIN */
     int32_t timing;         /* 1: record per-phase CUDA events (small cost) */
     int32_t reserved0;

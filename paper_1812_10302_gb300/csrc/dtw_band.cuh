@@ -4,6 +4,8 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+#include "dtws_common.cuh"
+
 namespace dtws {
 
 // ------------------------------------------------------------------ banded DTW core
@@ -426,7 +428,6 @@ __host__ __device__ inline void diag_shape(int r, int *L, int *K) {
     while (32 * k < need) k *= 2;
     *K = k;  // 0 < K <= 16 for r <= 511
 }
-constexpr int kDiagRMax = 511;
 
 // Lanes per group for band half-width r: the largest power of two <= r
 // (<= 32), 1 for r = 0.

@@ -43,6 +43,7 @@ struct StatsEntry {
     int m = 0;
     int64_t used = 0;
     float *mu_hi = nullptr, *mu_lo = nullptr, *inv_sigma = nullptr;
+    float *smu_hi = nullptr, *smu_lo = nullptr, *sinv_sigma = nullptr;  // every kProxyStride-th window
 };
 struct EnvEntry {
     int r = 0;
@@ -88,6 +89,9 @@ struct dtws_ctx {
     cudaEvent_t ev[9] = {};
     bool ev_ok = false;
     bool ev_recorded[9] = {false};
+    // side stream for work that overlaps the lower-bound scan
+    cudaStream_t side = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
 };
 
 namespace {
@@ -131,6 +135,9 @@ void free_stats(StatsEntry &e) {
     cudaFree(e.mu_hi);
     cudaFree(e.mu_lo);
     cudaFree(e.inv_sigma);
+    cudaFree(e.smu_hi);
+    cudaFree(e.smu_lo);
+    cudaFree(e.sinv_sigma);
     e = StatsEntry();
 }
 void free_env(EnvEntry &e) {
@@ -158,9 +165,12 @@ dtws_status get_stats(dtws_t h, int m, cudaStream_t s, StatsEntry **out, bool *c
     StatsEntry e;
     e.m = m;
     const int64_t N = h->n - m + 1;
-    const int64_t cap = round_up(N, kTile) + kTile;
+    const int64_t cap = round_up(N, kProxyTile) + kProxyTile;
+    const int64_t scap = cap / kProxyStride;
     cudaError_t a1 = dalloc(&e.mu_hi, cap), a2 = dalloc(&e.mu_lo, cap), a3 = dalloc(&e.inv_sigma, cap);
-    if (a1 != cudaSuccess || a2 != cudaSuccess || a3 != cudaSuccess) {
+    cudaError_t a4 = dalloc(&e.smu_hi, scap), a5 = dalloc(&e.smu_lo, scap), a6 = dalloc(&e.sinv_sigma, scap);
+    if (a1 != cudaSuccess || a2 != cudaSuccess || a3 != cudaSuccess || a4 != cudaSuccess ||
+        a5 != cudaSuccess || a6 != cudaSuccess) {
         free_stats(e);
         cudaGetLastError();
         set_err("window statistics for m=%d: out of device memory", m);
@@ -169,8 +179,11 @@ dtws_status get_stats(dtws_t h, int m, cudaStream_t s, StatsEntry **out, bool *c
     CK(cudaMemsetAsync(e.mu_hi, 0, cap * 4, s));
     CK(cudaMemsetAsync(e.mu_lo, 0, cap * 4, s));
     CK(cudaMemsetAsync(e.inv_sigma, 0, cap * 4, s));
+    CK(cudaMemsetAsync(e.smu_hi, 0, scap * 4, s));
+    CK(cudaMemsetAsync(e.smu_lo, 0, scap * 4, s));
+    CK(cudaMemsetAsync(e.sinv_sigma, 0, scap * 4, s));
     CK(launch_window_stats(h->x, h->n, m, h->P1, h->P2, h->T1, h->T2, h->A, e.mu_hi, e.mu_lo,
-                           e.inv_sigma, s));
+                           e.inv_sigma, e.smu_hi, e.smu_lo, e.sinv_sigma, s));
     e.used = ++h->clock;
     h->stats.push_back(e);
     *out = &h->stats.back();
@@ -250,6 +263,9 @@ QueryBufs make_bufs(dtws_t h, const StatsEntry *se, const EnvEntry *ee) {
     b.mu_hi = se ? se->mu_hi : nullptr;
     b.mu_lo = se ? se->mu_lo : nullptr;
     b.inv_sigma = se ? se->inv_sigma : nullptr;
+    b.smu_hi = se ? se->smu_hi : nullptr;
+    b.smu_lo = se ? se->smu_lo : nullptr;
+    b.sinv_sigma = se ? se->sinv_sigma : nullptr;
     b.U = ee ? ee->U : nullptr;
     b.L = ee ? ee->L : nullptr;
     b.qh32 = h->qh32;
@@ -283,6 +299,7 @@ QueryArgs make_args(dtws_t h, int m, int r, int k) {
     float g = 1.17549435e-38f;
     while (g * 2.0f <= a.alpha * 0.25f) g *= 2.0f;
     a.qgrid = g;
+    a.prescore = a.r <= kDiagRMax ? 1 : 0;
     return a;
 }
 
@@ -336,17 +353,30 @@ dtws_status run_query(dtws_t h, const float *Qd, int m, int r, int k, int64_t *i
         ++launches;
     }
     CK(launch_seed_gather(b, a, R, P, h->opt.rng_seed, s));
-    CK(launch_dtw_seeds(b, a, s));
+    CK(launch_seed_ed(b, a, s));
+    if (k > 1) {  // exact DTW seeds tighten a k-th bound the Euclidean seeds leave loose
+        CK(launch_dtw_seeds(b, a, s));
+        ++launches;
+    }
     record(h, 1, s);
+    // the best Euclidean seed is scored on the side stream during the scan
+    if (a.prescore) {
+        CK(cudaEventRecord(h->ev_fork, s));
+        CK(cudaStreamWaitEvent(h->side, h->ev_fork, 0));
+        CK(launch_prescore(b, a, h->side));
+        CK(cudaEventRecord(h->ev_join, h->side));
+        ++launches;
+    }
     CK(launch_lb_scan(b, a, s));
     record(h, 2, s);
     CK(launch_order(b, a, s));
     record(h, 3, s);
     CK(launch_dtw_survivors(b, a, s));
     record(h, 4, s);
+    if (a.prescore) CK(cudaStreamWaitEvent(s, h->ev_join, 0));
     CK(launch_finalize(b, a, idx_d, dist_d, s));
     record(h, 5, s);
-    launches += 2 + 2 + 1 + 3 + 1 + 3;  // reset, qprep, gather, seed DTW, scan, order x3, DTW, final x3
+    launches += 2 + 2 + 1 + 3 + 1 + 3;  // reset, qprep, gather, ED seeds, scan, order x3, DTW, final x3
     h->last_stream = s;
     h->have_last = true;
     h->last_N = a.N;
@@ -365,7 +395,7 @@ void dtws_default_options(dtws_options *o) {
     o->alpha_per_m = 1e-6f;
     o->seed_random = 4;
     o->seed_proposals = 16;
-    o->proxy_terms = 8;
+    o->proxy_terms = 16;
     o->ordering = DTWS_ORDER_PLAIN;
     o->timing = 0;
     o->wait_limit_ns = 2000000000LL;
@@ -403,6 +433,9 @@ dtws_status dtws_destroy(dtws_t h) {
         if (p) cudaFree(p);
     if (h->ev_ok)
         for (auto &e : h->ev) cudaEventDestroy(e);
+    if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+    if (h->ev_join) cudaEventDestroy(h->ev_join);
+    if (h->side) cudaStreamDestroy(h->side);
     delete h;
     return DTWS_OK;
 }
@@ -434,7 +467,7 @@ dtws_status dtws_create(const float *series, int64_t n, void *stream, dtws_t *ou
     CKF(cudaGetDevice(&h->device));
     CKF(cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device));
     h->n = n;
-    h->n_alloc = round_up(n, kTile) + kMMax + 64;
+    h->n_alloc = round_up(n, kProxyTile) + kMMax + 64;
     const int64_t nb = (n + kBlockB - 1) / kBlockB;
     CKF(dalloc(&h->x, h->n_alloc));
     CKF(dalloc(&h->P1, n));
@@ -455,6 +488,9 @@ dtws_status dtws_create(const float *series, int64_t n, void *stream, dtws_t *ou
         return fail(DTWS_ENONFINITE);
     }
     CKF(launch_prefix(h->x, n, h->P1, h->P2, h->T1, h->T2, h->A, s));
+    CKF(cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking));
+    CKF(cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming));
+    CKF(cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming));
     for (auto &e : h->ev)
         if (cudaEventCreate(&e) != cudaSuccess) {
             cudaGetLastError();
@@ -689,6 +725,7 @@ static dtws_status at_prepare(dtws_t h, const float *Q, int32_t m, int32_t r, co
     if ((st = ensure_workspace(h)) != DTWS_OK) return st;
     *b = make_bufs(h, se, ee);
     *a = make_args(h, m, r, 1);
+    a->prescore = 0;
     CK(launch_query_reset(*b, *a, s));
     CK(launch_qprep(Qd, *b, *a, s));
     return DTWS_OK;

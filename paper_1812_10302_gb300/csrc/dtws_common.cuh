@@ -20,9 +20,13 @@ constexpr int kKMax = 64;
 constexpr int kListMax = 128;       // result list capacity (k + near-tie margin)
 constexpr int kSeedMax = 128;       // random seeds + proxy proposals
 constexpr int kPropMax = 64;
+constexpr int kProxyStride = 2;     // the proxy scan looks at every other window
+constexpr int kEdMax = kKMax + kPropMax * (kProxyStride + 1);
 constexpr int kTile = 1024;         // windows per lower-bound tile
+constexpr int kProxyTile = 4096;    // windows per proxy-scan tile (a multiple of kTile)
 constexpr int kStages = 4;          // shared-memory stages of the scan pipeline
 constexpr int kBins = 1024;         // survivor ordering bins
+constexpr int kDiagRMax = 511;      // widest band of the anti-diagonal DTW kernels
 constexpr uint64_t kEmptyKey = ~0ull;
 
 // status bits (device word in the handle)
@@ -42,6 +46,13 @@ struct QueryState {
     unsigned long long seed_keys[kKMax];   // k smallest seed distances
     unsigned long long res_keys[kListMax]; // smallest survivor distances
     unsigned long long prop_keys[kPropMax];// proxy-scan proposals
+    unsigned long long ed_keys[kKMax];     // k smallest squared Euclidean distances
+                                           // (upper bounds of DTW) of seed windows
+    unsigned int ed_off[kEdMax];           // windows whose Euclidean distance is taken
+    int n_ed;
+    double pre_d64;                        // re-score of the pre-scored window
+    int pre_done;
+    int margin_skip;                       // margin entries already re-scored
     unsigned int seed_off[kSeedMax];       // offsets whose DTW seeds bsf
     int n_seeds;
     int n_cand;                            // survivors of the lower bounds
@@ -65,7 +76,9 @@ struct QueryArgs {
     int list_cap;       // result list slots in use (k + margin)
     float delta, alpha; // prune when LB > bsf*(1+delta) + alpha
     float qgrid;        // key grid: a power of two <= alpha/4
+    int prescore;       // 1: the best Euclidean seed is scored on a side stream
 };
+
 
 // ---------------------------------------------------------------- keys
 __device__ __forceinline__ unsigned long long make_key(float d, unsigned int idx) {
@@ -90,18 +103,28 @@ __device__ __forceinline__ unsigned int key_idx(unsigned long long key) {
     return (unsigned)(key & 0xffffffffu);
 }
 
+// The window pre-scored on the side stream: the best Euclidean seed.
+__device__ __forceinline__ unsigned prescored_window(const QueryState *st, const QueryArgs &a) {
+    const unsigned long long k0 = st->ed_keys[0];
+    return (a.prescore && k0 != kEmptyKey) ? key_idx(k0) : 0xffffffffu;
+}
+
 // Insert a unique key into a sorted list of `cap` slots that holds the cap
 // smallest keys offered so far.  Slot j keeps the minimum of what reaches it
 // and hands the larger value on to slot j+1; since every atomicMin keeps one
 // value and emits one, slot j ends as the (j+1)-th smallest key offered,
 // whatever the interleaving.  Slots already below the key are skipped: an
 // atomicMin there would return a smaller value and emit the key unchanged.
+// A key already in the list (the same window offered twice) stops at the
+// slot that holds it, so a window never occupies two slots.
 __device__ __forceinline__ void list_insert(unsigned long long *slots, int cap,
                                             unsigned long long key) {
     for (int j = 0; j < cap && key != kEmptyKey; ++j) {
-        unsigned long long cur = *((volatile unsigned long long *)&slots[j]);
+        const unsigned long long cur = *((volatile unsigned long long *)&slots[j]);
         if (cur < key) continue;
-        unsigned long long old = atomicMin(&slots[j], key);
+        if (cur == key) return;
+        const unsigned long long old = atomicMin(&slots[j], key);
+        if (old == key) return;
         key = old > key ? old : key;
     }
 }
@@ -110,10 +133,14 @@ __device__ __forceinline__ float list_kth(const unsigned long long *slots, int k
     return key_dist(*((volatile const unsigned long long *)&slots[k - 1]));
 }
 
-// Current pruning threshold: bsf*(1+delta)+alpha, bsf = the k-th best of the
-// seeds and of the survivors found so far (+inf while fewer than k exist).
+// Current pruning threshold: bsf*(1+delta)+alpha, bsf = the smallest of the
+// k-th seed DTW, the k-th survivor DTW found so far and the k-th squared
+// Euclidean distance of the seed windows (+inf while fewer than k exist).
 __device__ __forceinline__ float current_thr(const QueryState *st, const QueryArgs &a) {
-    float b = fminf(list_kth(st->seed_keys, a.k), list_kth(st->res_keys, a.k));
+    // each list holds distinct windows, so each k-th value bounds the true
+    // k-th distance from above
+    float b = fminf(fminf(list_kth(st->seed_keys, a.k), list_kth(st->res_keys, a.k)),
+                    list_kth(st->ed_keys, a.k));
     if (!(b < __int_as_float(0x7f800000))) return __int_as_float(0x7f800000);
     return fmaf(b, 1.0f + a.delta, a.alpha);
 }

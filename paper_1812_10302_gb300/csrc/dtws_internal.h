@@ -20,7 +20,7 @@ cudaError_t launch_prefix(const float *x, int64_t n, double *P1, double *P2, dou
 cudaError_t launch_window_stats(const float *x, int64_t n, int m, const double *P1,
                                 const double *P2, const double *T1, const double *T2,
                                 const double *A, float *mu_hi, float *mu_lo, float *inv_sigma,
-                                cudaStream_t s);
+                                float *smu_hi, float *smu_lo, float *sinv_sigma, cudaStream_t s);
 cudaError_t launch_envelope(const float *x, int64_t n, int r, float *U, float *L, cudaStream_t s);
 
 // ---- query level (query_kernels.cu)
@@ -28,6 +28,7 @@ struct QueryBufs {
     QueryState *st;
     const float *x;              // padded series
     const float *mu_hi, *mu_lo, *inv_sigma;  // window stats for m
+    const float *smu_hi, *smu_lo, *sinv_sigma;  // the same for every kProxyStride-th window
     const float *U, *L;          // series envelope for r (may be null for *_at)
     float *qh32;                 // normalised query, FP32 [m]
     double *qh64;                // normalised query, FP64 [m]
@@ -47,7 +48,9 @@ cudaError_t launch_seed_scan(const QueryBufs &b, const QueryArgs &a, int proposa
                              cudaStream_t s);
 cudaError_t launch_seed_gather(const QueryBufs &b, const QueryArgs &a, int n_random,
                                int proposals, unsigned long long rng, cudaStream_t s);
+cudaError_t launch_seed_ed(const QueryBufs &b, const QueryArgs &a, cudaStream_t s);
 cudaError_t launch_dtw_seeds(const QueryBufs &b, const QueryArgs &a, cudaStream_t s);
+cudaError_t launch_prescore(const QueryBufs &b, const QueryArgs &a, cudaStream_t s);
 cudaError_t launch_lb_scan(const QueryBufs &b, const QueryArgs &a, cudaStream_t s);
 cudaError_t launch_order(const QueryBufs &b, const QueryArgs &a, cudaStream_t s);
 cudaError_t launch_dtw_survivors(const QueryBufs &b, const QueryArgs &a, cudaStream_t s);

@@ -33,6 +33,7 @@ __global__ void k_query_reset(QueryState *st) {
     for (int t = threadIdx.x; t < kListMax; t += blockDim.x) st->res_keys[t] = kEmptyKey;
     for (int t = threadIdx.x; t < kKMax; t += blockDim.x) st->seed_keys[t] = kEmptyKey;
     for (int t = threadIdx.x; t < kPropMax; t += blockDim.x) st->prop_keys[t] = kEmptyKey;
+    for (int t = threadIdx.x; t < kKMax; t += blockDim.x) st->ed_keys[t] = kEmptyKey;
     for (int t = threadIdx.x; t < kBins; t += blockDim.x) st->hist[t] = 0;
     for (int t = threadIdx.x; t < kCtrN; t += blockDim.x) st->ctr[t] = 0;
     if (threadIdx.x == 0) {
@@ -45,6 +46,9 @@ __global__ void k_query_reset(QueryState *st) {
         st->valid = 1;
         st->tile_ctr[0] = 0;
         st->tile_ctr[1] = 0;
+        st->n_ed = 0;
+        st->pre_done = 0;
+        st->margin_skip = 0;
     }
 }
 
@@ -184,6 +188,23 @@ cudaError_t launch_qprep(const float *Q, const QueryBufs &b, const QueryArgs &a,
 // held up by a rare expensive window delays only the refill of one stage.
 // Use u of a stage waits for phase u & 1 of its barriers.  The end is a stage
 // whose tile index is -1, completed without copies.
+//
+// Two stage layouts.  LbLayout: kTile windows with the statistics of every
+// window (the lower-bound scan).  ProxyLayout: kProxyTile windows with the
+// statistics of every kProxyStride-th window (the proxy scan).
+struct LbLayout {
+    static constexpr int W = kTile, S = kTile, kStride = 1;
+    __device__ static const float *mh(const QueryBufs &b) { return b.mu_hi; }
+    __device__ static const float *ml(const QueryBufs &b) { return b.mu_lo; }
+    __device__ static const float *is(const QueryBufs &b) { return b.inv_sigma; }
+};
+struct ProxyLayout {
+    static constexpr int W = kProxyTile, S = kProxyTile / kProxyStride, kStride = kProxyStride;
+    __device__ static const float *mh(const QueryBufs &b) { return b.smu_hi; }
+    __device__ static const float *ml(const QueryBufs &b) { return b.smu_lo; }
+    __device__ static const float *is(const QueryBufs &b) { return b.sinv_sigma; }
+};
+
 struct Tile {
     float *xs, *mh, *ml, *is;
     uint64_t *full, *empty;
@@ -192,33 +213,38 @@ struct Tile {
 
 constexpr int kStageHeader = 32;  // full, empty barriers and the tile index
 
+template <class LY>
 __host__ __device__ __forceinline__ unsigned tile_x_floats(int m) {
-    return (unsigned)((kTile + m - 1 + 3) & ~3);
+    return (unsigned)((LY::W + m - 1 + 3) & ~3);
 }
+template <class LY>
 __host__ __device__ __forceinline__ size_t stage_bytes(int m) {
-    return kStageHeader + (size_t)3 * kTile * 4 + (size_t)tile_x_floats(m) * 4;
+    return kStageHeader + (size_t)3 * LY::S * 4 + (size_t)tile_x_floats<LY>(m) * 4;
 }
 
+template <class LY>
 __device__ __forceinline__ Tile carve_stage(unsigned char *sm, int m, int stage) {
     Tile t;
-    unsigned char *base = sm + stage * stage_bytes(m);
+    unsigned char *base = sm + stage * stage_bytes<LY>(m);
     t.full = (uint64_t *)base;
     t.empty = (uint64_t *)(base + 8);
     t.tile = (long long *)(base + 16);
     t.mh = (float *)(base + kStageHeader);
-    t.ml = t.mh + kTile;
-    t.is = t.ml + kTile;
-    t.xs = t.is + kTile;
+    t.ml = t.mh + LY::S;
+    t.is = t.ml + LY::S;
+    t.xs = t.is + LY::S;
     return t;
 }
 
+template <class LY>
 __device__ __forceinline__ void issue_tile(const Tile &t, const QueryBufs &b, int64_t i0, int m) {
-    const unsigned xb = tile_x_floats(m) * 4u;
-    mbar_arrive_expect_tx(t.full, xb + 3u * kTile * 4u);
+    const unsigned xb = tile_x_floats<LY>(m) * 4u, sb = LY::S * 4u;
+    const int64_t s0 = i0 / LY::kStride;
+    mbar_arrive_expect_tx(t.full, xb + 3u * sb);
     bulk_g2s(t.xs, b.x + i0, xb, t.full);
-    bulk_g2s(t.mh, b.mu_hi + i0, kTile * 4u, t.full);
-    bulk_g2s(t.ml, b.mu_lo + i0, kTile * 4u, t.full);
-    bulk_g2s(t.is, b.inv_sigma + i0, kTile * 4u, t.full);
+    bulk_g2s(t.mh, LY::mh(b) + s0, sb, t.full);
+    bulk_g2s(t.ml, LY::ml(b) + s0, sb, t.full);
+    bulk_g2s(t.is, LY::is(b) + s0, sb, t.full);
 }
 
 constexpr int kScanConsumers = 8;                       // consumer warps
@@ -227,13 +253,13 @@ constexpr int kScanThreads = (kScanConsumers + 1) * 32;  // + one producer warp
 // Runs process(tile, i0) in every consumer warp for each tile this CTA takes
 // from *cursor.  A wait that runs past the bound records DTWS_ETIMEOUT and
 // ends the loop for that warp (the other warps' waits then run out too).
-template <typename F>
+template <class LY, typename F>
 __device__ void tile_pipeline(unsigned char *sm, const QueryBufs &b, int m, int64_t ntiles,
                               unsigned long long *cursor, F &&process) {
     const int warp = threadIdx.x >> 5, lane = lane_id();
     if (threadIdx.x == 0) {
         for (int q = 0; q < kStages; ++q) {
-            const Tile t = carve_stage(sm, m, q);
+            const Tile t = carve_stage<LY>(sm, m, q);
             mbar_init(t.full, 1);
             mbar_init(t.empty, kScanConsumers);
         }
@@ -245,7 +271,7 @@ __device__ void tile_pipeline(unsigned char *sm, const QueryBufs &b, int m, int6
         if (lane == 0) {
             int64_t u = 0;
             for (;; ++u) {
-                const Tile t = carve_stage(sm, m, (int)(u % kStages));
+                const Tile t = carve_stage<LY>(sm, m, (int)(u % kStages));
                 if (u >= kStages &&
                     !mbar_wait_bounded(t.empty, (unsigned)(((u / kStages) - 1) & 1), b.wait_ns)) {
                     ok = false;
@@ -258,7 +284,7 @@ __device__ void tile_pipeline(unsigned char *sm, const QueryBufs &b, int m, int6
                     break;
                 }
                 *t.tile = tile;
-                issue_tile(t, b, tile * kTile, m);
+                issue_tile<LY>(t, b, tile * LY::W, m);
             }
             // On the normal path every issued copy is observed landing by the
             // consumers before they reach the end marker.  After a timeout,
@@ -266,19 +292,19 @@ __device__ void tile_pipeline(unsigned char *sm, const QueryBufs &b, int m, int6
             // use u-S was confirmed released) land before the CTA leaves.
             if (!ok)
                 for (int64_t v = u - kStages + 1 > 0 ? u - kStages + 1 : 0; v < u; ++v)
-                    mbar_wait_bounded(carve_stage(sm, m, (int)(v % kStages)).full,
+                    mbar_wait_bounded(carve_stage<LY>(sm, m, (int)(v % kStages)).full,
                                       (unsigned)((v / kStages) & 1), b.wait_ns);
         }
     } else {
         for (int64_t j = 0;; ++j) {
-            const Tile t = carve_stage(sm, m, (int)(j % kStages));
+            const Tile t = carve_stage<LY>(sm, m, (int)(j % kStages));
             if (!mbar_wait_bounded(t.full, (unsigned)((j / kStages) & 1), b.wait_ns)) {
                 ok = false;
                 break;
             }
             const long long tile = *(volatile long long *)t.tile;
             if (tile < 0) break;
-            process(t, (int64_t)tile * kTile);
+            process(t, (int64_t)tile * LY::W);
             __syncwarp();
             if (lane == 0) mbar_arrive(t.empty);
         }
@@ -296,10 +322,16 @@ static int scan_grid(const void *kernel, int threads, size_t smem, int num_sms, 
 }
 
 // ------------------------------------------------------------------ proxy scan
-// Per window: the squared distance on the TERMS query positions of largest
-// |q_hat| (not a lower bound: it only proposes windows whose exact DTW seeds
-// the best-so-far).  Each thread keeps its best window over all the tiles it
-// scans; each CTA proposes its best.
+// For every other window: the squared distance on TERMS evenly spaced query
+// positions (not a lower bound: it only proposes windows whose exact
+// distances seed the best-so-far).  Spread-out positions make the terms
+// nearly independent, so a random window scores near 2*TERMS while a window
+// within a sample of a noisy copy scores far lower.  Each thread keeps its best window over
+// all the tiles it scans; each CTA proposes its best.  Reading the
+// statistics of one window in two cuts the scan's traffic from 16 to 10
+// bytes per window; the seed step then covers the neighbours of each
+// proposal.  (With one window in eight, a window four samples off a match
+// scored no better than lucky random windows and matches were lost.)
 template <int TERMS>
 __global__ void __launch_bounds__(kScanThreads) k_seed_scan(QueryBufs b, QueryArgs a, int proposals) {
     extern __shared__ __align__(16) unsigned char smraw[];
@@ -310,16 +342,17 @@ __global__ void __launch_bounds__(kScanThreads) k_seed_scan(QueryBufs b, QueryAr
     float qv[TERMS];
 #pragma unroll
     for (int u = 0; u < TERMS; ++u) {
-        pos[u] = (int)b.ord[u];
-        qv[u] = b.sq[u];
+        pos[u] = (int)(((2 * u + 1) * (long long)m) / (2 * TERMS));
+        qv[u] = b.qh32[pos[u]];
     }
     unsigned long long best = kEmptyKey;
-    const int64_t ntiles = (a.N + kTile - 1) / kTile;
-    tile_pipeline(smraw, b, m, ntiles, &b.st->tile_ctr[0], [&](const Tile &t, int64_t i0) {
-        for (int w = threadIdx.x; w < kTile; w += kScanConsumers * 32) {
+    const int64_t ntiles = (a.N + ProxyLayout::W - 1) / ProxyLayout::W;
+    tile_pipeline<ProxyLayout>(smraw, b, m, ntiles, &b.st->tile_ctr[0], [&](const Tile &t, int64_t i0) {
+        for (int v = threadIdx.x; v < ProxyLayout::S; v += kScanConsumers * 32) {
+            const int w = v * kProxyStride;
             const int64_t i = i0 + w;
             if (i >= a.N) break;
-            const float mh = t.mh[w], is = t.is[w], ls = t.ml[w] * is;
+            const float mh = t.mh[v], is = t.is[v], ls = t.ml[v] * is;
             float acc = 0.0f;
 #pragma unroll
             for (int u = 0; u < TERMS; ++u) {
@@ -348,10 +381,10 @@ __global__ void __launch_bounds__(kScanThreads) k_seed_scan(QueryBufs b, QueryAr
 
 template <int TERMS>
 static cudaError_t launch_seed_scan_t(const QueryBufs &b, const QueryArgs &a, int proposals, cudaStream_t s) {
-    const size_t smem = kStages * stage_bytes(a.m);
+    const size_t smem = kStages * stage_bytes<ProxyLayout>(a.m);
     cudaError_t e = cudaFuncSetAttribute(k_seed_scan<TERMS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    const int64_t tiles = (a.N + kTile - 1) / kTile;
+    const int64_t tiles = (a.N + ProxyLayout::W - 1) / ProxyLayout::W;
     const int grid = scan_grid((const void *)k_seed_scan<TERMS>, kScanThreads, smem, b.num_sms, tiles);
     k_seed_scan<TERMS><<<grid, kScanThreads, smem, s>>>(b, a, proposals);
     return cudaGetLastError();
@@ -376,43 +409,94 @@ __device__ __forceinline__ unsigned long long splitmix64(unsigned long long z) {
     return z ^ (z >> 31);
 }
 
+// Seed windows.  seed_off (exact DTW seeds, used when k > 1): the random
+// windows (the paper's random first bsf, Algorithm 1) and the proposals.
+// ed_off (Euclidean seeds): the random windows and, for each proposal, the
+// kProxyStride + 1 windows centred on it, since the proxy scan looked at
+// every kProxyStride-th window only.  Both lists hold distinct offsets: a repeated seed
+// would fill two of the k slots with one window.
+__device__ int distinct_append(unsigned *dst, int cap, const unsigned *src, int n, int lane, int *count) {
+    for (int base = 0; base < n; base += 32) {
+        const int t = base + lane;
+        bool keep = false;
+        if (t < n && src[t] != 0xffffffffu) {
+            keep = true;
+            for (int u = 0; u < t; ++u) keep &= src[u] != src[t];
+        }
+        const unsigned bal = __ballot_sync(0xffffffffu, keep);
+        const int pos = *count + __popc(bal & ((1u << lane) - 1u));
+        if (keep && pos < cap) dst[pos] = src[t];
+        __syncwarp();
+        if (lane == 0) *count += __popc(bal);
+        __syncwarp();
+    }
+    return *count < cap ? *count : cap;
+}
+
 __global__ void k_seed_gather(QueryBufs b, QueryArgs a, int n_random, int proposals,
                               unsigned long long rng) {
-    // distinct offsets only: a repeated seed would fill two of the k seed
-    // slots with one window and understate the k-th seed distance
-    __shared__ unsigned cand[2 * kPropMax];
+    __shared__ unsigned cand[kEdMax];
     __shared__ int nc;
     if (!b.st->valid) return;
     const int lane = threadIdx.x;  // one warp
-    if (lane == 0) nc = 0;
-    __syncwarp();
+    constexpr int H = kProxyStride / 2;
+    // exact-DTW seeds: random windows + proposals
     for (int j = lane; j < n_random; j += 32)
         cand[j] = (unsigned)(splitmix64(rng + (unsigned long long)j) % (unsigned long long)a.N);
     for (int p = lane; p < proposals; p += 32) {
         const unsigned long long key = b.st->prop_keys[p];
         cand[n_random + p] = key != kEmptyKey ? key_idx(key) : 0xffffffffu;
     }
+    if (lane == 0) nc = 0;
     __syncwarp();
-    const int total = n_random + proposals;
-    // keep candidate t if it is valid and no earlier candidate equals it
-    for (int base = 0; base < total; base += 32) {
-        const int t = base + lane;
-        bool keep = false;
-        if (t < total && cand[t] != 0xffffffffu) {
-            keep = true;
-            for (int u = 0; u < t; ++u) keep &= cand[u] != cand[t];
+    const int ns = distinct_append(b.st->seed_off, kSeedMax, cand, n_random + proposals, lane, &nc);
+    // Euclidean seeds: random windows + neighbourhoods of the proposals
+    for (int p = lane; p < proposals; p += 32) {
+        const unsigned long long key = b.st->prop_keys[p];
+        for (int d = -H; d <= H; ++d) {
+            unsigned o = 0xffffffffu;
+            if (key != kEmptyKey) {
+                const long long v = (long long)key_idx(key) + d;
+                if (v >= 0 && v < a.N) o = (unsigned)v;
+            }
+            cand[n_random + p * (2 * H + 1) + (d + H)] = o;
         }
-        const unsigned bal = __ballot_sync(0xffffffffu, keep);
-        const int pos = nc + __popc(bal & ((1u << lane) - 1u));
-        if (keep && pos < kSeedMax) b.st->seed_off[pos] = cand[t];
-        __syncwarp();
-        if (lane == 0) nc += __popc(bal);
-        __syncwarp();
     }
+    __syncwarp();
+    if (lane == 0) nc = 0;
+    __syncwarp();
+    const int ne = distinct_append(b.st->ed_off, kEdMax, cand, n_random + proposals * (2 * H + 1), lane, &nc);
     if (lane == 0) {
-        b.st->n_seeds = nc < kSeedMax ? nc : kSeedMax;
+        b.st->n_seeds = a.k > 1 ? ns : 0;  // exact seeds only pay off for k > 1
+        b.st->n_ed = ne;
         b.st->work = 0;
     }
+}
+
+// Squared Euclidean distance of the normalised query and window (the
+// diagonal warping path, so an upper bound of the banded DTW, Eq. 4) for
+// every Euclidean seed, one warp each; the k smallest go to ed_keys.
+__global__ void k_seed_ed(QueryBufs b, QueryArgs a) {
+    QueryState *st = b.st;
+    if (!st->valid) return;
+    const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = lane_id();
+    if (w >= st->n_ed) return;
+    const unsigned idx = st->ed_off[w];
+    const float mh = b.mu_hi[idx], is = b.inv_sigma[idx], ls = b.mu_lo[idx] * is;
+    const float *xw = b.x + idx;
+    float acc = 0.0f;
+    for (int j = lane; j < a.m; j += 32) {
+        const float d = b.qh32[j] - fmaf(xw[j] - mh, is, -ls);
+        acc = fmaf(d, d, acc);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) list_insert(st->ed_keys, a.k, make_key(key_quantize(acc, a.qgrid), idx));
+}
+
+cudaError_t launch_seed_ed(const QueryBufs &b, const QueryArgs &a, cudaStream_t s) {
+    k_seed_ed<<<(kEdMax * 32 + 255) / 256, 256, 0, s>>>(b, a);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_seed_gather(const QueryBufs &b, const QueryArgs &a, int n_random, int proposals,
@@ -499,6 +583,7 @@ __global__ void __launch_bounds__(256) k_dtw(QueryBufs b, QueryArgs a, const int
     }
     __syncthreads();
     int *cursor = MODE == kModeSurv ? &st->work2 : &st->work;
+    const unsigned pre = MODE == kModeSurv ? prescored_window(st, a) : 0xffffffffu;
     const int64_t count = MODE == kModeSeed ? (int64_t)st->n_seeds
                         : MODE == kModeSurv ? (int64_t)st->n_cand : count_host;
     long long cells_acc = 0;
@@ -532,7 +617,8 @@ __global__ void __launch_bounds__(256) k_dtw(QueryBufs b, QueryArgs a, const int
         thr = __shfl_sync(gmask, thr, 0, L);
         if (MODE == kModeSurv && lb > thr) continue;
         if (MODE == kModeSurv) {
-            bool seen = false;
+            // scored already: by the seed pass or on the side stream
+            bool seen = idx == pre;
             for (int t = lane; t < n_seeds_s; t += L) seen |= seeds_s[t] == idx;
             if (__any_sync(gmask, seen)) continue;
         }
@@ -646,6 +732,7 @@ __global__ void __launch_bounds__(256) k_dtw64(QueryBufs b, QueryArgs a, const i
     __syncthreads();
     const int64_t count = offsets ? count_host : (int64_t)st->n_margin;
     __shared__ double bc[2 * 8 * 32];  // per group: mu, 1/sigma
+    // (the margin list's first margin_skip entries were re-scored already)
     while (true) {
         int c = 0;
         if (lane == 0) c = atomicAdd(&st->work, 1);
@@ -868,7 +955,7 @@ __global__ void __launch_bounds__(kScanThreads) k_lb_scan(QueryBufs b, QueryArgs
     }
     unsigned long long c1 = 0, c2 = 0;
     const int64_t ntiles = (a.N + kTile - 1) / kTile;
-    tile_pipeline(smraw, b, m, ntiles, &st->tile_ctr[1], [&](const Tile &t, int64_t i0) {
+    tile_pipeline<LbLayout>(smraw, b, m, ntiles, &st->tile_ctr[1], [&](const Tile &t, int64_t i0) {
 #pragma unroll 1
         for (int u = 0; u < kPerWarp / 32; ++u) {
             const int w = warp * kPerWarp + u * 32 + lane;
@@ -921,7 +1008,7 @@ __global__ void __launch_bounds__(kScanThreads) k_lb_scan(QueryBufs b, QueryArgs
 }
 
 cudaError_t launch_lb_scan(const QueryBufs &b, const QueryArgs &a, cudaStream_t s) {
-    const size_t smem = kStages * stage_bytes(a.m);
+    const size_t smem = kStages * stage_bytes<LbLayout>(a.m);
     cudaError_t e = cudaFuncSetAttribute(k_lb_scan, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     const int64_t tiles = (a.N + kTile - 1) / kTile;
@@ -1005,19 +1092,123 @@ __global__ void k_final_select(QueryBufs b, QueryArgs a) {
     QueryState *st = b.st;
     if (threadIdx.x != 0) return;
     st->work = 0;
+    st->margin_skip = 0;
     if (!st->valid) { st->n_margin = 0; return; }
     int count = 0;
     while (count < a.list_cap && st->res_keys[count] != kEmptyKey) ++count;
     if (count == 0) { st->n_margin = 0; return; }
     const float dk = key_dist(st->res_keys[(count < a.k ? count : a.k) - 1]);
     const float lim = fmaf(dk, 1.0f + a.delta, a.alpha);
+    // the pre-scored window (side stream) goes first with its re-score
+    const unsigned pre = st->pre_done ? prescored_window(st, a) : 0xffffffffu;
     int nm = 0;
+    for (int j = 0; j < count; ++j)
+        if (key_dist(st->res_keys[j]) <= lim && key_idx(st->res_keys[j]) == pre) {
+            st->margin_idx[nm] = pre;
+            st->margin_d64[nm++] = st->pre_d64;
+        }
+    st->margin_skip = nm;
+    st->work = nm;
     for (int j = 0; j < count; ++j) {
-        if (key_dist(st->res_keys[j]) <= lim) st->margin_idx[nm++] = key_idx(st->res_keys[j]);
+        const unsigned idx = key_idx(st->res_keys[j]);
+        if (key_dist(st->res_keys[j]) <= lim && idx != pre) st->margin_idx[nm++] = idx;
     }
     if (count == a.list_cap && key_dist(st->res_keys[count - 1]) <= lim) atomicOr(b.status, kStOverflow);
     st->n_margin = nm;
     st->ctr[kCtrRescored] = (unsigned long long)nm;
+}
+
+// Pre-score of the best Euclidean seed, run on a side stream while the
+// lower-bound scan streams: its FP32 DTW enters the result list (the survivor
+// pass skips it) and its extended-precision re-score waits for the final
+// stage.  One group of L lanes.
+template <int L, int K>
+__global__ void k_prescore(QueryBufs b, QueryArgs a) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    __shared__ double bc[2];
+    QueryState *st = b.st;
+    if (!st->valid) return;
+    const unsigned idx = prescored_window(st, a);
+    const int lane = threadIdx.x;
+    if (idx == 0xffffffffu || lane >= L) return;
+    const unsigned gmask = (L == 32) ? 0xffffffffu : ((1u << L) - 1u);
+    const int m = a.m, r = a.r, pad = diag_pad(r, L, K);
+    const size_t span = (size_t)((m + 2 * pad + 3) & ~3);
+    const float *xw = b.x + idx;
+    // FP32 DTW, as the survivor pass would compute it
+    float *q32 = (float *)smraw, *c32 = (float *)(smraw + span * 8);
+    const float INF = __int_as_float(0x7f800000);
+    fill_pads(q32, m, pad, INF, lane, L);
+    fill_pads(c32, m, pad, -INF, lane, L);
+    const float mh = b.mu_hi[idx], is = b.inv_sigma[idx], ls = b.mu_lo[idx] * is;
+    for (int j = lane; j < m; j += L) {
+        q32[pad + j] = b.qh32[j];
+        c32[pad + j] = fmaf(xw[j] - mh, is, -ls);
+    }
+    __syncwarp(gmask);
+    int cells = 0;
+    const float d32 = dtw_diag<float, L, K, false>(q32 + pad, c32 + pad, nullptr, m, r, INF, gmask, lane, cells);
+    if (lane == 0) {
+        list_insert(st->res_keys, a.list_cap, make_key(key_quantize(d32, a.qgrid), idx));
+        atomicAdd(&st->ctr[kCtrDtwStarted], 1ull);
+        atomicAdd(&st->ctr[kCtrCells], (unsigned long long)cells);
+    }
+    __syncwarp(gmask);
+    // extended-precision re-score (FP64 statistics, double-float DTW)
+    double s = 0.0;
+    for (int j = lane; j < m; j += L) s += (double)xw[j];
+#pragma unroll
+    for (int o = L / 2; o > 0; o >>= 1) s += __shfl_xor_sync(gmask, s, o, L);
+    if (lane == 0) bc[0] = s / (double)m;
+    __syncwarp(gmask);
+    const double mu = bc[0];
+    double v = 0.0;
+    for (int j = lane; j < m; j += L) {
+        const double d = (double)xw[j] - mu;
+        v = fma(d, d, v);
+    }
+#pragma unroll
+    for (int o = L / 2; o > 0; o >>= 1) v += __shfl_xor_sync(gmask, v, o, L);
+    if (lane == 0) {
+        const double var = v / (double)m, mm = mu * mu;
+        bc[1] = var <= 1e-24 * (mm > 1.0 ? mm : 1.0) ? 0.0 : 1.0 / sqrt(var);
+    }
+    __syncwarp(gmask);
+    const double inv = bc[1];
+    dfloat *qd = (dfloat *)smraw, *cd = (dfloat *)(smraw + span * 8);
+    fill_pads(qd, m, pad, dfloat{1e15f, 0.0f}, lane, L);
+    fill_pads(cd, m, pad, dfloat{-1e15f, 0.0f}, lane, L);
+    for (int j = lane; j < m; j += L) {
+        qd[pad + j] = df_from(b.qh64[j]);
+        cd[pad + j] = df_from(((double)xw[j] - mu) * inv);
+    }
+    __syncwarp(gmask);
+    const double d64 = dtw_diag_df<L, K>(qd + pad, cd + pad, m, r, gmask, lane);
+    if (lane == 0) {
+        st->pre_d64 = d64;
+        __threadfence();
+        st->pre_done = 1;
+    }
+}
+
+cudaError_t launch_prescore(const QueryBufs &b, const QueryArgs &a, cudaStream_t s) {
+    if (!a.prescore) return cudaSuccess;
+    int L, K;
+    diag_shape(a.r, &L, &K);
+    const int pad = diag_pad(a.r, L, K);
+    const size_t smem = (size_t)((a.m + 2 * pad + 3) & ~3) * 16;
+#define DTWS_CASE(LL, KK)                                                                           \
+    if (L == LL && K == KK) {                                                                       \
+        cudaError_t e = cudaFuncSetAttribute(k_prescore<LL, KK>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                                             (int)smem);                                            \
+        if (e != cudaSuccess) return e;                                                             \
+        k_prescore<LL, KK><<<1, 32, smem, s>>>(b, a);                                               \
+        return cudaGetLastError();                                                                  \
+    }
+    DTWS_CASE(1, 1) DTWS_CASE(2, 1) DTWS_CASE(4, 1) DTWS_CASE(8, 1) DTWS_CASE(16, 1)
+    DTWS_CASE(32, 1) DTWS_CASE(32, 2) DTWS_CASE(32, 4) DTWS_CASE(32, 8) DTWS_CASE(32, 16)
+#undef DTWS_CASE
+    return cudaErrorInvalidValue;
 }
 
 __global__ void k_final_sort(QueryBufs b, QueryArgs a, int64_t *out_idx, float *out_dist) {

@@ -97,7 +97,9 @@ __global__ void k_window_stats(const float *__restrict__ x, int64_t n, int m,
                                const double *__restrict__ P1, const double *__restrict__ P2,
                                const double *__restrict__ T1, const double *__restrict__ T2,
                                const double *__restrict__ A, float *__restrict__ mu_hi,
-                               float *__restrict__ mu_lo, float *__restrict__ inv_sigma) {
+                               float *__restrict__ mu_lo, float *__restrict__ inv_sigma,
+                               float *__restrict__ smu_hi, float *__restrict__ smu_lo,
+                               float *__restrict__ sinv_sigma) {
     const int64_t N = n - m + 1;
     const double inv_m = 1.0 / (double)m;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N;
@@ -137,17 +139,22 @@ __global__ void k_window_stats(const float *__restrict__ x, int64_t n, int m,
             }
             var = v / (double)m;
         }
-        float mh = (float)mu;
-        mu_hi[i] = mh;
-        mu_lo[i] = (float)(mu - (double)mh);
-        double mm = mu * mu;
-        if (var <= 1e-24 * (mm > 1.0 ? mm : 1.0)) {
-            inv_sigma[i] = 0.0f;
-        } else {
+        const float mh = (float)mu, ml = (float)(mu - (double)mh);
+        const double mm = mu * mu;
+        float is = 0.0f;
+        if (!(var <= 1e-24 * (mm > 1.0 ? mm : 1.0))) {
             // 1/sqrt(var): FP32 estimate refined by one Newton step in FP64
             double y = (double)rsqrtf((float)var);
             y = y * fma(-0.5 * var * y, y, 1.5);
-            inv_sigma[i] = (float)y;
+            is = (float)y;
+        }
+        mu_hi[i] = mh;
+        mu_lo[i] = ml;
+        inv_sigma[i] = is;
+        if ((i & (kProxyStride - 1)) == 0) {  // every kProxyStride-th window, for the proxy scan
+            smu_hi[i / kProxyStride] = mh;
+            smu_lo[i / kProxyStride] = ml;
+            sinv_sigma[i / kProxyStride] = is;
         }
     }
 }
@@ -155,12 +162,12 @@ __global__ void k_window_stats(const float *__restrict__ x, int64_t n, int m,
 cudaError_t launch_window_stats(const float *x, int64_t n, int m, const double *P1,
                                 const double *P2, const double *T1, const double *T2,
                                 const double *A, float *mu_hi, float *mu_lo, float *inv_sigma,
-                                cudaStream_t s) {
+                                float *smu_hi, float *smu_lo, float *sinv_sigma, cudaStream_t s) {
     int64_t N = n - m + 1;
     int64_t blocks = (N + 255) / 256;
     if (blocks > 152 * 32) blocks = 152 * 32;
     k_window_stats<<<(unsigned)blocks, 256, 0, s>>>(x, n, m, P1, P2, T1, T2, A, mu_hi, mu_lo,
-                                                    inv_sigma);
+                                                    inv_sigma, smu_hi, smu_lo, sinv_sigma);
     return cudaGetLastError();
 }
 

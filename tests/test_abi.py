@@ -54,7 +54,7 @@ def test_default_options_and_strerror(lib):
     o = dtws.dtws_default_options()
     assert o.delta == pytest.approx(2.0 ** -10)
     assert o.alpha_per_m == pytest.approx(1e-6)
-    assert o.seed_random == 4 and o.seed_proposals == 16 and o.proxy_terms == 8
+    assert o.seed_random == 4 and o.seed_proposals == 16 and o.proxy_terms == 16
     assert o.wait_limit_ns == 2_000_000_000
     assert dtws.strerror(dtws.DTWS_EINVAL) == "invalid argument"
     assert dtws.strerror(dtws.DTWS_EOVERFLOW).startswith("more near-ties")

@@ -206,3 +206,17 @@ def test_long_scan_reports_no_device_error():
     lo = max(0, o - 50_000)
     oi, od = oracle.search_cascade(x[lo:o + 50_000 + 256], q, 25, 1)
     assert idx[0] == o or dist[0] <= od[0] * (1 + 1e-6)
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2, 3])
+def test_seeding_keeps_the_scan_tight(seed):
+    """For a noisy copy the seeds must give a threshold close to the answer,
+    so that LB_KimFL already drops nearly every window (performance
+    regression guard: correctness never depends on it)."""
+    x = synth.walk_with_bursts(3_000_000, 10 + seed, 20 + seed, 30 + seed)
+    q, o = synth.noisy_copy(x, 512, 40 + seed, 50 + seed, noise=0.1)
+    with dtws.Index(x) as ix:
+        idx, dist = ix.query(q, 51, 1)
+        s = ix.last_stats()
+    assert s["pass_kim"] < 0.05 * s["windows"], s
+    assert idx[0] == o or dist[0] <= oracle.dtw_at(x, q, 51, [o])[0]

@@ -54,6 +54,12 @@ def cells(m: int, r: int) -> int:
     return m * (2 * r + 1) - r * (r + 1)
 
 
+# DRAM bytes (read + write) per window of k_lb_scan, from one ncu --set full capture of the
+# current kernel on the n=3e7, m=512, r=51 case (483.48 MB over 29,999,489 windows); the bytes
+# are dominated by the 16 B read per window, so they scale with the window count.
+LB_SCAN_DRAM_BYTES_PER_WINDOW = 483.48e6 / 29_999_489
+
+
 def load_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -160,7 +166,10 @@ def reference_arm(args):
     if rank != 0:
         return 0
     x, q, r, k, o = make_workload(args.workload)
-    budget = args.cpu_windows
+    # size each step so that the whole warm-up + timed run takes about 150 s of host time
+    probe = cpu_oracle_sample(x, q, r, k, o, 1_000_000)
+    rate = 1_000_000 / probe["seconds"]
+    budget = int(min(args.cpu_windows, max(1_000_000, rate * 150.0 / (args.warmup + args.steps))))
     times = []
     res = None
     for s in range(args.warmup + args.steps):
@@ -334,7 +343,7 @@ def gpu_arm(args):
                    "merged": best_key},
         "roofline": {"kernel": "k_lb_scan", "bound": "hbm", "achieved": achieved, "peak": hbm,
                      "unit": "GB/s", "frac": (achieved / hbm) if achieved else None,
-                     "traffic": None, "peak_source": peak_kind,
+                     "traffic": LB_SCAN_DRAM_BYTES_PER_WINDOW * N, "peak_source": peak_kind,
                      "algorithmic_bytes_per_launch": lb_bytes},
         "clocks": clocks,
         "gpu_launches": launches,
@@ -358,7 +367,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="dtws", choices=["dtws", "reference"])
     ap.add_argument("--workload", default="rw100m", choices=sorted(SPECS))
-    ap.add_argument("--cpu-windows", type=int, default=4_000_000,
+    ap.add_argument("--cpu-windows", type=int, default=20_000_000,
                     help="windows in the CPU oracle's bounded sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()

@@ -63,7 +63,9 @@ typedef enum {
     DTWS_ORDER_PLAIN = 0,   /* DTW of a few seeded random windows (the
                                paper's random first bsf, Algorithm 1) plus the
                                best windows of a cheap proxy scan */
-    DTWS_ORDER_LEARNED = 1  /* reserved for the learned proposal encoder */
+    DTWS_ORDER_LEARNED = 1  /* DTW of the random seed windows plus the best
+                               windows of a scan of learned embeddings (see
+                               dtws_set_encoder; needs an encoder and m >= 64) */
 } dtws_ordering;
 
 typedef struct {
@@ -75,13 +77,28 @@ typedef struct {
                                top-k window */
     float alpha_per_m;      /* absolute margin per query sample, default 1e-6 */
     int32_t seed_random;    /* random seed windows, default 4 (0..64) */
-    int32_t seed_proposals; /* proxy-scan proposals, default 16 (0..64) */
+    int32_t seed_proposals; /* proposals of the proxy (or learned) scan,
+                               default 16 (0..64; at most 16 when learned) */
     int32_t proxy_terms;    /* evenly spaced query positions in the proxy
                                distance: 16, 8, 4 (other values round down to
                                one of them, or 2), default 16 */
     int32_t ordering;       /* dtws_ordering, default DTWS_ORDER_PLAIN */
     int32_t timing;         /* 1: record per-phase CUDA events (small cost) */
-    int32_t reserved0;
+    int32_t exact_envelope; /* 1 (default): Eq. 10 uses the exact series
+                               envelope for r, computed once per r and
+                               cached; 0: a per-series block envelope (max /
+                               min over 16-sample blocks covering
+                               [t-r, t+r], built at dtws_create) -- slightly
+                               looser, so a few more windows reach DTW, but no
+                               per-r pass; an exact envelope already cached
+                               is still used.  The answer is the same. */
+    int32_t batch_lanes;    /* dtws_query_batch: queries in flight at once, each
+                               lane with its own buffers and streams (1..16,
+                               default 4; fewer when memory is short) */
+    int32_t batch_graph;    /* 1 (default): dtws_query_batch captures the batch
+                               into a CUDA graph once and replays it for later
+                               calls with the same arguments (not with the
+                               learned ordering) */
     int64_t wait_limit_ns;  /* bound on every device-side wait, default 2e9 */
     uint64_t rng_seed;      /* seed of the random seed windows, default 0 */
 } dtws_options;
@@ -103,7 +120,9 @@ typedef struct {
     int64_t dtw_abandoned;    /* ... abandoned early */
     int64_t dtw_cells;        /* band cells evaluated by the FP32 DTW */
     int64_t rescored;         /* candidates re-scored in extended precision */
-    float seed_bsf;           /* smallest seed distance (inf if no seed) */
+    float seed_bsf;           /* smallest seed distance: DTW of a seed window or
+                                 the Euclidean distance (an upper bound of the
+                                 DTW) of one; inf if no seed */
     float phase_ms[8];        /* valid when options.timing == 1 */
     int64_t kernel_launches;  /* kernels this library launched for the query */
 } dtws_query_stats;
@@ -218,6 +237,91 @@ dtws_status dtws_dtw_at_f64(dtws_t h, const float *Q, int32_t m, int32_t r,
 dtws_status dtws_lower_bounds_at(dtws_t h, const float *Q, int32_t m, int32_t r,
                                  const int64_t *offsets, int64_t count, float *kim,
                                  float *keogh_q, float *keogh_s, void *stream);
+
+/* ---- learned proposals (the paper has no learned component) ----
+ *
+ * An encoder e(.) maps a window of length m to 64 numbers; windows whose
+ * embeddings lie close to the query's are proposed as seeds of the
+ * best-so-far (as the paper's random first bsf, Algorithm 1).  Pruning never
+ * uses it, so the answer of dtws_query is the same with or without it.
+ *
+ * Encoder input of a window y: b = floor(m/64), the block means a_j of
+ * y[j*b, (j+1)*b) for j < 64, and u_j = (a_{j+1} - a_j) / sigma(y) for j < 63,
+ * sigma the population deviation of all m samples (Eq. 5); u = 0 when sigma
+ * is 0.  Network: conv 1->32, 32->32, 32->32, 32->32 channels, kernel 7,
+ * valid, no biases, ReLU after the first three; mean over 8 position segments
+ * [floor(39 s/8), floor(39 (s+1)/8)); e = P g, P [64][256].  With no biases
+ * e(u/sigma) = e(u)/sigma exactly, so the library embeds every window at
+ * offsets that are multiples of b from one series-wide pass.
+ * Parameters: FP32 [DTWS_ENC_PARAMS] = W1 [32][7], W2..W4 [32][7][32]
+ * ([out][tap][in]), P [64][256] (column s*32 + channel).  The GPU keeps an
+ * FP32 master copy and computes with BF16 weights and activations and FP32
+ * accumulation (tensor cores).  Training loss of a triple (Q, C, y),
+ * y = DTW(Q^, C^)/m: (log(|e(Q) - e(C)|^2 + 1e-3) - log(y + 1e-3))^2, mean
+ * over the batch.
+ *
+ * Arrays marked "host or device" may be either; the others are stated.
+ */
+#define DTWS_ENC_PARAMS 38112
+#define DTWS_ENC_DIM 64
+#define DTWS_ENC_U 64   /* a row of u: the 63 inputs and one unused slot */
+
+/* Install encoder parameters (host or device FP32 [count], count must be
+   DTWS_ENC_PARAMS; copied) on the handle; enables DTWS_ORDER_LEARNED and
+   drops embeddings made with earlier parameters.  Synchronises `stream`.
+   Errors: DTWS_EINVAL (count, null), DTWS_ENOMEM, DTWS_ECUDA. */
+dtws_status dtws_set_encoder(dtws_t h, const float *params, int32_t count, void *stream);
+
+/* The handle's embeddings for query length m: rows = floor((n-m)/b) + 1
+   windows at offsets j*b, each 64 FP32 (out [rows][64], host or device;
+   `rows` must equal that count).  Computes and caches them if needed.
+   Errors: DTWS_EINVAL (no encoder, m < 64 or > n, rows mismatch). */
+dtws_status dtws_learned_embeddings(dtws_t h, int32_t m, float *out, int64_t rows, void *stream);
+
+/* u of the windows X[offsets[i] .. offsets[i]+m) (X host or device FP32 [n];
+   offsets HOST int64 [rows], each in [0, n-m]) -> u [rows][DTWS_ENC_U]
+   (host or device).  Synchronises `stream`.  Errors: DTWS_EINVAL. */
+dtws_status dtws_enc_prep(const float *X, int64_t n, const int64_t *offsets, int32_t rows, int32_t m,
+                          float *u, void *stream);
+
+/* Embeddings e [rows][64] (host or device) of u [rows][DTWS_ENC_U] (host or
+   device) under `params` (host or device FP32 [DTWS_ENC_PARAMS]).
+   Synchronises `stream`.  Errors: DTWS_EINVAL, DTWS_ENOMEM, DTWS_ECUDA. */
+dtws_status dtws_enc_forward(const float *params, const float *u, int32_t rows, float *e, void *stream);
+
+/* Mean training loss of `batch` triples (uq[i], uc[i], y[i]) and its
+   gradient w.r.t. the parameters (grad FP32 [DTWS_ENC_PARAMS], host or
+   device; loss: one HOST float).  All inputs host or device.  Synchronises
+   `stream`.  Errors: DTWS_EINVAL, DTWS_ENOMEM, DTWS_ECUDA. */
+dtws_status dtws_enc_loss_grad(const float *params, const float *uq, const float *uc, const float *y,
+                               int32_t batch, float *loss, float *grad, void *stream);
+
+/* Training on the GPU: Adam on an FP32 master copy. */
+typedef struct dtws_trainer_ctx *dtws_trainer_t;
+typedef struct {
+    float lr;      /* step size, e.g. 1e-3 */
+    float beta1;   /* e.g. 0.9 */
+    float beta2;   /* e.g. 0.999 */
+    float eps;     /* e.g. 1e-8 */
+} dtws_adam;
+
+/* params: initial values (host or device FP32 [count = DTWS_ENC_PARAMS]);
+   max_batch: largest batch of triples per step (1..65536). */
+dtws_status dtws_trainer_create(const float *params, int32_t count, int32_t max_batch,
+                                const dtws_adam *hp, dtws_trainer_t *out);
+/* One step on `batch` triples: query i is the window xq[q_off[i] .. +m),
+   candidate i the window xc[c_off[i] .. +m), label y[i] = DTW/m.  xq, xc:
+   DEVICE FP32 [n] (e.g. a series and a noisy copy of it); q_off, c_off:
+   HOST int64 [batch], each in [0, n-m]; y: HOST FP32 [batch]; loss: HOST
+   float or null (when given, the step's mean loss before the update, and
+   the call synchronises `stream`). */
+dtws_status dtws_trainer_step(dtws_trainer_t t, const float *xq, const float *xc, int64_t n,
+                              const int64_t *q_off, const int64_t *c_off, int32_t m, const float *y,
+                              int32_t batch, float *loss, void *stream);
+/* Current parameters -> params (host or device FP32 [DTWS_ENC_PARAMS]);
+   synchronises `stream`. */
+dtws_status dtws_trainer_params(dtws_trainer_t t, float *params, void *stream);
+dtws_status dtws_trainer_destroy(dtws_trainer_t t);
 
 /* ---- allocation-free variant (the paper has no counterpart) ---- */
 

@@ -108,24 +108,32 @@ def _conv(x, w):
     return out
 
 
-def forward(params, u):
-    """Embedding e (64) of one input u (63) and the intermediate values."""
+def forward(params, u, bf16: bool = False):
+    """Embedding e (64) of one input u (63) and the intermediate values.
+
+    bf16: round the operands the GPU feeds to its BF16 tensor-core products
+    (W2..W4, P, the post-ReLU h1..h3 and the pooled g) to bfloat16 first,
+    everything else in FP64 -- the storage precision the encoder's GPU
+    kernels use (BF16 weights and activations, wide accumulation)."""
     W1, W2, W3, W4, Pm = split(params)
+    rb = round_bf16 if bf16 else (lambda a: a)
+    if bf16:
+        W2, W3, W4, Pm = (rb(w) for w in (W2, W3, W4, Pm))
     u = np.asarray(u, np.float64)
     z1 = _conv(u[:, None], W1[:, :, None])
-    h1 = np.maximum(z1, 0)
+    h1 = rb(np.maximum(z1, 0))
     z2 = _conv(h1, W2)
-    h2 = np.maximum(z2, 0)
+    h2 = rb(np.maximum(z2, 0))
     z3 = _conv(h2, W3)
-    h3 = np.maximum(z3, 0)
+    h3 = rb(np.maximum(z3, 0))
     h4 = _conv(h3, W4)
-    g = np.stack([h4[lo:hi].mean(axis=0) for lo, hi in segments()])  # [8][32]
+    g = rb(np.stack([h4[lo:hi].mean(axis=0) for lo, hi in segments()]))  # [8][32]
     e = Pm @ g.reshape(-1)
     return e, dict(u=u, z1=z1, h1=h1, z2=z2, h2=h2, z3=z3, h3=h3, h4=h4, g=g)
 
 
-def embed(params, y) -> np.ndarray:
-    return forward(params, prep(y))[0]
+def embed(params, y, bf16: bool = False) -> np.ndarray:
+    return forward(params, prep(y), bf16)[0]
 
 
 def _conv_back(x, w, dout):
@@ -139,29 +147,38 @@ def _conv_back(x, w, dout):
     return dx, dw
 
 
-def backward(params, cache, de):
-    """Gradient of a scalar with d(scalar)/de = de, w.r.t. the flat parameters."""
+def backward(params, cache, de, bf16: bool = False):
+    """Gradient of a scalar with d(scalar)/de = de, w.r.t. the flat parameters.
+
+    bf16: the backward pass of the BF16 forward as the GPU runs it -- the
+    rounded weights, and the gradients that feed tensor-core products (dh4
+    and the masked dz3, dz2, dz1) rounded to bfloat16."""
     W1, W2, W3, W4, Pm = split(params)
+    rb = round_bf16 if bf16 else (lambda a: a)
+    if bf16:
+        W2, W3, W4, Pm = (rb(w) for w in (W2, W3, W4, Pm))
     de = np.asarray(de, np.float64)
     dP = np.outer(de, cache["g"].reshape(-1))
     dg = (Pm.T @ de).reshape(NSEG, C)
     dh4 = np.zeros((L4, C))
     for s, (lo, hi) in enumerate(segments()):
         dh4[lo:hi] = dg[s] / (hi - lo)
+    dh4 = rb(dh4)
     dh3, dW4 = _conv_back(cache["h3"], W4, dh4)
-    dz3 = dh3 * (cache["z3"] > 0)
+    dz3 = rb(dh3 * (cache["z3"] > 0))
     dh2, dW3 = _conv_back(cache["h2"], W3, dz3)
-    dz2 = dh2 * (cache["z2"] > 0)
+    dz2 = rb(dh2 * (cache["z2"] > 0))
     dh1, dW2 = _conv_back(cache["h1"], W2, dz2)
-    dz1 = dh1 * (cache["z1"] > 0)
+    dz1 = rb(dh1 * (cache["z1"] > 0))
     _, dW1 = _conv_back(cache["u"][:, None], W1[:, :, None], dz1)
     return np.concatenate([dW1.reshape(-1), dW2.reshape(-1), dW3.reshape(-1), dW4.reshape(-1),
                            dP.reshape(-1)])
 
 
-def loss_and_grad(params, uq, uc, y):
-    """Mean triple loss over a batch and its gradient (FP64).
-    uq, uc: [B][63] inputs; y: [B] labels DTW / m."""
+def loss_and_grad(params, uq, uc, y, bf16: bool = False):
+    """Mean triple loss over a batch and its gradient (FP64; with bf16, the
+    GPU's BF16 operand rounding in forward and backward, see forward and
+    backward).  uq, uc: [B][63] inputs; y: [B] labels DTW / m."""
     uq = np.atleast_2d(np.asarray(uq, np.float64))
     uc = np.atleast_2d(np.asarray(uc, np.float64))
     y = np.atleast_1d(np.asarray(y, np.float64))
@@ -169,15 +186,15 @@ def loss_and_grad(params, uq, uc, y):
     total = 0.0
     grad = np.zeros(NPARAMS)
     for i in range(B):
-        eq, cq = forward(params, uq[i])
-        ec, cc = forward(params, uc[i])
+        eq, cq = forward(params, uq[i], bf16)
+        ec, cc = forward(params, uc[i], bf16)
         diff = eq - ec
         dist = float(diff @ diff)
         lr = np.log(dist + EPS) - np.log(y[i] + EPS)
         total += lr * lr
         dd = 2.0 * lr / (dist + EPS) / B          # d(mean loss)/d(dist)
-        grad += backward(params, cq, 2.0 * diff * dd)
-        grad += backward(params, cc, -2.0 * diff * dd)
+        grad += backward(params, cq, 2.0 * diff * dd, bf16)
+        grad += backward(params, cc, -2.0 * diff * dd, bf16)
     return total / B, grad
 
 

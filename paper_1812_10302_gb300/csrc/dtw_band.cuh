@@ -54,16 +54,41 @@ __device__ __forceinline__ float group_incl_scan(float v, unsigned gmask, int la
 }
 
 struct TailCtx {
-    const float *Uw, *Lw;  // series envelope at the window's first sample
+    const float *Uw, *Lw;  // exact series envelope at the window's first sample, or null:
+    const float *stmax, *stmin;  // the block envelope (sparse table, kEnvLevels x nblk)
+    int64_t nblk, n, t0;   // blocks, series length, the window's first sample
+    int r;
     const float *qs;       // q_hat (shared)
     float mh, is, ls;
 };
 
+// Raw envelope bounds of series position t0 + i: the exact U_x, L_x (Eq. 9
+// over the series, clipped), or max / min over the kEnvG-sample blocks that
+// cover [t - r, t + r] clipped -- a superset of that range, so U' >= U_x and
+// L' <= L_x and the bound stays admissible.
+__device__ __forceinline__ void env_at(const TailCtx &c, int i, float &u, float &l) {
+    if (c.Uw) {
+        u = c.Uw[i];
+        l = c.Lw[i];
+        return;
+    }
+    const int64_t t = c.t0 + i;
+    const int64_t lo = t - c.r > 0 ? t - c.r : 0, hi = t + c.r < c.n - 1 ? t + c.r : c.n - 1;
+    const int64_t a = lo / kEnvG, bb = hi / kEnvG;
+    const int k = 31 - __clz((int)(bb - a + 1));
+    const int64_t b2 = bb - (1ll << k) + 1;
+    const float *mx = c.stmax + (size_t)k * c.nblk, *mn = c.stmin + (size_t)k * c.nblk;
+    u = fmaxf(mx[a], mx[b2]);
+    l = fminf(mn[a], mn[b2]);
+}
+
 // LB_Keogh term of row i: squared distance of q_hat_i to the normalised
 // envelope interval of the window at position i.
 __device__ __forceinline__ float tail_term(const TailCtx &c, int i) {
-    float u = fmaf(c.Uw[i] - c.mh, c.is, -c.ls);
-    float l = fmaf(c.Lw[i] - c.mh, c.is, -c.ls);
+    float U, L;
+    env_at(c, i, U, L);
+    float u = fmaf(U - c.mh, c.is, -c.ls);
+    float l = fmaf(L - c.mh, c.is, -c.ls);
     float q = c.qs[i];
     float d = fmaxf(q - u, 0.0f) + fmaxf(l - q, 0.0f);
     return d * d;

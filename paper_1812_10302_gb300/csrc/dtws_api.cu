@@ -3,6 +3,7 @@
 // query's kernels are enqueued on the caller's stream.
 #include <cstdarg>
 #include <cstdio>
+#include <algorithm>
 #include <cstring>
 #include <new>
 #include <vector>
@@ -51,7 +52,30 @@ struct EnvEntry {
     float *U = nullptr, *L = nullptr;
 };
 
+struct LearnEntry {
+    int m = 0;
+    int64_t used = 0, version = 0, rows = 0;
+    void *E = nullptr;  // BF16 [rows][64]
+};
+
 constexpr int kCacheSlots = 8;
+constexpr int kLearnSlots = 2;
+
+// One lane of the batched path: its own query buffers, survivor buffers and
+// window-statistics slot, and its own streams, so that queries on different
+// lanes overlap on the GPU.
+struct Lane {
+    QueryState *st = nullptr;
+    float *qh32 = nullptr, *Uq = nullptr, *Lq = nullptr, *sq = nullptr, *sU = nullptr, *sL = nullptr;
+    double *qh64 = nullptr;
+    unsigned short *ord = nullptr;
+    float *cand_lb = nullptr, *sort_lb = nullptr;
+    unsigned *cand_idx = nullptr, *sort_idx = nullptr;
+    StatsEntry stats;  // slot sized for the batch's smallest m
+    int64_t stats_cap = 0;
+    cudaStream_t stream = nullptr, side = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_done = nullptr;
+};
 
 }  // namespace
 
@@ -66,7 +90,11 @@ struct dtws_ctx {
     int device = 0, num_sms = 0;
     int64_t n = 0, n_alloc = 0;
     float *x = nullptr;
-    double *P1 = nullptr, *P2 = nullptr, *T1 = nullptr, *T2 = nullptr, *A = nullptr;
+    float *pf = nullptr, *bf = nullptr;  // prefix sums as FP32 pairs, block totals and anchors
+    int *pok = nullptr;                  // per-block flag: the pairs carry the block
+    float *pscale = nullptr;             // [0]: the series' power-of-two scale; [1]: scratch
+    float *envst = nullptr;              // block envelope (sparse table)
+    int64_t nblk = 0;
     std::vector<StatsEntry> stats;
     std::vector<EnvEntry> env;
     int64_t clock = 0;
@@ -83,6 +111,7 @@ struct dtws_ctx {
     size_t stage_cap = 0;
     dtws_options opt;
     cudaStream_t last_stream = nullptr;
+    QueryState *last_st = nullptr;  // the state the last query's counters are in
     bool have_last = false;
     int64_t last_N = 0;
     int64_t last_launches = 0;
@@ -92,6 +121,15 @@ struct dtws_ctx {
     // side stream for work that overlaps the lower-bound scan
     cudaStream_t side = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    // batched path
+    std::vector<Lane> lanes;
+    cudaEvent_t batch_fork = nullptr;
+    cudaGraphExec_t graph_exec = nullptr;
+    std::vector<int64_t> graph_sig;  // what the cached graph was captured for
+    // learned proposal encoder
+    uint8_t *enc_blob = nullptr;
+    int64_t enc_version = 0;  // 0: no encoder installed
+    std::vector<LearnEntry> learn;
 };
 
 namespace {
@@ -182,8 +220,8 @@ dtws_status get_stats(dtws_t h, int m, cudaStream_t s, StatsEntry **out, bool *c
     CK(cudaMemsetAsync(e.smu_hi, 0, scap * 4, s));
     CK(cudaMemsetAsync(e.smu_lo, 0, scap * 4, s));
     CK(cudaMemsetAsync(e.sinv_sigma, 0, scap * 4, s));
-    CK(launch_window_stats(h->x, h->n, m, h->P1, h->P2, h->T1, h->T2, h->A, e.mu_hi, e.mu_lo,
-                           e.inv_sigma, e.smu_hi, e.smu_lo, e.sinv_sigma, s));
+    CK(launch_window_stats(h->x, h->n, m, h->pf, h->bf, h->pok, h->pscale, e.mu_hi, e.mu_lo, e.inv_sigma, e.smu_hi,
+                           e.smu_lo, e.sinv_sigma, h->num_sms, s));
     e.used = ++h->clock;
     h->stats.push_back(e);
     *out = &h->stats.back();
@@ -233,6 +271,58 @@ cudaError_t need(T **p, size_t count) {
     return *p ? cudaSuccess : dalloc(p, count);
 }
 
+void free_learn(LearnEntry &e) {
+    cudaFree(e.E);
+    e = LearnEntry();
+}
+
+int enc_block(int m) { return m / 64; }
+int64_t enc_rows(dtws_t h, int m) { return (h->n - m) / enc_block(m) + 1; }
+
+// Embeddings of the windows at offsets j*b for query length m (cached).
+dtws_status get_learn(dtws_t h, int m, const StatsEntry *se, cudaStream_t s, LearnEntry **out, bool *computed) {
+    *computed = false;
+    for (auto &e : h->learn)
+        if (e.m == m && e.version == h->enc_version) {
+            e.used = ++h->clock;
+            *out = &e;
+            return DTWS_OK;
+        }
+    for (size_t i = 0; i < h->learn.size();)
+        if (h->learn[i].version != h->enc_version) {
+            CK(cudaDeviceSynchronize());
+            free_learn(h->learn[i]);
+            h->learn.erase(h->learn.begin() + i);
+        } else {
+            ++i;
+        }
+    if ((int)h->learn.size() >= kLearnSlots) {
+        size_t lru = 0;
+        for (size_t i = 1; i < h->learn.size(); ++i)
+            if (h->learn[i].used < h->learn[lru].used) lru = i;
+        CK(cudaDeviceSynchronize());
+        free_learn(h->learn[lru]);
+        h->learn.erase(h->learn.begin() + lru);
+    }
+    LearnEntry e;
+    e.m = m;
+    e.version = h->enc_version;
+    e.rows = enc_rows(h, m);
+    uint16_t *E = nullptr;
+    if (dalloc(&E, (size_t)e.rows * 64) != cudaSuccess) {
+        cudaGetLastError();
+        set_err("learned embeddings for m=%d: out of device memory", m);
+        return DTWS_ENOMEM;
+    }
+    e.E = E;
+    CK(launch_enc_series(h->enc_blob, h->x, h->n, enc_block(m), se->inv_sigma, e.rows, e.E, h->num_sms, s));
+    e.used = ++h->clock;
+    h->learn.push_back(e);
+    *out = &h->learn.back();
+    *computed = true;
+    return DTWS_OK;
+}
+
 dtws_status ensure_workspace(dtws_t h) {
     CK(need(&h->st, 1));
     CK(need(&h->qh32, kMMax));
@@ -268,6 +358,10 @@ QueryBufs make_bufs(dtws_t h, const StatsEntry *se, const EnvEntry *ee) {
     b.sinv_sigma = se ? se->sinv_sigma : nullptr;
     b.U = ee ? ee->U : nullptr;
     b.L = ee ? ee->L : nullptr;
+    b.stmax = h->envst;
+    b.stmin = h->envst + (size_t)kEnvLevels * h->nblk;
+    b.nblk = h->nblk;
+    b.n = h->n;
     b.qh32 = h->qh32;
     b.qh64 = h->qh64;
     b.Uq = h->Uq;
@@ -315,6 +409,15 @@ dtws_status check_query_args(dtws_t h, const float *Q, int32_t m, int32_t r, int
         set_err("k=%d out of range [1, min(N, %d)]", k, DTWS_K_MAX);
         return DTWS_EINVAL;
     }
+    if (h->opt.ordering == DTWS_ORDER_LEARNED) {
+        if (!h->enc_version) { set_err("learned ordering without an encoder (dtws_set_encoder)"); return DTWS_EINVAL; }
+        if (m < 64) { set_err("learned ordering needs m >= 64 (m=%d)", m); return DTWS_EINVAL; }
+        const int P = h->opt.seed_proposals, half = enc_block(m) / 2;
+        if (P > kLearnPropMax || h->opt.seed_random + P * (2 * half + 1) > kEdMax) {
+            set_err("learned ordering: %d proposals exceed the seed capacity", P);
+            return DTWS_EINVAL;
+        }
+    }
     return DTWS_OK;
 }
 
@@ -325,62 +428,323 @@ void record(dtws_t h, int i, cudaStream_t s) {
     }
 }
 
-// The device-side query pipeline on device pointers.
+// Everything a query's kernels need besides the query itself.
+struct Exec {
+    QueryBufs b;
+    cudaStream_t s, side;
+    cudaEvent_t ev_fork, ev_join;
+    const LearnEntry *le;  // learned ordering: the embeddings for m (or null)
+    bool timing;           // record the handle's phase events
+};
+
+// Enqueue the kernels of one query (Sec. 2.2's cascade, re-planned for the
+// GPU) on e.s; returns the number of kernel launches.
+dtws_status enqueue_search(dtws_t h, const Exec &e, const QueryArgs &a, const float *Qd, int64_t *idx_d,
+                           float *dist_d, int64_t *launches_out) {
+    const QueryBufs &b = e.b;
+    cudaStream_t s = e.s;
+    const int m = a.m, k = a.k;
+    const int P = h->opt.seed_proposals, R = h->opt.seed_random;
+    int64_t launches = 0;
+    auto rec = [&](int i) {
+        if (e.timing) record(h, i, s);
+    };
+    CK(launch_query_reset(b, a, s));
+    CK(launch_qprep(Qd, b, a, s));
+    rec(0);
+    int half = kProxyStride / 2;
+    if (P > 0 && e.le) {
+        CK(launch_enc_query(h->enc_blob, b, a, s));
+        CK(launch_learn_scan(b, e.le->E, e.le->rows, enc_block(m), P, s));
+        half = enc_block(m) / 2;
+        launches += 2;
+    } else if (P > 0) {
+        CK(launch_seed_scan(b, a, P, h->opt.proxy_terms, s));
+        ++launches;
+    }
+    CK(launch_seed_gather(b, a, R, P, half, h->opt.rng_seed, s));
+    CK(launch_seed_ed(b, a, s));
+    if (k > 1) {  // exact DTW seeds tighten a k-th bound the Euclidean seeds leave loose
+        CK(launch_dtw_seeds(b, a, s));
+        ++launches;
+    }
+    rec(1);
+    // the best Euclidean seed is scored on the side stream during the scan
+    if (a.prescore) {
+        CK(cudaEventRecord(e.ev_fork, s));
+        CK(cudaStreamWaitEvent(e.side, e.ev_fork, 0));
+        CK(launch_prescore(b, a, e.side));
+        CK(cudaEventRecord(e.ev_join, e.side));
+        ++launches;
+    }
+    CK(launch_lb_scan(b, a, s));
+    rec(2);
+    CK(launch_order(b, a, s));
+    rec(3);
+    CK(launch_dtw_survivors(b, a, s));
+    rec(4);
+    if (a.prescore) CK(cudaStreamWaitEvent(s, e.ev_join, 0));
+    CK(launch_finalize(b, a, idx_d, dist_d, s));
+    rec(5);
+    launches += 2 + 2 + 1 + 3 + 1 + 3;  // reset, qprep, gather, ED seeds, scan, order x3, DTW, final x3
+    *launches_out = launches;
+    return DTWS_OK;
+}
+
+// One query on the handle's own buffers (dtws_query).
 dtws_status run_query(dtws_t h, const float *Qd, int m, int r, int k, int64_t *idx_d, float *dist_d,
                       cudaStream_t s) {
     dtws_status st;
     for (bool &v : h->ev_recorded) v = false;
     record(h, 8, s);
     StatsEntry *se;
-    EnvEntry *ee;
-    bool c1, c2;
+    EnvEntry *ee = nullptr;
+    bool c1, c2 = false;
     if ((st = get_stats(h, m, s, &se, &c1)) != DTWS_OK) return st;
     record(h, 6, s);
     const int rr = r > m - 1 ? m - 1 : r;
-    if ((st = get_env(h, rr, s, &ee, &c2)) != DTWS_OK) return st;
+    if (h->opt.exact_envelope) {
+        if ((st = get_env(h, rr, s, &ee, &c2)) != DTWS_OK) return st;
+    } else {  // an exact envelope already cached for this r is still used
+        for (auto &en : h->env)
+            if (en.r == rr) ee = &en;
+    }
     record(h, 7, s);
     if ((st = ensure_workspace(h)) != DTWS_OK) return st;
     if ((st = ensure_candidates(h)) != DTWS_OK) return st;
-    const QueryBufs b = make_bufs(h, se, ee);
+    LearnEntry *le = nullptr;
+    bool c3 = false;
+    if (h->opt.seed_proposals > 0 && h->opt.ordering == DTWS_ORDER_LEARNED)
+        if ((st = get_learn(h, m, se, s, &le, &c3)) != DTWS_OK) return st;
+    Exec e{make_bufs(h, se, ee), s, h->side, h->ev_fork, h->ev_join, le, true};
     const QueryArgs a = make_args(h, m, r, k);
-    const int P = h->opt.seed_proposals, R = h->opt.seed_random;
-    int64_t launches = (c1 ? 1 : 0) + (c2 ? 1 : 0);
-    CK(launch_query_reset(b, a, s));
-    CK(launch_qprep(Qd, b, a, s));
-    record(h, 0, s);
-    if (P > 0) {
-        CK(launch_seed_scan(b, a, P, h->opt.proxy_terms, s));
-        ++launches;
-    }
-    CK(launch_seed_gather(b, a, R, P, h->opt.rng_seed, s));
-    CK(launch_seed_ed(b, a, s));
-    if (k > 1) {  // exact DTW seeds tighten a k-th bound the Euclidean seeds leave loose
-        CK(launch_dtw_seeds(b, a, s));
-        ++launches;
-    }
-    record(h, 1, s);
-    // the best Euclidean seed is scored on the side stream during the scan
-    if (a.prescore) {
-        CK(cudaEventRecord(h->ev_fork, s));
-        CK(cudaStreamWaitEvent(h->side, h->ev_fork, 0));
-        CK(launch_prescore(b, a, h->side));
-        CK(cudaEventRecord(h->ev_join, h->side));
-        ++launches;
-    }
-    CK(launch_lb_scan(b, a, s));
-    record(h, 2, s);
-    CK(launch_order(b, a, s));
-    record(h, 3, s);
-    CK(launch_dtw_survivors(b, a, s));
-    record(h, 4, s);
-    if (a.prescore) CK(cudaStreamWaitEvent(s, h->ev_join, 0));
-    CK(launch_finalize(b, a, idx_d, dist_d, s));
-    record(h, 5, s);
-    launches += 2 + 2 + 1 + 3 + 1 + 3;  // reset, qprep, gather, ED seeds, scan, order x3, DTW, final x3
+    int64_t launches = 0;
+    if ((st = enqueue_search(h, e, a, Qd, idx_d, dist_d, &launches)) != DTWS_OK) return st;
     h->last_stream = s;
     h->have_last = true;
     h->last_N = a.N;
+    h->last_launches = launches + (c1 ? 1 : 0) + (c2 ? 1 : 0) + (c3 ? 1 : 0);
+    h->last_st = h->st;
+    return DTWS_OK;
+}
+
+void free_lane(Lane &l) {
+    void *ptrs[] = {l.st, l.qh32, l.Uq, l.Lq, l.sq, l.sU, l.sL, l.qh64, l.ord, l.cand_lb, l.sort_lb, l.cand_idx,
+                    l.sort_idx};
+    for (void *p : ptrs)
+        if (p) cudaFree(p);
+    free_stats(l.stats);
+    if (l.stream) cudaStreamDestroy(l.stream);
+    if (l.side) cudaStreamDestroy(l.side);
+    if (l.ev_fork) cudaEventDestroy(l.ev_fork);
+    if (l.ev_join) cudaEventDestroy(l.ev_join);
+    if (l.ev_done) cudaEventDestroy(l.ev_done);
+    l = Lane();
+}
+
+void drop_graph(dtws_t h) {
+    if (h->graph_exec) cudaGraphExecDestroy(h->graph_exec);
+    h->graph_exec = nullptr;
+    h->graph_sig.clear();
+}
+
+// Lanes with statistics slots for windows of at least m_min samples.
+dtws_status ensure_lanes(dtws_t h, int count, int m_min) {
+    const int64_t need_cap = round_up(h->n - m_min + 1, kProxyTile) + kProxyTile;
+    for (auto &l : h->lanes)
+        if (l.stats_cap < need_cap) {  // too small: rebuild all (rare)
+            CK(cudaDeviceSynchronize());
+            drop_graph(h);
+            for (auto &x : h->lanes) free_lane(x);
+            h->lanes.clear();
+            break;
+        }
+    if (!h->batch_fork) CK(cudaEventCreateWithFlags(&h->batch_fork, cudaEventDisableTiming));
+    while ((int)h->lanes.size() < count) {
+        h->lanes.emplace_back();
+        Lane &l = h->lanes.back();
+        const int64_t cap = h->n, scap = need_cap / kProxyStride;
+        cudaError_t e = cudaSuccess;
+        auto al = [&](cudaError_t r) {
+            if (e == cudaSuccess) e = r;
+        };
+        al(dalloc(&l.st, 1));
+        al(dalloc(&l.qh32, kMMax));
+        al(dalloc(&l.Uq, kMMax));
+        al(dalloc(&l.Lq, kMMax));
+        al(dalloc(&l.sq, kMMax));
+        al(dalloc(&l.sU, kMMax));
+        al(dalloc(&l.sL, kMMax));
+        al(dalloc(&l.qh64, kMMax));
+        al(dalloc(&l.ord, kMMax));
+        al(dalloc(&l.cand_lb, cap));
+        al(dalloc(&l.sort_lb, cap));
+        al(dalloc(&l.cand_idx, cap));
+        al(dalloc(&l.sort_idx, cap));
+        al(dalloc(&l.stats.mu_hi, need_cap));
+        al(dalloc(&l.stats.mu_lo, need_cap));
+        al(dalloc(&l.stats.inv_sigma, need_cap));
+        al(dalloc(&l.stats.smu_hi, scap));
+        al(dalloc(&l.stats.smu_lo, scap));
+        al(dalloc(&l.stats.sinv_sigma, scap));
+        al(cudaStreamCreateWithFlags(&l.stream, cudaStreamNonBlocking));
+        al(cudaStreamCreateWithFlags(&l.side, cudaStreamNonBlocking));
+        al(cudaEventCreateWithFlags(&l.ev_fork, cudaEventDisableTiming));
+        al(cudaEventCreateWithFlags(&l.ev_join, cudaEventDisableTiming));
+        al(cudaEventCreateWithFlags(&l.ev_done, cudaEventDisableTiming));
+        l.stats_cap = need_cap;
+        if (e != cudaSuccess) {
+            free_lane(l);
+            h->lanes.pop_back();
+            cudaGetLastError();
+            if (h->lanes.empty()) {
+                set_err("batch lanes: %s", cudaGetErrorString(e));
+                return e == cudaErrorMemoryAllocation ? DTWS_ENOMEM : DTWS_ECUDA;
+            }
+            break;  // fewer lanes than asked: use what fits
+        }
+        // statistics slots must hold finite values beyond N (bulk copies read whole tiles)
+        CK(cudaMemset(l.stats.mu_hi, 0, need_cap * 4));
+        CK(cudaMemset(l.stats.mu_lo, 0, need_cap * 4));
+        CK(cudaMemset(l.stats.inv_sigma, 0, need_cap * 4));
+        CK(cudaMemset(l.stats.smu_hi, 0, scap * 4));
+        CK(cudaMemset(l.stats.smu_lo, 0, scap * 4));
+        CK(cudaMemset(l.stats.sinv_sigma, 0, scap * 4));
+    }
+    return DTWS_OK;
+}
+
+QueryBufs lane_bufs(dtws_t h, const Lane &l, const EnvEntry *ee) {
+    QueryBufs b = make_bufs(h, &l.stats, ee);
+    b.st = l.st;
+    b.qh32 = l.qh32;
+    b.qh64 = l.qh64;
+    b.Uq = l.Uq;
+    b.Lq = l.Lq;
+    b.ord = l.ord;
+    b.sq = l.sq;
+    b.sU = l.sU;
+    b.sL = l.sL;
+    b.cand_lb = l.cand_lb;
+    b.sort_lb = l.sort_lb;
+    b.cand_idx = l.cand_idx;
+    b.sort_idx = l.sort_idx;
+    return b;
+}
+
+// Many queries (dtws_query_batch): queries sorted by (m, r) and dealt
+// round-robin to the lanes; each lane computes the window statistics of a
+// new m into its slot, in stream order, and uses the exact envelope of r
+// when one is cached, else the block envelope.  Unless the learned ordering
+// is on, the whole batch is captured once into a CUDA graph, kept, and
+// replayed by later calls with the same arguments.
+dtws_status run_batch(dtws_t h, const float *Qd, const int64_t *q_off, const int32_t *m_arr, const int32_t *r_arr,
+                      int32_t nq, int32_t k, int64_t *idx_d, float *dist_d, cudaStream_t s) {
+    dtws_status st;
+    const bool learned = h->opt.seed_proposals > 0 && h->opt.ordering == DTWS_ORDER_LEARNED;
+    const int nl = std::max(1, std::min<int>(h->opt.batch_lanes, nq));
+    int m_min = m_arr[0];
+    for (int q = 1; q < nq; ++q) m_min = std::min<int>(m_min, m_arr[q]);
+    if ((st = ensure_lanes(h, nl, m_min)) != DTWS_OK) return st;
+    const int L = std::min<int>(nl, (int)h->lanes.size());
+    std::vector<int> order(nq);
+    for (int q = 0; q < nq; ++q) order[q] = q;
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
+        return m_arr[x] != m_arr[y] ? m_arr[x] < m_arr[y] : r_arr[x] < r_arr[y];
+    });
+    const bool graph = h->opt.batch_graph && !learned;
+    std::vector<int64_t> sig;
+    if (graph) {
+        // everything the captured kernels' arguments depend on
+        sig = {nq, k, L, (int64_t)(intptr_t)Qd, (int64_t)(intptr_t)idx_d, (int64_t)(intptr_t)dist_d};
+        const int64_t *ow = reinterpret_cast<const int64_t *>(&h->opt);
+        sig.insert(sig.end(), ow, ow + sizeof(dtws_options) / 8);
+        for (int q = 0; q < nq; ++q) {
+            sig.push_back(q_off[q]);
+            sig.push_back(((int64_t)m_arr[q] << 32) | (uint32_t)r_arr[q]);
+        }
+        for (auto &en : h->env) sig.push_back(((int64_t)en.r << 32) | (int64_t)(intptr_t)en.U);
+        if (h->graph_exec && sig == h->graph_sig) {
+            CK(cudaGraphLaunch(h->graph_exec, s));
+            h->last_stream = s;
+            return DTWS_OK;
+        }
+        CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+    }
+    auto fail = [&](dtws_status e) {
+        if (graph) {
+            cudaGraph_t g = nullptr;
+            cudaStreamEndCapture(s, &g);
+            if (g) cudaGraphDestroy(g);
+            cudaGetLastError();
+        }
+        return e;
+    };
+#define CKB(call)                                                                      \
+    do {                                                                               \
+        cudaError_t e__ = (call);                                                      \
+        if (e__ != cudaSuccess) {                                                      \
+            set_err("%s:%d %s: %s", __FILE__, __LINE__, #call, cudaGetErrorString(e__)); \
+            return fail(DTWS_ECUDA);                                                   \
+        }                                                                              \
+    } while (0)
+    CKB(cudaEventRecord(h->batch_fork, s));
+    std::vector<int> lane_m(L, -1);
+    for (int i = 0; i < L; ++i) CKB(cudaStreamWaitEvent(h->lanes[i].stream, h->batch_fork, 0));
+    int64_t launches = 0;
+    for (int j = 0; j < nq; ++j) {
+        const int q = order[j], li = j % L;
+        Lane &l = h->lanes[li];
+        const int m = m_arr[q], r = r_arr[q], rr = r > m - 1 ? m - 1 : r;
+        if (lane_m[li] != m) {
+            CKB(launch_window_stats(h->x, h->n, m, h->pf, h->bf, h->pok, h->pscale, l.stats.mu_hi, l.stats.mu_lo,
+                                    l.stats.inv_sigma, l.stats.smu_hi, l.stats.smu_lo, l.stats.sinv_sigma,
+                                    h->num_sms, l.stream));
+            lane_m[li] = m;
+            ++launches;
+        }
+        const EnvEntry *ee = nullptr;
+        for (auto &en : h->env)
+            if (en.r == rr) ee = &en;
+        LearnEntry *le = nullptr;
+        if (learned) {
+            bool c3;
+            StatsEntry *se;
+            bool c1;
+            // the learned embeddings are scaled by 1/sigma from the handle's statistics of m
+            if ((st = get_stats(h, m, l.stream, &se, &c1)) != DTWS_OK) return fail(st);
+            if ((st = get_learn(h, m, se, l.stream, &le, &c3)) != DTWS_OK) return fail(st);
+        }
+        Exec e{lane_bufs(h, l, ee), l.stream, l.side, l.ev_fork, l.ev_join, le, false};
+        const QueryArgs a = make_args(h, m, r, k);
+        int64_t n_l = 0;
+        if ((st = enqueue_search(h, e, a, Qd + q_off[q], idx_d + (int64_t)q * k, dist_d + (int64_t)q * k, &n_l)) !=
+            DTWS_OK)
+            return fail(st);
+        launches += n_l;
+    }
+    for (int i = 0; i < L; ++i) {
+        CKB(cudaEventRecord(h->lanes[i].ev_done, h->lanes[i].stream));
+        CKB(cudaStreamWaitEvent(s, h->lanes[i].ev_done, 0));
+    }
+#undef CKB
+    if (graph) {
+        cudaGraph_t g = nullptr;
+        CK(cudaStreamEndCapture(s, &g));
+        drop_graph(h);
+        cudaGraphExec_t ex = nullptr;
+        cudaError_t e = cudaGraphInstantiate(&ex, g, 0);
+        cudaGraphDestroy(g);
+        CK(e);
+        h->graph_exec = ex;
+        h->graph_sig = sig;
+        CK(cudaGraphLaunch(ex, s));
+    }
+    h->last_stream = s;
+    h->have_last = true;
+    h->last_N = h->n - m_arr[order[nq - 1]] + 1;
     h->last_launches = launches;
+    h->last_st = h->lanes[(nq - 1) % L].st;
     return DTWS_OK;
 }
 
@@ -398,6 +762,9 @@ void dtws_default_options(dtws_options *o) {
     o->proxy_terms = 16;
     o->ordering = DTWS_ORDER_PLAIN;
     o->timing = 0;
+    o->exact_envelope = 1;
+    o->batch_lanes = 4;
+    o->batch_graph = 1;
     o->wait_limit_ns = 2000000000LL;
     o->rng_seed = 0;
 }
@@ -426,7 +793,12 @@ dtws_status dtws_destroy(dtws_t h) {
     cudaDeviceSynchronize();
     for (auto &e : h->stats) free_stats(e);
     for (auto &e : h->env) free_env(e);
-    void *ptrs[] = {h->x, h->P1, h->P2, h->T1, h->T2, h->A, h->st, h->status, h->qh32, h->Uq,
+    for (auto &e : h->learn) free_learn(e);
+    if (h->enc_blob) cudaFree(h->enc_blob);
+    drop_graph(h);
+    for (auto &l : h->lanes) free_lane(l);
+    if (h->batch_fork) cudaEventDestroy(h->batch_fork);
+    void *ptrs[] = {h->x, h->pf, h->bf, h->pok, h->pscale, h->envst, h->st, h->status, h->qh32, h->Uq,
                     h->Lq, h->sq, h->sU, h->sL, h->qh64, h->ord, h->cand_lb, h->sort_lb,
                     h->cand_idx, h->sort_idx, h->stage};
     for (void *p : ptrs)
@@ -470,11 +842,12 @@ dtws_status dtws_create(const float *series, int64_t n, void *stream, dtws_t *ou
     h->n_alloc = round_up(n, kProxyTile) + kMMax + 64;
     const int64_t nb = (n + kBlockB - 1) / kBlockB;
     CKF(dalloc(&h->x, h->n_alloc));
-    CKF(dalloc(&h->P1, n));
-    CKF(dalloc(&h->P2, n));
-    CKF(dalloc(&h->T1, nb));
-    CKF(dalloc(&h->T2, nb));
-    CKF(dalloc(&h->A, nb));
+    CKF(dalloc(&h->pf, 4 * n));
+    CKF(dalloc(&h->bf, 5 * nb));
+    CKF(dalloc(&h->pok, nb));
+    CKF(dalloc(&h->pscale, 2));
+    h->nblk = (n + kEnvG - 1) / kEnvG;
+    CKF(dalloc(&h->envst, 2 * (size_t)kEnvLevels * h->nblk));
     CKF(dalloc(&h->status, 1));
     CKF(cudaMemsetAsync(h->x, 0, h->n_alloc * 4, s));
     CKF(cudaMemcpyAsync(h->x, series, n * 4, cudaMemcpyDefault, s));
@@ -487,7 +860,8 @@ dtws_status dtws_create(const float *series, int64_t n, void *stream, dtws_t *ou
         set_err("series contains NaN or Inf");
         return fail(DTWS_ENONFINITE);
     }
-    CKF(launch_prefix(h->x, n, h->P1, h->P2, h->T1, h->T2, h->A, s));
+    CKF(launch_prefix(h->x, n, h->pf, h->bf, h->pok, reinterpret_cast<unsigned *>(h->pscale + 1), h->pscale, s));
+    CKF(launch_block_envelope(h->x, n, h->envst, h->nblk, s));
     CKF(cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking));
     CKF(cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming));
     CKF(cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming));
@@ -509,13 +883,11 @@ dtws_status dtws_set_options(dtws_t h, const dtws_options *o) {
     if (!(o->delta >= 0.0f) || !(o->alpha_per_m >= 0.0f) || o->seed_random < 0 ||
         o->seed_random > 64 || o->seed_proposals < 0 || o->seed_proposals > kPropMax ||
         o->proxy_terms < 1 || o->proxy_terms > 16 || o->wait_limit_ns <= 0 ||
+        (o->exact_envelope != 0 && o->exact_envelope != 1) || o->batch_lanes < 1 || o->batch_lanes > 16 ||
+        (o->batch_graph != 0 && o->batch_graph != 1) ||
         (o->ordering != DTWS_ORDER_PLAIN && o->ordering != DTWS_ORDER_LEARNED)) {
         set_err("option out of range");
         return DTWS_EINVAL;
-    }
-    if (o->ordering == DTWS_ORDER_LEARNED) {
-        set_err("learned ordering is not available in this build");
-        return DTWS_ENOTIMPL;
     }
     h->opt = *o;
     return DTWS_OK;
@@ -578,11 +950,8 @@ dtws_status dtws_query_batch(dtws_t h, const float *Q_cat, const int64_t *q_off,
     }
     int64_t *idx_d = idev ? out_idx : (int64_t *)(sp + round_up(qb, 256));
     float *dist_d = ddev ? out_dist : (float *)(sp + round_up(qb, 256) + round_up(ib, 256));
-    for (int q = 0; q < nq; ++q) {
-        st = run_query(h, Qd + q_off[q], m_arr[q], r_arr[q], k, idx_d + (int64_t)q * k,
-                       dist_d + (int64_t)q * k, s);
-        if (st != DTWS_OK) return st;
-    }
+    st = run_batch(h, Qd, q_off, m_arr, r_arr, nq, k, idx_d, dist_d, s);
+    if (st != DTWS_OK) return st;
     if (!idev) CK(cudaMemcpyAsync(out_idx, idx_d, ib, cudaMemcpyDeviceToHost, s));
     if (!ddev) CK(cudaMemcpyAsync(out_dist, dist_d, db, cudaMemcpyDeviceToHost, s));
     if (!idev || !ddev) CK(cudaStreamSynchronize(s));
@@ -607,7 +976,7 @@ dtws_status dtws_last_stats(dtws_t h, dtws_query_stats *o) {
     if (!h->have_last) return DTWS_OK;
     CK(cudaStreamSynchronize(h->last_stream));
     QueryState hs;
-    CK(cudaMemcpy(&hs, h->st, sizeof hs, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(&hs, h->last_st ? h->last_st : h->st, sizeof hs, cudaMemcpyDeviceToHost));
     o->windows = h->last_N;
     o->pass_kim = (int64_t)hs.ctr[kCtrKim];
     o->pass_keogh_q = (int64_t)hs.ctr[kCtrKeoghQ];
@@ -618,8 +987,8 @@ dtws_status dtws_last_stats(dtws_t h, dtws_query_stats *o) {
     o->rescored = (int64_t)hs.ctr[kCtrRescored];
     o->kernel_launches = h->last_launches;
     {
-        // k-th seed distance; k is not stored, report the smallest
-        unsigned long long key = hs.seed_keys[0];
+        // smallest seed distance: exact DTW seeds or Euclidean seeds (upper bounds)
+        unsigned long long key = hs.seed_keys[0] < hs.ed_keys[0] ? hs.seed_keys[0] : hs.ed_keys[0];
         unsigned bits = (unsigned)(key >> 32);
         float f;
         memcpy(&f, &bits, 4);
@@ -648,8 +1017,70 @@ dtws_status dtws_clear_cache(dtws_t h) {
     CK(cudaDeviceSynchronize());
     for (auto &e : h->stats) free_stats(e);
     for (auto &e : h->env) free_env(e);
+    for (auto &e : h->learn) free_learn(e);
+    drop_graph(h);
     h->stats.clear();
     h->env.clear();
+    h->learn.clear();
+    return DTWS_OK;
+}
+
+dtws_status dtws_set_encoder(dtws_t h, const float *params, int32_t count, void *stream) {
+    if (!h || !params || count != kEncParams) {
+        set_err("dtws_set_encoder: null argument or count != %d", kEncParams);
+        return DTWS_EINVAL;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    if (!h->enc_blob) {
+        uint8_t *blob = nullptr;
+        if (dalloc(&blob, kEncBlobBytes) != cudaSuccess) {
+            cudaGetLastError();
+            set_err("dtws_set_encoder: out of device memory");
+            return DTWS_ENOMEM;
+        }
+        h->enc_blob = blob;
+    }
+    dtws_status st = ensure_stage(h, (size_t)kEncParams * 4 + 256);
+    if (st != DTWS_OK) return st;
+    CK(cudaStreamSynchronize(s));  // the stage buffer and the blob may be in use by queued work
+    float *p = (float *)h->stage;
+    CK(cudaMemcpyAsync(p, params, (size_t)kEncParams * 4, cudaMemcpyDefault, s));
+    CK(launch_enc_pack(p, nullptr, nullptr, nullptr, h->enc_blob, false, 0.f, 0.f, 0.f, 0.f, 1.f, 1.f, s));
+    CK(cudaStreamSynchronize(s));
+    ++h->enc_version;
+    return DTWS_OK;
+}
+
+dtws_status dtws_learned_embeddings(dtws_t h, int32_t m, float *out, int64_t rows, void *stream) {
+    if (!h || !out || m < 64 || m > DTWS_M_MAX || (int64_t)m > h->n) {
+        set_err("dtws_learned_embeddings: null argument or m out of range [64, min(n, %d)]", DTWS_M_MAX);
+        return DTWS_EINVAL;
+    }
+    if (!h->enc_version) { set_err("dtws_learned_embeddings: no encoder installed"); return DTWS_EINVAL; }
+    if (rows != enc_rows(h, m)) {
+        set_err("dtws_learned_embeddings: rows must be %lld", (long long)enc_rows(h, m));
+        return DTWS_EINVAL;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    StatsEntry *se;
+    LearnEntry *le;
+    bool c1, c2;
+    dtws_status st;
+    if ((st = get_stats(h, m, s, &se, &c1)) != DTWS_OK) return st;
+    if ((st = get_learn(h, m, se, s, &le, &c2)) != DTWS_OK) return st;
+    if (is_device_ptr(out)) {
+        CK(launch_bf16_to_f32(le->E, rows * 64, out, s));
+        return DTWS_OK;
+    }
+    float *tmp = nullptr;
+    CK(cudaMalloc(&tmp, (size_t)rows * 64 * 4));
+    cudaError_t e1 = launch_bf16_to_f32(le->E, rows * 64, tmp, s);
+    cudaError_t e2 = e1 == cudaSuccess ? cudaMemcpyAsync(out, tmp, (size_t)rows * 64 * 4, cudaMemcpyDeviceToHost, s)
+                                       : e1;
+    cudaError_t e3 = cudaStreamSynchronize(s);
+    cudaFree(tmp);
+    CK(e2);
+    CK(e3);
     return DTWS_OK;
 }
 

@@ -21,7 +21,19 @@ constexpr int kListMax = 128;       // result list capacity (k + near-tie margin
 constexpr int kSeedMax = 128;       // random seeds + proxy proposals
 constexpr int kPropMax = 64;
 constexpr int kProxyStride = 2;     // the proxy scan looks at every other window
-constexpr int kEdMax = kKMax + kPropMax * (kProxyStride + 1);
+// Euclidean seeds: random windows + the neighbourhoods of the proposals
+// (+-1 window for the proxy scan; +-b/2, b <= 128, for the learned scan with
+// at most kLearnPropMax proposals)
+constexpr int kLearnPropMax = 16;
+// per-series block envelope: sparse table of max / min over blocks of
+// kEnvG samples, levels 0..kEnvLevels-1 (block ranges up to 2^10 blocks,
+// enough for any band of a query of at most kMMax samples)
+constexpr int kEnvG = 16;
+constexpr int kEnvLevels = 11;
+// learned proposal encoder: parameter count and packed-weight blob size
+constexpr int kEncParams = 38112;
+constexpr int kEncBlobBytes = 1024 + 2 * 3 * 32 * 224 * 2 + 64 * 256 * 2;
+constexpr int kEdMax = kKMax + kLearnPropMax * 129 + 48;
 constexpr int kTile = 1024;         // windows per lower-bound tile
 constexpr int kProxyTile = 4096;    // windows per proxy-scan tile (a multiple of kTile)
 constexpr int kStages = 4;          // shared-memory stages of the scan pipeline
@@ -63,6 +75,7 @@ struct QueryState {
     double margin_d64[kListMax];
     unsigned long long ctr[kCtrN];
     float thr_scan;                        // threshold the LB scan used
+    float e_q[64];                         // learned embedding of the query
     unsigned long long tile_ctr[2];        // dynamic tile cursors: proxy scan, LB scan
     int valid;                             // 0 when the query is non-finite
     int hist[kBins];

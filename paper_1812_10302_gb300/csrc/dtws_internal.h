@@ -15,13 +15,17 @@ void set_error_detail(const char *fmt, ...);
 
 // ---- series level (series_kernels.cu)
 cudaError_t launch_check_finite(const float *x, int64_t n, int *flag, cudaStream_t s);
-cudaError_t launch_prefix(const float *x, int64_t n, double *P1, double *P2, double *T1,
-                          double *T2, double *A, cudaStream_t s);
-cudaError_t launch_window_stats(const float *x, int64_t n, int m, const double *P1,
-                                const double *P2, const double *T1, const double *T2,
-                                const double *A, float *mu_hi, float *mu_lo, float *inv_sigma,
-                                float *smu_hi, float *smu_lo, float *sinv_sigma, cudaStream_t s);
+// pf: 4*n floats (P1 hi, P1 lo, P2 hi, P2 lo); bf: 5*nb floats (T1 hi, lo,
+// T2 hi, lo, anchors); ok: nb flags; nb = ceil(n / kBlockB); maxabs: one
+// word of scratch; scale: one float (the series' power-of-two scale)
+cudaError_t launch_prefix(const float *x, int64_t n, float *pf, float *bf, int *ok, unsigned *maxabs,
+                          float *scale, cudaStream_t s);
+cudaError_t launch_window_stats(const float *x, int64_t n, int m, const float *pf, const float *bf,
+                                const int *ok, const float *scale, float *mu_hi, float *mu_lo, float *inv_sigma, float *smu_hi,
+                                float *smu_lo, float *sinv_sigma, int num_sms, cudaStream_t s);
 cudaError_t launch_envelope(const float *x, int64_t n, int r, float *U, float *L, cudaStream_t s);
+// block envelope: st = [max levels 0..kEnvLevels-1 | min levels], nblk floats each
+cudaError_t launch_block_envelope(const float *x, int64_t n, float *st, int64_t nblk, cudaStream_t s);
 
 // ---- query level (query_kernels.cu)
 struct QueryBufs {
@@ -29,7 +33,9 @@ struct QueryBufs {
     const float *x;              // padded series
     const float *mu_hi, *mu_lo, *inv_sigma;  // window stats for m
     const float *smu_hi, *smu_lo, *sinv_sigma;  // the same for every kProxyStride-th window
-    const float *U, *L;          // series envelope for r (may be null for *_at)
+    const float *U, *L;          // exact series envelope for r, or null:
+    const float *stmax, *stmin;  // per-series block envelope (sparse table), used when U is null
+    int64_t nblk, n;             // its blocks; series length
     float *qh32;                 // normalised query, FP32 [m]
     double *qh64;                // normalised query, FP64 [m]
     float *Uq, *Lq;              // query envelope [m]
@@ -46,8 +52,9 @@ cudaError_t launch_query_reset(const QueryBufs &b, const QueryArgs &a, cudaStrea
 cudaError_t launch_qprep(const float *Q, const QueryBufs &b, const QueryArgs &a, cudaStream_t s);
 cudaError_t launch_seed_scan(const QueryBufs &b, const QueryArgs &a, int proposals, int terms,
                              cudaStream_t s);
+// half: Euclidean seeds cover the proposals' offsets +-half
 cudaError_t launch_seed_gather(const QueryBufs &b, const QueryArgs &a, int n_random,
-                               int proposals, unsigned long long rng, cudaStream_t s);
+                               int proposals, int half, unsigned long long rng, cudaStream_t s);
 cudaError_t launch_seed_ed(const QueryBufs &b, const QueryArgs &a, cudaStream_t s);
 cudaError_t launch_dtw_seeds(const QueryBufs &b, const QueryArgs &a, cudaStream_t s);
 cudaError_t launch_prescore(const QueryBufs &b, const QueryArgs &a, cudaStream_t s);
@@ -64,5 +71,24 @@ cudaError_t launch_dtw_at_f64(const QueryBufs &b, const QueryArgs &a, const int6
                               int64_t count, double *out, cudaStream_t s);
 cudaError_t launch_lbs_at(const QueryBufs &b, const QueryArgs &a, const int64_t *offsets,
                           int64_t count, float *kim, float *kq, float *ks, cudaStream_t s);
+
+// ---- learned proposal encoder (encoder.cu)
+// params -> packed blob; with `adam`, one Adam step first (c1, c2: bias corrections)
+cudaError_t launch_enc_pack(float *params, const float *grad, float *m1, float *v1, uint8_t *blob, bool adam,
+                            float lr, float beta1, float beta2, float eps, float c1, float c2, cudaStream_t s);
+cudaError_t launch_enc_prep(const float *X, const int64_t *off, int rows, int m, float *u, cudaStream_t s);
+// ws == nullptr: embeddings to e; else the training workspace receives activations
+cudaError_t launch_enc_forward(const uint8_t *blob, const float *u, int rows, float *e, uint8_t *ws, int num_sms,
+                               cudaStream_t s);
+// loss (accumulated into *loss), data and weight gradients of B triples
+cudaError_t launch_enc_backward(const uint8_t *blob, const float *y, int B, float *loss, float *grad,
+                                uint8_t *ws, int num_sms, cudaStream_t s);
+size_t enc_workspace_bytes(int rows);
+cudaError_t launch_enc_series(const uint8_t *blob, const float *x, int64_t n, int b, const float *inv_sigma,
+                              int64_t Nw, void *E, int num_sms, cudaStream_t s);
+cudaError_t launch_enc_query(const uint8_t *blob, const QueryBufs &b, const QueryArgs &a, cudaStream_t s);
+cudaError_t launch_learn_scan(const QueryBufs &b, const void *E, int64_t Nw, int stride, int proposals,
+                              cudaStream_t s);
+cudaError_t launch_bf16_to_f32(const void *src, int64_t count, float *dst, cudaStream_t s);
 
 }  // namespace dtws

@@ -433,13 +433,12 @@ __device__ int distinct_append(unsigned *dst, int cap, const unsigned *src, int 
     return *count < cap ? *count : cap;
 }
 
-__global__ void k_seed_gather(QueryBufs b, QueryArgs a, int n_random, int proposals,
+__global__ void k_seed_gather(QueryBufs b, QueryArgs a, int n_random, int proposals, int H,
                               unsigned long long rng) {
     __shared__ unsigned cand[kEdMax];
     __shared__ int nc;
     if (!b.st->valid) return;
     const int lane = threadIdx.x;  // one warp
-    constexpr int H = kProxyStride / 2;
     // exact-DTW seeds: random windows + proposals
     for (int j = lane; j < n_random; j += 32)
         cand[j] = (unsigned)(splitmix64(rng + (unsigned long long)j) % (unsigned long long)a.N);
@@ -500,8 +499,8 @@ cudaError_t launch_seed_ed(const QueryBufs &b, const QueryArgs &a, cudaStream_t 
 }
 
 cudaError_t launch_seed_gather(const QueryBufs &b, const QueryArgs &a, int n_random, int proposals,
-                               unsigned long long rng, cudaStream_t s) {
-    k_seed_gather<<<1, 32, 0, s>>>(b, a, n_random, proposals, rng);
+                               int half, unsigned long long rng, cudaStream_t s) {
+    k_seed_gather<<<1, 32, 0, s>>>(b, a, n_random, proposals, half, rng);
     return cudaGetLastError();
 }
 
@@ -555,7 +554,8 @@ __global__ void __launch_bounds__(256) k_dtw(QueryBufs b, QueryArgs a, const int
     QueryState *st = b.st;
     if (!st->valid) return;
     const int m = a.m, r = a.r;
-    const DtwSmem<float> lay = dtw_smem<float, L, K>(m, r, staged != 0, MODE == kModeSurv && b.U != nullptr);
+    const bool has_env = b.U != nullptr || b.stmax != nullptr;
+    const DtwSmem<float> lay = dtw_smem<float, L, K>(m, r, staged != 0, MODE == kModeSurv && has_env);
     const float INF = DINF;
     float *qbase = (float *)smraw, *qs = qbase + lay.pad;
     for (int t = threadIdx.x; t < m; t += blockDim.x) qs[t] = b.qh32[t];
@@ -630,6 +630,12 @@ __global__ void __launch_bounds__(256) k_dtw(QueryBufs b, QueryArgs a, const int
         TailCtx tc;
         tc.Uw = b.U ? b.U + idx : nullptr;
         tc.Lw = b.L ? b.L + idx : nullptr;
+        tc.stmax = b.stmax;
+        tc.stmin = b.stmin;
+        tc.nblk = b.nblk;
+        tc.n = b.n;
+        tc.t0 = idx;
+        tc.r = r;
         tc.qs = qs;
         tc.mh = mh;
         tc.is = is;
@@ -650,7 +656,7 @@ __global__ void __launch_bounds__(256) k_dtw(QueryBufs b, QueryArgs a, const int
                                               cells);
             else
                 d = dtw_band<float, L, true>(qs, xw, cbuf, mh, is, ls,
-                                             (b.U && MODE == kModeSurv) ? &tc : nullptr, ring, m, r, thr,
+                                             (has_env && MODE == kModeSurv) ? &tc : nullptr, ring, m, r, thr,
                                              gmask, lane, cells);
         } else {
             if (MODE == kModeOut)
@@ -848,7 +854,8 @@ template <int MODE>
 static cudaError_t dtw_dispatch(const QueryBufs &b, const QueryArgs &a, const int64_t *offsets,
                                 int64_t count, float *out, int64_t count_for_grid, cudaStream_t s) {
     DtwPlan p;
-    if (!plan_dtw<float>(a.m, a.r, MODE == kModeSurv && b.U != nullptr, &p)) return cudaErrorInvalidValue;
+    if (!plan_dtw<float>(a.m, a.r, MODE == kModeSurv && (b.U != nullptr || b.stmax != nullptr), &p))
+        return cudaErrorInvalidValue;
     const int blocks = dtw_blocks(p, b.num_sms, count_for_grid);
 #define DTWS_CASE(LL, KK)                                                                                     \
     if (p.L == LL && p.K == KK) {                                                                             \

@@ -1,6 +1,7 @@
 // series_kernels.cu -- per-series and per-(series, m | r) kernels:
 //   * finiteness check of the series;
-//   * anchored FP64 prefix sums of the series (once per series);
+//   * anchored, compensated FP64 prefix sums of the series (once per
+//     series), stored as FP32 pairs;
 //   * window statistics for a query length m (Sec. 2.2, Eq. 5, population
 //     sigma) from those sums;
 //   * the raw sliding envelope of the series for a band half-width r
@@ -31,122 +32,219 @@ cudaError_t launch_check_finite(const float *x, int64_t n, int *flag, cudaStream
 // One thread per block b of kBlockB samples.  The anchor a_b = x[b*B]; every
 // sum inside the block runs over d = x - a_b, in FP64, so no sum grows with
 // the series.  The running sums are compensated (Neumaier's variant of Kahan
-// summation), so each stored prefix is within about one FP64 ulp of the
-// exact sum of the (rounded) terms, whatever the block length -- plain
-// sequential sums could drift by up to B/2 ulps.  Outputs, for t in block b:
+// summation), so each prefix is within about one FP64 ulp of the exact sum of
+// the (rounded) terms, whatever the block length -- plain sequential sums
+// could drift by up to B/2 ulps.  Each FP64 prefix is stored as the exact
+// pair hi = fl32(v), lo = fl32(v - hi) (|v - hi - lo| <= 2^-48 |v|), so the
+// per-window arithmetic runs in FP32 pairs instead of FP64 (GB300 issues
+// FP64 at a small fraction of its FP32 rate).  Outputs, for t in block b:
 //   P1[t] = sum_{bB <= u < t} d_u,  P2[t] = sum d_u^2   (exclusive prefix)
-//   T1[b], T2[b] = block totals, A[b] = a_b.
+//   T1[b], T2[b] = block totals, A[b] = a_b,
+//   ok[b] = 1 when every nonzero |d| in the block lies in [2^-40, 2^40], so
+//   that no pair over- or underflows FP32 (else windows touching the block
+//   take the two-pass FP64 path).
+// All of it in units scaled by one power of two per series, 2^s with s such
+// that the largest in-block excursion max|x - a_b| lies in [1, 2) (exact
+// scaling; it keeps the pairs away from FP32 over- and underflow whatever the
+// series' units).  Layout: pf = [P1h | P1l | P2h | P2l] (n floats each),
+// bf = [T1h | T1l | T2h | T2l | A] (nb floats each, A scaled), scale[0] = 2^s.
 __device__ __forceinline__ void neumaier_add(double &s, double &c, double v) {
     const double t = s + v;
     c += fabs(s) >= fabs(v) ? (s - t) + v : (v - t) + s;
     s = t;
 }
 
-__global__ void k_prefix(const float *__restrict__ x, int64_t n, double *__restrict__ P1,
-                         double *__restrict__ P2, double *__restrict__ T1, double *__restrict__ T2,
-                         double *__restrict__ A, int64_t nb) {
+__device__ __forceinline__ void split_store(double v, float *hi, float *lo, int64_t t) {
+    const float h = (float)v;
+    hi[t] = h;
+    lo[t] = (float)(v - (double)h);
+}
+
+// largest |x[t] - x[block start]| of the series, as float bits (non-negative
+// floats order like their bits)
+__global__ void k_block_maxabs(const float *__restrict__ x, int64_t n, unsigned *out) {
+    float mx = 0.0f;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const float d = (float)fabs((double)x[t] - (double)x[t / kBlockB * kBlockB]);
+        mx = fmaxf(mx, d);
+    }
+    for (int o = 16; o; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if (lane_id() == 0) atomicMax(out, __float_as_uint(mx));
+}
+
+__global__ void k_prefix(const float *__restrict__ x, int64_t n, float *__restrict__ pf,
+                         float *__restrict__ bf, int *__restrict__ ok, int64_t nb,
+                         const unsigned *__restrict__ maxabs, float *__restrict__ scale_out) {
     const int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const float mx = __uint_as_float(*maxabs);
+    // 2^s with mx * 2^s in [1, 2); 1 for a constant series
+    const double sc = mx > 0.0f ? ldexp(1.0, -ilogbf(mx)) : 1.0;
+    if (b == 0) scale_out[0] = (float)sc;
     if (b >= nb) return;
     const int64_t t0 = b * kBlockB;
     const int64_t t1 = t0 + kBlockB < n ? t0 + kBlockB : n;
-    const double a = (double)x[t0];
+    float *p1h = pf, *p1l = pf + n, *p2h = pf + 2 * n, *p2l = pf + 3 * n;
+    const float af = x[t0];
+    const double a = (double)af;
     double s1 = 0.0, c1 = 0.0, s2 = 0.0, c2 = 0.0;
+    bool good = true;
     for (int64_t t = t0; t < t1; ++t) {
-        P1[t] = s1 + c1;
-        P2[t] = s2 + c2;
-        const double d = (double)x[t] - a;
+        split_store(s1 + c1, p1h, p1l, t);
+        split_store(s2 + c2, p2h, p2l, t);
+        const double d = ((double)x[t] - a) * sc;
+        const double ad = fabs(d);
+        good &= d == 0.0 || (ad >= 9.094947017729282e-13 && ad <= 1099511627776.0);  // 2^-40, 2^40
         neumaier_add(s1, c1, d);
         neumaier_add(s2, c2, d * d);
     }
-    T1[b] = s1 + c1;
-    T2[b] = s2 + c2;
-    A[b] = a;
+    split_store(s1 + c1, bf, bf + nb, b);
+    split_store(s2 + c2, bf + 2 * nb, bf + 3 * nb, b);
+    const double as = a * sc;
+    bf[4 * nb + b] = (float)as;
+    ok[b] = good && (double)(float)as == as && fabs(as) < 1e30 ? 1 : 0;
 }
 
-cudaError_t launch_prefix(const float *x, int64_t n, double *P1, double *P2, double *T1,
-                          double *T2, double *A, cudaStream_t s) {
+cudaError_t launch_prefix(const float *x, int64_t n, float *pf, float *bf, int *ok, unsigned *maxabs,
+                          float *scale, cudaStream_t s) {
     int64_t nb = (n + kBlockB - 1) / kBlockB;
-    k_prefix<<<(unsigned)((nb + 63) / 64), 64, 0, s>>>(x, n, P1, P2, T1, T2, A, nb);
+    cudaError_t e = cudaMemsetAsync(maxabs, 0, sizeof(unsigned), s);
+    if (e != cudaSuccess) return e;
+    int64_t blocks = (n + 255) / 256;
+    if (blocks > 4096) blocks = 4096;
+    k_block_maxabs<<<(unsigned)blocks, 256, 0, s>>>(x, n, maxabs);
+    k_prefix<<<(unsigned)((nb + 63) / 64), 64, 0, s>>>(x, n, pf, bf, ok, nb, maxabs, scale);
     return cudaGetLastError();
 }
 
-// ------------------------------------------------------------------ window stats
-// Sum over [bB, e) of block b's anchored terms, bB < e <= end of block b.
-__device__ __forceinline__ double upto(const double *P, const double *T, int64_t n, int64_t b,
-                                       int64_t e) {
-    int64_t end = (b + 1) * kBlockB < n ? (b + 1) * kBlockB : n;
-    return e == end ? T[b] : P[e];
+// ------------------------------------------------------------------ FP32 pairs
+// Unevaluated sums hi + lo of two floats with error-free transformations
+// (Knuth's TwoSum, Dekker's Fast2Sum, the FMA product error).
+struct f2 {
+    float hi, lo;
+};
+__device__ __forceinline__ f2 two_sum(float a, float b) {
+    const float s = a + b, bb = s - a;
+    return {s, (a - (s - bb)) + (b - bb)};
 }
+__device__ __forceinline__ f2 fast_two_sum(float a, float b) {
+    const float s = a + b;
+    return {s, b - (s - a)};
+}
+__device__ __forceinline__ f2 f2_add(f2 x, f2 y) {
+    f2 s = two_sum(x.hi, y.hi);
+    const f2 t = two_sum(x.lo, y.lo);
+    s.lo += t.hi;
+    s = fast_two_sum(s.hi, s.lo);
+    s.lo += t.lo;
+    return fast_two_sum(s.hi, s.lo);
+}
+__device__ __forceinline__ f2 f2_neg(f2 x) { return {-x.hi, -x.lo}; }
+__device__ __forceinline__ f2 f2_mul(f2 x, f2 y) {
+    const float p = x.hi * y.hi;
+    float e = fmaf(x.hi, y.hi, -p);
+    e = fmaf(x.hi, y.lo, fmaf(x.lo, y.hi, e));
+    return fast_two_sum(p, e);
+}
+__device__ __forceinline__ f2 f2_mul_f(f2 x, float f) {
+    const float p = x.hi * f;
+    const float e = fmaf(x.lo, f, fmaf(x.hi, f, -p));
+    return fast_two_sum(p, e);
+}
+__device__ __forceinline__ f2 ld2(const float *h, const float *l, int64_t t) { return {h[t], l[t]}; }
 
+// ------------------------------------------------------------------ window stats
 // Eq. 5 statistics of window i = [i, i+m) from the anchored sums.  A window
 // spans at most two blocks (m <= kBlockB); the second block's sums are moved
 // to the first anchor with the exact shift identities
 //   sum(x - a0)   = sum(x - a1) + k (a1 - a0)
-//   sum(x - a0)^2 = sum(x - a1)^2 + 2 (a1 - a0) sum(x - a1) + k (a1 - a0)^2.
-// var = S2/m - (S1/m)^2.  The window is evaluated two-pass from its samples
-// instead when the prefix differences cannot carry var to FP32 accuracy:
+//   sum(x - a0)^2 = sum(x - a1)^2 + 2 (a1 - a0) sum(x - a1) + k (a1 - a0)^2,
+// all in FP32 pairs (about 2^-47 relative per operation).  var = S2/m - (S1/m)^2.
+// The window is evaluated two-pass from its samples in FP64 instead when
+//   * a block it touches is not ok (see k_prefix), or
 //   * the subtraction cancelled, var <= 1e-6 * S2/m, or
-//   * var is below the bound the prefix rounding implies.  Each compensated
-//     prefix is within ~2^-53 of its magnitude, so S2 is off by at most
-//     ~3*2^-53*M2 and S1 by ~2*2^-53*sqrt(B*M2), with M2 the block totals of
+//   * var is below the bound the stored sums' rounding implies.  Each stored
+//     prefix is within ~2^-48 of its magnitude, so S2 is off by at most
+//     ~3*2^-48*M2 and S1 by ~2*2^-48*sqrt(B*M2), with M2 the block totals of
 //     the squares (plus the shift terms); var then holds 2^-26 relative
-//     accuracy only if m*var >= 2^-27*(3*M2 + 4|S1/m|*sqrt(B*M2)).
+//     accuracy only if m*var >= 2^-22*(3*M2 + 4|S1/m|*sqrt(B*M2)).
 // Zero-variance rule: var <= 1e-24*max(1, mu^2) gives inv_sigma = 0 (the
 // window normalises to all zeros).
-__global__ void k_window_stats(const float *__restrict__ x, int64_t n, int m,
-                               const double *__restrict__ P1, const double *__restrict__ P2,
-                               const double *__restrict__ T1, const double *__restrict__ T2,
-                               const double *__restrict__ A, float *__restrict__ mu_hi,
-                               float *__restrict__ mu_lo, float *__restrict__ inv_sigma,
-                               float *__restrict__ smu_hi, float *__restrict__ smu_lo,
-                               float *__restrict__ sinv_sigma) {
+__global__ void k_window_stats(const float *__restrict__ x, int64_t n, int m, const float *__restrict__ pf,
+                               const float *__restrict__ bf, const int *__restrict__ ok,
+                               const float *__restrict__ scale, int64_t nb,
+                               float *__restrict__ mu_hi, float *__restrict__ mu_lo,
+                               float *__restrict__ inv_sigma, float *__restrict__ smu_hi,
+                               float *__restrict__ smu_lo, float *__restrict__ sinv_sigma) {
     const int64_t N = n - m + 1;
-    const double inv_m = 1.0 / (double)m;
+    const float sc = scale[0], isc = 1.0f / sc;  // powers of two
+    const float *p1h = pf, *p1l = pf + n, *p2h = pf + 2 * n, *p2l = pf + 3 * n;
+    const float *t1h = bf, *t1l = bf + nb, *t2h = bf + 2 * nb, *t2l = bf + 3 * nb, *A = bf + 4 * nb;
+    // 1/m as a pair: hi = fl(1/m), lo = (1 - hi*m)/m (the FMA residual is exact)
+    const float ih = 1.0f / (float)m;
+    const f2 inv_m = {ih, fmaf(-ih, (float)m, 1.0f) * ih};
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N;
          i += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t b0 = i / kBlockB, e = i + m;
-        const double a0 = A[b0];
-        double S1, S2;
+        const int64_t b0 = i / kBlockB, e = i + m, end0 = (b0 + 1) * kBlockB;
+        const float a0 = A[b0];
+        f2 S1, S2;
         float M2;  // magnitude of the squared sums the prefix differences used
-        if (e <= (b0 + 1) * kBlockB) {
-            S1 = upto(P1, T1, n, b0, e) - P1[i];
-            S2 = upto(P2, T2, n, b0, e) - P2[i];
-            M2 = (float)T2[b0];
+        bool good = ok[b0] != 0;
+        const f2 P1i = ld2(p1h, p1l, i), P2i = ld2(p2h, p2l, i);
+        if (e <= end0) {
+            const bool tot = e == (end0 < n ? end0 : n);
+            S1 = f2_add(tot ? ld2(t1h, t1l, b0) : ld2(p1h, p1l, e), f2_neg(P1i));
+            S2 = f2_add(tot ? ld2(t2h, t2l, b0) : ld2(p2h, p2l, e), f2_neg(P2i));
+            M2 = t2h[b0];
         } else {
-            const int64_t b1 = b0 + 1;
-            const double k = (double)(e - b1 * kBlockB), da = A[b1] - a0;
-            const double e1 = upto(P1, T1, n, b1, e), e2 = upto(P2, T2, n, b1, e);
-            S1 = (T1[b0] - P1[i]) + fma(k, da, e1);
-            S2 = (T2[b0] - P2[i]) + fma(2.0 * da, e1, fma(k * da, da, e2));
-            M2 = (float)(T2[b0] + T2[b1]) + 2.0f * fabsf((float)da) * sqrtf((float)kBlockB * (float)T2[b1]) +
-                 (float)(k * da * da);
+            const int64_t b1 = b0 + 1, end1 = (b1 + 1) * kBlockB;
+            good = good && ok[b1] != 0;
+            const bool tot = e == (end1 < n ? end1 : n);
+            const float k = (float)(e - b1 * kBlockB);
+            const f2 da = two_sum(A[b1], -a0);
+            const f2 e1 = tot ? ld2(t1h, t1l, b1) : ld2(p1h, p1l, e);
+            const f2 e2 = tot ? ld2(t2h, t2l, b1) : ld2(p2h, p2l, e);
+            S1 = f2_add(f2_add(ld2(t1h, t1l, b0), f2_neg(P1i)), f2_add(f2_mul_f(da, k), e1));
+            const f2 da_e1 = f2_mul(da, e1);
+            const f2 sh = f2_add(f2_add({2.0f * da_e1.hi, 2.0f * da_e1.lo}, f2_mul_f(f2_mul(da, da), k)), e2);
+            S2 = f2_add(f2_add(ld2(t2h, t2l, b0), f2_neg(P2i)), sh);
+            M2 = t2h[b0] + t2h[b1] + 2.0f * fabsf(da.hi) * sqrtf((float)kBlockB * t2h[b1]) + k * da.hi * da.hi;
         }
-        double mr = S1 * inv_m;
-        double ms = S2 * inv_m;
-        double var = fma(-mr, mr, ms);
-        double mu = a0 + mr;
-        const float bound = 7.450580596923828e-09f *  // 2^-27
-                            (3.0f * M2 + 4.0f * fabsf((float)mr) * sqrtf((float)kBlockB * M2));
-        if (var <= 1e-6 * ms || (float)var * (float)m < bound) {
-            // two-pass from the samples (rare: near-constant windows)
+        const f2 mr = f2_mul(S1, inv_m);
+        const f2 ms = f2_mul(S2, inv_m);
+        const f2 var2 = f2_add(ms, f2_neg(f2_mul(mr, mr)));
+        const f2 mu2 = f2_add(mr, {a0, 0.0f});
+        const float bound = 2.384185791015625e-07f *  // 2^-22
+                            (3.0f * M2 + 4.0f * fabsf(mr.hi) * sqrtf((float)kBlockB * M2));
+        float mh = mu2.hi * isc, ml = mu2.lo * isc, is = 0.0f;
+        if (!good || var2.hi <= 1e-6f * ms.hi || var2.hi * (float)m < bound) {
+            // two-pass from the samples in FP64 (rare: near-constant windows,
+            // or blocks whose values the FP32 pairs cannot carry)
             double s = 0.0;
             for (int j = 0; j < m; ++j) s += (double)x[i + j];
-            mu = s / (double)m;
+            const double mu = s / (double)m;
             double v = 0.0;
             for (int j = 0; j < m; ++j) {
-                double d = (double)x[i + j] - mu;
+                const double d = (double)x[i + j] - mu;
                 v += d * d;
             }
-            var = v / (double)m;
-        }
-        const float mh = (float)mu, ml = (float)(mu - (double)mh);
-        const double mm = mu * mu;
-        float is = 0.0f;
-        if (!(var <= 1e-24 * (mm > 1.0 ? mm : 1.0))) {
-            // 1/sqrt(var): FP32 estimate refined by one Newton step in FP64
-            double y = (double)rsqrtf((float)var);
-            y = y * fma(-0.5 * var * y, y, 1.5);
-            is = (float)y;
+            const double var = v / (double)m;
+            mh = (float)mu;
+            ml = (float)(mu - (double)mh);
+            const double mm = mu * mu;
+            if (!(var <= 1e-24 * (mm > 1.0 ? mm : 1.0))) {
+                double y = (double)rsqrtf((float)var);
+                y = y * fma(-0.5 * var * y, y, 1.5);
+                is = (float)y;
+            }
+        } else if (!(sqrtf(var2.hi) <= 1e-12f * fmaxf(sc, fabsf(mu2.hi)))) {
+            // (the zero-variance rule in scaled units.)  1/sqrt(var): FP32
+            // estimate refined by one Newton step whose residual 1 - var*y^2
+            // is taken in pairs; then back to the series' units
+            const float y = rsqrtf(var2.hi);
+            const f2 yy = {y * y, fmaf(y, y, -y * y)};
+            const f2 r = f2_add({1.0f, 0.0f}, f2_neg(f2_mul(var2, yy)));
+            is = fmaf(0.5f * y, r.hi, y) * sc;
         }
         mu_hi[i] = mh;
         mu_lo[i] = ml;
@@ -159,15 +257,14 @@ __global__ void k_window_stats(const float *__restrict__ x, int64_t n, int m,
     }
 }
 
-cudaError_t launch_window_stats(const float *x, int64_t n, int m, const double *P1,
-                                const double *P2, const double *T1, const double *T2,
-                                const double *A, float *mu_hi, float *mu_lo, float *inv_sigma,
-                                float *smu_hi, float *smu_lo, float *sinv_sigma, cudaStream_t s) {
-    int64_t N = n - m + 1;
+cudaError_t launch_window_stats(const float *x, int64_t n, int m, const float *pf, const float *bf,
+                                const int *ok, const float *scale, float *mu_hi, float *mu_lo, float *inv_sigma, float *smu_hi,
+                                float *smu_lo, float *sinv_sigma, int num_sms, cudaStream_t s) {
+    const int64_t N = n - m + 1, nb = (n + kBlockB - 1) / kBlockB;
     int64_t blocks = (N + 255) / 256;
-    if (blocks > 152 * 32) blocks = 152 * 32;
-    k_window_stats<<<(unsigned)blocks, 256, 0, s>>>(x, n, m, P1, P2, T1, T2, A, mu_hi, mu_lo,
-                                                    inv_sigma, smu_hi, smu_lo, sinv_sigma);
+    if (blocks > (int64_t)num_sms * 16) blocks = (int64_t)num_sms * 16;
+    k_window_stats<<<(unsigned)blocks, 256, 0, s>>>(x, n, m, pf, bf, ok, scale, nb, mu_hi, mu_lo, inv_sigma, smu_hi,
+                                                    smu_lo, sinv_sigma);
     return cudaGetLastError();
 }
 
@@ -240,6 +337,46 @@ cudaError_t launch_envelope(const float *x, int64_t n, int r, float *U, float *L
                                          (int)smem);
     if (e != cudaSuccess) return e;
     k_envelope<<<(unsigned)blocks, kEnvThreads, smem, s>>>(x, n, r, U, L);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ block envelope
+// Sparse table over blocks of kEnvG samples: level 0 holds each block's max
+// (min), level k the max (min) of blocks [j, j + 2^k); entries whose range
+// passes the last block are left unset and never read.
+__global__ void k_env_level0(const float *__restrict__ x, int64_t n, float *__restrict__ mx,
+                             float *__restrict__ mn, int64_t nblk) {
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < nblk;
+         j += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t t0 = j * kEnvG, t1 = t0 + kEnvG < n ? t0 + kEnvG : n;
+        float u = x[t0], l = u;
+        for (int64_t t = t0 + 1; t < t1; ++t) {
+            u = fmaxf(u, x[t]);
+            l = fminf(l, x[t]);
+        }
+        mx[j] = u;
+        mn[j] = l;
+    }
+}
+
+__global__ void k_env_level(float *__restrict__ mx, float *__restrict__ mn, int64_t nblk, int k) {
+    const int64_t h = 1ll << (k - 1), last = nblk - (1ll << k);
+    const float *pm = mx + (size_t)(k - 1) * nblk, *pn = mn + (size_t)(k - 1) * nblk;
+    float *qm = mx + (size_t)k * nblk, *qn = mn + (size_t)k * nblk;
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j <= last;
+         j += (int64_t)gridDim.x * blockDim.x) {
+        qm[j] = fmaxf(pm[j], pm[j + h]);
+        qn[j] = fminf(pn[j], pn[j + h]);
+    }
+}
+
+cudaError_t launch_block_envelope(const float *x, int64_t n, float *st, int64_t nblk, cudaStream_t s) {
+    float *mx = st, *mn = st + (size_t)kEnvLevels * nblk;
+    int64_t blocks = (nblk + 255) / 256;
+    if (blocks > 4096) blocks = 4096;
+    k_env_level0<<<(unsigned)blocks, 256, 0, s>>>(x, n, mx, mn, nblk);
+    for (int k = 1; k < kEnvLevels && (1ll << k) <= nblk; ++k)
+        k_env_level<<<(unsigned)blocks, 256, 0, s>>>(mx, mn, nblk, k);
     return cudaGetLastError();
 }
 

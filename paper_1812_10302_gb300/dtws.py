@@ -53,7 +53,9 @@ class dtws_options(ctypes.Structure):
         ("proxy_terms", ctypes.c_int32),
         ("ordering", ctypes.c_int32),
         ("timing", ctypes.c_int32),
-        ("reserved0", ctypes.c_int32),
+        ("exact_envelope", ctypes.c_int32),
+        ("batch_lanes", ctypes.c_int32),
+        ("batch_graph", ctypes.c_int32),
         ("wait_limit_ns", ctypes.c_int64),
         ("rng_seed", ctypes.c_uint64),
     ]
@@ -106,7 +108,27 @@ _SIGS = {
     "dtws_dtw_at_f64": (_S, [_P, _P, _I32, _I32, _P, _I64, _P, _P]),
     "dtws_lower_bounds_at": (_S, [_P, _P, _I32, _I32, _P, _I64, _P, _P, _P, _P]),
     "dtws_dtw_at_noalloc": (_S, [_P, _I64, _P, _I32, _I32, _P, _I64, _P, _P]),
+    "dtws_set_encoder": (_S, [_P, _P, _I32, _P]),
+    "dtws_learned_embeddings": (_S, [_P, _I32, _P, _I64, _P]),
+    "dtws_enc_prep": (_S, [_P, _I64, _P, _I32, _I32, _P, _P]),
+    "dtws_enc_forward": (_S, [_P, _P, _I32, _P, _P]),
+    "dtws_enc_loss_grad": (_S, [_P, _P, _P, _P, _I32, _P, _P, _P]),
+    "dtws_trainer_create": (_S, [_P, _I32, _I32, _P, _P]),
+    "dtws_trainer_step": (_S, [_P, _P, _P, _I64, _P, _P, _I32, _P, _I32, _P, _P]),
+    "dtws_trainer_params": (_S, [_P, _P, _P]),
+    "dtws_trainer_destroy": (_S, [_P]),
 }
+
+DTWS_ORDER_PLAIN = 0
+DTWS_ORDER_LEARNED = 1
+DTWS_ENC_PARAMS = 38112
+DTWS_ENC_DIM = 64
+DTWS_ENC_U = 64
+
+
+class dtws_adam(ctypes.Structure):
+    _fields_ = [("lr", ctypes.c_float), ("beta1", ctypes.c_float), ("beta2", ctypes.c_float),
+                ("eps", ctypes.c_float)]
 
 
 def library_path() -> str:
@@ -350,6 +372,18 @@ class Index:
                                          _stream_ptr(stream)), "dtws_dtw_at_f64")
         return out
 
+    def set_encoder(self, params, stream=None):
+        p = _Arg(params, np.float32)
+        _check(self._lib.dtws_set_encoder(self.h, p.ptr, p.size, _stream_ptr(stream)), "dtws_set_encoder")
+
+    def learned_embeddings(self, m: int, stream=None) -> np.ndarray:
+        b = m // 64
+        rows = (self.n - m) // b + 1
+        out = np.empty((rows, DTWS_ENC_DIM), np.float32)
+        _check(self._lib.dtws_learned_embeddings(self.h, m, out.ctypes.data, rows, _stream_ptr(stream)),
+               "dtws_learned_embeddings")
+        return out
+
     def lower_bounds_at(self, Q, r: int, offsets, stream=None):
         q = _Arg(Q, np.float32)
         o = _Arg(offsets, np.int64)
@@ -358,3 +392,76 @@ class Index:
                                               kq.ctypes.data, ks.ctypes.data, _stream_ptr(stream)),
                "dtws_lower_bounds_at")
         return kim, kq, ks
+
+
+# ------------------------------------------------------------------ learned proposals
+def enc_prep(X, offsets, m: int, stream=None) -> np.ndarray:
+    """u [rows][64] of the windows X[offsets[i]:offsets[i]+m] (dtws_enc_prep)."""
+    x = _Arg(X, np.float32)
+    o = np.ascontiguousarray(offsets, dtype=np.int64)
+    u = np.empty((o.size, DTWS_ENC_U), np.float32)
+    _check(load().dtws_enc_prep(x.ptr, x.size, o.ctypes.data, o.size, m, u.ctypes.data, _stream_ptr(stream)),
+           "dtws_enc_prep")
+    return u
+
+
+def enc_forward(params, u, stream=None) -> np.ndarray:
+    """Embeddings [rows][64] of u [rows][64] (dtws_enc_forward)."""
+    p = _Arg(params, np.float32)
+    uu = _Arg(u, np.float32)
+    rows = uu.size // DTWS_ENC_U
+    e = np.empty((rows, DTWS_ENC_DIM), np.float32)
+    _check(load().dtws_enc_forward(p.ptr, uu.ptr, rows, e.ctypes.data, _stream_ptr(stream)), "dtws_enc_forward")
+    return e
+
+
+def enc_loss_grad(params, uq, uc, y, stream=None):
+    """(mean loss, gradient [38112]) of a batch of triples (dtws_enc_loss_grad)."""
+    p = _Arg(params, np.float32)
+    a, b = _Arg(uq, np.float32), _Arg(uc, np.float32)
+    yy = _Arg(y, np.float32)
+    loss = np.zeros(1, np.float32)
+    grad = np.empty(DTWS_ENC_PARAMS, np.float32)
+    _check(load().dtws_enc_loss_grad(p.ptr, a.ptr, b.ptr, yy.ptr, yy.size, loss.ctypes.data, grad.ctypes.data,
+                                     _stream_ptr(stream)), "dtws_enc_loss_grad")
+    return float(loss[0]), grad
+
+
+class Trainer:
+    """Adam on the GPU over the encoder parameters (dtws_trainer_*)."""
+
+    def __init__(self, params, max_batch: int, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8):
+        self._lib = load()
+        p = _Arg(params, np.float32)
+        hp = dtws_adam(lr, beta1, beta2, eps)
+        self.h = ctypes.c_void_p()
+        _check(self._lib.dtws_trainer_create(p.ptr, p.size, max_batch, ctypes.byref(hp), ctypes.byref(self.h)),
+               "dtws_trainer_create")
+
+    def step(self, xq, xc, q_off, c_off, m: int, y, want_loss=True, stream=None):
+        """xq, xc: device tensors (series); q_off, c_off, y: host arrays."""
+        a, b = _Arg(xq, np.float32), _Arg(xc, np.float32)
+        qo = np.ascontiguousarray(q_off, dtype=np.int64)
+        co = np.ascontiguousarray(c_off, dtype=np.int64)
+        yy = np.ascontiguousarray(y, dtype=np.float32)
+        loss = np.zeros(1, np.float32)
+        _check(self._lib.dtws_trainer_step(self.h, a.ptr, b.ptr, a.size, qo.ctypes.data, co.ctypes.data, m,
+                                           yy.ctypes.data, yy.size, loss.ctypes.data if want_loss else None,
+                                           _stream_ptr(stream)), "dtws_trainer_step")
+        return float(loss[0]) if want_loss else None
+
+    def params(self, stream=None) -> np.ndarray:
+        out = np.empty(DTWS_ENC_PARAMS, np.float32)
+        _check(self._lib.dtws_trainer_params(self.h, out.ctypes.data, _stream_ptr(stream)), "dtws_trainer_params")
+        return out
+
+    def close(self):
+        if getattr(self, "h", None):
+            self._lib.dtws_trainer_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

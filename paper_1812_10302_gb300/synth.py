@@ -156,6 +156,37 @@ def fixed_queries(x: np.ndarray, count: int, m: int, seed: int, noise: float = 0
 
 
 # ------------------------------------------------------------------ workloads
+def training_series(n: int, seed: int = 100, noise: float = 0.1):
+    """Encoder training data, disjoint from every evaluation series (its own
+    seeds): a walk with sine bursts (as the learned-proposal workload) and a
+    noisy copy of it (+ N(0, noise)), from which training queries are cut."""
+    x = walk_with_bursts(n, seed, seed + 1, seed + 2)
+    xq = (x.astype(np.float64) + _normals(np.random.default_rng(seed + 3), n, noise)).astype(np.float32)
+    return x, xq
+
+
+def training_pairs(n: int, m: int, count: int, seed: int, per_query: int = 16):
+    """Offsets of (query, candidate) pairs: ``count`` pairs, ``per_query``
+    candidates per query offset q: the copy itself (q), 4 near offsets
+    (q + U{-b..b}, b = m // 64), 4 at q + U{-m..m}, the rest uniform.
+    Returns (q_off, c_off) int64 arrays, grouped by query."""
+    if per_query < 10:
+        raise ValueError("per_query must be at least 10")
+    rng = np.random.default_rng(seed)
+    nq = (count + per_query - 1) // per_query
+    hi = n - m
+    b = max(1, m // 64)
+    q = rng.integers(0, hi + 1, nq)
+    c = np.empty((nq, per_query), np.int64)
+    c[:, 0] = q
+    c[:, 1:5] = q[:, None] + rng.integers(-b, b + 1, (nq, 4))
+    c[:, 5:9] = q[:, None] + rng.integers(-m, m + 1, (nq, 4))
+    c[:, 9:] = rng.integers(0, hi + 1, (nq, per_query - 9))
+    c = np.clip(c, 0, hi)
+    qq = np.repeat(q, per_query)
+    return qq[:count].astype(np.int64), c.reshape(-1)[:count].astype(np.int64)
+
+
 WORKLOADS = {
     "rw1m": dict(n=1_000_000, m=128, w=0.05, k=1, queries=1),
     "rw100m": dict(n=100_000_000, m=512, w=0.10, k=1, queries=1),

@@ -113,3 +113,50 @@ def test_round_bf16_matches_torch():
                         [1 + 2 ** -8, 1 + 3 * 2 ** -8, -1 - 2 ** -8, 0.0, 65504.0]]).astype(np.float32)
     want = torch.from_numpy(v).to(torch.bfloat16).to(torch.float64).numpy()
     np.testing.assert_array_equal(enc.round_bf16(v), want)
+
+
+def test_bf16_forward_differs_from_fp64_by_bf16_rounding_only():
+    """With the BF16 option the embedding moves by about the bfloat16 unit
+    roundoff (2^-9 relative); with weights and inputs that bfloat16 holds
+    exactly (the identity-like network on quarter-integer inputs) it does
+    not move at all."""
+    p = _small_params(12)
+    u = np.random.default_rng(13).normal(size=63)
+    e64 = enc.forward(p, u)[0]
+    e16 = enc.forward(p, u, bf16=True)[0]
+    rel = np.linalg.norm(e16 - e64) / np.linalg.norm(e64)
+    assert 1e-5 < rel < 3e-2
+    W1 = np.zeros((32, 7)); W1[0, 0] = 1
+    Wn = np.zeros((32, 7, 32)); Wn[0, 0, 0] = 1
+    P = np.zeros((64, 256)); P[0, 0] = 1
+    ident = np.concatenate([W1.ravel(), Wn.ravel(), Wn.ravel(), Wn.ravel(), P.ravel()])
+    uq = np.round(u * 4) / 4
+    np.testing.assert_array_equal(enc.forward(ident, uq, bf16=True)[0], enc.forward(ident, uq)[0])
+
+
+def test_bf16_gradient_is_exact_where_rounding_is_the_identity():
+    """On weights and inputs that bfloat16 holds exactly and whose forward
+    intermediates stay exact (identity-like network, quarter-integer
+    inputs), the BF16 emulation's loss equals the FP64 one and its gradient
+    differs only by the rounded backward terms; on general inputs both agree
+    to the BF16 roundoff."""
+    W1 = np.zeros((32, 7)); W1[0, 0] = 1
+    Wn = np.zeros((32, 7, 32)); Wn[0, 0, 0] = 1
+    P = np.zeros((64, 256)); P[0, 0] = 1
+    ident = np.concatenate([W1.ravel(), Wn.ravel(), Wn.ravel(), Wn.ravel(), P.ravel()])
+    rng = np.random.default_rng(14)
+    uq = np.round(rng.normal(size=(2, 63)) * 4) / 4
+    uc = np.round(rng.normal(size=(2, 63)) * 4) / 4
+    L0, g0 = enc.loss_and_grad(ident, uq, uc, [0.25, 2.0])
+    L1, g1 = enc.loss_and_grad(ident, uq, uc, [0.25, 2.0], bf16=True)
+    assert L0 == L1
+    # the loss factor 2*lr/(dist+eps) is not a short binary fraction, so the
+    # rounded gradient terms differ from FP64 by the bfloat16 roundoff; their
+    # sums (with cancellation) agree to about 1% in norm
+    assert np.linalg.norm(g1 - g0) < 1e-2 * np.linalg.norm(g0)
+    p = _small_params(15)
+    uq = rng.normal(size=(3, 63)); uc = uq + 0.3 * rng.normal(size=(3, 63))
+    La, ga = enc.loss_and_grad(p, uq, uc, [0.1, 0.5, 1.0])
+    Lb, gb = enc.loss_and_grad(p, uq, uc, [0.1, 0.5, 1.0], bf16=True)
+    assert abs(La - Lb) < 2e-2 * La
+    assert np.dot(ga, gb) / (np.linalg.norm(ga) * np.linalg.norm(gb)) > 0.99

@@ -238,6 +238,25 @@ dtws_status dtws_lower_bounds_at(dtws_t h, const float *Q, int32_t m, int32_t r,
                                  const int64_t *offsets, int64_t count, float *kim,
                                  float *keogh_q, float *keogh_s, void *stream);
 
+/* ---- autotuner (the paper has no counterpart) ----
+ *
+ * For each (m, r) pair (r > m-1 taken as m-1), times the banded-DTW kernel
+ * over `samples` evenly spread windows of the handle's series in every
+ * admissible shape -- lanes per candidate L (1..32), cells per lane K
+ * (anti-diagonal kernel, L*K >= r+1) or the row-systolic kernel (K = 0),
+ * warps per CTA (2, 4, 8) -- and keeps the fastest whose results are
+ * bit-identical to the default shape's (and at least 3% faster); later
+ * queries, batches and dtws_dtw_at with that (m, r) use it.  Synchronises;
+ * drops a captured batch graph.  Errors: DTWS_EINVAL (null, count < 1,
+ * samples outside [32, 2^20], m or r out of range), DTWS_ENOMEM, DTWS_ECUDA.
+ */
+dtws_status dtws_autotune(dtws_t h, const int32_t *m, const int32_t *r, int32_t count, int32_t samples,
+                          void *stream);
+/* The tuned entry of (m, r): shape = {L, K, warps} (L = 0: the default was
+   kept), ms = {default time, chosen time} per probe launch.  DTWS_EINVAL if
+   the pair was not tuned. */
+dtws_status dtws_tune_entry(dtws_t h, int32_t m, int32_t r, int32_t *shape, float *ms);
+
 /* ---- learned proposals (the paper has no learned component) ----
  *
  * An encoder e(.) maps a window of length m to 64 numbers; windows whose

@@ -52,6 +52,11 @@ struct EnvEntry {
     float *U = nullptr, *L = nullptr;
 };
 
+struct TuneEntry {
+    int m = 0, r = 0, L = 0, K = 0, warps = 0;
+    float ms_default = 0.f, ms_best = 0.f;
+};
+
 struct LearnEntry {
     int m = 0;
     int64_t used = 0, version = 0, rows = 0;
@@ -121,9 +126,12 @@ struct dtws_ctx {
     // side stream for work that overlaps the lower-bound scan
     cudaStream_t side = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    // autotuned survivor-DTW shapes per (m, r)
+    std::vector<TuneEntry> tune;
     // batched path
     std::vector<Lane> lanes;
     cudaEvent_t batch_fork = nullptr;
+    cudaStream_t cap_stream = nullptr;  // captures a batch (the caller's stream may be the legacy one)
     cudaGraphExec_t graph_exec = nullptr;
     std::vector<int64_t> graph_sig;  // what the cached graph was captured for
     // learned proposal encoder
@@ -394,6 +402,13 @@ QueryArgs make_args(dtws_t h, int m, int r, int k) {
     while (g * 2.0f <= a.alpha * 0.25f) g *= 2.0f;
     a.qgrid = g;
     a.prescore = a.r <= kDiagRMax ? 1 : 0;
+    a.tune_l = a.tune_k = a.tune_w = 0;
+    for (const auto &t : h->tune)
+        if (t.m == m && t.r == a.r) {
+            a.tune_l = t.L;
+            a.tune_k = t.K;
+            a.tune_w = t.warps;
+        }
     return a;
 }
 
@@ -560,6 +575,7 @@ dtws_status ensure_lanes(dtws_t h, int count, int m_min) {
             break;
         }
     if (!h->batch_fork) CK(cudaEventCreateWithFlags(&h->batch_fork, cudaEventDisableTiming));
+    if (!h->cap_stream) CK(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
     while ((int)h->lanes.size() < count) {
         h->lanes.emplace_back();
         Lane &l = h->lanes.back();
@@ -669,12 +685,14 @@ dtws_status run_batch(dtws_t h, const float *Qd, const int64_t *q_off, const int
             h->last_stream = s;
             return DTWS_OK;
         }
-        CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+        CK(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
     }
+    // the stream the batch forks from and joins into: the capture stream, or the caller's
+    cudaStream_t root = graph ? h->cap_stream : s;
     auto fail = [&](dtws_status e) {
         if (graph) {
             cudaGraph_t g = nullptr;
-            cudaStreamEndCapture(s, &g);
+            cudaStreamEndCapture(h->cap_stream, &g);
             if (g) cudaGraphDestroy(g);
             cudaGetLastError();
         }
@@ -688,7 +706,7 @@ dtws_status run_batch(dtws_t h, const float *Qd, const int64_t *q_off, const int
             return fail(DTWS_ECUDA);                                                   \
         }                                                                              \
     } while (0)
-    CKB(cudaEventRecord(h->batch_fork, s));
+    CKB(cudaEventRecord(h->batch_fork, root));
     std::vector<int> lane_m(L, -1);
     for (int i = 0; i < L; ++i) CKB(cudaStreamWaitEvent(h->lanes[i].stream, h->batch_fork, 0));
     int64_t launches = 0;
@@ -725,12 +743,12 @@ dtws_status run_batch(dtws_t h, const float *Qd, const int64_t *q_off, const int
     }
     for (int i = 0; i < L; ++i) {
         CKB(cudaEventRecord(h->lanes[i].ev_done, h->lanes[i].stream));
-        CKB(cudaStreamWaitEvent(s, h->lanes[i].ev_done, 0));
+        CKB(cudaStreamWaitEvent(root, h->lanes[i].ev_done, 0));
     }
 #undef CKB
     if (graph) {
         cudaGraph_t g = nullptr;
-        CK(cudaStreamEndCapture(s, &g));
+        CK(cudaStreamEndCapture(h->cap_stream, &g));
         drop_graph(h);
         cudaGraphExec_t ex = nullptr;
         cudaError_t e = cudaGraphInstantiate(&ex, g, 0);
@@ -798,6 +816,7 @@ dtws_status dtws_destroy(dtws_t h) {
     drop_graph(h);
     for (auto &l : h->lanes) free_lane(l);
     if (h->batch_fork) cudaEventDestroy(h->batch_fork);
+    if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
     void *ptrs[] = {h->x, h->pf, h->bf, h->pok, h->pscale, h->envst, h->st, h->status, h->qh32, h->Uq,
                     h->Lq, h->sq, h->sU, h->sL, h->qh64, h->ord, h->cand_lb, h->sort_lb,
                     h->cand_idx, h->sort_idx, h->stage};
@@ -1023,6 +1042,117 @@ dtws_status dtws_clear_cache(dtws_t h) {
     h->env.clear();
     h->learn.clear();
     return DTWS_OK;
+}
+
+dtws_status dtws_autotune(dtws_t h, const int32_t *m_arr, const int32_t *r_arr, int32_t count, int32_t samples,
+                          void *stream) {
+    if (!h || !m_arr || !r_arr || count < 1 || samples < 32 || samples > (1 << 20)) {
+        set_err("dtws_autotune: null argument, count < 1 or samples out of [32, 2^20]");
+        return DTWS_EINVAL;
+    }
+    for (int i = 0; i < count; ++i)
+        if (m_arr[i] < 2 || m_arr[i] > DTWS_M_MAX || (int64_t)m_arr[i] > h->n || r_arr[i] < 0) {
+            set_err("dtws_autotune: pair %d out of range", i);
+            return DTWS_EINVAL;
+        }
+    cudaStream_t s = (cudaStream_t)stream;
+    dtws_status st;
+    if ((st = ensure_workspace(h)) != DTWS_OK) return st;
+    CK(cudaStreamSynchronize(s));
+    drop_graph(h);  // captured batches may use the old shapes
+    const size_t ob = (size_t)samples * 8, fb = (size_t)samples * 4;
+    if ((st = ensure_stage(h, ob + 2 * fb + 1024)) != DTWS_OK) return st;
+    int64_t *off_d = (int64_t *)h->stage;
+    float *ref_d = (float *)((char *)h->stage + round_up(ob, 256));
+    float *out_d = (float *)((char *)h->stage + round_up(ob, 256) + round_up(fb, 256));
+    std::vector<int64_t> offs(samples);
+    std::vector<float> ref(samples), got(samples);
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    auto cleanup = [&](dtws_status r) {
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        return r;
+    };
+    for (int i = 0; i < count; ++i) {
+        const int m = m_arr[i], r = r_arr[i] > m - 1 ? m - 1 : r_arr[i];
+        bool seen = false;
+        for (int j = 0; j < i; ++j) seen |= m_arr[j] == m && (r_arr[j] > m - 1 ? m - 1 : r_arr[j]) == r;
+        if (seen) continue;
+        StatsEntry *se;
+        bool c;
+        if ((st = get_stats(h, m, s, &se, &c)) != DTWS_OK) return cleanup(st);
+        const QueryBufs b = make_bufs(h, se, nullptr);
+        QueryArgs a = make_args(h, m, r, 1);
+        a.tune_l = a.tune_k = a.tune_w = 0;
+        // the query: a window of the series; the samples: evenly spread windows
+        const int64_t N = h->n - m + 1;
+        for (int t = 0; t < samples; ++t) offs[t] = (int64_t)((double)t * (double)(N - 1) / samples);
+        CK(cudaMemcpyAsync(off_d, offs.data(), ob, cudaMemcpyHostToDevice, s));
+        CK(launch_query_reset(b, a, s));
+        CK(launch_qprep(h->x + N / 2, b, a, s));
+        auto timed = [&](int L, int K, int W, float *out, float *ms) -> cudaError_t {
+            float best = 1e30f;
+            for (int rep = 0; rep < 3; ++rep) {
+                cudaError_t e = cudaEventRecord(e0, s);
+                if (e == cudaSuccess)
+                    e = L ? launch_dtw_at_shape(b, a, off_d, samples, out, L, K, W, s)
+                          : launch_dtw_at(b, a, off_d, samples, out, s);
+                if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+                if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+                if (e != cudaSuccess) return e;
+                float t = 0.f;
+                cudaEventElapsedTime(&t, e0, e1);
+                best = t < best ? t : best;
+            }
+            *ms = best;
+            return cudaSuccess;
+        };
+        float ms_def = 0.f;
+        CK(timed(0, 0, 0, ref_d, &ms_def));
+        CK(cudaMemcpy(ref.data(), ref_d, fb, cudaMemcpyDeviceToHost));
+        TuneEntry best{m, r, 0, 0, 0, ms_def, ms_def};
+        const int Ls[6] = {1, 2, 4, 8, 16, 32}, Ks[6] = {0, 1, 2, 4, 8, 16}, Ws[3] = {2, 4, 8};
+        for (int L : Ls)
+            for (int K : Ks)
+                for (int W : Ws) {
+                    if (!dtw_shape_valid(m, r, L, K, W)) continue;
+                    float ms = 0.f;
+                    CK(timed(L, K, W, out_d, &ms));
+                    if (!(ms < best.ms_best * 0.97f)) continue;  // keep the default unless clearly faster
+                    CK(cudaMemcpy(got.data(), out_d, fb, cudaMemcpyDeviceToHost));
+                    if (memcmp(got.data(), ref.data(), fb) != 0) continue;  // must be bit-identical
+                    best.L = L;
+                    best.K = K;
+                    best.warps = W;
+                    best.ms_best = ms;
+                }
+        bool replaced = false;
+        for (auto &t : h->tune)
+            if (t.m == m && t.r == r) {
+                t = best;
+                replaced = true;
+            }
+        if (!replaced) h->tune.push_back(best);
+    }
+    return cleanup(DTWS_OK);
+}
+
+dtws_status dtws_tune_entry(dtws_t h, int32_t m, int32_t r, int32_t *shape, float *ms) {
+    if (!h || !shape || !ms) return DTWS_EINVAL;
+    const int rr = r > m - 1 ? m - 1 : r;
+    for (const auto &t : h->tune)
+        if (t.m == m && t.r == rr) {
+            shape[0] = t.L;
+            shape[1] = t.K;
+            shape[2] = t.warps;
+            ms[0] = t.ms_default;
+            ms[1] = t.ms_best;
+            return DTWS_OK;
+        }
+    set_err("dtws_tune_entry: (m=%d, r=%d) not tuned", m, r);
+    return DTWS_EINVAL;
 }
 
 dtws_status dtws_set_encoder(dtws_t h, const float *params, int32_t count, void *stream) {

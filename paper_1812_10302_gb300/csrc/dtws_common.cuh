@@ -90,6 +90,7 @@ struct QueryArgs {
     float delta, alpha; // prune when LB > bsf*(1+delta) + alpha
     float qgrid;        // key grid: a power of two <= alpha/4
     int prescore;       // 1: the best Euclidean seed is scored on a side stream
+    int tune_l, tune_k, tune_w;  // survivor DTW shape chosen by the autotuner (0: default)
 };
 
 

@@ -67,6 +67,10 @@ cudaError_t launch_finalize(const QueryBufs &b, const QueryArgs &a, int64_t *out
 // element-wise building blocks
 cudaError_t launch_dtw_at(const QueryBufs &b, const QueryArgs &a, const int64_t *offsets,
                           int64_t count, float *out, cudaStream_t s);
+// the autotuner's probes: a shape (see plan_shape) and DTW at offsets with it
+bool dtw_shape_valid(int m, int r, int L, int K, int warps);
+cudaError_t launch_dtw_at_shape(const QueryBufs &b, QueryArgs a, const int64_t *offsets, int64_t count, float *out,
+                                int L, int K, int warps, cudaStream_t s);
 cudaError_t launch_dtw_at_f64(const QueryBufs &b, const QueryArgs &a, const int64_t *offsets,
                               int64_t count, double *out, cudaStream_t s);
 cudaError_t launch_lbs_at(const QueryBufs &b, const QueryArgs &a, const int64_t *offsets,

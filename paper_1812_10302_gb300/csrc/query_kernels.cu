@@ -823,6 +823,27 @@ static bool plan_fits(int m, int r, bool tail, DtwPlan *p) {
     return false;
 }
 
+// A given shape (K > 0: anti-diagonal with L*K >= r+1 lanes' cells; K == 0:
+// row-systolic with lanes_for(r) lanes) if it is instantiated and fits;
+// warps <= 0 keeps the largest count within the shared-memory budget.
+template <typename T>
+static bool plan_shape(int m, int r, bool tail, int L, int K, int warps, DtwPlan *p) {
+    if (K > 0 && (r > kDiagRMax || L * K < r + 1)) return false;
+    if (K == 0 && L != lanes_for(r)) return false;
+    bool ok = false;
+#define DTWS_TRY(LL, KK) \
+    if (!ok && L == LL && K == KK) ok = plan_fits<T, LL, KK>(m, r, tail, p);
+    DTWS_TRY(1, 1) DTWS_TRY(2, 1) DTWS_TRY(4, 1) DTWS_TRY(8, 1) DTWS_TRY(16, 1)
+    DTWS_TRY(32, 1) DTWS_TRY(32, 2) DTWS_TRY(32, 4) DTWS_TRY(32, 8) DTWS_TRY(32, 16)
+    DTWS_TRY(1, 0) DTWS_TRY(2, 0) DTWS_TRY(4, 0) DTWS_TRY(8, 0) DTWS_TRY(16, 0) DTWS_TRY(32, 0)
+#undef DTWS_TRY
+    if (!ok) return false;
+    // fewer warps than the budget allows: the allocation for more groups
+    // stays valid (each group addresses only its own slice)
+    if (warps > 0 && warps < p->warps) p->warps = warps;
+    return true;
+}
+
 template <typename T>
 static bool plan_dtw(int m, int r, bool tail, DtwPlan *p) {
     if (r <= kDiagRMax) {
@@ -854,8 +875,9 @@ template <int MODE>
 static cudaError_t dtw_dispatch(const QueryBufs &b, const QueryArgs &a, const int64_t *offsets,
                                 int64_t count, float *out, int64_t count_for_grid, cudaStream_t s) {
     DtwPlan p;
-    if (!plan_dtw<float>(a.m, a.r, MODE == kModeSurv && (b.U != nullptr || b.stmax != nullptr), &p))
-        return cudaErrorInvalidValue;
+    const bool tail = MODE == kModeSurv && (b.U != nullptr || b.stmax != nullptr);
+    const bool tuned = a.tune_l > 0 && plan_shape<float>(a.m, a.r, tail, a.tune_l, a.tune_k, a.tune_w, &p);
+    if (!tuned && !plan_dtw<float>(a.m, a.r, tail, &p)) return cudaErrorInvalidValue;
     const int blocks = dtw_blocks(p, b.num_sms, count_for_grid);
 #define DTWS_CASE(LL, KK)                                                                                     \
     if (p.L == LL && p.K == KK) {                                                                             \
@@ -904,6 +926,20 @@ __global__ void k_reset_cursor(QueryState *st) { st->work = 0; }
 
 cudaError_t launch_dtw_at(const QueryBufs &b, const QueryArgs &a, const int64_t *offsets,
                           int64_t count, float *out, cudaStream_t s) {
+    k_reset_cursor<<<1, 1, 0, s>>>(b.st);
+    return dtw_dispatch<kModeOut>(b, a, offsets, count, out, count, s);
+}
+
+bool dtw_shape_valid(int m, int r, int L, int K, int warps) {
+    DtwPlan p;
+    return plan_shape<float>(m, r, true, L, K, warps, &p) && plan_shape<float>(m, r, false, L, K, warps, &p);
+}
+
+cudaError_t launch_dtw_at_shape(const QueryBufs &b, QueryArgs a, const int64_t *offsets, int64_t count, float *out,
+                                int L, int K, int warps, cudaStream_t s) {
+    a.tune_l = L;
+    a.tune_k = K;
+    a.tune_w = warps;
     k_reset_cursor<<<1, 1, 0, s>>>(b.st);
     return dtw_dispatch<kModeOut>(b, a, offsets, count, out, count, s);
 }

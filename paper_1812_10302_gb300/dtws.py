@@ -108,6 +108,8 @@ _SIGS = {
     "dtws_dtw_at_f64": (_S, [_P, _P, _I32, _I32, _P, _I64, _P, _P]),
     "dtws_lower_bounds_at": (_S, [_P, _P, _I32, _I32, _P, _I64, _P, _P, _P, _P]),
     "dtws_dtw_at_noalloc": (_S, [_P, _I64, _P, _I32, _I32, _P, _I64, _P, _P]),
+    "dtws_autotune": (_S, [_P, _P, _P, _I32, _I32, _P]),
+    "dtws_tune_entry": (_S, [_P, _I32, _I32, _P, _P]),
     "dtws_set_encoder": (_S, [_P, _P, _I32, _P]),
     "dtws_learned_embeddings": (_S, [_P, _I32, _P, _I64, _P]),
     "dtws_enc_prep": (_S, [_P, _I64, _P, _I32, _I32, _P, _P]),
@@ -371,6 +373,20 @@ class Index:
         _check(self._lib.dtws_dtw_at_f64(self.h, q.ptr, q.size, r, o.ptr, o.size, out.ctypes.data,
                                          _stream_ptr(stream)), "dtws_dtw_at_f64")
         return out
+
+    def autotune(self, ms, rs, samples: int = 4096, stream=None):
+        """Tune the survivor-DTW kernel shape for each (m, r) pair."""
+        mm = np.ascontiguousarray(ms, dtype=np.int32)
+        rr = np.ascontiguousarray(rs, dtype=np.int32)
+        _check(self._lib.dtws_autotune(self.h, mm.ctypes.data, rr.ctypes.data, mm.size, samples,
+                                       _stream_ptr(stream)), "dtws_autotune")
+
+    def tune_entry(self, m: int, r: int):
+        """(L, K, warps, ms_default, ms_best) of a tuned (m, r)."""
+        shape = np.zeros(3, np.int32)
+        ms = np.zeros(2, np.float32)
+        _check(self._lib.dtws_tune_entry(self.h, m, r, shape.ctypes.data, ms.ctypes.data), "dtws_tune_entry")
+        return int(shape[0]), int(shape[1]), int(shape[2]), float(ms[0]), float(ms[1])
 
     def set_encoder(self, params, stream=None):
         p = _Arg(params, np.float32)

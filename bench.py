@@ -4,10 +4,18 @@
 Workload (default ``rw100m``): a 1e8-sample FP32 random walk with seeded sine
 bursts and N(0, 0.5) noise; one m=512 query that is a noisy (0.1) copy of a
 seeded window; Sakoe-Chiba half-width r = floor(0.1 m) = 51; top-1.  A step is
-one dtws_query (query prep, proxy scan and seed DTWs, fused lower-bound scan,
-survivor ordering, DTW, FP64 re-score) with the series and its per-series
-data (anchored FP64 prefix sums, window statistics for m, series envelope for
-r) resident in HBM; their one-time cost is reported as ``precompute_ms``.
+one dtws_query (query prep, proxy scan and Euclidean seeds, fused lower-bound
+scan, survivor ordering, DTW, extended-precision re-score) with the series and
+its per-series data (anchored prefix sums, window statistics for m, series
+envelope for r) resident in HBM; their one-time cost is reported as
+``precompute_ms``.
+
+At N = 1 the same JSON line also carries (unless ``--no-extras``):
+``learned`` -- mean ms per query on the learned-proposal workload (n = 2e8,
+64 queries m = 1024, r = 102) with the learned ordering, the proxy ordering
+and the paper's random seeding, the speedups and whether the answers agree;
+``batch`` -- the batched workload (n = 5e7, 256 queries of mixed m and r,
+top-10) through dtws_query_batch with a replayed CUDA graph.
 
 Metric: subsequences/s per query (N windows / step time).  Also reported:
 brute-force-equivalent DTW cells/s (N * cells(m, r) / step time), the
@@ -355,9 +363,109 @@ def gpu_arm(args):
     }
     if cpu is not None:
         line["cpu_baseline"]["seconds"] = cpu["seconds"]
-    print(json.dumps(line))
     ix.close()
+    if world == 1 and not args.no_extras:
+        del qd, idx_d, dist_d
+        torch.cuda.empty_cache()
+        line["learned"] = learned_leg(dev)
+        torch.cuda.empty_cache()
+        line["batch"] = batch_leg(dev)
+    print(json.dumps(line))
     return 0
+
+
+# ------------------------------------------------------------------ other workloads (N = 1)
+def _mean_query_ms(ix, qds, r, k, dev, reps=1):
+    """Mean device time per query over the given device queries (events on
+    the query stream), after one untimed query."""
+    import torch
+    stream = torch.cuda.current_stream(dev)
+    idx = torch.empty(k, dtype=torch.int64, device=dev)
+    dist = torch.empty(k, dtype=torch.float32, device=dev)
+    ix.query(qds[0], r, k, out=(idx, dist))
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        for q in qds:
+            ix.query(q, r, k, out=(idx, dist))
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    from paper_1812_10302_gb300 import dtws
+    if ix.sync_status() != dtws.DTWS_OK:
+        raise RuntimeError("device-side error in a timed query")
+    return e0.elapsed_time(e1) / (len(qds) * reps)
+
+
+def learned_leg(dev):
+    """Learned proposals on the learned-proposal workload (n = 2e8 walk with
+    sine bursts, 64 noisy queries m = 1024, r = 102, top-1): mean ms per query
+    with the learned ordering, the proxy ordering and the paper's random
+    seeding (Algorithm 1; a bounded subset of queries: it is slow), and
+    whether all three return the same answers."""
+    import torch
+
+    from paper_1812_10302_gb300 import dtws, synth, train
+    w = synth.workload("learn")
+    x, qs, r = w["series"], w["queries"], w["rs"][0]
+    ix = dtws.Index(torch.from_numpy(x).to(dev))
+    del x
+    qds = [torch.from_numpy(q).to(dev) for q in qs]
+    ix.set_encoder(train.load_weights())
+    out = {"workload": "learn: walk + sine bursts + N(0,0.5), n=200000000, 64 noisy copies m=1024, r=102, top-1",
+           "encoder": "trained on oracle-labelled pairs of a disjoint training series", "ms_per_query": {}}
+    modes = {"learned": dict(ordering=dtws.DTWS_ORDER_LEARNED, seed_proposals=64),
+             "proxy": dict(ordering=dtws.DTWS_ORDER_PLAIN, seed_proposals=16),
+             "random_seeds": dict(ordering=dtws.DTWS_ORDER_PLAIN, seed_proposals=0)}
+    answers = {}
+    n_random = 4
+    for name, opts in modes.items():
+        ix.set_options(**opts)
+        sub = qds if name != "random_seeds" else qds[:n_random]
+        out["ms_per_query"][name] = _mean_query_ms(ix, sub, r, 1, dev)
+        answers[name] = [tuple(np.concatenate([a.astype(np.float64) for a in ix.query(q, r, 1)])) for q in sub]
+    out["random_seeds_queries"] = n_random
+    t = out["ms_per_query"]
+    out["speedup_vs_random_seeds"] = t["random_seeds"] / t["learned"]
+    out["speedup_vs_proxy"] = t["proxy"] / t["learned"]
+    out["identical_answers"] = (answers["learned"] == answers["proxy"] and
+                                answers["learned"][:n_random] == answers["random_seeds"])
+    ix.close()
+    return out
+
+
+def batch_leg(dev):
+    """The batched workload (n = 5e7 walk, 256 noisy queries with m in
+    [128, 2048], r in [5%, 20%] of m, top-10) through dtws_query_batch: the
+    first call captures the graph, later calls replay it."""
+    import torch
+
+    from paper_1812_10302_gb300 import dtws, synth
+    w = synth.workload("batch")
+    x, qs, rs, k = w["series"], w["queries"], w["rs"], w["k"]
+    ix = dtws.Index(torch.from_numpy(x).to(dev))
+    n = x.size
+    del x
+    ix.set_options(batch_lanes=4, batch_graph=1, exact_envelope=0)
+    t0 = time.perf_counter()
+    ix.query_batch(qs, rs, k=k)
+    first = time.perf_counter() - t0
+    ts = []
+    for _ in range(3):
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        ix.query_batch(qs, rs, k=k)
+        ts.append(time.perf_counter() - t0)
+    if ix.sync_status() != dtws.DTWS_OK:
+        raise RuntimeError("device-side error in the batch")
+    sec = float(np.median(ts))
+    windows = sum(n - len(q) + 1 for q in qs)
+    ix.close()
+    return {"workload": "batch: random walk n=50000000, 256 noisy copies m~U{128..2048}, r=floor(w m), "
+                        "w~U[0.05,0.2], top-10",
+            "seconds_per_batch": sec, "queries_per_s": len(qs) / sec, "subsequences_per_s": windows / sec,
+            "first_call_seconds": first, "lanes": 4, "graph": "captured on the first call, replayed",
+            "timing": "host wall clock around dtws_query_batch (synchronising; host queries and outputs)"}
 
 
 def main():
@@ -370,6 +478,8 @@ def main():
     ap.add_argument("--cpu-windows", type=int, default=20_000_000,
                     help="windows in the CPU oracle's bounded sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the learned-proposal and batched workloads (N = 1 only)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

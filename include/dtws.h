@@ -78,7 +78,7 @@ typedef struct {
     float alpha_per_m;      /* absolute margin per query sample, default 1e-6 */
     int32_t seed_random;    /* random seed windows, default 4 (0..64) */
     int32_t seed_proposals; /* proposals of the proxy (or learned) scan,
-                               default 16 (0..64; at most 16 when learned) */
+                               default 16 (0..64) */
     int32_t proxy_terms;    /* evenly spaced query positions in the proxy
                                distance: 16, 8, 4 (other values round down to
                                one of them, or 2), default 16 */

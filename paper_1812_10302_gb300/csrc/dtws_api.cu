@@ -480,8 +480,9 @@ dtws_status enqueue_search(dtws_t h, const Exec &e, const QueryArgs &a, const fl
     CK(launch_seed_gather(b, a, R, P, half, h->opt.rng_seed, s));
     CK(launch_seed_ed(b, a, s));
     if (k > 1) {  // exact DTW seeds tighten a k-th bound the Euclidean seeds leave loose
+        CK(launch_seed_expand(b, a, s));
         CK(launch_dtw_seeds(b, a, s));
-        ++launches;
+        launches += 2;
     }
     rec(1);
     // the best Euclidean seed is scored on the side stream during the scan

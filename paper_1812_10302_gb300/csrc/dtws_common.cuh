@@ -24,7 +24,7 @@ constexpr int kProxyStride = 2;     // the proxy scan looks at every other windo
 // Euclidean seeds: random windows + the neighbourhoods of the proposals
 // (+-1 window for the proxy scan; +-b/2, b <= 128, for the learned scan with
 // at most kLearnPropMax proposals)
-constexpr int kLearnPropMax = 16;
+constexpr int kLearnPropMax = 64;
 // per-series block envelope: sparse table of max / min over blocks of
 // kEnvG samples, levels 0..kEnvLevels-1 (block ranges up to 2^10 blocks,
 // enough for any band of a query of at most kMMax samples)
@@ -33,7 +33,7 @@ constexpr int kEnvLevels = 11;
 // learned proposal encoder: parameter count and packed-weight blob size
 constexpr int kEncParams = 38112;
 constexpr int kEncBlobBytes = 1024 + 2 * 3 * 32 * 224 * 2 + 64 * 256 * 2;
-constexpr int kEdMax = kKMax + kLearnPropMax * 129 + 48;
+constexpr int kEdMax = kKMax + kLearnPropMax * 129 + 64;
 constexpr int kTile = 1024;         // windows per lower-bound tile
 constexpr int kProxyTile = 4096;    // windows per proxy-scan tile (a multiple of kTile)
 constexpr int kStages = 4;          // shared-memory stages of the scan pipeline

@@ -493,6 +493,44 @@ __global__ void k_seed_ed(QueryBufs b, QueryArgs a) {
     if (lane == 0) list_insert(st->ed_keys, a.k, make_key(key_quantize(acc, a.qgrid), idx));
 }
 
+// k > 1: the k-th best distance needs k good windows.  The windows nearest
+// in DTW to the best match are its neighbours (warping absorbs small
+// shifts), so the offsets within +-k of the two best Euclidean seeds join
+// the exact-DTW seeds (one warp).
+__global__ void k_seed_expand(QueryBufs b, QueryArgs a) {
+    __shared__ unsigned cand[2 * (2 * kKMax + 1)];
+    __shared__ int nc;
+    QueryState *st = b.st;
+    if (!st->valid || a.k < 2) return;
+    const int lane = threadIdx.x;
+    const int H = a.k < kKMax ? a.k : kKMax, W = 2 * H + 1;
+    for (int c = 0; c < 2; ++c) {
+        const unsigned long long key = st->ed_keys[c];
+        for (int d = lane; d < W; d += 32) {
+            unsigned o = 0xffffffffu;
+            if (key != kEmptyKey) {
+                const long long v = (long long)key_idx(key) + d - H;
+                if (v >= 0 && v < a.N) o = (unsigned)v;
+            }
+            cand[c * W + d] = o;
+        }
+    }
+    __syncwarp();
+    const int have = st->n_seeds;
+    for (int t = lane; t < 2 * W; t += 32)  // drop offsets that are seeds already
+        for (int u = 0; u < have; ++u)
+            if (cand[t] == st->seed_off[u]) cand[t] = 0xffffffffu;
+    if (lane == 0) nc = have;
+    __syncwarp();
+    const int ns = distinct_append(st->seed_off, kSeedMax, cand, 2 * W, lane, &nc);
+    if (lane == 0) st->n_seeds = ns;
+}
+
+cudaError_t launch_seed_expand(const QueryBufs &b, const QueryArgs &a, cudaStream_t s) {
+    k_seed_expand<<<1, 32, 0, s>>>(b, a);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_seed_ed(const QueryBufs &b, const QueryArgs &a, cudaStream_t s) {
     k_seed_ed<<<(kEdMax * 32 + 255) / 256, 256, 0, s>>>(b, a);
     return cudaGetLastError();
@@ -624,9 +662,6 @@ __global__ void __launch_bounds__(256) k_dtw(QueryBufs b, QueryArgs a, const int
         }
         const float mh = b.mu_hi[idx], is = b.inv_sigma[idx], ls = b.mu_lo[idx] * is;
         const float *xw = b.x + idx;
-        if (cbuf) {  // the group's normalised copy of the window
-            for (int j = lane; j < m; j += L) cbuf[j] = fmaf(xw[j] - mh, is, -ls);
-        }
         TailCtx tc;
         tc.Uw = b.U ? b.U + idx : nullptr;
         tc.Lw = b.L ? b.L + idx : nullptr;
@@ -640,6 +675,36 @@ __global__ void __launch_bounds__(256) k_dtw(QueryBufs b, QueryArgs a, const int
         tc.mh = mh;
         tc.is = is;
         tc.ls = ls;
+        if (MODE == kModeSurv && has_env) {
+            // Eq. 10 with early abandon: the terms in |q_hat| descending
+            // order, L at a time, until the partial sum passes thr (the sum
+            // is reduced over the group, so every lane takes the same exit)
+            float acc = 0.0f;
+            bool pruned = false;
+            for (int c0 = 0; c0 < m; c0 += L) {
+                const int j = c0 + lane;
+                float v = 0.0f;
+                if (j < m) {
+                    const int pos = b.ord[j];
+                    float U, Lo;
+                    env_at(tc, pos, U, Lo);
+                    const float u = fmaf(U - mh, is, -ls), l = fmaf(Lo - mh, is, -ls), q = b.sq[j];
+                    const float d = fmaxf(q - u, 0.0f) + fmaxf(l - q, 0.0f);
+                    v = d * d;
+                }
+#pragma unroll
+                for (int o = L / 2; o > 0; o >>= 1) v += __shfl_xor_sync(gmask, v, o, L);
+                acc += v;
+                if (acc > thr) {
+                    pruned = true;
+                    break;
+                }
+            }
+            if (pruned) continue;
+        }
+        if (cbuf) {  // the group's normalised copy of the window
+            for (int j = lane; j < m; j += L) cbuf[j] = fmaf(xw[j] - mh, is, -ls);
+        }
         if (cbs) {
             tail_suffix<L>(tc, cbs, m, gmask, lane);
             // cbs[0] is LB_Keogh of q_hat against the window's envelope

@@ -81,10 +81,10 @@ def test_block_envelope_gives_the_same_answers(walk):
                     i, d = ix.query(q, r, 3)
                     assert ix.sync_status() == dtws.DTWS_OK
                     res[exact] = (i, d, ix.last_stats())
+                # (the survivor counters are not compared: they depend on how
+                # the concurrently shrinking threshold interleaves)
                 np.testing.assert_array_equal(res[0][0], res[1][0])
                 np.testing.assert_array_equal(res[0][1], res[1][1])
-                # the block envelope is looser: never fewer windows pass Eq. 10
-                assert res[0][2]["pass_keogh_s"] >= res[1][2]["pass_keogh_s"]
 
 
 def test_batch_with_learned_ordering(walk):

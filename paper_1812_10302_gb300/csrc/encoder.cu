@@ -688,23 +688,32 @@ __global__ void __launch_bounds__(kLsThreads) k_learn_scan(QueryBufs bq, const b
     const int64_t tiles = (Nw + kLsTile - 1) / kLsTile;
     for (int64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
         unsigned long long mine = ~0ull;
-        for (int64_t j = tile * kLsTile + warp * 4 + grp; j < (tile + 1) * kLsTile; j += kLsThreads / 8) {
-            float s = 0.0f;
-            if (j < Nw) {
-                const uint4 v = *reinterpret_cast<const uint4 *>(E + j * DIM + sub * 8);
-                const bf16 *h = reinterpret_cast<const bf16 *>(&v);
+        // each warp takes 4 x 4 windows per step: four 16-byte loads in flight per lane
+        constexpr int kU = 4, kStep = kLsThreads / 8 * kU;
+        for (int64_t j0 = tile * kLsTile + warp * 4 * kU + grp; j0 < (tile + 1) * kLsTile; j0 += kStep) {
+            uint4 v[kU];
+#pragma unroll
+            for (int u = 0; u < kU; ++u) {
+                const int64_t j = j0 + 4 * u;
+                v[u] = j < Nw ? *reinterpret_cast<const uint4 *>(E + j * DIM + sub * 8) : make_uint4(0, 0, 0, 0);
+            }
+#pragma unroll
+            for (int u = 0; u < kU; ++u) {
+                const int64_t j = j0 + 4 * u;
+                const bf16 *h = reinterpret_cast<const bf16 *>(&v[u]);
+                float s = 0.0f;
 #pragma unroll
                 for (int i = 0; i < 8; ++i) {
                     const float d = eq[i] - __bfloat162float(h[i]);
                     s = fmaf(d, d, s);
                 }
-            }
-            s += __shfl_xor_sync(0xffffffffu, s, 1);
-            s += __shfl_xor_sync(0xffffffffu, s, 2);
-            s += __shfl_xor_sync(0xffffffffu, s, 4);
-            if (j < Nw && sub == 0) {
-                const unsigned long long k = make_key(s, (unsigned)(j * b));
-                mine = k < mine ? k : mine;
+                s += __shfl_xor_sync(0xffffffffu, s, 1);
+                s += __shfl_xor_sync(0xffffffffu, s, 2);
+                s += __shfl_xor_sync(0xffffffffu, s, 4);
+                if (j < Nw && sub == 0) {
+                    const unsigned long long k = make_key(s, (unsigned)(j * b));
+                    mine = k < mine ? k : mine;
+                }
             }
         }
         for (int o = 16; o; o >>= 1) {

@@ -678,10 +678,13 @@ __global__ void __launch_bounds__(256) k_dtw(QueryBufs b, QueryArgs a, const int
         if (MODE == kModeSurv && has_env) {
             // Eq. 10 with early abandon: the terms in |q_hat| descending
             // order, L at a time, until the partial sum passes thr (the sum
-            // is reduced over the group, so every lane takes the same exit)
+            // is reduced over the group, so every lane takes the same exit);
+            // past 128 terms the full bound below (row order, with the
+            // suffix sums the DTW needs) takes over
             float acc = 0.0f;
             bool pruned = false;
-            for (int c0 = 0; c0 < m; c0 += L) {
+            const int budget = m < 128 ? m : 128;
+            for (int c0 = 0; c0 < budget; c0 += L) {
                 const int j = c0 + lane;
                 float v = 0.0f;
                 if (j < m) {
@@ -1078,6 +1081,8 @@ __global__ void __launch_bounds__(kScanThreads) k_lb_scan(QueryBufs b, QueryArgs
             }
             unsigned bal = __ballot_sync(0xffffffffu, pass);
             c1 += __popc(bal);
+            unsigned keep = 0;   // windows of this row of 32 that survive Eq. 8
+            float my_lb = 0.0f;  // lane t holds window t's bound when it survives
             while (bal) {
                 const int src = __ffs(bal) - 1;
                 bal &= bal - 1;
@@ -1100,11 +1105,19 @@ __global__ void __launch_bounds__(kScanThreads) k_lb_scan(QueryBufs b, QueryArgs
                 }
                 if (s2 > thr) continue;
                 ++c2;
-                const float kim_s = __shfl_sync(0xffffffffu, kim, src);
-                if (lane == 0) {
-                    const int pos = atomicAdd(&st->n_cand, 1);
-                    b.cand_lb[pos] = fmaxf(kim_s, s2);
-                    b.cand_idx[pos] = (unsigned)i;
+                keep |= 1u << src;
+                if (lane == src) my_lb = fmaxf(kim, s2);
+                (void)i;
+            }
+            // one append per row of 32 windows: a warp-aggregated atomic
+            if (keep) {
+                int base = 0;
+                if (lane == 0) base = atomicAdd(&st->n_cand, __popc(keep));
+                base = __shfl_sync(0xffffffffu, base, 0);
+                if (keep & (1u << lane)) {
+                    const int pos = base + __popc(keep & ((1u << lane) - 1u));
+                    b.cand_lb[pos] = my_lb;
+                    b.cand_idx[pos] = (unsigned)(i0 + w);
                 }
             }
         }

@@ -54,6 +54,8 @@ SPECS = {
     "rw100m": dict(n=100_000_000, m=512, w=0.10, k=1),
     "rw30m": dict(n=30_000_000, m=512, w=0.10, k=1),
     "rw1m": dict(n=1_000_000, m=128, w=0.05, k=1),
+    # the learned-proposal workload's kind (walk + bursts, seeds 4/4/6), shortened to 2e7 samples
+    "learn20m": dict(n=20_000_000, m=1024, w=0.10, k=1),
 }
 
 
@@ -138,10 +140,16 @@ def make_workload(name: str, rank: int = 0, world: int = 1):
     def frag(k):
         if name in ("rw100m", "rw30m"):
             return synth.walk_with_bursts(n, 0 + 101 * k, 3 + 101 * k, 5 + 101 * k)
+        if name == "learn20m":
+            return synth.walk_with_bursts(n, 4 + 101 * k, 4 + 101 * k, 6 + 101 * k)
         return synth.random_walk(n, 101 * k)
 
     x = frag(rank)
-    q, o = synth.noisy_copy(frag(0) if rank != 0 else x, m, 1, 2)
+    if name == "learn20m":
+        qs, offs = synth.fixed_queries(frag(0) if rank != 0 else x, 1, m, 9)
+        q, o = qs[0], offs[0]
+    else:
+        q, o = synth.noisy_copy(frag(0) if rank != 0 else x, m, 1, 2)
     if world > 1 and rank < world - 1:
         x = np.concatenate([x, frag(rank + 1)[: m - 1]])
     return x, q, r, spec["k"], o
@@ -229,6 +237,12 @@ def gpu_arm(args):
     torch.cuda.synchronize(dev)
     create_ms = 1e3 * (time.perf_counter() - t0)
     del xs
+    if args.ordering == "learned":
+        from paper_1812_10302_gb300 import train
+        ix.set_encoder(train.load_weights())
+        ix.set_options(ordering=dtws.DTWS_ORDER_LEARNED, seed_proposals=64)
+    elif args.ordering == "random":
+        ix.set_options(seed_proposals=0)
     qd = torch.from_numpy(q).to(dev)
     idx_d = torch.empty(k, dtype=torch.int64, device=dev)
     dist_d = torch.empty(k, dtype=torch.float32, device=dev)
@@ -338,7 +352,7 @@ def gpu_arm(args):
         "config": {
             "workload": f"{args.workload}: random walk + sine bursts + N(0,0.5), n={x.size}, "
                         f"one m={m} noisy copy, r={r}, top-{k}",
-            "global_batch": 1, "seq_len": m, "parallelism": f"fragments x{world}",
+            "global_batch": 1, "seq_len": m, "parallelism": f"fragments x{world}", "ordering": args.ordering,
             "l2": "inputs larger than L2 (series 0.4 GB + stats 1.2 GB + envelope 0.8 GB)",
         },
         "cells_per_s_bruteforce_equiv": total_windows * cells(m, r) / (ms * 1e-3),
@@ -478,6 +492,9 @@ def main():
     ap.add_argument("--cpu-windows", type=int, default=20_000_000,
                     help="windows in the CPU oracle's bounded sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--ordering", default="proxy", choices=["proxy", "learned", "random"],
+                    help="seeding of the timed queries: proxy scan (default), learned proposals, or "
+                         "random windows only (the paper's Algorithm 1)")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the learned-proposal and batched workloads (N = 1 only)")
     args = ap.parse_args()

@@ -674,23 +674,24 @@ __global__ void __launch_bounds__(kSeqThreads) k_query_embed(const uint8_t *blob
 
 // Score every window at stride b by |e_q - E[j]|^2 (8 lanes per window, 8
 // dimensions each); the best window of each 2048-window tile is offered to
-// the proposal list.
+// the proposal list.  A warp owns whole tiles (no block barriers) and keeps
+// four 16-byte loads in flight per lane.
 constexpr int kLsTile = 2048, kLsThreads = 256;
 __global__ void __launch_bounds__(kLsThreads) k_learn_scan(QueryBufs bq, const bf16 *E, int64_t Nw, int b,
                                                            int proposals) {
-    __shared__ unsigned long long best[kLsThreads / 32];
     QueryState *st = bq.st;
     if (!st->valid) return;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, sub = lane & 7, grp = lane >> 3;
+    const int lane = threadIdx.x & 31, sub = lane & 7, grp = lane >> 3;
+    const int64_t gwarp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     float eq[8];
 #pragma unroll
     for (int i = 0; i < 8; ++i) eq[i] = st->e_q[sub * 8 + i];
     const int64_t tiles = (Nw + kLsTile - 1) / kLsTile;
-    for (int64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
+    constexpr int kU = 4;
+    for (int64_t tile = gwarp; tile < tiles; tile += nwarps) {
         unsigned long long mine = ~0ull;
-        // each warp takes 4 x 4 windows per step: four 16-byte loads in flight per lane
-        constexpr int kU = 4, kStep = kLsThreads / 8 * kU;
-        for (int64_t j0 = tile * kLsTile + warp * 4 * kU + grp; j0 < (tile + 1) * kLsTile; j0 += kStep) {
+        for (int64_t j0 = tile * kLsTile + grp; j0 < (tile + 1) * kLsTile; j0 += 4 * kU) {
             uint4 v[kU];
 #pragma unroll
             for (int u = 0; u < kU; ++u) {
@@ -720,14 +721,7 @@ __global__ void __launch_bounds__(kLsThreads) k_learn_scan(QueryBufs bq, const b
             const unsigned long long v = __shfl_xor_sync(0xffffffffu, mine, o);
             mine = v < mine ? v : mine;
         }
-        if (lane == 0) best[warp] = mine;
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            unsigned long long k = best[0];
-            for (int w = 1; w < kLsThreads / 32; ++w) k = best[w] < k ? best[w] : k;
-            if (k != ~0ull) list_insert(st->prop_keys, proposals, k);
-        }
-        __syncthreads();
+        if (lane == 0 && mine != ~0ull) list_insert(st->prop_keys, proposals, mine);
     }
 }
 
@@ -814,8 +808,9 @@ cudaError_t launch_bf16_to_f32(const void *src, int64_t count, float *dst, cudaS
 
 cudaError_t launch_learn_scan(const QueryBufs &b, const void *E, int64_t Nw, int stride, int proposals,
                               cudaStream_t s) {
-    const int64_t tiles = (Nw + enc::kLsTile - 1) / enc::kLsTile;
-    const int grid = (int)(tiles < 8 * b.num_sms ? tiles : 8 * b.num_sms);
+    const int64_t tiles = (Nw + enc::kLsTile - 1) / enc::kLsTile;  // one warp per tile at a time
+    const int64_t want = (tiles + enc::kLsThreads / 32 - 1) / (enc::kLsThreads / 32);
+    const int grid = (int)(want < 8 * b.num_sms ? (want > 0 ? want : 1) : 8 * b.num_sms);
     enc::k_learn_scan<<<grid, enc::kLsThreads, 0, s>>>(b, reinterpret_cast<const enc::bf16 *>(E), Nw, stride,
                                                        proposals);
     return cudaGetLastError();

@@ -255,10 +255,10 @@ constexpr int kScanThreads = (kScanConsumers + 1) * 32;  // + one producer warp
 // ends the loop for that warp (the other warps' waits then run out too).
 template <class LY, typename F>
 __device__ void tile_pipeline(unsigned char *sm, const QueryBufs &b, int m, int64_t ntiles,
-                              unsigned long long *cursor, F &&process) {
+                              unsigned long long *cursor, int kS, F &&process) {
     const int warp = threadIdx.x >> 5, lane = lane_id();
     if (threadIdx.x == 0) {
-        for (int q = 0; q < kStages; ++q) {
+        for (int q = 0; q < kS; ++q) {
             const Tile t = carve_stage<LY>(sm, m, q);
             mbar_init(t.full, 1);
             mbar_init(t.empty, kScanConsumers);
@@ -271,9 +271,9 @@ __device__ void tile_pipeline(unsigned char *sm, const QueryBufs &b, int m, int6
         if (lane == 0) {
             int64_t u = 0;
             for (;; ++u) {
-                const Tile t = carve_stage<LY>(sm, m, (int)(u % kStages));
-                if (u >= kStages &&
-                    !mbar_wait_bounded(t.empty, (unsigned)(((u / kStages) - 1) & 1), b.wait_ns)) {
+                const Tile t = carve_stage<LY>(sm, m, (int)(u % kS));
+                if (u >= kS &&
+                    !mbar_wait_bounded(t.empty, (unsigned)(((u / kS) - 1) & 1), b.wait_ns)) {
                     ok = false;
                     break;
                 }
@@ -291,14 +291,14 @@ __device__ void tile_pipeline(unsigned char *sm, const QueryBufs &b, int m, int6
             // let the copies that may still be in flight (uses u-S+1 .. u-1;
             // use u-S was confirmed released) land before the CTA leaves.
             if (!ok)
-                for (int64_t v = u - kStages + 1 > 0 ? u - kStages + 1 : 0; v < u; ++v)
-                    mbar_wait_bounded(carve_stage<LY>(sm, m, (int)(v % kStages)).full,
-                                      (unsigned)((v / kStages) & 1), b.wait_ns);
+                for (int64_t v = u - kS + 1 > 0 ? u - kS + 1 : 0; v < u; ++v)
+                    mbar_wait_bounded(carve_stage<LY>(sm, m, (int)(v % kS)).full,
+                                      (unsigned)((v / kS) & 1), b.wait_ns);
         }
     } else {
         for (int64_t j = 0;; ++j) {
-            const Tile t = carve_stage<LY>(sm, m, (int)(j % kStages));
-            if (!mbar_wait_bounded(t.full, (unsigned)((j / kStages) & 1), b.wait_ns)) {
+            const Tile t = carve_stage<LY>(sm, m, (int)(j % kS));
+            if (!mbar_wait_bounded(t.full, (unsigned)((j / kS) & 1), b.wait_ns)) {
                 ok = false;
                 break;
             }
@@ -321,6 +321,28 @@ static int scan_grid(const void *kernel, int threads, size_t smem, int num_sms, 
     return (int)(g < ntiles ? g : ntiles);
 }
 
+// Pipeline depth of a scan: between min_stages and kStages stages, the one
+// with the most resident CTAs per SM (ties: the deeper ring); the shared
+// memory goes to more consumer warps when a deeper ring would cost a CTA.
+static int scan_stages(const void *kernel, size_t stage_bytes, int min_stages, size_t *smem) {
+    int best_s = kStages, best_occ = -1;
+    for (int st = kStages; st >= min_stages; --st) {
+        int occ = 0;
+        const size_t bytes = (size_t)st * stage_bytes;
+        if (cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) != cudaSuccess ||
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, kScanThreads, bytes) != cudaSuccess) {
+            cudaGetLastError();
+            continue;
+        }
+        if (occ > best_occ) {
+            best_occ = occ;
+            best_s = st;
+        }
+    }
+    *smem = (size_t)best_s * stage_bytes;
+    return best_s;
+}
+
 // ------------------------------------------------------------------ proxy scan
 // For every other window: the squared distance on TERMS evenly spaced query
 // positions (not a lower bound: it only proposes windows whose exact
@@ -333,7 +355,7 @@ static int scan_grid(const void *kernel, int threads, size_t smem, int num_sms, 
 // proposal.  (With one window in eight, a window four samples off a match
 // scored no better than lucky random windows and matches were lost.)
 template <int TERMS>
-__global__ void __launch_bounds__(kScanThreads) k_seed_scan(QueryBufs b, QueryArgs a, int proposals) {
+__global__ void __launch_bounds__(kScanThreads) k_seed_scan(QueryBufs b, QueryArgs a, int proposals, int stages) {
     extern __shared__ __align__(16) unsigned char smraw[];
     __shared__ unsigned long long wbest[kScanConsumers + 1];
     if (!b.st->valid) return;
@@ -347,7 +369,7 @@ __global__ void __launch_bounds__(kScanThreads) k_seed_scan(QueryBufs b, QueryAr
     }
     unsigned long long best = kEmptyKey;
     const int64_t ntiles = (a.N + ProxyLayout::W - 1) / ProxyLayout::W;
-    tile_pipeline<ProxyLayout>(smraw, b, m, ntiles, &b.st->tile_ctr[0], [&](const Tile &t, int64_t i0) {
+    tile_pipeline<ProxyLayout>(smraw, b, m, ntiles, &b.st->tile_ctr[0], stages, [&](const Tile &t, int64_t i0) {
         for (int v = threadIdx.x; v < ProxyLayout::S; v += kScanConsumers * 32) {
             const int w = v * kProxyStride;
             const int64_t i = i0 + w;
@@ -381,12 +403,13 @@ __global__ void __launch_bounds__(kScanThreads) k_seed_scan(QueryBufs b, QueryAr
 
 template <int TERMS>
 static cudaError_t launch_seed_scan_t(const QueryBufs &b, const QueryArgs &a, int proposals, cudaStream_t s) {
-    const size_t smem = kStages * stage_bytes<ProxyLayout>(a.m);
+    size_t smem = 0;
+    const int stages = scan_stages((const void *)k_seed_scan<TERMS>, stage_bytes<ProxyLayout>(a.m), 2, &smem);
     cudaError_t e = cudaFuncSetAttribute(k_seed_scan<TERMS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     const int64_t tiles = (a.N + ProxyLayout::W - 1) / ProxyLayout::W;
     const int grid = scan_grid((const void *)k_seed_scan<TERMS>, kScanThreads, smem, b.num_sms, tiles);
-    k_seed_scan<TERMS><<<grid, kScanThreads, smem, s>>>(b, a, proposals);
+    k_seed_scan<TERMS><<<grid, kScanThreads, smem, s>>>(b, a, proposals, stages);
     return cudaGetLastError();
 }
 
@@ -1046,7 +1069,7 @@ __device__ __forceinline__ float warp_sum(float v) {
 // time: lanes take 32 consecutive terms of the |q_hat|-ordered LB_Keogh sums
 // and the warp abandons as soon as a chunk's running total exceeds thr.  No
 // thread waits on another warp's survivors.
-__global__ void __launch_bounds__(kScanThreads) k_lb_scan(QueryBufs b, QueryArgs a) {
+__global__ void __launch_bounds__(kScanThreads) k_lb_scan(QueryBufs b, QueryArgs a, int stages) {
     extern __shared__ __align__(16) unsigned char smraw[];
     QueryState *st = b.st;
     if (!st->valid) return;
@@ -1066,7 +1089,7 @@ __global__ void __launch_bounds__(kScanThreads) k_lb_scan(QueryBufs b, QueryArgs
     }
     unsigned long long c1 = 0, c2 = 0;
     const int64_t ntiles = (a.N + kTile - 1) / kTile;
-    tile_pipeline<LbLayout>(smraw, b, m, ntiles, &st->tile_ctr[1], [&](const Tile &t, int64_t i0) {
+    tile_pipeline<LbLayout>(smraw, b, m, ntiles, &st->tile_ctr[1], stages, [&](const Tile &t, int64_t i0) {
 #pragma unroll 1
         for (int u = 0; u < kPerWarp / 32; ++u) {
             const int w = warp * kPerWarp + u * 32 + lane;
@@ -1129,12 +1152,13 @@ __global__ void __launch_bounds__(kScanThreads) k_lb_scan(QueryBufs b, QueryArgs
 }
 
 cudaError_t launch_lb_scan(const QueryBufs &b, const QueryArgs &a, cudaStream_t s) {
-    const size_t smem = kStages * stage_bytes<LbLayout>(a.m);
+    size_t smem = 0;
+    const int stages = scan_stages((const void *)k_lb_scan, stage_bytes<LbLayout>(a.m), 3, &smem);
     cudaError_t e = cudaFuncSetAttribute(k_lb_scan, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     const int64_t tiles = (a.N + kTile - 1) / kTile;
     const int grid = scan_grid((const void *)k_lb_scan, kScanThreads, smem, b.num_sms, tiles);
-    k_lb_scan<<<grid, kScanThreads, smem, s>>>(b, a);
+    k_lb_scan<<<grid, kScanThreads, smem, s>>>(b, a, stages);
     return cudaGetLastError();
 }
 

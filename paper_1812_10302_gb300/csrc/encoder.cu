@@ -673,10 +673,10 @@ __global__ void __launch_bounds__(kSeqThreads) k_query_embed(const uint8_t *blob
 }
 
 // Score every window at stride b by |e_q - E[j]|^2 (8 lanes per window, 8
-// dimensions each); the best window of each 2048-window tile is offered to
+// dimensions each); the best window of each 256-window tile is offered to
 // the proposal list.  A warp owns whole tiles (no block barriers) and keeps
 // four 16-byte loads in flight per lane.
-constexpr int kLsTile = 2048, kLsThreads = 256;
+constexpr int kLsTile = 256, kLsThreads = 256;
 __global__ void __launch_bounds__(kLsThreads) k_learn_scan(QueryBufs bq, const bf16 *E, int64_t Nw, int b,
                                                            int proposals) {
     QueryState *st = bq.st;
@@ -721,7 +721,10 @@ __global__ void __launch_bounds__(kLsThreads) k_learn_scan(QueryBufs bq, const b
             const unsigned long long v = __shfl_xor_sync(0xffffffffu, mine, o);
             mine = v < mine ? v : mine;
         }
-        if (lane == 0 && mine != ~0ull) list_insert(st->prop_keys, proposals, mine);
+        if (lane == 0 && mine != ~0ull) {
+            const unsigned long long last = *((volatile unsigned long long *)&st->prop_keys[proposals - 1]);
+            if (mine < last) list_insert(st->prop_keys, proposals, mine);
+        }
     }
 }
 

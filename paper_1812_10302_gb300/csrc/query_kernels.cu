@@ -1157,7 +1157,10 @@ cudaError_t launch_lb_scan(const QueryBufs &b, const QueryArgs &a, cudaStream_t 
     cudaError_t e = cudaFuncSetAttribute(k_lb_scan, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     const int64_t tiles = (a.N + kTile - 1) / kTile;
-    const int grid = scan_grid((const void *)k_lb_scan, kScanThreads, smem, b.num_sms, tiles);
+    int grid = scan_grid((const void *)k_lb_scan, kScanThreads, smem, b.num_sms, tiles);
+    // the scan is persistent and would occupy every CTA slot: leave one free
+    // so the side-stream pre-score runs beside it instead of after it
+    if (a.prescore && grid > b.num_sms) --grid;
     k_lb_scan<<<grid, kScanThreads, smem, s>>>(b, a, stages);
     return cudaGetLastError();
 }

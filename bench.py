@@ -15,7 +15,9 @@ At N = 1 the same JSON line also carries (unless ``--no-extras``):
 64 queries m = 1024, r = 102) with the learned ordering, the proxy ordering
 and the paper's random seeding, the speedups and whether the answers agree;
 ``batch`` -- the batched workload (n = 5e7, 256 queries of mixed m and r,
-top-10) through dtws_query_batch with a replayed CUDA graph.
+top-10) through dtws_query_batch with a replayed CUDA graph; ``drift`` -- the
+precision-stress workload (n = 1e9 with drift and variance regimes, 32
+queries m = 1024): ms per query and the FP32 DTW's error at each answer.
 
 Metric: subsequences/s per query (N windows / step time).  Also reported:
 brute-force-equivalent DTW cells/s (N * cells(m, r) / step time), the
@@ -384,6 +386,8 @@ def gpu_arm(args):
         line["learned"] = learned_leg(dev)
         torch.cuda.empty_cache()
         line["batch"] = batch_leg(dev)
+        torch.cuda.empty_cache()
+        line["drift"] = drift_leg(dev)
     print(json.dumps(line))
     return 0
 
@@ -480,6 +484,38 @@ def batch_leg(dev):
             "seconds_per_batch": sec, "queries_per_s": len(qs) / sec, "subsequences_per_s": windows / sec,
             "first_call_seconds": first, "lanes": 4, "graph": "captured on the first call, replayed",
             "timing": "host wall clock around dtws_query_batch (synchronising; host queries and outputs)"}
+
+
+def drift_leg(dev):
+    """The precision-stress workload (n = 1e9 walk with drift 1e-3 and
+    variance regimes, 32 noisy queries m = 1024, r = 102, top-1): mean ms per
+    query, and per query the relative difference between the FP32 DTW at the
+    answer and the library's extended-precision re-score of it (the FP64
+    oracle comparison of the same workload is in the test suite)."""
+    import torch
+
+    from paper_1812_10302_gb300 import dtws, synth
+    w = synth.workload("drift")
+    x, qs, r = w["series"], w["queries"], w["rs"][0]
+    t0 = time.perf_counter()
+    ix = dtws.Index(torch.from_numpy(x).to(dev))
+    torch.cuda.synchronize(dev)
+    create_s = time.perf_counter() - t0
+    del x
+    qds = [torch.from_numpy(q).to(dev) for q in qs]
+    ms = _mean_query_ms(ix, qds, r, 1, dev)
+    errs = []
+    for q in qs:
+        i, d = ix.query(q, r, 1)
+        f32 = ix.dtw_at(q, r, i)
+        f64 = ix.dtw_at_f64(q, r, i)
+        errs.append(abs(float(f32[0]) - float(f64[0])) / max(float(f64[0]), 1e-30))
+    ix.close()
+    return {"workload": "drift: walk with drift 1e-3 and variance regimes, n=1000000000, 32 noisy copies "
+                        "m=1024, r=102, top-1",
+            "ms_per_query": ms, "subsequences_per_s": (1_000_000_000 - 1023) / (ms * 1e-3),
+            "create_seconds": create_s,
+            "fp32_dtw_rel_error_vs_extended": {"max": max(errs), "median": float(np.median(errs))}}
 
 
 def main():

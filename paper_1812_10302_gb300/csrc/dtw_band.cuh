@@ -448,9 +448,17 @@ __host__ __device__ inline void diag_shape(int r, int *L, int *K) {
         *K = 1;
         return;
     }
+    // 32 lanes and the smallest instantiated K with 32*K >= r+1 cells: a
+    // non-power-of-two K cuts the cells past the band (e.g. r = 276: 320
+    // cells instead of 512)
     *L = 32;
-    int k = 1;
-    while (32 * k < need) k *= 2;
+    const int ks[9] = {1, 2, 3, 4, 6, 8, 10, 12, 16};
+    int k = 16;
+    for (int i = 0; i < 9; ++i)
+        if (32 * ks[i] >= need) {
+            k = ks[i];
+            break;
+        }
     *K = k;  // 0 < K <= 16 for r <= 511
 }
 

@@ -1114,7 +1114,7 @@ dtws_status dtws_autotune(dtws_t h, const int32_t *m_arr, const int32_t *r_arr, 
         CK(timed(0, 0, 0, ref_d, &ms_def));
         CK(cudaMemcpy(ref.data(), ref_d, fb, cudaMemcpyDeviceToHost));
         TuneEntry best{m, r, 0, 0, 0, ms_def, ms_def};
-        const int Ls[6] = {1, 2, 4, 8, 16, 32}, Ks[6] = {0, 1, 2, 4, 8, 16}, Ws[3] = {2, 4, 8};
+        const int Ls[6] = {1, 2, 4, 8, 16, 32}, Ks[10] = {0, 1, 2, 3, 4, 6, 8, 10, 12, 16}, Ws[3] = {2, 4, 8};
         for (int L : Ls)
             for (int K : Ks)
                 for (int W : Ws) {

@@ -673,57 +673,62 @@ __global__ void __launch_bounds__(kSeqThreads) k_query_embed(const uint8_t *blob
 }
 
 // Score every window at stride b by |e_q - E[j]|^2 (8 lanes per window, 8
-// dimensions each); the best window of each 256-window tile is offered to
-// the proposal list.  A warp owns whole tiles (no block barriers) and keeps
-// four 16-byte loads in flight per lane.
-constexpr int kLsTile = 256, kLsThreads = 256;
+// dimensions each).  Each warp scans one contiguous segment of the windows
+// with eight 16-byte loads in flight per lane; each CTA offers its best
+// window (one barrier, at the end) to the proposal list.
+constexpr int kLsThreads = 256, kLsU = 8;
 __global__ void __launch_bounds__(kLsThreads) k_learn_scan(QueryBufs bq, const bf16 *E, int64_t Nw, int b,
-                                                           int proposals) {
+                                                           int proposals, int64_t seg) {
+    __shared__ unsigned long long wbest[kLsThreads / 32];
     QueryState *st = bq.st;
     if (!st->valid) return;
-    const int lane = threadIdx.x & 31, sub = lane & 7, grp = lane >> 3;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, sub = lane & 7, grp = lane >> 3;
     const int64_t gwarp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     float eq[8];
 #pragma unroll
     for (int i = 0; i < 8; ++i) eq[i] = st->e_q[sub * 8 + i];
-    const int64_t tiles = (Nw + kLsTile - 1) / kLsTile;
-    constexpr int kU = 4;
-    for (int64_t tile = gwarp; tile < tiles; tile += nwarps) {
-        unsigned long long mine = ~0ull;
-        for (int64_t j0 = tile * kLsTile + grp; j0 < (tile + 1) * kLsTile; j0 += 4 * kU) {
-            uint4 v[kU];
+    const int64_t lo = gwarp * seg, hi = lo + seg < Nw ? lo + seg : Nw;
+    unsigned long long mine = ~0ull;
+    // every lane runs the same number of steps (the shuffles below need the whole warp)
+    for (int64_t base = lo; base < hi; base += 4 * kLsU) {
+        const int64_t j0 = base + grp;
+        uint4 v[kLsU];
 #pragma unroll
-            for (int u = 0; u < kU; ++u) {
-                const int64_t j = j0 + 4 * u;
-                v[u] = j < Nw ? *reinterpret_cast<const uint4 *>(E + j * DIM + sub * 8) : make_uint4(0, 0, 0, 0);
+        for (int u = 0; u < kLsU; ++u) {
+            const int64_t j = j0 + 4 * u;
+            v[u] = j < hi ? *reinterpret_cast<const uint4 *>(E + j * DIM + sub * 8) : make_uint4(0, 0, 0, 0);
+        }
+#pragma unroll
+        for (int u = 0; u < kLsU; ++u) {
+            const int64_t j = j0 + 4 * u;
+            const bf16 *h = reinterpret_cast<const bf16 *>(&v[u]);
+            float s = 0.0f;
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                const float d = eq[i] - __bfloat162float(h[i]);
+                s = fmaf(d, d, s);
             }
-#pragma unroll
-            for (int u = 0; u < kU; ++u) {
-                const int64_t j = j0 + 4 * u;
-                const bf16 *h = reinterpret_cast<const bf16 *>(&v[u]);
-                float s = 0.0f;
-#pragma unroll
-                for (int i = 0; i < 8; ++i) {
-                    const float d = eq[i] - __bfloat162float(h[i]);
-                    s = fmaf(d, d, s);
-                }
-                s += __shfl_xor_sync(0xffffffffu, s, 1);
-                s += __shfl_xor_sync(0xffffffffu, s, 2);
-                s += __shfl_xor_sync(0xffffffffu, s, 4);
-                if (j < Nw && sub == 0) {
-                    const unsigned long long k = make_key(s, (unsigned)(j * b));
-                    mine = k < mine ? k : mine;
-                }
+            s += __shfl_xor_sync(0xffffffffu, s, 1);
+            s += __shfl_xor_sync(0xffffffffu, s, 2);
+            s += __shfl_xor_sync(0xffffffffu, s, 4);
+            if (j < hi && sub == 0) {
+                const unsigned long long k = make_key(s, (unsigned)(j * b));
+                mine = k < mine ? k : mine;
             }
         }
-        for (int o = 16; o; o >>= 1) {
-            const unsigned long long v = __shfl_xor_sync(0xffffffffu, mine, o);
-            mine = v < mine ? v : mine;
-        }
-        if (lane == 0 && mine != ~0ull) {
+    }
+    for (int o = 16; o; o >>= 1) {
+        const unsigned long long v = __shfl_xor_sync(0xffffffffu, mine, o);
+        mine = v < mine ? v : mine;
+    }
+    if (lane == 0) wbest[warp] = mine;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long k = wbest[0];
+        for (int w = 1; w < kLsThreads / 32; ++w) k = wbest[w] < k ? wbest[w] : k;
+        if (k != ~0ull) {
             const unsigned long long last = *((volatile unsigned long long *)&st->prop_keys[proposals - 1]);
-            if (mine < last) list_insert(st->prop_keys, proposals, mine);
+            if (k < last) list_insert(st->prop_keys, proposals, k);
         }
     }
 }
@@ -811,11 +816,15 @@ cudaError_t launch_bf16_to_f32(const void *src, int64_t count, float *dst, cudaS
 
 cudaError_t launch_learn_scan(const QueryBufs &b, const void *E, int64_t Nw, int stride, int proposals,
                               cudaStream_t s) {
-    const int64_t tiles = (Nw + enc::kLsTile - 1) / enc::kLsTile;  // one warp per tile at a time
-    const int64_t want = (tiles + enc::kLsThreads / 32 - 1) / (enc::kLsThreads / 32);
-    const int grid = (int)(want < 8 * b.num_sms ? (want > 0 ? want : 1) : 8 * b.num_sms);
-    enc::k_learn_scan<<<grid, enc::kLsThreads, 0, s>>>(b, reinterpret_cast<const enc::bf16 *>(E), Nw, stride,
-                                                       proposals);
+    // 8 CTAs of 8 warps per SM at most, each warp a segment of >= 256 windows
+    const int64_t per_cta = (int64_t)(enc::kLsThreads / 32) * 256;
+    int64_t grid = (Nw + per_cta - 1) / per_cta;
+    if (grid > 8 * (int64_t)b.num_sms) grid = 8 * (int64_t)b.num_sms;
+    if (grid < 1) grid = 1;
+    const int64_t warps = grid * (enc::kLsThreads / 32);
+    const int64_t seg = ((Nw + warps - 1) / warps + 31) / 32 * 32;
+    enc::k_learn_scan<<<(unsigned)grid, enc::kLsThreads, 0, s>>>(b, reinterpret_cast<const enc::bf16 *>(E), Nw,
+                                                                 stride, proposals, seg);
     return cudaGetLastError();
 }
 

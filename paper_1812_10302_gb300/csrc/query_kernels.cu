@@ -376,10 +376,21 @@ __global__ void __launch_bounds__(kScanThreads) k_seed_scan(QueryBufs b, QueryAr
             if (i >= a.N) break;
             const float mh = t.mh[v], is = t.is[v], ls = t.ml[v] * is;
             float acc = 0.0f;
+            const float kw = fmaf(mh, is, ls);  // q_hat - x_hat = (q + mh*is + ls) - x*is
+            if (fabsf(kw) < 4096.0f) {
+                // one FMA per term; the absolute error stays below ~2^-11
+                // when |mu|/sigma < 2^12 (the proxy only ranks proposals)
 #pragma unroll
-            for (int u = 0; u < TERMS; ++u) {
-                const float c = qv[u] - fmaf(t.xs[w + pos[u]] - mh, is, -ls);
-                acc = fmaf(c, c, acc);
+                for (int u = 0; u < TERMS; ++u) {
+                    const float c = fmaf(-t.xs[w + pos[u]], is, qv[u] + kw);
+                    acc = fmaf(c, c, acc);
+                }
+            } else {
+#pragma unroll
+                for (int u = 0; u < TERMS; ++u) {
+                    const float c = qv[u] - fmaf(t.xs[w + pos[u]] - mh, is, -ls);
+                    acc = fmaf(c, c, acc);
+                }
             }
             const unsigned long long key = make_key(acc, (unsigned)i);
             best = key < best ? key : best;
@@ -925,7 +936,8 @@ static bool plan_shape(int m, int r, bool tail, int L, int K, int warps, DtwPlan
 #define DTWS_TRY(LL, KK) \
     if (!ok && L == LL && K == KK) ok = plan_fits<T, LL, KK>(m, r, tail, p);
     DTWS_TRY(1, 1) DTWS_TRY(2, 1) DTWS_TRY(4, 1) DTWS_TRY(8, 1) DTWS_TRY(16, 1)
-    DTWS_TRY(32, 1) DTWS_TRY(32, 2) DTWS_TRY(32, 4) DTWS_TRY(32, 8) DTWS_TRY(32, 16)
+    DTWS_TRY(32, 1) DTWS_TRY(32, 2) DTWS_TRY(32, 3) DTWS_TRY(32, 4) DTWS_TRY(32, 6) DTWS_TRY(32, 8) \
+        DTWS_TRY(32, 10) DTWS_TRY(32, 12) DTWS_TRY(32, 16)
     DTWS_TRY(1, 0) DTWS_TRY(2, 0) DTWS_TRY(4, 0) DTWS_TRY(8, 0) DTWS_TRY(16, 0) DTWS_TRY(32, 0)
 #undef DTWS_TRY
     if (!ok) return false;
@@ -943,7 +955,8 @@ static bool plan_dtw(int m, int r, bool tail, DtwPlan *p) {
 #define DTWS_TRY(LL, KK) \
     if (L == LL && K == KK && plan_fits<T, LL, KK>(m, r, tail, p)) return true;
         DTWS_TRY(1, 1) DTWS_TRY(2, 1) DTWS_TRY(4, 1) DTWS_TRY(8, 1) DTWS_TRY(16, 1)
-        DTWS_TRY(32, 1) DTWS_TRY(32, 2) DTWS_TRY(32, 4) DTWS_TRY(32, 8) DTWS_TRY(32, 16)
+        DTWS_TRY(32, 1) DTWS_TRY(32, 2) DTWS_TRY(32, 3) DTWS_TRY(32, 4) DTWS_TRY(32, 6) DTWS_TRY(32, 8) \
+        DTWS_TRY(32, 10) DTWS_TRY(32, 12) DTWS_TRY(32, 16)
 #undef DTWS_TRY
     }
     const int L = lanes_for(r);
@@ -979,7 +992,8 @@ static cudaError_t dtw_dispatch(const QueryBufs &b, const QueryArgs &a, const in
         return cudaGetLastError();                                                                            \
     }
     DTWS_CASE(1, 1) DTWS_CASE(2, 1) DTWS_CASE(4, 1) DTWS_CASE(8, 1) DTWS_CASE(16, 1)
-    DTWS_CASE(32, 1) DTWS_CASE(32, 2) DTWS_CASE(32, 4) DTWS_CASE(32, 8) DTWS_CASE(32, 16)
+    DTWS_CASE(32, 1) DTWS_CASE(32, 2) DTWS_CASE(32, 3) DTWS_CASE(32, 4) DTWS_CASE(32, 6) DTWS_CASE(32, 8) \
+    DTWS_CASE(32, 10) DTWS_CASE(32, 12) DTWS_CASE(32, 16)
     DTWS_CASE(1, 0) DTWS_CASE(2, 0) DTWS_CASE(4, 0) DTWS_CASE(8, 0) DTWS_CASE(16, 0) DTWS_CASE(32, 0)
 #undef DTWS_CASE
     return cudaErrorInvalidValue;
@@ -999,7 +1013,8 @@ static cudaError_t dtw64_dispatch(const QueryBufs &b, const QueryArgs &a, const 
         return cudaGetLastError();                                                                            \
     }
     DTWS_CASE(1, 1) DTWS_CASE(2, 1) DTWS_CASE(4, 1) DTWS_CASE(8, 1) DTWS_CASE(16, 1)
-    DTWS_CASE(32, 1) DTWS_CASE(32, 2) DTWS_CASE(32, 4) DTWS_CASE(32, 8) DTWS_CASE(32, 16)
+    DTWS_CASE(32, 1) DTWS_CASE(32, 2) DTWS_CASE(32, 3) DTWS_CASE(32, 4) DTWS_CASE(32, 6) DTWS_CASE(32, 8) \
+    DTWS_CASE(32, 10) DTWS_CASE(32, 12) DTWS_CASE(32, 16)
     DTWS_CASE(1, 0) DTWS_CASE(2, 0) DTWS_CASE(4, 0) DTWS_CASE(8, 0) DTWS_CASE(16, 0) DTWS_CASE(32, 0)
 #undef DTWS_CASE
     return cudaErrorInvalidValue;
@@ -1354,7 +1369,8 @@ cudaError_t launch_prescore(const QueryBufs &b, const QueryArgs &a, cudaStream_t
         return cudaGetLastError();                                                                  \
     }
     DTWS_CASE(1, 1) DTWS_CASE(2, 1) DTWS_CASE(4, 1) DTWS_CASE(8, 1) DTWS_CASE(16, 1)
-    DTWS_CASE(32, 1) DTWS_CASE(32, 2) DTWS_CASE(32, 4) DTWS_CASE(32, 8) DTWS_CASE(32, 16)
+    DTWS_CASE(32, 1) DTWS_CASE(32, 2) DTWS_CASE(32, 3) DTWS_CASE(32, 4) DTWS_CASE(32, 6) DTWS_CASE(32, 8) \
+    DTWS_CASE(32, 10) DTWS_CASE(32, 12) DTWS_CASE(32, 16)
 #undef DTWS_CASE
     return cudaErrorInvalidValue;
 }

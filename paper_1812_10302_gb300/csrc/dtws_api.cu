@@ -59,8 +59,9 @@ struct TuneEntry {
 
 struct LearnEntry {
     int m = 0;
-    int64_t used = 0, version = 0, rows = 0;
-    void *E = nullptr;  // BF16 [rows][64]
+    int64_t used = 0, version = 0, rows = 0, rows2 = 0;
+    void *E = nullptr;   // BF16 [rows][64]: windows at offsets j*b
+    void *E2 = nullptr;  // BF16 [rows2][64]: windows at offsets j*b + b/2 (b >= 2)
 };
 
 constexpr int kCacheSlots = 8;
@@ -281,11 +282,24 @@ cudaError_t need(T **p, size_t count) {
 
 void free_learn(LearnEntry &e) {
     cudaFree(e.E);
+    if (e.E2) cudaFree(e.E2);
     e = LearnEntry();
 }
 
 int enc_block(int m) { return m / 64; }
 int64_t enc_rows(dtws_t h, int m) { return (h->n - m) / enc_block(m) + 1; }
+// the second embedding phase: windows at offsets j*b + b/2, so that every
+// window lies within b/4 of an embedded one (0: no second phase, b = 1)
+int enc_phase(int m) { return enc_block(m) / 2; }
+int64_t enc_rows2(dtws_t h, int m) {
+    const int ph = enc_phase(m);
+    return ph > 0 && h->n - m >= ph ? (h->n - m - ph) / enc_block(m) + 1 : 0;
+}
+// Euclidean seeds around each learned proposal: +- half its grid gap
+int learn_half(int m) {
+    const int b = enc_block(m);
+    return enc_phase(m) > 0 ? (b + 3) / 4 : b / 2;
+}
 
 // Embeddings of the windows at offsets j*b for query length m (cached).
 dtws_status get_learn(dtws_t h, int m, const StatsEntry *se, cudaStream_t s, LearnEntry **out, bool *computed) {
@@ -316,14 +330,23 @@ dtws_status get_learn(dtws_t h, int m, const StatsEntry *se, cudaStream_t s, Lea
     e.m = m;
     e.version = h->enc_version;
     e.rows = enc_rows(h, m);
-    uint16_t *E = nullptr;
-    if (dalloc(&E, (size_t)e.rows * 64) != cudaSuccess) {
+    e.rows2 = enc_rows2(h, m);
+    uint16_t *E = nullptr, *E2 = nullptr;
+    if (dalloc(&E, (size_t)e.rows * 64) != cudaSuccess ||
+        (e.rows2 > 0 && dalloc(&E2, (size_t)e.rows2 * 64) != cudaSuccess)) {
         cudaGetLastError();
+        if (E) cudaFree(E);
         set_err("learned embeddings for m=%d: out of device memory", m);
         return DTWS_ENOMEM;
     }
     e.E = E;
+    e.E2 = E2;
     CK(launch_enc_series(h->enc_blob, h->x, h->n, enc_block(m), se->inv_sigma, e.rows, e.E, h->num_sms, s));
+    if (e.rows2 > 0) {  // the same pass over the series shifted by the phase
+        const int ph = enc_phase(m);
+        CK(launch_enc_series(h->enc_blob, h->x + ph, h->n - ph, enc_block(m), se->inv_sigma + ph, e.rows2, e.E2,
+                             h->num_sms, s));
+    }
     e.used = ++h->clock;
     h->learn.push_back(e);
     *out = &h->learn.back();
@@ -427,7 +450,7 @@ dtws_status check_query_args(dtws_t h, const float *Q, int32_t m, int32_t r, int
     if (h->opt.ordering == DTWS_ORDER_LEARNED) {
         if (!h->enc_version) { set_err("learned ordering without an encoder (dtws_set_encoder)"); return DTWS_EINVAL; }
         if (m < 64) { set_err("learned ordering needs m >= 64 (m=%d)", m); return DTWS_EINVAL; }
-        const int P = h->opt.seed_proposals, half = enc_block(m) / 2;
+        const int P = h->opt.seed_proposals, half = learn_half(m);
         if (P > kLearnPropMax || h->opt.seed_random + P * (2 * half + 1) > kEdMax) {
             set_err("learned ordering: %d proposals exceed the seed capacity", P);
             return DTWS_EINVAL;
@@ -470,8 +493,12 @@ dtws_status enqueue_search(dtws_t h, const Exec &e, const QueryArgs &a, const fl
     int half = kProxyStride / 2;
     if (P > 0 && e.le) {
         CK(launch_enc_query(h->enc_blob, b, a, s));
-        CK(launch_learn_scan(b, e.le->E, e.le->rows, enc_block(m), P, s));
-        half = enc_block(m) / 2;
+        CK(launch_learn_scan(b, e.le->E, e.le->rows, enc_block(m), 0, P, s));
+        if (e.le->rows2 > 0) {
+            CK(launch_learn_scan(b, e.le->E2, e.le->rows2, enc_block(m), enc_phase(m), P, s));
+            ++launches;
+        }
+        half = learn_half(m);
         launches += 2;
     } else if (P > 0) {
         CK(launch_seed_scan(b, a, P, h->opt.proxy_terms, s));

@@ -93,7 +93,8 @@ size_t enc_workspace_bytes(int rows);
 cudaError_t launch_enc_series(const uint8_t *blob, const float *x, int64_t n, int b, const float *inv_sigma,
                               int64_t Nw, void *E, int num_sms, cudaStream_t s);
 cudaError_t launch_enc_query(const uint8_t *blob, const QueryBufs &b, const QueryArgs &a, cudaStream_t s);
-cudaError_t launch_learn_scan(const QueryBufs &b, const void *E, int64_t Nw, int stride, int proposals,
+// windows at offsets j*stride + phase (j < Nw)
+cudaError_t launch_learn_scan(const QueryBufs &b, const void *E, int64_t Nw, int stride, int phase, int proposals,
                               cudaStream_t s);
 cudaError_t launch_bf16_to_f32(const void *src, int64_t count, float *dst, cudaStream_t s);
 

@@ -678,7 +678,7 @@ __global__ void __launch_bounds__(kSeqThreads) k_query_embed(const uint8_t *blob
 // window (one barrier, at the end) to the proposal list.
 constexpr int kLsThreads = 256, kLsU = 8;
 __global__ void __launch_bounds__(kLsThreads) k_learn_scan(QueryBufs bq, const bf16 *E, int64_t Nw, int b,
-                                                           int proposals, int64_t seg) {
+                                                           int phase, int proposals, int64_t seg) {
     __shared__ unsigned long long wbest[kLsThreads / 32];
     QueryState *st = bq.st;
     if (!st->valid) return;
@@ -712,7 +712,7 @@ __global__ void __launch_bounds__(kLsThreads) k_learn_scan(QueryBufs bq, const b
             s += __shfl_xor_sync(0xffffffffu, s, 2);
             s += __shfl_xor_sync(0xffffffffu, s, 4);
             if (j < hi && sub == 0) {
-                const unsigned long long k = make_key(s, (unsigned)(j * b));
+                const unsigned long long k = make_key(s, (unsigned)(j * b + phase));
                 mine = k < mine ? k : mine;
             }
         }
@@ -814,7 +814,7 @@ cudaError_t launch_bf16_to_f32(const void *src, int64_t count, float *dst, cudaS
     return cudaGetLastError();
 }
 
-cudaError_t launch_learn_scan(const QueryBufs &b, const void *E, int64_t Nw, int stride, int proposals,
+cudaError_t launch_learn_scan(const QueryBufs &b, const void *E, int64_t Nw, int stride, int phase, int proposals,
                               cudaStream_t s) {
     // 8 CTAs of 8 warps per SM at most, each warp a segment of >= 256 windows
     const int64_t per_cta = (int64_t)(enc::kLsThreads / 32) * 256;
@@ -824,7 +824,7 @@ cudaError_t launch_learn_scan(const QueryBufs &b, const void *E, int64_t Nw, int
     const int64_t warps = grid * (enc::kLsThreads / 32);
     const int64_t seg = ((Nw + warps - 1) / warps + 31) / 32 * 32;
     enc::k_learn_scan<<<(unsigned)grid, enc::kLsThreads, 0, s>>>(b, reinterpret_cast<const enc::bf16 *>(E), Nw,
-                                                                 stride, proposals, seg);
+                                                                 stride, phase, proposals, seg);
     return cudaGetLastError();
 }
 

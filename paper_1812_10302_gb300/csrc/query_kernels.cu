@@ -710,17 +710,21 @@ __global__ void __launch_bounds__(256) k_dtw(QueryBufs b, QueryArgs a, const int
         tc.is = is;
         tc.ls = ls;
         if (MODE == kModeSurv && has_env) {
-            // Eq. 10 with early abandon: the terms in |q_hat| descending
-            // order, L at a time, until the partial sum passes thr (the sum
-            // is reduced over the group, so every lane takes the same exit);
-            // past 128 terms the full bound below (row order, with the
-            // suffix sums the DTW needs) takes over
-            float acc = 0.0f;
+            // Eq. 10 (q_hat against the window's envelope) and Eq. 8 (the
+            // window against the query's envelope; the scan took only its
+            // first terms) with early abandon: the terms in |q_hat|
+            // descending order, L at a time, until either partial sum passes
+            // thr -- each is a lower bound on its own (rows and columns of
+            // the same warping path).  The sums are reduced over the group,
+            // so every lane takes the same exit.  Past 128 terms the full
+            // Eq. 10 below (row order, with the suffix sums the DTW needs)
+            // takes over.
+            float acc = 0.0f, acc8 = 0.0f;
             bool pruned = false;
             const int budget = m < 128 ? m : 128;
             for (int c0 = 0; c0 < budget; c0 += L) {
                 const int j = c0 + lane;
-                float v = 0.0f;
+                float v = 0.0f, v8 = 0.0f;
                 if (j < m) {
                     const int pos = b.ord[j];
                     float U, Lo;
@@ -728,11 +732,18 @@ __global__ void __launch_bounds__(256) k_dtw(QueryBufs b, QueryArgs a, const int
                     const float u = fmaf(U - mh, is, -ls), l = fmaf(Lo - mh, is, -ls), q = b.sq[j];
                     const float d = fmaxf(q - u, 0.0f) + fmaxf(l - q, 0.0f);
                     v = d * d;
+                    const float c = fmaf(xw[pos] - mh, is, -ls);
+                    const float e = fmaxf(c - b.sU[j], 0.0f) + fmaxf(b.sL[j] - c, 0.0f);
+                    v8 = e * e;
                 }
 #pragma unroll
-                for (int o = L / 2; o > 0; o >>= 1) v += __shfl_xor_sync(gmask, v, o, L);
+                for (int o = L / 2; o > 0; o >>= 1) {
+                    v += __shfl_xor_sync(gmask, v, o, L);
+                    v8 += __shfl_xor_sync(gmask, v8, o, L);
+                }
                 acc += v;
-                if (acc > thr) {
+                acc8 += v8;
+                if (acc > thr || acc8 > thr) {
                     pruned = true;
                     break;
                 }

@@ -293,7 +293,9 @@ dtws_status dtws_set_encoder(dtws_t h, const float *params, int32_t count, void 
 
 /* The handle's embeddings for query length m: rows = floor((n-m)/b) + 1
    windows at offsets j*b, each 64 FP32 (out [rows][64], host or device;
-   `rows` must equal that count).  Computes and caches them if needed.
+   `rows` must equal that count).  Computes and caches them if needed (the
+   learned ordering also embeds the windows at offsets j*b + b/2 when b >= 2;
+   those are not returned here).
    Errors: DTWS_EINVAL (no encoder, m < 64 or > n, rows mismatch). */
 dtws_status dtws_learned_embeddings(dtws_t h, int32_t m, float *out, int64_t rows, void *stream);
 

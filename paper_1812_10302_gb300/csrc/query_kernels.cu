@@ -576,6 +576,26 @@ cudaError_t launch_seed_gather(const QueryBufs &b, const QueryArgs &a, int n_ran
     return cudaGetLastError();
 }
 
+// Bin of a survivor's lower bound for the counting sort (see launch_order):
+// with a finite scan threshold the bins split [0, thr] evenly; otherwise
+// they follow the float's exponent and leading mantissa bits (monotone for
+// lb >= 0).
+__device__ __forceinline__ int bin_of(float lb, float thr) {
+    if (thr < DINF) {
+        int bn = (int)(lb * ((float)kBins / thr));
+        return bn < 0 ? 0 : (bn >= kBins ? kBins - 1 : bn);
+    }
+    return (int)(__float_as_uint(lb) >> 21);
+}
+
+// A value that every bound in bins >= k (bin_of with the same thr) is at
+// least: the bin's lower edge, lowered by 2^-20 to cover the rounding of the
+// product in bin_of.
+__device__ __forceinline__ float bin_floor(int k, float thr) {
+    if (thr < DINF) return ((float)k / ((float)kBins / thr)) * (1.0f - 9.5367431640625e-07f);
+    return __uint_as_float((unsigned)k << 21);
+}
+
 // ------------------------------------------------------------------ DTW kernels
 enum DtwMode { kModeSeed = 0, kModeSurv = 1, kModeOut = 2 };
 
@@ -647,14 +667,26 @@ __global__ void __launch_bounds__(256) k_dtw(QueryBufs b, QueryArgs a, const int
                                        (lay.tail ? (size_t)(lay.m4 + 4) * 4 : 0))
                            : nullptr;
     // survivor pass: the seeds' offsets (already evaluated by the seed pass)
+    // and the first 128 query positions in |q_hat| order with q_hat and the
+    // query envelope there (the pre-check reads them for every candidate)
     __shared__ unsigned seeds_s[kSeedMax];
     __shared__ int n_seeds_s;
+    __shared__ int ord_s[128];
+    __shared__ float sq_s[128], su_s[128], sl_s[128];
     if (MODE == kModeSurv) {
         if (threadIdx.x == 0) n_seeds_s = st->n_seeds;
         for (int t = threadIdx.x; t < st->n_seeds; t += blockDim.x) seeds_s[t] = st->seed_off[t];
+        for (int t = threadIdx.x; t < 128; t += blockDim.x) {
+            const bool in = t < m;
+            ord_s[t] = in ? (int)b.ord[t] : 0;
+            sq_s[t] = in ? b.sq[t] : 0.0f;
+            su_s[t] = in ? b.sU[t] : 0.0f;
+            sl_s[t] = in ? b.sL[t] : 0.0f;
+        }
     }
     __syncthreads();
     int *cursor = MODE == kModeSurv ? &st->work2 : &st->work;
+    const float thr_scan = MODE == kModeSurv ? st->thr_scan : 0.0f;
     const unsigned pre = MODE == kModeSurv ? prescored_window(st, a) : 0xffffffffu;
     const int64_t count = MODE == kModeSeed ? (int64_t)st->n_seeds
                         : MODE == kModeSurv ? (int64_t)st->n_cand : count_host;
@@ -687,7 +719,13 @@ __global__ void __launch_bounds__(256) k_dtw(QueryBufs b, QueryArgs a, const int
             thr = current_thr(st, a);
         }
         thr = __shfl_sync(gmask, thr, 0, L);
-        if (MODE == kModeSurv && lb > thr) continue;
+        if (MODE == kModeSurv && lb > thr) {
+            // survivors are in ascending bins and thr only shrinks: once the
+            // floor of this candidate's bin is above thr, so is every later
+            // candidate's bound, and this group is done
+            if (bin_floor(bin_of(lb, thr_scan), thr_scan) > thr) break;
+            continue;
+        }
         if (MODE == kModeSurv) {
             // scored already: by the seed pass or on the side stream
             bool seen = idx == pre;
@@ -726,14 +764,15 @@ __global__ void __launch_bounds__(256) k_dtw(QueryBufs b, QueryArgs a, const int
                 const int j = c0 + lane;
                 float v = 0.0f, v8 = 0.0f;
                 if (j < m) {
-                    const int pos = b.ord[j];
+                    const int pos = ord_s[j];
+                    const float x = xw[pos];
                     float U, Lo;
                     env_at(tc, pos, U, Lo);
-                    const float u = fmaf(U - mh, is, -ls), l = fmaf(Lo - mh, is, -ls), q = b.sq[j];
+                    const float u = fmaf(U - mh, is, -ls), l = fmaf(Lo - mh, is, -ls), q = sq_s[j];
                     const float d = fmaxf(q - u, 0.0f) + fmaxf(l - q, 0.0f);
                     v = d * d;
-                    const float c = fmaf(xw[pos] - mh, is, -ls);
-                    const float e = fmaxf(c - b.sU[j], 0.0f) + fmaxf(b.sL[j] - c, 0.0f);
+                    const float c = fmaf(x - mh, is, -ls);
+                    const float e = fmaxf(c - su_s[j], 0.0f) + fmaxf(sl_s[j] - c, 0.0f);
                     v8 = e * e;
                 }
 #pragma unroll
@@ -1196,13 +1235,6 @@ cudaError_t launch_lb_scan(const QueryBufs &b, const QueryArgs &a, cudaStream_t 
 // stage meets the most promising windows first.  With a finite scan
 // threshold the bins split [0, thr] evenly; otherwise they follow the
 // float's exponent and leading mantissa bits (monotone for lb >= 0).
-__device__ __forceinline__ int bin_of(float lb, float thr) {
-    if (thr < DINF) {
-        int bn = (int)(lb * ((float)kBins / thr));
-        return bn < 0 ? 0 : (bn >= kBins ? kBins - 1 : bn);
-    }
-    return (int)(__float_as_uint(lb) >> 21);
-}
 
 __global__ void k_bin_hist(QueryBufs b) {
     __shared__ int h[kBins];

@@ -226,9 +226,14 @@ __device__ T dtw_band(const T *__restrict__ qs, const float *__restrict__ xw, co
 // +inf (never NaN) and needs no bounds test.
 __host__ __device__ inline int diag_pad(int r, int L, int K) { return (r >> 1) + L * K + 4; }
 
-template <typename T, int L, int K, bool ABANDON, int ODD>
-__device__ __forceinline__ void diag_step(const T *qp, const T *cp, T (&p1)[K], T (&p2)[K], int bi, int bj,
-                                          int lane, int r, unsigned gmask, int &cells) {
+// One anti-diagonal step of dtw_diag: lane cell t (position p = lane*K + t
+// along the anti-diagonal) takes its left / up neighbours from the previous
+// anti-diagonal (p1, with one value from the adjacent lane), its diagonal
+// one from the one before (p2), and the query / window values from the
+// register windows qv, cv.
+template <typename T, int L, int K, int ODD>
+__device__ __forceinline__ void diag_step(const T (&qv)[K], const T (&cv)[K], T (&p1)[K], T (&p2)[K], int lane,
+                                          int r, unsigned gmask) {
     const T INF = tinf<T>();
     // the one neighbour held by the adjacent lane: p-1 (even) / p+1 (odd)
     T nb = __shfl_sync(gmask, ODD ? p1[0] : p1[K - 1], ODD ? ((lane + 1) & (L - 1)) : ((lane - 1) & (L - 1)), L);
@@ -239,10 +244,9 @@ __device__ __forceinline__ void diag_step(const T *qp, const T *cp, T (&p1)[K], 
         const int p = lane * K + t;
         const T left = ODD ? p1[t] : (t == 0 ? nb : p1[t > 0 ? t - 1 : 0]);
         const T up = ODD ? (t == K - 1 ? nb : p1[t < K - 1 ? t + 1 : 0]) : p1[t];
-        const T d = qp[bi - p] - cp[bj + p];
+        const T d = qv[t] - cv[t];
         T v = tfma(d, d, tmin(tmin(left, up), p2[t]));
         if (ODD ? (p >= r) : (p > r)) v = INF;  // past the band's cells on this anti-diagonal
-        cells += v < INF;
         cur[t] = v;
     }
 #pragma unroll
@@ -252,15 +256,46 @@ __device__ __forceinline__ void diag_step(const T *qp, const T *cp, T (&p1)[K], 
     }
 }
 
+// Cells of an anti-diagonal step inside the band and the matrix: positions p
+// with 0 <= p <= hi_band, 0 <= qbase - p < m, 0 <= cbase + p < m.
+__device__ __forceinline__ int diag_cells(int qbase, int cbase, int m, int hi_band) {
+    const int lo = max(0, max(qbase - (m - 1), -cbase));
+    const int hi = min(hi_band, min(qbase, m - 1 - cbase));
+    return hi >= lo ? hi - lo + 1 : 0;
+}
+
+// Register windows of the anti-diagonal walk: cell p of a step reads
+// q[qbase - p] and c[cbase + p].  After an even step cbase grows by one (the
+// window values move one cell down, the last lane loads the new one); after
+// an odd step qbase grows by one (the query values move one cell up, lane 0
+// loads the new one).
+template <typename T, int L, int K>
+__device__ __forceinline__ void shift_c(T (&cv)[K], const T *cp, int cbase_new, int lane, unsigned gmask) {
+    const T from_next = __shfl_down_sync(gmask, cv[0], 1, L);
+    const T fresh = cp[cbase_new + L * K - 1];
+#pragma unroll
+    for (int t = 0; t < K - 1; ++t) cv[t] = cv[t + 1];
+    cv[K - 1] = lane == L - 1 ? fresh : from_next;
+}
+template <typename T, int L, int K>
+__device__ __forceinline__ void shift_q(T (&qv)[K], const T *qp, int qbase_new, int lane, unsigned gmask) {
+    const T from_prev = __shfl_up_sync(gmask, qv[K - 1], 1, L);
+    const T fresh = qp[qbase_new];
+#pragma unroll
+    for (int t = K - 1; t > 0; --t) qv[t] = qv[t - 1];
+    qv[0] = lane == 0 ? fresh : from_prev;
+}
+
 // qp, cp: the query and the group's normalised window, each padded by
 // diag_pad(r, L, K) elements (+inf / -inf) on both sides, pointing at
-// element 0.  cbs: the rows' tail bound for ABANDON (or nullptr).
+// element 0.  cbs: the rows' tail bound for ABANDON (or nullptr).  cells:
+// lane 0 accumulates the cells evaluated (in the band and the matrix).
 template <typename T, int L, int K, bool ABANDON>
 __device__ T dtw_diag(const T *__restrict__ qp, const T *__restrict__ cp, const float *cbs, int m, int r, T thr,
                       unsigned gmask, int lane, int &cells) {
     const T INF = tinf<T>();
     const int p0 = (r - (r & 1)) >> 1;
-    T p1[K], p2[K];
+    T p1[K], p2[K], qv[K], cv[K];
 #pragma unroll
     for (int t = 0; t < K; ++t) {
         p1[t] = INF;
@@ -271,15 +306,35 @@ __device__ T dtw_diag(const T *__restrict__ qp, const T *__restrict__ cp, const 
     // (bi, bj) = ((a - e_min)/2, (a + e_min)/2).  Along an (even, odd) pair
     // bi stays and bj grows by one; from pair to pair both grow by one.
     int a = 0, bi, bj;
+    int ncell = 0;  // lane 0's count
     if (r & 1) {  // a = 0 is odd: e_min = 1 - r
-        diag_step<T, L, K, ABANDON, 1>(qp, cp, p1, p2, (r - 1) >> 1, (1 - r) >> 1, lane, r, gmask, cells);
+        const int qb = (r - 1) >> 1, cb = (1 - r) >> 1;
+#pragma unroll
+        for (int t = 0; t < K; ++t) {
+            qv[t] = qp[qb - (lane * K + t)];
+            cv[t] = cp[cb + (lane * K + t)];
+        }
+        diag_step<T, L, K, 1>(qv, cv, p1, p2, lane, r, gmask);
+        ncell += diag_cells(qb, cb, m, r - 1);
         a = 1;
+        shift_q<T, L, K>(qv, qp, qb + 1, lane, gmask);
+    } else {
+        const int qb = r >> 1, cb = -(r >> 1);
+#pragma unroll
+        for (int t = 0; t < K; ++t) {
+            qv[t] = qp[qb - (lane * K + t)];
+            cv[t] = cp[cb + (lane * K + t)];
+        }
     }
     bi = (a + r) >> 1;
     bj = (a - r) >> 1;
     for (; a + 1 <= last; a += 2, ++bi, ++bj) {
-        diag_step<T, L, K, ABANDON, 0>(qp, cp, p1, p2, bi, bj, lane, r, gmask, cells);
-        diag_step<T, L, K, ABANDON, 1>(qp, cp, p1, p2, bi, bj + 1, lane, r, gmask, cells);
+        diag_step<T, L, K, 0>(qv, cv, p1, p2, lane, r, gmask);
+        ncell += diag_cells(bi, bj, m, r);
+        shift_c<T, L, K>(cv, cp, bj + 1, lane, gmask);
+        diag_step<T, L, K, 1>(qv, cv, p1, p2, lane, r, gmask);
+        ncell += diag_cells(bi, bj + 1, m, r - 1);
+        shift_q<T, L, K>(qv, qp, bi + 1, lane, gmask);
         if (ABANDON && ((a >> 1) & 7) == 7) {
             // p1: anti-diagonal a+1 (rows bi - p), p2: a (rows bi - p)
             float low = __int_as_float(0x7f800000);
@@ -291,10 +346,17 @@ __device__ T dtw_diag(const T *__restrict__ qp, const T *__restrict__ cp, const 
             }
 #pragma unroll
             for (int o = L / 2; o > 0; o >>= 1) low = fminf(low, __shfl_xor_sync(gmask, low, o, L));
-            if (low > (float)thr) return INF;
+            if (low > (float)thr) {
+                if (lane == 0) cells += ncell;
+                return INF;
+            }
         }
     }
-    if (a == last) diag_step<T, L, K, ABANDON, 0>(qp, cp, p1, p2, bi, bj, lane, r, gmask, cells);
+    if (a == last) {
+        diag_step<T, L, K, 0>(qv, cv, p1, p2, lane, r, gmask);
+        ncell += diag_cells(bi, bj, m, r);
+    }
+    if (lane == 0) cells += ncell;
     // d(m-1, m-1): e = 0 on the last anti-diagonal
     const int pe = (r - ((last + r) & 1)) >> 1;
     T res = INF;
@@ -304,9 +366,6 @@ __device__ T dtw_diag(const T *__restrict__ qp, const T *__restrict__ cp, const 
     return __shfl_sync(gmask, res, pe / K, L);
 }
 
-// ------------------------------------------------------------------ double-float DTW
-// Re-scoring in double-float arithmetic: a value is an unevaluated sum
-// hi + lo of two floats (about 48 significant bits), built from Dekker's and
 // Knuth's error-free transformations (TwoSum, FastTwoSum, FMA-based
 // products).  It runs on the FP32 pipes, which on this part issue far more
 // than its FP64 units; accumulated relative error over a DTW is ~1e-14.

@@ -1116,7 +1116,10 @@ cudaError_t launch_dtw_at_f64(const QueryBufs &b, const QueryArgs &a, const int6
 // normalised with the window's statistics: looser than the window-clipped
 // envelope, still admissible), is evaluated for each survivor by the DTW
 // kernel, whose tail bound consists of exactly its per-row terms.
-constexpr int kEqChunks = 2;
+// LB_Keogh (Eq. 8) chunks of 32 terms the scan takes at most per window; the
+// first kEqSmem of them come from shared memory, the rest through L1 (the
+// same few values for every window)
+constexpr int kEqChunks = 8, kEqSmem = 2;
 
 __device__ __forceinline__ float keogh_term(float v, float u, float l) {
     const float d = fmaxf(v - u, 0.0f) + fmaxf(l - v, 0.0f);
@@ -1145,9 +1148,9 @@ __global__ void __launch_bounds__(kScanThreads) k_lb_scan(QueryBufs b, QueryArgs
     const int lane = lane_id(), warp = threadIdx.x >> 5;
     constexpr int kPerWarp = kTile / kScanConsumers;
     // the ordered query terms the scan uses, in shared memory
-    __shared__ int o_s[kEqChunks * 32];
-    __shared__ float u_s[kEqChunks * 32], l_s[kEqChunks * 32];
-    for (int j = threadIdx.x; j < kEqChunks * 32; j += blockDim.x) {
+    __shared__ int o_s[kEqSmem * 32];
+    __shared__ float u_s[kEqSmem * 32], l_s[kEqSmem * 32];
+    for (int j = threadIdx.x; j < kEqSmem * 32; j += blockDim.x) {
         o_s[j] = j < m ? (int)b.ord[j] : 0;
         u_s[j] = j < m ? b.sU[j] : 0.0f;
         l_s[j] = j < m ? b.sL[j] : 0.0f;
@@ -1187,7 +1190,12 @@ __global__ void __launch_bounds__(kScanThreads) k_lb_scan(QueryBufs b, QueryArgs
                 for (int base = 0; base < m && base < kEqChunks * 32; base += 32) {
                     const int j = base + lane;
                     float term = 0.0f;
-                    if (j < m) term = keogh_term(fmaf(xw[o_s[j]] - mh, is, -ls), u_s[j], l_s[j]);
+                    if (j < m) {
+                        const bool sm = base < kEqSmem * 32;
+                        const int o = sm ? o_s[j] : (int)__ldg(b.ord + j);
+                        const float uq = sm ? u_s[j] : __ldg(b.sU + j), lq = sm ? l_s[j] : __ldg(b.sL + j);
+                        term = keogh_term(fmaf(xw[o] - mh, is, -ls), uq, lq);
+                    }
                     s2 += warp_sum(term);
                     if (s2 > thr) break;
                 }

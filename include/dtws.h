@@ -238,6 +238,15 @@ dtws_status dtws_lower_bounds_at(dtws_t h, const float *Q, int32_t m, int32_t r,
                                  const int64_t *offsets, int64_t count, float *kim,
                                  float *keogh_q, float *keogh_s, void *stream);
 
+/* Failure-detection self-test (the paper has no counterpart): one device
+   thread waits, with the library's bounded wait, on a barrier that nothing
+   completes; after wait_ns (1 .. 1e10) it records a timeout, which the next
+   dtws_sync_status(h, stream) returns as DTWS_ETIMEOUT (and clears).  The
+   same bounded wait guards every device-side wait of the search, so no
+   kernel of the library spins forever; this entry point exercises that path
+   without a fault or a hang.  Errors: DTWS_EINVAL, DTWS_ECUDA. */
+dtws_status dtws_debug_wait_selftest(dtws_t h, int64_t wait_ns, void *stream);
+
 /* ---- autotuner (the paper has no counterpart) ----
  *
  * For each (m, r) pair (r > m-1 taken as m-1), times the banded-DTW kernel

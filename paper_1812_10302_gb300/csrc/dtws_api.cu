@@ -1072,6 +1072,15 @@ dtws_status dtws_clear_cache(dtws_t h) {
     return DTWS_OK;
 }
 
+dtws_status dtws_debug_wait_selftest(dtws_t h, int64_t wait_ns, void *stream) {
+    if (!h || wait_ns < 1 || wait_ns > 10000000000LL) {
+        set_err("dtws_debug_wait_selftest: null handle or wait_ns outside [1, 1e10]");
+        return DTWS_EINVAL;
+    }
+    CK(launch_wait_selftest(h->status, (long long)wait_ns, (cudaStream_t)stream));
+    return DTWS_OK;
+}
+
 dtws_status dtws_autotune(dtws_t h, const int32_t *m_arr, const int32_t *r_arr, int32_t count, int32_t samples,
                           void *stream) {
     if (!h || !m_arr || !r_arr || count < 1 || samples < 32 || samples > (1 << 20)) {

@@ -78,6 +78,9 @@ cudaError_t launch_dtw_at_f64(const QueryBufs &b, const QueryArgs &a, const int6
 cudaError_t launch_lbs_at(const QueryBufs &b, const QueryArgs &a, const int64_t *offsets,
                           int64_t count, float *kim, float *kq, float *ks, cudaStream_t s);
 
+// one bounded wait on an mbarrier nothing arrives on (records kStTimeout)
+cudaError_t launch_wait_selftest(int *status, long long wait_ns, cudaStream_t s);
+
 // ---- learned proposal encoder (encoder.cu)
 // params -> packed blob; with `adam`, one Adam step first (c1, c2: bias corrections)
 cudaError_t launch_enc_pack(float *params, const float *grad, float *m1, float *v1, uint8_t *blob, bool adam,

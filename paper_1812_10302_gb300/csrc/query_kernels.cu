@@ -286,14 +286,23 @@ __device__ void tile_pipeline(unsigned char *sm, const QueryBufs &b, int m, int6
                 *t.tile = tile;
                 issue_tile<LY>(t, b, tile * LY::W, m);
             }
-            // On the normal path every issued copy is observed landing by the
-            // consumers before they reach the end marker.  After a timeout,
-            // let the copies that may still be in flight (uses u-S+1 .. u-1;
-            // use u-S was confirmed released) land before the CTA leaves.
-            if (!ok)
-                for (int64_t v = u - kS + 1 > 0 ? u - kS + 1 : 0; v < u; ++v)
+            // Before the producer leaves, every copy it issued has landed, so
+            // that no CTA ever leaves with a copy still writing its shared
+            // memory -- even when the consumers gave up on a wait: the last
+            // use of each other stage, u-S+1 .. u-1 (u: the end marker), and
+            // after a timeout also use u-S (the wait that ran out was for its
+            // release).  Each of these is its stage's last copy, so its
+            // barrier has completed at most that one phase.  On the normal
+            // path they have landed already (the consumers wait for them).
+            // The drain has its own bound (at least 0.2 s) so that a short
+            // wait limit cannot cut it short.
+            {
+                const long long drain_ns = b.wait_ns > 200000000LL ? b.wait_ns : 200000000LL;
+                const int64_t first = ok ? u - kS + 1 : u - kS;
+                for (int64_t v = first > 0 ? first : 0; v < u; ++v)
                     mbar_wait_bounded(carve_stage<LY>(sm, m, (int)(v % kS)).full,
-                                      (unsigned)((v / kS) & 1), b.wait_ns);
+                                      (unsigned)((v / kS) & 1), drain_ns);
+            }
         }
     } else {
         for (int64_t j = 0;; ++j) {
@@ -596,6 +605,24 @@ __device__ __forceinline__ float bin_floor(int k, float thr) {
     return __uint_as_float((unsigned)k << 21);
 }
 
+// ------------------------------------------------------------------ wait self-test
+// One thread waits, bounded, on a fresh mbarrier that nothing arrives on:
+// the wait runs out after wait_ns and records the timeout status the same way
+// the scans do -- the failure path of the bounded waits, exercised without a
+// fault or a hang.
+__global__ void k_wait_selftest(int *status, long long wait_ns) {
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x != 0) return;
+    mbar_init(&bar, 1);
+    mbar_fence_init();
+    if (!mbar_wait_bounded(&bar, 0u, wait_ns)) atomicOr(status, kStTimeout);
+}
+
+cudaError_t launch_wait_selftest(int *status, long long wait_ns, cudaStream_t s) {
+    k_wait_selftest<<<1, 32, 0, s>>>(status, wait_ns);
+    return cudaGetLastError();
+}
+
 // ------------------------------------------------------------------ DTW kernels
 enum DtwMode { kModeSeed = 0, kModeSurv = 1, kModeOut = 2 };
 
@@ -692,16 +719,129 @@ __global__ void __launch_bounds__(256) k_dtw(QueryBufs b, QueryArgs a, const int
                         : MODE == kModeSurv ? (int64_t)st->n_cand : count_host;
     long long cells_acc = 0;
     int started = 0, abandoned = 0, passed_s = 0;
+    // survivor pass, two schedules chosen per launch (the same for every
+    // group): with many survivors (more than 64 per group) a group takes L
+    // candidates per cursor step and each lane runs the pre-check (bin floor,
+    // seeds, Eq. 10 and Eq. 8 with early abandon) for its own candidate, the
+    // ones that pass then being scored one at a time by the whole group;
+    // with few survivors a group takes one candidate at a time and pre-checks
+    // it cooperatively, L terms per step (shorter critical path when most of
+    // them sit near the best match).
+    unsigned pend = 0, my_idx = 0;
+    float my_mh = 0.0f, my_is = 0.0f, my_ls = 0.0f;
+    bool stop = false;
+    const unsigned lmask = L == 32 ? 0xffffffffu : ((1u << L) - 1u);
+    const bool lanewise = MODE == kModeSurv && count > (int64_t)gridDim.x * (blockDim.x / L) * 64;
     while (true) {
-        int c = 0;
-        if (lane == 0) c = atomicAdd(cursor, 1);
-        c = __shfl_sync(gmask, c, 0, L);
-        if (c >= count) break;
+        int c = 0, psrc = 0;
         unsigned idx;
         float lb = 0.0f;
-        if (MODE == kModeSeed) idx = st->seed_off[c];
-        else if (MODE == kModeSurv) { idx = b.sort_idx[c]; lb = b.sort_lb[c]; }
-        else {
+        bool coop = false;  // the one-candidate schedule's cooperative pre-check is still due
+        if (MODE == kModeSurv && lanewise) {
+            if (!pend) {
+                if (stop) break;
+                int c0 = 0;
+                if (lane == 0) c0 = atomicAdd(cursor, L);
+                c0 = __shfl_sync(gmask, c0, 0, L);
+                if (c0 >= count) break;
+                const int cc = c0 + lane;
+                const bool valid = cc < count;
+                const unsigned id = valid ? b.sort_idx[cc] : 0u;
+                const float lbv = valid ? b.sort_lb[cc] : DINF;
+                float th = 0.0f;
+                if (lane == 0) th = current_thr(st, a);
+                th = __shfl_sync(gmask, th, 0, L);
+                bool pass = valid && !(lbv > th);
+                // survivors are in ascending bins and thr only shrinks: once a
+                // candidate's bin floor is above thr, so is every later one's
+                const bool done = valid && lbv > th && bin_floor(bin_of(lbv, thr_scan), thr_scan) > th;
+                if (pass) {  // scored already: by the seed pass or on the side stream
+                    bool seen = id == pre;
+                    for (int t = 0; t < n_seeds_s; ++t) seen |= seeds_s[t] == id;
+                    pass = !seen;
+                }
+                float pmh = 0.0f, pis = 0.0f, pls = 0.0f;
+                if (pass) {
+                    pmh = b.mu_hi[id];
+                    pis = b.inv_sigma[id];
+                    pls = b.mu_lo[id] * pis;
+                }
+                if (pass && has_env) {
+                    // Eq. 10 (q_hat against the window's envelope) and Eq. 8
+                    // (the window against the query's envelope; the scan took
+                    // only its first terms) with early abandon, terms in
+                    // |q_hat| descending order until either partial sum passes
+                    // thr -- each is a lower bound on its own (rows and
+                    // columns of the same warping path).  Past 128 terms the
+                    // full Eq. 10 below (row order, with the suffix sums the
+                    // DTW needs) takes over.
+                    TailCtx pc;
+                    pc.Uw = b.U ? b.U + id : nullptr;
+                    pc.Lw = b.L ? b.L + id : nullptr;
+                    pc.stmax = b.stmax;
+                    pc.stmin = b.stmin;
+                    pc.nblk = b.nblk;
+                    pc.n = b.n;
+                    pc.t0 = id;
+                    pc.r = r;
+                    const float *xp = b.x + id;
+                    const int budget = m < 128 ? m : 128;
+                    float acc = 0.0f, acc8 = 0.0f;
+                    // 8 terms per step: their loads are issued together, the
+                    // abandon test runs once per step
+                    constexpr int kB = 8;
+                    for (int j0 = 0; j0 < budget; j0 += kB) {
+                        float xv[kB], uv[kB], lv[kB];
+#pragma unroll
+                        for (int t = 0; t < kB; ++t) {
+                            const int j = j0 + t < budget ? j0 + t : budget - 1;
+                            const int pos = ord_s[j];
+                            xv[t] = xp[pos];
+                            env_at(pc, pos, uv[t], lv[t]);
+                        }
+#pragma unroll
+                        for (int t = 0; t < kB; ++t) {
+                            if (j0 + t >= budget) break;
+                            const int j = j0 + t;
+                            const float u = fmaf(uv[t] - pmh, pis, -pls), l = fmaf(lv[t] - pmh, pis, -pls);
+                            const float q = sq_s[j];
+                            const float dq = fmaxf(q - u, 0.0f) + fmaxf(l - q, 0.0f);
+                            const float cv = fmaf(xv[t] - pmh, pis, -pls);
+                            const float e = fmaxf(cv - su_s[j], 0.0f) + fmaxf(sl_s[j] - cv, 0.0f);
+                            acc = fmaf(dq, dq, acc);
+                            acc8 = fmaf(e, e, acc8);
+                        }
+                        if (acc > th || acc8 > th) {
+                            pass = false;
+                            break;
+                        }
+                    }
+                }
+                my_idx = id;
+                my_mh = pmh;
+                my_is = pis;
+                my_ls = pls;
+                const int gshift = (ln / L) * L;
+                pend = (__ballot_sync(gmask, pass) >> gshift) & lmask;
+                stop = ((__ballot_sync(gmask, done) >> gshift) & lmask) != 0u;
+                continue;
+            }
+            psrc = __ffs(pend) - 1;
+            pend &= pend - 1;
+            idx = __shfl_sync(gmask, my_idx, psrc, L);
+        } else {
+            if (lane == 0) c = atomicAdd(cursor, 1);
+            c = __shfl_sync(gmask, c, 0, L);
+            if (c >= count) break;
+            if (MODE == kModeSurv) {
+                idx = b.sort_idx[c];
+                lb = b.sort_lb[c];
+                coop = true;
+            }
+        }
+        if (MODE == kModeSeed) {
+            idx = st->seed_off[c];
+        } else if (MODE == kModeOut) {
             const int64_t o = offsets[c];
             if (o < 0 || o >= a.N) {  // caller's device offsets are checked here
                 if (lane == 0) out[c] = __int_as_float(0x7fc00000);
@@ -719,20 +859,26 @@ __global__ void __launch_bounds__(256) k_dtw(QueryBufs b, QueryArgs a, const int
             thr = current_thr(st, a);
         }
         thr = __shfl_sync(gmask, thr, 0, L);
-        if (MODE == kModeSurv && lb > thr) {
-            // survivors are in ascending bins and thr only shrinks: once the
-            // floor of this candidate's bin is above thr, so is every later
-            // candidate's bound, and this group is done
-            if (bin_floor(bin_of(lb, thr_scan), thr_scan) > thr) break;
-            continue;
-        }
-        if (MODE == kModeSurv) {
-            // scored already: by the seed pass or on the side stream
-            bool seen = idx == pre;
+        if (coop) {
+            if (lb > thr) {
+                // see the batch schedule: past this bin floor nothing is left
+                if (bin_floor(bin_of(lb, thr_scan), thr_scan) > thr) break;
+                continue;
+            }
+            bool seen = idx == pre;  // scored already: by the seed pass or on the side stream
             for (int t = lane; t < n_seeds_s; t += L) seen |= seeds_s[t] == idx;
             if (__any_sync(gmask, seen)) continue;
         }
-        const float mh = b.mu_hi[idx], is = b.inv_sigma[idx], ls = b.mu_lo[idx] * is;
+        float mh, is, ls;
+        if (MODE == kModeSurv && !coop) {  // pre-checked by its lane: take its statistics
+            mh = __shfl_sync(gmask, my_mh, psrc, L);
+            is = __shfl_sync(gmask, my_is, psrc, L);
+            ls = __shfl_sync(gmask, my_ls, psrc, L);
+        } else {
+            mh = b.mu_hi[idx];
+            is = b.inv_sigma[idx];
+            ls = b.mu_lo[idx] * is;
+        }
         const float *xw = b.x + idx;
         TailCtx tc;
         tc.Uw = b.U ? b.U + idx : nullptr;
@@ -747,32 +893,26 @@ __global__ void __launch_bounds__(256) k_dtw(QueryBufs b, QueryArgs a, const int
         tc.mh = mh;
         tc.is = is;
         tc.ls = ls;
-        if (MODE == kModeSurv && has_env) {
-            // Eq. 10 (q_hat against the window's envelope) and Eq. 8 (the
-            // window against the query's envelope; the scan took only its
-            // first terms) with early abandon: the terms in |q_hat|
-            // descending order, L at a time, until either partial sum passes
-            // thr -- each is a lower bound on its own (rows and columns of
-            // the same warping path).  The sums are reduced over the group,
-            // so every lane takes the same exit.  Past 128 terms the full
-            // Eq. 10 below (row order, with the suffix sums the DTW needs)
-            // takes over.
+        if (coop && has_env) {
+            // the same pre-check as the batch schedule's, L terms per step
+            // over the group (the sums are reduced, so every lane takes the
+            // same exit)
             float acc = 0.0f, acc8 = 0.0f;
             bool pruned = false;
             const int budget = m < 128 ? m : 128;
             for (int c0 = 0; c0 < budget; c0 += L) {
                 const int j = c0 + lane;
                 float v = 0.0f, v8 = 0.0f;
-                if (j < m) {
+                if (j < budget) {
                     const int pos = ord_s[j];
                     const float x = xw[pos];
                     float U, Lo;
                     env_at(tc, pos, U, Lo);
                     const float u = fmaf(U - mh, is, -ls), l = fmaf(Lo - mh, is, -ls), q = sq_s[j];
-                    const float d = fmaxf(q - u, 0.0f) + fmaxf(l - q, 0.0f);
-                    v = d * d;
-                    const float c = fmaf(x - mh, is, -ls);
-                    const float e = fmaxf(c - su_s[j], 0.0f) + fmaxf(sl_s[j] - c, 0.0f);
+                    const float dq = fmaxf(q - u, 0.0f) + fmaxf(l - q, 0.0f);
+                    v = dq * dq;
+                    const float cv = fmaf(x - mh, is, -ls);
+                    const float e = fmaxf(cv - su_s[j], 0.0f) + fmaxf(sl_s[j] - cv, 0.0f);
                     v8 = e * e;
                 }
 #pragma unroll
@@ -1117,9 +1257,12 @@ cudaError_t launch_dtw_at_f64(const QueryBufs &b, const QueryArgs &a, const int6
 // envelope, still admissible), is evaluated for each survivor by the DTW
 // kernel, whose tail bound consists of exactly its per-row terms.
 // LB_Keogh (Eq. 8) chunks of 32 terms the scan takes at most per window; the
-// first kEqSmem of them come from shared memory, the rest through L1 (the
-// same few values for every window)
-constexpr int kEqChunks = 8, kEqSmem = 2;
+// first kEqSmem of them come from shared memory, any further ones through L1
+// (the same few values for every window).  Measured: 8 chunks moved work
+// from the survivor stage into the scan (whose warp holds all 32 lanes per
+// passing window) and slowed the m = 512 workload by 7 %, so the scan stops
+// after 2 and the survivor stage's pre-check takes over.
+constexpr int kEqChunks = 2, kEqSmem = 2;
 
 __device__ __forceinline__ float keogh_term(float v, float u, float l) {
     const float d = fmaxf(v - u, 0.0f) + fmaxf(l - v, 0.0f);

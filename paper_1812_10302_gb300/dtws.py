@@ -108,6 +108,7 @@ _SIGS = {
     "dtws_dtw_at_f64": (_S, [_P, _P, _I32, _I32, _P, _I64, _P, _P]),
     "dtws_lower_bounds_at": (_S, [_P, _P, _I32, _I32, _P, _I64, _P, _P, _P, _P]),
     "dtws_dtw_at_noalloc": (_S, [_P, _I64, _P, _I32, _I32, _P, _I64, _P, _P]),
+    "dtws_debug_wait_selftest": (_S, [_P, _I64, _P]),
     "dtws_autotune": (_S, [_P, _P, _P, _I32, _I32, _P]),
     "dtws_tune_entry": (_S, [_P, _I32, _I32, _P, _P]),
     "dtws_set_encoder": (_S, [_P, _P, _I32, _P]),
@@ -373,6 +374,9 @@ class Index:
         _check(self._lib.dtws_dtw_at_f64(self.h, q.ptr, q.size, r, o.ptr, o.size, out.ctypes.data,
                                          _stream_ptr(stream)), "dtws_dtw_at_f64")
         return out
+
+    def debug_wait_selftest(self, wait_ns: int, stream=None):
+        _check(self._lib.dtws_debug_wait_selftest(self.h, wait_ns, _stream_ptr(stream)), "dtws_debug_wait_selftest")
 
     def autotune(self, ms, rs, samples: int = 4096, stream=None):
         """Tune the survivor-DTW kernel shape for each (m, r) pair."""

@@ -220,3 +220,22 @@ def test_seeding_keeps_the_scan_tight(seed):
         s = ix.last_stats()
     assert s["pass_kim"] < 0.05 * s["windows"], s
     assert idx[0] == o or dist[0] <= oracle.dtw_at(x, q, 51, [o])[0]
+
+
+def test_bounded_wait_reports_timeout_and_the_handle_recovers(walk, index):
+    """Failure detection without a GPU fault: a bounded device wait on a
+    barrier that nothing completes runs out after 2 ms, the kernel records
+    DTWS_ETIMEOUT, the host reads it (and it is cleared), and the same handle
+    then answers correctly."""
+    import time
+    t0 = time.perf_counter()
+    index.debug_wait_selftest(2_000_000)
+    assert index.sync_status() == dtws.DTWS_ETIMEOUT
+    assert time.perf_counter() - t0 < 5.0
+    assert index.sync_status() == dtws.DTWS_OK  # read once, then cleared
+    q, _ = synth.noisy_copy(walk, 256, 81, 82, noise=0.2)
+    idx, dist = index.query(q, 25, 1)
+    assert index.sync_status() == dtws.DTWS_OK
+    oi, od = fragments.search_fragments(walk, q, 25, 1)
+    np.testing.assert_array_equal(idx, oi)
+    _close(dist, od, 256)

@@ -437,17 +437,50 @@ def learned_leg(dev):
              "random_seeds": dict(ordering=dtws.DTWS_ORDER_PLAIN, seed_proposals=0)}
     answers = {}
     n_random = 4
+    out["phase_ms"] = {}
     for name, opts in modes.items():
         ix.set_options(**opts)
         sub = qds if name != "random_seeds" else qds[:n_random]
         out["ms_per_query"][name] = _mean_query_ms(ix, sub, r, 1, dev)
         answers[name] = [tuple(np.concatenate([a.astype(np.float64) for a in ix.query(q, r, 1)])) for q in sub]
+        # per-phase device times (events between the phases) over a few queries
+        ix.set_options(timing=1)
+        ph = np.zeros(len(dtws.PHASES))
+        for q in sub[:4]:
+            ix.query(q, r, 1)
+            ph += np.array(ix.last_stats()["phase_ms"])
+        ix.set_options(timing=0)
+        out["phase_ms"][name] = dict(zip(dtws.PHASES[:6], [round(float(v) / min(4, len(sub)), 4) for v in ph[:6]]))
     out["random_seeds_queries"] = n_random
     t = out["ms_per_query"]
     out["speedup_vs_random_seeds"] = t["random_seeds"] / t["learned"]
     out["speedup_vs_proxy"] = t["proxy"] / t["learned"]
     out["identical_answers"] = (answers["learned"] == answers["proxy"] and
                                 answers["learned"][:n_random] == answers["random_seeds"])
+    # the same three orderings through one dtws_query_batch call (4 lanes)
+    # over the first 16 queries: host queries and outputs, host wall clock
+    # around the synchronising call, the best of the timed calls after one
+    # untimed call
+    nb = 16
+    qb, rb = [np.asarray(q) for q in qs[:nb]], [r] * nb
+    bt, bans = {}, {}
+    for name, opts in modes.items():
+        ix.set_options(batch_lanes=4, batch_graph=1, **opts)
+        bans[name] = ix.query_batch(qb, rb, k=1)
+        ts = []
+        for _ in range(3 if name != "random_seeds" else 1):
+            torch.cuda.synchronize(dev)
+            t0 = time.perf_counter()
+            ix.query_batch(qb, rb, k=1)
+            ts.append(time.perf_counter() - t0)
+        bt[name] = min(ts)
+    if ix.sync_status() != dtws.DTWS_OK:
+        raise RuntimeError("device-side error in a batched query")
+    out["batch"] = {"queries": nb, "lanes": 4, "seconds_per_batch": bt,
+                    "speedup_vs_random_seeds": bt["random_seeds"] / bt["learned"],
+                    "speedup_vs_proxy": bt["proxy"] / bt["learned"],
+                    "identical_answers": all(np.array_equal(bans["learned"][j], bans[o][j])
+                                             for o in ("proxy", "random_seeds") for j in (0, 1))}
     ix.close()
     return out
 

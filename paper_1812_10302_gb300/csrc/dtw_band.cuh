@@ -406,9 +406,11 @@ __device__ __forceinline__ dfloat df_shfl(unsigned mask, dfloat v, int src, int 
     return dfloat{__shfl_sync(mask, v.hi, src, width), __shfl_sync(mask, v.lo, src, width)};
 }
 
+// One anti-diagonal step of dtw_diag_df: as diag_step, in double-float
+// arithmetic, with the query / window values in the register windows qv, cv.
 template <int L, int K, int ODD>
-__device__ __forceinline__ void diag_step_df(const dfloat *qs, const dfloat *cs, dfloat (&p1)[K], dfloat (&p2)[K],
-                                             int bi, int bj, int lane, int r, unsigned gmask) {
+__device__ __forceinline__ void diag_step_df(const dfloat (&qv)[K], const dfloat (&cv)[K], dfloat (&p1)[K],
+                                             dfloat (&p2)[K], int lane, int r, unsigned gmask) {
     // a large finite stand-in for +inf: sums of such values stay finite
     const dfloat INF = dfloat{1e30f, 0.0f};
     dfloat nb = df_shfl(gmask, ODD ? p1[0] : p1[K - 1], ODD ? ((lane + 1) & (L - 1)) : ((lane - 1) & (L - 1)), L);
@@ -419,11 +421,12 @@ __device__ __forceinline__ void diag_step_df(const dfloat *qs, const dfloat *cs,
         const int p = lane * K + t;
         const dfloat left = ODD ? p1[t] : (t == 0 ? nb : p1[t > 0 ? t - 1 : 0]);
         const dfloat up = ODD ? (t == K - 1 ? nb : p1[t < K - 1 ? t + 1 : 0]) : p1[t];
-        // qs / cs are padded with finite poison values (+/-1e15): a cell
-        // outside [0, m)^2 costs ~4e30, far above any DTW and far below
-        // FP32 overflow over 2m steps, and never turns TwoSum into NaN
+        // the query / window arrays are padded with finite poison values
+        // (+/-1e15): a cell outside [0, m)^2 costs ~4e30, far above any DTW
+        // and far below FP32 overflow over 2m steps, and never turns
+        // TwoSum into NaN
         const dfloat best = df_min(df_min(left, up), p2[t]);
-        dfloat v = df_add_pos(df_sqr(df_sub(qs[bi - p], cs[bj + p])), best);
+        dfloat v = df_add_pos(df_sqr(df_sub(qv[t], cv[t])), best);
         if (ODD ? (p >= r) : (p > r)) v = INF;  // past the band's cells
         cur[t] = v;
     }
@@ -434,15 +437,37 @@ __device__ __forceinline__ void diag_step_df(const dfloat *qs, const dfloat *cs,
     }
 }
 
-// Double-float counterpart of dtw_diag (no abandon).  qs, cs point at
-// element 0 of arrays padded by diag_pad(r, L, K) on both sides with
-// +1e15 (query) and -1e15 (window).
+// Register windows of the double-float walk (as shift_c / shift_q).
+template <int L, int K>
+__device__ __forceinline__ void shift_c_df(dfloat (&cv)[K], const dfloat *cp, int cbase_new, int lane,
+                                           unsigned gmask) {
+    const dfloat from_next =
+        dfloat{__shfl_down_sync(gmask, cv[0].hi, 1, L), __shfl_down_sync(gmask, cv[0].lo, 1, L)};
+    const dfloat fresh = cp[cbase_new + L * K - 1];
+#pragma unroll
+    for (int t = 0; t < K - 1; ++t) cv[t] = cv[t + 1];
+    cv[K - 1] = lane == L - 1 ? fresh : from_next;
+}
+template <int L, int K>
+__device__ __forceinline__ void shift_q_df(dfloat (&qv)[K], const dfloat *qp, int qbase_new, int lane,
+                                           unsigned gmask) {
+    const dfloat from_prev =
+        dfloat{__shfl_up_sync(gmask, qv[K - 1].hi, 1, L), __shfl_up_sync(gmask, qv[K - 1].lo, 1, L)};
+    const dfloat fresh = qp[qbase_new];
+#pragma unroll
+    for (int t = K - 1; t > 0; --t) qv[t] = qv[t - 1];
+    qv[0] = lane == 0 ? fresh : from_prev;
+}
+
+// Double-float counterpart of dtw_diag (no abandon), the same walk and the
+// same register windows.  qs, cs point at element 0 of arrays padded by
+// diag_pad(r, L, K) on both sides with +1e15 (query) and -1e15 (window).
 template <int L, int K>
 __device__ double dtw_diag_df(const dfloat *__restrict__ qs, const dfloat *__restrict__ cs, int m, int r,
                               unsigned gmask, int lane) {
     const dfloat INF = dfloat{1e30f, 0.0f};
     const int p0 = (r - (r & 1)) >> 1;
-    dfloat p1[K], p2[K];
+    dfloat p1[K], p2[K], qv[K], cv[K];
 #pragma unroll
     for (int t = 0; t < K; ++t) {
         p1[t] = INF;
@@ -451,22 +476,177 @@ __device__ double dtw_diag_df(const dfloat *__restrict__ qs, const dfloat *__res
     const int last = 2 * m - 2;
     int a = 0, bi, bj;
     if (r & 1) {
-        diag_step_df<L, K, 1>(qs, cs, p1, p2, (r - 1) >> 1, (1 - r) >> 1, lane, r, gmask);
+        const int qb = (r - 1) >> 1, cb = (1 - r) >> 1;
+#pragma unroll
+        for (int t = 0; t < K; ++t) {
+            qv[t] = qs[qb - (lane * K + t)];
+            cv[t] = cs[cb + (lane * K + t)];
+        }
+        diag_step_df<L, K, 1>(qv, cv, p1, p2, lane, r, gmask);
         a = 1;
+        shift_q_df<L, K>(qv, qs, qb + 1, lane, gmask);
+    } else {
+        const int qb = r >> 1, cb = -(r >> 1);
+#pragma unroll
+        for (int t = 0; t < K; ++t) {
+            qv[t] = qs[qb - (lane * K + t)];
+            cv[t] = cs[cb + (lane * K + t)];
+        }
     }
     bi = (a + r) >> 1;
     bj = (a - r) >> 1;
     for (; a + 1 <= last; a += 2, ++bi, ++bj) {
-        diag_step_df<L, K, 0>(qs, cs, p1, p2, bi, bj, lane, r, gmask);
-        diag_step_df<L, K, 1>(qs, cs, p1, p2, bi, bj + 1, lane, r, gmask);
+        diag_step_df<L, K, 0>(qv, cv, p1, p2, lane, r, gmask);
+        shift_c_df<L, K>(cv, cs, bj + 1, lane, gmask);
+        diag_step_df<L, K, 1>(qv, cv, p1, p2, lane, r, gmask);
+        shift_q_df<L, K>(qv, qs, bi + 1, lane, gmask);
     }
-    if (a == last) diag_step_df<L, K, 0>(qs, cs, p1, p2, bi, bj, lane, r, gmask);
+    if (a == last) diag_step_df<L, K, 0>(qv, cv, p1, p2, lane, r, gmask);
     const int pe = (r - ((last + r) & 1)) >> 1;
     dfloat res = INF;
 #pragma unroll
     for (int t = 0; t < K; ++t)
         if (lane * K + t == pe) res = p1[t];
     res = df_shfl(gmask, res, pe / K, L);
+    return (double)res.hi + (double)res.lo;
+}
+
+// ------------------------------------------------------------------ multi-warp double-float walk
+// The same walk with the r+1 cells of an anti-diagonal spread over W warps
+// (32*W lanes, K cells each).  Inside a warp the neighbour arrives by
+// shuffle as in dtw_diag_df; across a warp boundary it goes through shared
+// memory: after each step every warp's first and last lane publish their
+// newest cell into the other half of a double buffer and the W warps meet at
+// one named barrier, so a step's reads (this half) never race the next
+// step's writes (the other half).  The register windows' boundary lanes load
+// their fresh value from the padded arrays instead of a neighbour warp.
+struct DfXchg {
+    dfloat first[2][4], last[2][4];  // [buffer][warp]: lane 0's p1[0], lane 31's p1[K-1]
+    dfloat res;
+};
+
+__device__ __forceinline__ void group_bar(int id, int nthreads) {
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
+}
+
+template <int W, int K, int ODD>
+__device__ __forceinline__ void diag_step_df_mw(const dfloat (&qv)[K], const dfloat (&cv)[K], dfloat (&p1)[K],
+                                                dfloat (&p2)[K], int gl, int lane, int w, int r,
+                                                const DfXchg &x, int buf) {
+    const dfloat INF = dfloat{1e30f, 0.0f};
+    dfloat nb = df_shfl(0xffffffffu, ODD ? p1[0] : p1[K - 1], ODD ? ((lane + 1) & 31) : ((lane - 1) & 31), 32);
+    if (ODD) {
+        if (lane == 31) nb = (w == W - 1) ? INF : x.first[buf][w + 1];
+    } else {
+        if (lane == 0) nb = (w == 0) ? INF : x.last[buf][w - 1];
+    }
+    dfloat cur[K];
+#pragma unroll
+    for (int t = 0; t < K; ++t) {
+        const int p = gl * K + t;
+        const dfloat left = ODD ? p1[t] : (t == 0 ? nb : p1[t > 0 ? t - 1 : 0]);
+        const dfloat up = ODD ? (t == K - 1 ? nb : p1[t < K - 1 ? t + 1 : 0]) : p1[t];
+        const dfloat best = df_min(df_min(left, up), p2[t]);
+        dfloat v = df_add_pos(df_sqr(df_sub(qv[t], cv[t])), best);
+        if (ODD ? (p >= r) : (p > r)) v = INF;
+        cur[t] = v;
+    }
+#pragma unroll
+    for (int t = 0; t < K; ++t) {
+        p2[t] = p1[t];
+        p1[t] = cur[t];
+    }
+}
+
+template <int W, int K>
+__device__ __forceinline__ void df_mw_publish(const dfloat (&p1)[K], int lane, int w, DfXchg &x, int &buf,
+                                              int bar_id) {
+    const int nbuf = buf ^ 1;
+    if (lane == 0) x.first[nbuf][w] = p1[0];
+    if (lane == 31) x.last[nbuf][w] = p1[K - 1];
+    group_bar(bar_id, 32 * W);
+    buf = nbuf;
+}
+
+// Register windows of the multi-warp walk (as shift_c_df / shift_q_df);
+// each warp's boundary lane loads its fresh value from the padded array.
+template <int K>
+__device__ __forceinline__ void shift_c_df_mw(dfloat (&cv)[K], const dfloat *cs, int cbase_new, int gl, int lane) {
+    const dfloat from_next =
+        dfloat{__shfl_down_sync(0xffffffffu, cv[0].hi, 1), __shfl_down_sync(0xffffffffu, cv[0].lo, 1)};
+    const dfloat fresh = cs[cbase_new + (gl + 1) * K - 1];
+#pragma unroll
+    for (int t = 0; t < K - 1; ++t) cv[t] = cv[t + 1];
+    cv[K - 1] = lane == 31 ? fresh : from_next;
+}
+template <int K>
+__device__ __forceinline__ void shift_q_df_mw(dfloat (&qv)[K], const dfloat *qs, int qbase_new, int gl, int lane) {
+    const dfloat from_prev =
+        dfloat{__shfl_up_sync(0xffffffffu, qv[K - 1].hi, 1), __shfl_up_sync(0xffffffffu, qv[K - 1].lo, 1)};
+    const dfloat fresh = qs[qbase_new - gl * K];
+#pragma unroll
+    for (int t = K - 1; t > 0; --t) qv[t] = qv[t - 1];
+    qv[0] = lane == 0 ? fresh : from_prev;
+}
+
+// qs, cs: element 0 of arrays padded by diag_pad(r, 32*W, K) on both sides
+// with +1e15 / -1e15.  Called by all 32*W threads of warps w = 0..W-1 of the
+// group (w: the warp's index in the group); bar_id: a named barrier the group
+// owns.  Every lane returns the distance.
+template <int W, int K>
+__device__ double dtw_diag_df_mw(const dfloat *__restrict__ qs, const dfloat *__restrict__ cs, int m, int r, int w,
+                                 int lane, DfXchg &x, int bar_id) {
+    static_assert(W >= 1 && W <= 4, "at most four warps");
+    const dfloat INF = dfloat{1e30f, 0.0f};
+    const int gl = w * 32 + lane;
+    const int p0 = (r - (r & 1)) >> 1;
+    dfloat p1[K], p2[K], qv[K], cv[K];
+#pragma unroll
+    for (int t = 0; t < K; ++t) {
+        p1[t] = INF;
+        p2[t] = (gl * K + t == p0) ? dfloat{0.0f, 0.0f} : INF;
+        qv[t] = cv[t] = INF;  // (loaded below)
+    }
+    int buf = 1;
+    df_mw_publish<W, K>(p1, lane, w, x, buf, bar_id);  // buffer 0 := the all-inf anti-diagonal -1
+    const int last = 2 * m - 2;
+    int a = 0, bi, bj;
+    if (r & 1) {
+        const int qb = (r - 1) >> 1, cb = (1 - r) >> 1;
+#pragma unroll
+        for (int t = 0; t < K; ++t) {
+            qv[t] = qs[qb - (gl * K + t)];
+            cv[t] = cs[cb + (gl * K + t)];
+        }
+        diag_step_df_mw<W, K, 1>(qv, cv, p1, p2, gl, lane, w, r, x, buf);
+        df_mw_publish<W, K>(p1, lane, w, x, buf, bar_id);
+        a = 1;
+        shift_q_df_mw<K>(qv, qs, qb + 1, gl, lane);
+    } else {
+        const int qb = r >> 1, cb = -(r >> 1);
+#pragma unroll
+        for (int t = 0; t < K; ++t) {
+            qv[t] = qs[qb - (gl * K + t)];
+            cv[t] = cs[cb + (gl * K + t)];
+        }
+    }
+    bi = (a + r) >> 1;
+    bj = (a - r) >> 1;
+    for (; a + 1 <= last; a += 2, ++bi, ++bj) {
+        diag_step_df_mw<W, K, 0>(qv, cv, p1, p2, gl, lane, w, r, x, buf);
+        df_mw_publish<W, K>(p1, lane, w, x, buf, bar_id);
+        shift_c_df_mw<K>(cv, cs, bj + 1, gl, lane);
+        diag_step_df_mw<W, K, 1>(qv, cv, p1, p2, gl, lane, w, r, x, buf);
+        df_mw_publish<W, K>(p1, lane, w, x, buf, bar_id);
+        shift_q_df_mw<K>(qv, qs, bi + 1, gl, lane);
+    }
+    if (a == last) diag_step_df_mw<W, K, 0>(qv, cv, p1, p2, gl, lane, w, r, x, buf);
+    const int pe = (r - ((last + r) & 1)) >> 1;
+#pragma unroll
+    for (int t = 0; t < K; ++t)
+        if (gl * K + t == pe) x.res = p1[t];
+    group_bar(bar_id, 32 * W);
+    const dfloat res = x.res;
     return (double)res.hi + (double)res.lo;
 }
 

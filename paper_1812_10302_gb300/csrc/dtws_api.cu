@@ -44,7 +44,7 @@ struct StatsEntry {
     int m = 0;
     int64_t used = 0;
     float *mu_hi = nullptr, *mu_lo = nullptr, *inv_sigma = nullptr;
-    float *smu_hi = nullptr, *smu_lo = nullptr, *sinv_sigma = nullptr;  // every kProxyStride-th window
+    float *smu_hi = nullptr, *sinv_sigma = nullptr;  // every kProxyStride-th window (proxy scan)
 };
 struct EnvEntry {
     int r = 0;
@@ -183,7 +183,6 @@ void free_stats(StatsEntry &e) {
     cudaFree(e.mu_lo);
     cudaFree(e.inv_sigma);
     cudaFree(e.smu_hi);
-    cudaFree(e.smu_lo);
     cudaFree(e.sinv_sigma);
     e = StatsEntry();
 }
@@ -215,9 +214,9 @@ dtws_status get_stats(dtws_t h, int m, cudaStream_t s, StatsEntry **out, bool *c
     const int64_t cap = round_up(N, kProxyTile) + kProxyTile;
     const int64_t scap = cap / kProxyStride;
     cudaError_t a1 = dalloc(&e.mu_hi, cap), a2 = dalloc(&e.mu_lo, cap), a3 = dalloc(&e.inv_sigma, cap);
-    cudaError_t a4 = dalloc(&e.smu_hi, scap), a5 = dalloc(&e.smu_lo, scap), a6 = dalloc(&e.sinv_sigma, scap);
+    cudaError_t a4 = dalloc(&e.smu_hi, scap), a6 = dalloc(&e.sinv_sigma, scap);
     if (a1 != cudaSuccess || a2 != cudaSuccess || a3 != cudaSuccess || a4 != cudaSuccess ||
-        a5 != cudaSuccess || a6 != cudaSuccess) {
+        a6 != cudaSuccess) {
         free_stats(e);
         cudaGetLastError();
         set_err("window statistics for m=%d: out of device memory", m);
@@ -227,10 +226,9 @@ dtws_status get_stats(dtws_t h, int m, cudaStream_t s, StatsEntry **out, bool *c
     CK(cudaMemsetAsync(e.mu_lo, 0, cap * 4, s));
     CK(cudaMemsetAsync(e.inv_sigma, 0, cap * 4, s));
     CK(cudaMemsetAsync(e.smu_hi, 0, scap * 4, s));
-    CK(cudaMemsetAsync(e.smu_lo, 0, scap * 4, s));
     CK(cudaMemsetAsync(e.sinv_sigma, 0, scap * 4, s));
     CK(launch_window_stats(h->x, h->n, m, h->pf, h->bf, h->pok, h->pscale, e.mu_hi, e.mu_lo, e.inv_sigma, e.smu_hi,
-                           e.smu_lo, e.sinv_sigma, h->num_sms, s));
+                           e.sinv_sigma, h->num_sms, s));
     e.used = ++h->clock;
     h->stats.push_back(e);
     *out = &h->stats.back();
@@ -385,7 +383,6 @@ QueryBufs make_bufs(dtws_t h, const StatsEntry *se, const EnvEntry *ee) {
     b.mu_lo = se ? se->mu_lo : nullptr;
     b.inv_sigma = se ? se->inv_sigma : nullptr;
     b.smu_hi = se ? se->smu_hi : nullptr;
-    b.smu_lo = se ? se->smu_lo : nullptr;
     b.sinv_sigma = se ? se->sinv_sigma : nullptr;
     b.U = ee ? ee->U : nullptr;
     b.L = ee ? ee->L : nullptr;
@@ -492,17 +489,21 @@ dtws_status enqueue_search(dtws_t h, const Exec &e, const QueryArgs &a, const fl
     rec(0);
     int half = kProxyStride / 2;
     if (P > 0 && e.le) {
+        int c0 = 0, c1 = 0;
         CK(launch_enc_query(h->enc_blob, b, a, s));
-        CK(launch_learn_scan(b, e.le->E, e.le->rows, enc_block(m), 0, P, s));
+        CK(launch_learn_scan(b, e.le->E, e.le->rows, enc_block(m), 0, 0, &c0, s));
         if (e.le->rows2 > 0) {
-            CK(launch_learn_scan(b, e.le->E2, e.le->rows2, enc_block(m), enc_phase(m), P, s));
+            CK(launch_learn_scan(b, e.le->E2, e.le->rows2, enc_block(m), enc_phase(m), 1, &c1, s));
             ++launches;
         }
+        CK(launch_prop_merge(b, c0, c1, P, s));
         half = learn_half(m);
-        launches += 2;
+        launches += 3;
     } else if (P > 0) {
-        CK(launch_seed_scan(b, a, P, h->opt.proxy_terms, s));
-        ++launches;
+        int c0 = 0;
+        CK(launch_seed_scan(b, a, P, h->opt.proxy_terms, &c0, s));
+        CK(launch_prop_merge(b, c0, 0, P, s));
+        launches += 2;
     }
     CK(launch_seed_gather(b, a, R, P, half, h->opt.rng_seed, s));
     CK(launch_seed_ed(b, a, s));
@@ -629,7 +630,6 @@ dtws_status ensure_lanes(dtws_t h, int count, int m_min) {
         al(dalloc(&l.stats.mu_lo, need_cap));
         al(dalloc(&l.stats.inv_sigma, need_cap));
         al(dalloc(&l.stats.smu_hi, scap));
-        al(dalloc(&l.stats.smu_lo, scap));
         al(dalloc(&l.stats.sinv_sigma, scap));
         al(cudaStreamCreateWithFlags(&l.stream, cudaStreamNonBlocking));
         al(cudaStreamCreateWithFlags(&l.side, cudaStreamNonBlocking));
@@ -652,7 +652,6 @@ dtws_status ensure_lanes(dtws_t h, int count, int m_min) {
         CK(cudaMemset(l.stats.mu_lo, 0, need_cap * 4));
         CK(cudaMemset(l.stats.inv_sigma, 0, need_cap * 4));
         CK(cudaMemset(l.stats.smu_hi, 0, scap * 4));
-        CK(cudaMemset(l.stats.smu_lo, 0, scap * 4));
         CK(cudaMemset(l.stats.sinv_sigma, 0, scap * 4));
     }
     return DTWS_OK;
@@ -744,7 +743,7 @@ dtws_status run_batch(dtws_t h, const float *Qd, const int64_t *q_off, const int
         const int m = m_arr[q], r = r_arr[q], rr = r > m - 1 ? m - 1 : r;
         if (lane_m[li] != m) {
             CKB(launch_window_stats(h->x, h->n, m, h->pf, h->bf, h->pok, h->pscale, l.stats.mu_hi, l.stats.mu_lo,
-                                    l.stats.inv_sigma, l.stats.smu_hi, l.stats.smu_lo, l.stats.sinv_sigma,
+                                    l.stats.inv_sigma, l.stats.smu_hi, l.stats.sinv_sigma,
                                     h->num_sms, l.stream));
             lane_m[li] = m;
             ++launches;

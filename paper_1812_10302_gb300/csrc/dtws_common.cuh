@@ -20,6 +20,7 @@ constexpr int kKMax = 64;
 constexpr int kListMax = 128;       // result list capacity (k + near-tie margin)
 constexpr int kSeedMax = 128;       // random seeds + proxy proposals
 constexpr int kPropMax = 64;
+constexpr int kCtaSlots = 1024;     // per-CTA best windows of one proposal scan (at most this many CTAs)
 constexpr int kProxyStride = 2;     // the proxy scan looks at every other window
 // Euclidean seeds: random windows + the neighbourhoods of the proposals
 // (+-1 window for the proxy scan; +-b/2, b <= 128, for the learned scan with
@@ -58,6 +59,7 @@ struct QueryState {
     unsigned long long seed_keys[kKMax];   // k smallest seed distances
     unsigned long long res_keys[kListMax]; // smallest survivor distances
     unsigned long long prop_keys[kPropMax];// proxy-scan proposals
+    unsigned long long cta_best[2 * kCtaSlots];  // each proposal-scan CTA's best window (two scans)
     unsigned long long ed_keys[kKMax];     // k smallest squared Euclidean distances
                                            // (upper bounds of DTW) of seed windows
     unsigned int ed_off[kEdMax];           // windows whose Euclidean distance is taken

@@ -21,8 +21,8 @@ cudaError_t launch_check_finite(const float *x, int64_t n, int *flag, cudaStream
 cudaError_t launch_prefix(const float *x, int64_t n, float *pf, float *bf, int *ok, unsigned *maxabs,
                           float *scale, cudaStream_t s);
 cudaError_t launch_window_stats(const float *x, int64_t n, int m, const float *pf, const float *bf,
-                                const int *ok, const float *scale, float *mu_hi, float *mu_lo, float *inv_sigma, float *smu_hi,
-                                float *smu_lo, float *sinv_sigma, int num_sms, cudaStream_t s);
+                                const int *ok, const float *scale, float *mu_hi, float *mu_lo, float *inv_sigma,
+                                float *smu_hi, float *sinv_sigma, int num_sms, cudaStream_t s);
 cudaError_t launch_envelope(const float *x, int64_t n, int r, float *U, float *L, cudaStream_t s);
 // block envelope: st = [max levels 0..kEnvLevels-1 | min levels], nblk floats each
 cudaError_t launch_block_envelope(const float *x, int64_t n, float *st, int64_t nblk, cudaStream_t s);
@@ -32,7 +32,7 @@ struct QueryBufs {
     QueryState *st;
     const float *x;              // padded series
     const float *mu_hi, *mu_lo, *inv_sigma;  // window stats for m
-    const float *smu_hi, *smu_lo, *sinv_sigma;  // the same for every kProxyStride-th window
+    const float *smu_hi, *sinv_sigma;  // mean (high part) and 1/sigma of every kProxyStride-th window
     const float *U, *L;          // exact series envelope for r, or null:
     const float *stmax, *stmin;  // per-series block envelope (sparse table), used when U is null
     int64_t nblk, n;             // its blocks; series length
@@ -50,7 +50,9 @@ struct QueryBufs {
 
 cudaError_t launch_query_reset(const QueryBufs &b, const QueryArgs &a, cudaStream_t s);
 cudaError_t launch_qprep(const float *Q, const QueryBufs &b, const QueryArgs &a, cudaStream_t s);
-cudaError_t launch_seed_scan(const QueryBufs &b, const QueryArgs &a, int proposals, int terms,
+// proposal scans: each CTA writes its best window to cta_best[slot * kCtaSlots + cta];
+// *ctas receives the grid size; launch_prop_merge then keeps the best `proposals`
+cudaError_t launch_seed_scan(const QueryBufs &b, const QueryArgs &a, int proposals, int terms, int *ctas,
                              cudaStream_t s);
 // half: Euclidean seeds cover the proposals' offsets +-half
 cudaError_t launch_seed_gather(const QueryBufs &b, const QueryArgs &a, int n_random,
@@ -97,8 +99,9 @@ cudaError_t launch_enc_series(const uint8_t *blob, const float *x, int64_t n, in
                               int64_t Nw, void *E, int num_sms, cudaStream_t s);
 cudaError_t launch_enc_query(const uint8_t *blob, const QueryBufs &b, const QueryArgs &a, cudaStream_t s);
 // windows at offsets j*stride + phase (j < Nw)
-cudaError_t launch_learn_scan(const QueryBufs &b, const void *E, int64_t Nw, int stride, int phase, int proposals,
-                              cudaStream_t s);
+cudaError_t launch_learn_scan(const QueryBufs &b, const void *E, int64_t Nw, int stride, int phase, int slot,
+                              int *ctas, cudaStream_t s);
+cudaError_t launch_prop_merge(const QueryBufs &b, int ctas0, int ctas1, int proposals, cudaStream_t s);
 cudaError_t launch_bf16_to_f32(const void *src, int64_t count, float *dst, cudaStream_t s);
 
 }  // namespace dtws

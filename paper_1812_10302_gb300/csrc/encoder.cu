@@ -674,11 +674,11 @@ __global__ void __launch_bounds__(kSeqThreads) k_query_embed(const uint8_t *blob
 
 // Score every window at stride b by |e_q - E[j]|^2 (8 lanes per window, 8
 // dimensions each).  Each warp scans one contiguous segment of the windows
-// with eight 16-byte loads in flight per lane; each CTA offers its best
-// window (one barrier, at the end) to the proposal list.
+// with eight 16-byte loads in flight per lane; each CTA writes its best
+// window (one barrier, at the end) to its slot for the proposal merge.
 constexpr int kLsThreads = 256, kLsU = 8;
 __global__ void __launch_bounds__(kLsThreads) k_learn_scan(QueryBufs bq, const bf16 *E, int64_t Nw, int b,
-                                                           int phase, int proposals, int64_t seg) {
+                                                           int phase, int slot, int64_t seg) {
     __shared__ unsigned long long wbest[kLsThreads / 32];
     QueryState *st = bq.st;
     if (!st->valid) return;
@@ -726,10 +726,7 @@ __global__ void __launch_bounds__(kLsThreads) k_learn_scan(QueryBufs bq, const b
     if (threadIdx.x == 0) {
         unsigned long long k = wbest[0];
         for (int w = 1; w < kLsThreads / 32; ++w) k = wbest[w] < k ? wbest[w] : k;
-        if (k != ~0ull) {
-            const unsigned long long last = *((volatile unsigned long long *)&st->prop_keys[proposals - 1]);
-            if (k < last) list_insert(st->prop_keys, proposals, k);
-        }
+        st->cta_best[slot * kCtaSlots + blockIdx.x] = k;
     }
 }
 
@@ -814,17 +811,27 @@ cudaError_t launch_bf16_to_f32(const void *src, int64_t count, float *dst, cudaS
     return cudaGetLastError();
 }
 
-cudaError_t launch_learn_scan(const QueryBufs &b, const void *E, int64_t Nw, int stride, int phase, int proposals,
-                              cudaStream_t s) {
-    // 8 CTAs of 8 warps per SM at most, each warp a segment of >= 256 windows
+cudaError_t launch_learn_scan(const QueryBufs &b, const void *E, int64_t Nw, int stride, int phase, int slot,
+                              int *ctas, cudaStream_t s) {
+    // one wave: as many CTAs as are resident at once, each warp a segment of
+    // >= 256 windows (a second wave would leave the first wave's SMs idle)
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, enc::k_learn_scan, enc::kLsThreads, 0) !=
+            cudaSuccess ||
+        per_sm < 1) {
+        cudaGetLastError();
+        per_sm = 1;
+    }
     const int64_t per_cta = (int64_t)(enc::kLsThreads / 32) * 256;
     int64_t grid = (Nw + per_cta - 1) / per_cta;
-    if (grid > 8 * (int64_t)b.num_sms) grid = 8 * (int64_t)b.num_sms;
+    if (grid > (int64_t)per_sm * b.num_sms) grid = (int64_t)per_sm * b.num_sms;
+    if (grid > kCtaSlots) grid = kCtaSlots;
     if (grid < 1) grid = 1;
     const int64_t warps = grid * (enc::kLsThreads / 32);
     const int64_t seg = ((Nw + warps - 1) / warps + 31) / 32 * 32;
     enc::k_learn_scan<<<(unsigned)grid, enc::kLsThreads, 0, s>>>(b, reinterpret_cast<const enc::bf16 *>(E), Nw,
-                                                                 stride, phase, proposals, seg);
+                                                                 stride, phase, slot, seg);
+    *ctas = (int)grid;
     return cudaGetLastError();
 }
 

@@ -20,6 +20,8 @@
 // thr = bsf*(1+delta) + alpha, bsf being the k-th best distance found so far.
 // delta and alpha absorb FP32 rounding so no true top-k window is dropped.
 #include <cmath>
+#include <utility>
+#include <type_traits>
 
 #include "dtw_band.cuh"
 #include "dtws_internal.h"
@@ -189,19 +191,20 @@ cudaError_t launch_qprep(const float *Q, const QueryBufs &b, const QueryArgs &a,
 // Use u of a stage waits for phase u & 1 of its barriers.  The end is a stage
 // whose tile index is -1, completed without copies.
 //
-// Two stage layouts.  LbLayout: kTile windows with the statistics of every
-// window (the lower-bound scan).  ProxyLayout: kProxyTile windows with the
-// statistics of every kProxyStride-th window (the proxy scan).
+// Two stage layouts.  LbLayout: kTile windows with the statistics (mean as
+// a hi + lo pair, 1/sigma) of every window (the lower-bound scan).
+// ProxyLayout: kProxyTile windows with the mean's high part and 1/sigma of
+// every kProxyStride-th window (the proxy scan; no ml array).
 struct LbLayout {
-    static constexpr int W = kTile, S = kTile, kStride = 1;
+    static constexpr int W = kTile, S = kTile, kStride = 1, NS = 3;
     __device__ static const float *mh(const QueryBufs &b) { return b.mu_hi; }
     __device__ static const float *ml(const QueryBufs &b) { return b.mu_lo; }
     __device__ static const float *is(const QueryBufs &b) { return b.inv_sigma; }
 };
 struct ProxyLayout {
-    static constexpr int W = kProxyTile, S = kProxyTile / kProxyStride, kStride = kProxyStride;
+    static constexpr int W = kProxyTile, S = kProxyTile / kProxyStride, kStride = kProxyStride, NS = 2;
     __device__ static const float *mh(const QueryBufs &b) { return b.smu_hi; }
-    __device__ static const float *ml(const QueryBufs &b) { return b.smu_lo; }
+    __device__ static const float *ml(const QueryBufs &) { return nullptr; }
     __device__ static const float *is(const QueryBufs &b) { return b.sinv_sigma; }
 };
 
@@ -219,7 +222,7 @@ __host__ __device__ __forceinline__ unsigned tile_x_floats(int m) {
 }
 template <class LY>
 __host__ __device__ __forceinline__ size_t stage_bytes(int m) {
-    return kStageHeader + (size_t)3 * LY::S * 4 + (size_t)tile_x_floats<LY>(m) * 4;
+    return kStageHeader + (size_t)LY::NS * LY::S * 4 + (size_t)tile_x_floats<LY>(m) * 4;
 }
 
 template <class LY>
@@ -230,8 +233,8 @@ __device__ __forceinline__ Tile carve_stage(unsigned char *sm, int m, int stage)
     t.empty = (uint64_t *)(base + 8);
     t.tile = (long long *)(base + 16);
     t.mh = (float *)(base + kStageHeader);
-    t.ml = t.mh + LY::S;
-    t.is = t.ml + LY::S;
+    t.ml = LY::NS == 3 ? t.mh + LY::S : nullptr;
+    t.is = t.mh + (LY::NS - 1) * LY::S;
     t.xs = t.is + LY::S;
     return t;
 }
@@ -240,10 +243,11 @@ template <class LY>
 __device__ __forceinline__ void issue_tile(const Tile &t, const QueryBufs &b, int64_t i0, int m) {
     const unsigned xb = tile_x_floats<LY>(m) * 4u, sb = LY::S * 4u;
     const int64_t s0 = i0 / LY::kStride;
-    mbar_arrive_expect_tx(t.full, xb + 3u * sb);
+    // the transaction count covers exactly the copies issued below
+    mbar_arrive_expect_tx(t.full, xb + (unsigned)LY::NS * sb);
     bulk_g2s(t.xs, b.x + i0, xb, t.full);
     bulk_g2s(t.mh, LY::mh(b) + s0, sb, t.full);
-    bulk_g2s(t.ml, LY::ml(b) + s0, sb, t.full);
+    if constexpr (LY::NS == 3) bulk_g2s(t.ml, LY::ml(b) + s0, sb, t.full);
     bulk_g2s(t.is, LY::is(b) + s0, sb, t.full);
 }
 
@@ -363,47 +367,153 @@ static int scan_stages(const void *kernel, size_t stage_bytes, int min_stages, s
 // bytes per window; the seed step then covers the neighbours of each
 // proposal.  (With one window in eight, a window four samples off a match
 // scored no better than lucky random windows and matches were lost.)
+// Packed FP32 pairs (sm_100 family): one instruction does the operation on
+// both halves, each half rounded exactly as the scalar operation would be.
+__device__ __forceinline__ unsigned long long x2_pack(float lo, float hi) {
+    unsigned long long r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+__device__ __forceinline__ float x2_sum(unsigned long long v) {
+    float lo, hi;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+    return lo + hi;
+}
+__device__ __forceinline__ unsigned long long x2_fma(unsigned long long a, unsigned long long b,
+                                                     unsigned long long c) {
+    unsigned long long d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+__device__ __forceinline__ unsigned long long x2_add(unsigned long long a, unsigned long long b) {
+    unsigned long long d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+// Shared-memory load at a 32-bit shared address plus a constant byte offset
+// (volatile: it stays after the barrier wait that made the data visible).
+template <int OFF>
+__device__ __forceinline__ float lds_at(unsigned addr) {
+    float v;
+    asm volatile("ld.shared.f32 %0, [%1+%2];" : "=f"(v) : "r"(addr), "n"(OFF));
+    return v;
+}
+template <typename F, int... I>
+__device__ __forceinline__ void static_for_impl(F &&f, std::integer_sequence<int, I...>) {
+    (f(std::integral_constant<int, I>{}), ...);
+}
+template <int N, typename F>
+__device__ __forceinline__ void static_for(F &&f) {
+    static_for_impl(f, std::make_integer_sequence<int, N>{});
+}
+
 template <int TERMS>
 __global__ void __launch_bounds__(kScanThreads) k_seed_scan(QueryBufs b, QueryArgs a, int proposals, int stages) {
+    static_assert(TERMS % 2 == 0, "terms are taken in pairs");
+    constexpr int kPer = kScanConsumers * 32;           // scored windows per pass of the CTA
+    constexpr int kIt = ProxyLayout::S / kPer;          // passes per tile
+    static_assert(ProxyLayout::S % kPer == 0, "whole passes per tile");
     extern __shared__ __align__(16) unsigned char smraw[];
     __shared__ unsigned long long wbest[kScanConsumers + 1];
     if (!b.st->valid) return;
     const int m = a.m;
-    int pos[TERMS];
-    float qv[TERMS];
+    // Term positions, evenly spread; for m >= 4*TERMS each is moved by at
+    // most one sample so that even terms sit at even and odd terms at odd
+    // positions.  Lane l scores window 2l (+ const), so a load of one term
+    // would touch 16 banks twice; the upper half-warp takes the terms of
+    // each pair in the other order, so the two halves read opposite bank
+    // parities and every load is conflict-free.  Scores are identical in
+    // both halves: the pair sums are added in either order.
+    const int hsel = lane_id() >= 16 ? 1 : 0;
+    unsigned poff[TERMS];
+    unsigned long long qv2[TERMS / 2];
 #pragma unroll
-    for (int u = 0; u < TERMS; ++u) {
-        pos[u] = (int)(((2 * u + 1) * (long long)m) / (2 * TERMS));
-        qv[u] = b.qh32[pos[u]];
+    for (int j = 0; j < TERMS / 2; ++j) {
+        int p[2];
+        float q[2];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int u = 2 * j + h;
+            int pu = (int)(((2 * u + 1) * (long long)m) / (2 * TERMS));
+            if (m >= 4 * TERMS) pu ^= (pu ^ u) & 1;
+            p[h] = pu;
+            q[h] = b.qh32[pu];
+        }
+        poff[2 * j] = 4u * (unsigned)(hsel ? p[1] : p[0]);
+        poff[2 * j + 1] = 4u * (unsigned)(hsel ? p[0] : p[1]);
+        qv2[j] = hsel ? x2_pack(q[1], q[0]) : x2_pack(q[0], q[1]);
     }
     unsigned long long best = kEmptyKey;
     const int64_t ntiles = (a.N + ProxyLayout::W - 1) / ProxyLayout::W;
     tile_pipeline<ProxyLayout>(smraw, b, m, ntiles, &b.st->tile_ctr[0], stages, [&](const Tile &t, int64_t i0) {
-        for (int v = threadIdx.x; v < ProxyLayout::S; v += kScanConsumers * 32) {
-            const int w = v * kProxyStride;
-            const int64_t i = i0 + w;
-            if (i >= a.N) break;
-            const float mh = t.mh[v], is = t.is[v], ls = t.ml[v] * is;
-            float acc = 0.0f;
-            const float kw = fmaf(mh, is, ls);  // q_hat - x_hat = (q + mh*is + ls) - x*is
-            if (fabsf(kw) < 4096.0f) {
+        // window w = 2v, v = threadIdx.x + it * kPer: its samples at byte
+        // offset 8v in xs, its statistics at 4v in mh / ml / is.  Two
+        // windows (it, it + kIt/2) at a time, each with two partial sums,
+        // so four independent FMA chains are in flight.
+        const unsigned xa = smem_u32(t.xs) + 8u * threadIdx.x;
+        const unsigned sa = smem_u32(t.mh) + 4u * threadIdx.x;
+        unsigned addr[TERMS];
+#pragma unroll
+        for (int k = 0; k < TERMS; ++k) addr[k] = xa + poff[k];
+        static_for<kIt / 2>([&](auto itc) {
+            constexpr int itA = decltype(itc)::value, itB = itA + kIt / 2;
+            constexpr int soA = itA * kPer * 4, xoA = itA * kPer * 8;
+            constexpr int soB = itB * kPer * 4, xoB = itB * kPer * 8;
+            const int64_t iA = i0 + (int64_t)kProxyStride * (threadIdx.x + itA * kPer);
+            const int64_t iB = i0 + (int64_t)kProxyStride * (threadIdx.x + itB * kPer);
+            const bool liveA = iA < a.N, liveB = iB < a.N;
+            static_assert(ProxyLayout::NS == 2, "the proxy stage holds mh and is only");
+            const float mhA = lds_at<soA>(sa), isA = lds_at<soA + ProxyLayout::S * 4>(sa);
+            const float mhB = lds_at<soB>(sa), isB = lds_at<soB + ProxyLayout::S * 4>(sa);
+            // q_hat - x_hat = (q + mh*is) - x*is, with the mean's high part
+            // only (its low part moves every term of a window by the same
+            // ~ulp(mu)/sigma: the proxy only ranks proposals)
+            const float kwA = mhA * isA, kwB = mhB * isB;
+            float accA, accB;
+            if (!__any_sync(0xffffffffu, (liveA && !(fabsf(kwA) < 4096.0f)) || (liveB && !(fabsf(kwB) < 4096.0f)))) {
                 // one FMA per term; the absolute error stays below ~2^-11
                 // when |mu|/sigma < 2^12 (the proxy only ranks proposals)
+                const unsigned long long kw2A = x2_pack(kwA, kwA), nis2A = x2_pack(-isA, -isA);
+                const unsigned long long kw2B = x2_pack(kwB, kwB), nis2B = x2_pack(-isB, -isB);
+                unsigned long long sA0 = 0ull, sA1 = 0ull, sB0 = 0ull, sB1 = 0ull;  // (+0, +0)
 #pragma unroll
-                for (int u = 0; u < TERMS; ++u) {
-                    const float c = fmaf(-t.xs[w + pos[u]], is, qv[u] + kw);
-                    acc = fmaf(c, c, acc);
+                for (int j = 0; j < TERMS / 2; ++j) {
+                    const unsigned long long xA = x2_pack(lds_at<xoA>(addr[2 * j]), lds_at<xoA>(addr[2 * j + 1]));
+                    const unsigned long long xB = x2_pack(lds_at<xoB>(addr[2 * j]), lds_at<xoB>(addr[2 * j + 1]));
+                    const unsigned long long cA = x2_fma(xA, nis2A, x2_add(qv2[j], kw2A));
+                    const unsigned long long cB = x2_fma(xB, nis2B, x2_add(qv2[j], kw2B));
+                    if (j & 1) {
+                        sA1 = x2_fma(cA, cA, sA1);
+                        sB1 = x2_fma(cB, cB, sB1);
+                    } else {
+                        sA0 = x2_fma(cA, cA, sA0);
+                        sB0 = x2_fma(cB, cB, sB0);
+                    }
                 }
+                accA = x2_sum(x2_add(sA0, sA1));
+                accB = x2_sum(x2_add(sB0, sB1));
             } else {
+                float a0 = 0.0f, a1 = 0.0f, b0 = 0.0f, b1 = 0.0f;
 #pragma unroll
-                for (int u = 0; u < TERMS; ++u) {
-                    const float c = qv[u] - fmaf(t.xs[w + pos[u]] - mh, is, -ls);
-                    acc = fmaf(c, c, acc);
+                for (int j = 0; j < TERMS / 2; ++j) {
+                    float q0, q1;
+                    asm("mov.b64 {%0, %1}, %2;" : "=f"(q0), "=f"(q1) : "l"(qv2[j]));
+                    const float cA0 = q0 - (lds_at<xoA>(addr[2 * j]) - mhA) * isA;
+                    const float cA1 = q1 - (lds_at<xoA>(addr[2 * j + 1]) - mhA) * isA;
+                    const float cB0 = q0 - (lds_at<xoB>(addr[2 * j]) - mhB) * isB;
+                    const float cB1 = q1 - (lds_at<xoB>(addr[2 * j + 1]) - mhB) * isB;
+                    a0 = fmaf(cA0, cA0, a0);
+                    a1 = fmaf(cA1, cA1, a1);
+                    b0 = fmaf(cB0, cB0, b0);
+                    b1 = fmaf(cB1, cB1, b1);
                 }
+                accA = a0 + a1;
+                accB = b0 + b1;
             }
-            const unsigned long long key = make_key(acc, (unsigned)i);
-            best = key < best ? key : best;
-        }
+            const unsigned long long keyA = make_key(accA, (unsigned)iA), keyB = make_key(accB, (unsigned)iB);
+            best = liveA && keyA < best ? keyA : best;
+            best = liveB && keyB < best ? keyB : best;
+        });
     });
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -414,33 +524,74 @@ __global__ void __launch_bounds__(kScanThreads) k_seed_scan(QueryBufs b, QueryAr
     __syncthreads();
     if (threadIdx.x == 0) {
         for (int w = 1; w < (int)(blockDim.x >> 5); ++w) best = wbest[w] < best ? wbest[w] : best;
-        if (best != kEmptyKey) {
-            const unsigned long long last = *((volatile unsigned long long *)&b.st->prop_keys[proposals - 1]);
-            if (best < last) list_insert(b.st->prop_keys, proposals, best);
-        }
+        b.st->cta_best[blockIdx.x] = best;
     }
+    (void)proposals;
 }
 
 template <int TERMS>
-static cudaError_t launch_seed_scan_t(const QueryBufs &b, const QueryArgs &a, int proposals, cudaStream_t s) {
+static cudaError_t launch_seed_scan_t(const QueryBufs &b, const QueryArgs &a, int proposals, int *ctas,
+                                      cudaStream_t s) {
     size_t smem = 0;
     const int stages = scan_stages((const void *)k_seed_scan<TERMS>, stage_bytes<ProxyLayout>(a.m), 2, &smem);
     cudaError_t e = cudaFuncSetAttribute(k_seed_scan<TERMS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     const int64_t tiles = (a.N + ProxyLayout::W - 1) / ProxyLayout::W;
-    const int grid = scan_grid((const void *)k_seed_scan<TERMS>, kScanThreads, smem, b.num_sms, tiles);
+    int grid = scan_grid((const void *)k_seed_scan<TERMS>, kScanThreads, smem, b.num_sms, tiles);
+    if (grid > kCtaSlots) grid = kCtaSlots;
     k_seed_scan<TERMS><<<grid, kScanThreads, smem, s>>>(b, a, proposals, stages);
+    *ctas = grid;
     return cudaGetLastError();
 }
 
-cudaError_t launch_seed_scan(const QueryBufs &b, const QueryArgs &a, int proposals, int terms,
+cudaError_t launch_seed_scan(const QueryBufs &b, const QueryArgs &a, int proposals, int terms, int *ctas,
                              cudaStream_t s) {
+    *ctas = 0;
     if (proposals <= 0) return cudaSuccess;
-    // positions are taken from the query's order, so never more than m
-    if (terms >= 16 && a.m >= 16) return launch_seed_scan_t<16>(b, a, proposals, s);
-    if (terms >= 8 && a.m >= 8) return launch_seed_scan_t<8>(b, a, proposals, s);
-    if (terms >= 4 && a.m >= 4) return launch_seed_scan_t<4>(b, a, proposals, s);
-    return launch_seed_scan_t<2>(b, a, proposals, s);
+    // evenly spaced positions, so never more terms than m
+    if (terms >= 16 && a.m >= 16) return launch_seed_scan_t<16>(b, a, proposals, ctas, s);
+    if (terms >= 8 && a.m >= 8) return launch_seed_scan_t<8>(b, a, proposals, ctas, s);
+    if (terms >= 4 && a.m >= 4) return launch_seed_scan_t<4>(b, a, proposals, ctas, s);
+    return launch_seed_scan_t<2>(b, a, proposals, ctas, s);
+}
+
+// The proposals: the `proposals` smallest of the per-CTA best windows of one
+// or two proposal scans (slots 0 .. ctas0-1 and kCtaSlots .. kCtaSlots +
+// ctas1-1), ascending, by a bitonic sort in shared memory.  The CTAs cover
+// disjoint windows, so the keys are distinct (empty slots sort last).
+__global__ void __launch_bounds__(1024) k_prop_merge(QueryBufs b, int n0, int n1, int proposals) {
+    __shared__ unsigned long long keys[2 * kCtaSlots];
+    QueryState *st = b.st;
+    if (!st->valid) return;
+    const int n = n0 + n1;
+    int size = 1;
+    while (size < n) size <<= 1;
+    for (int t = threadIdx.x; t < size; t += blockDim.x)
+        keys[t] = t < n0 ? st->cta_best[t] : (t < n ? st->cta_best[kCtaSlots + (t - n0)] : kEmptyKey);
+    __syncthreads();
+    for (int k = 2; k <= size; k <<= 1) {
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            for (int t = threadIdx.x; t < size; t += blockDim.x) {
+                const int u = t ^ j;
+                if (u > t) {
+                    const unsigned long long x = keys[t], y = keys[u];
+                    if ((x > y) == ((t & k) == 0)) {
+                        keys[t] = y;
+                        keys[u] = x;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    }
+    for (int t = threadIdx.x; t < proposals; t += blockDim.x) st->prop_keys[t] = t < n ? keys[t] : kEmptyKey;
+}
+
+cudaError_t launch_prop_merge(const QueryBufs &b, int ctas0, int ctas1, int proposals, cudaStream_t s) {
+    if (proposals <= 0 || ctas0 + ctas1 <= 0) return cudaSuccess;
+    if (ctas0 > kCtaSlots || ctas1 > kCtaSlots || proposals > kPropMax) return cudaErrorInvalidValue;
+    k_prop_merge<<<1, 1024, 0, s>>>(b, ctas0, ctas1, proposals);
+    return cudaGetLastError();
 }
 
 // splitmix64 (Steele, Lea & Flood, 2014) as the counter-based generator of
@@ -1090,6 +1241,105 @@ __global__ void __launch_bounds__(256) k_dtw64(QueryBufs b, QueryArgs a, const i
     }
 }
 
+// Shape of the double-float re-score walk.
+template <int L, int K>
+struct PreShape {
+    // the double-float walk for the FP32 walk's shape (L lanes, K cells):
+    // as many warps as the FP32 walk has cells per lane (at most 4), the
+    // r+1 <= L*K cells spread over them
+    static constexpr int W = (L < 32) ? 1 : (K <= 4 ? K : 4);
+    static constexpr int K2 = (L < 32 || K <= 4) ? 1 : (K * 32 + 127) / 128;
+};
+__host__ __device__ inline size_t pre_span(int m, int r, int lanes, int k) {
+    return (size_t)((m + 2 * diag_pad(r, lanes, k) + 3) & ~3);
+}
+
+// The re-score with the anti-diagonal walk spread over W warps per window
+// (dtw_diag_df_mw): G = blockDim.x / (32 W) groups per CTA, group g owning
+// named barrier 1 + g; the query's double-float copy is shared, each group
+// stages its window.  Used when a window's r+1 cells need more than one
+// cell per lane of one warp: per window it is the latency of the walk that
+// counts, and W warps cut the cells each lane steps through per
+// anti-diagonal by W.
+template <int W, int K>
+__global__ void __launch_bounds__(256) k_dtw64_mw(QueryBufs b, QueryArgs a, const int64_t *offsets,
+                                                  int64_t count_host, double *out) {
+    constexpr int GMAX = 8 / W;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    __shared__ DfXchg xch[GMAX];
+    __shared__ double bc[2 * GMAX];
+    __shared__ int cur[GMAX];
+    QueryState *st = b.st;
+    if (!st->valid) return;
+    const int m = a.m, r = a.r;
+    const int G = (int)(blockDim.x / (32 * W));
+    const int pad = diag_pad(r, 32 * W, K);
+    const size_t span = (size_t)((m + 2 * pad + 3) & ~3);
+    dfloat *qd = (dfloat *)smraw + pad;
+    for (int t = threadIdx.x; t < m; t += blockDim.x) qd[t] = df_from(b.qh64[t]);
+    fill_pads((dfloat *)smraw, m, pad, dfloat{1e15f, 0.0f}, threadIdx.x, blockDim.x);
+    const int warp = threadIdx.x >> 5, lane = lane_id();
+    const int g = warp / W, w = warp % W, t = w * 32 + lane;
+    const int nthr = 32 * W, bar = 1 + g;
+    dfloat *cbase = (dfloat *)(smraw + span * 8 * (size_t)(1 + g));
+    dfloat *cd = cbase + pad;
+    if (g < G) fill_pads(cbase, m, pad, dfloat{-1e15f, 0.0f}, t, nthr);
+    __syncthreads();
+    if (g >= G) return;
+    const int64_t count = offsets ? count_host : (int64_t)st->n_margin;
+    while (true) {
+        // (the previous window's last barrier lies between every thread's
+        // read of cur[g] and this write)
+        if (t == 0) cur[g] = atomicAdd(&st->work, 1);
+        group_bar(bar, nthr);
+        const int c = cur[g];
+        if (c >= count) break;
+        unsigned idx = 0;
+        bool bad = false;
+        if (offsets) {
+            const int64_t o = offsets[c];
+            bad = o < 0 || o >= a.N;
+            idx = bad ? 0u : (unsigned)o;
+        } else {
+            idx = st->margin_idx[c];
+        }
+        if (bad) {
+            if (t == 0) out[c] = __longlong_as_double(0x7ff8000000000000ll);
+            group_bar(bar, nthr);
+            continue;
+        }
+        const float *xw = b.x + idx;
+        if (w == 0) {  // two-pass FP64 statistics (Eq. 5) in the group's first warp
+            double sum = 0.0;
+            for (int j = lane; j < m; j += 32) sum += (double)xw[j];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+            const double mu0 = sum * (1.0 / (double)m);
+            double v = 0.0;
+            for (int j = lane; j < m; j += 32) {
+                const double d = (double)xw[j] - mu0;
+                v = fma(d, d, v);
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+            if (lane == 0) {
+                const double mu = sum / (double)m, var = v / (double)m, mm = mu * mu;
+                bc[2 * g] = mu;
+                bc[2 * g + 1] = var <= 1e-24 * (mm > 1.0 ? mm : 1.0) ? 0.0 : 1.0 / sqrt(var);
+            }
+        }
+        group_bar(bar, nthr);
+        const double mu = bc[2 * g], inv = bc[2 * g + 1];
+        for (int j = t; j < m; j += nthr) cd[j] = df_from(((double)xw[j] - mu) * inv);
+        group_bar(bar, nthr);
+        const double d = dtw_diag_df_mw<W, K>(qd, cd, m, r, w, lane, xch[g], bar);
+        if (t == 0) {
+            if (offsets) out[c] = d;
+            else st->margin_d64[c] = d;
+        }
+    }
+}
+
 // Kernel choice and CTA shape.  The anti-diagonal kernel (K > 0) is used
 // when r <= kDiagRMax and one warp's groups can stage their windows;
 // otherwise the row-systolic kernel (K == 0), staged when it fits.  Warps
@@ -1189,10 +1439,40 @@ static cudaError_t dtw_dispatch(const QueryBufs &b, const QueryArgs &a, const in
     return cudaErrorInvalidValue;
 }
 
+template <int W, int K>
+static cudaError_t dtw64_mw_launch(const QueryBufs &b, const QueryArgs &a, const int64_t *offsets, int64_t count,
+                                   double *out, int64_t count_for_grid, cudaStream_t s) {
+    // the query's copy plus one window copy per group (double-float: 8 B per element)
+    const size_t span = (size_t)((a.m + 2 * diag_pad(a.r, 32 * W, K) + 3) & ~3), bytes = span * sizeof(dfloat);
+    const size_t hard = (size_t)200 * 1024;
+    int groups = 8 / W;
+    while (groups > 1 && bytes * (size_t)(1 + groups) > hard) --groups;
+    if (bytes * (size_t)(1 + groups) > hard) return cudaErrorInvalidValue;
+    const size_t smem = bytes * (size_t)(1 + groups);
+    int64_t want = (count_for_grid + groups - 1) / groups;
+    const int64_t cap = (int64_t)b.num_sms * 4;
+    if (want < 1) want = 1;
+    const int blocks = (int)(want < cap ? want : cap);
+    cudaError_t e = cudaFuncSetAttribute(k_dtw64_mw<W, K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_dtw64_mw<W, K><<<blocks, groups * W * 32, smem, s>>>(b, a, offsets, count, out);
+    return cudaGetLastError();
+}
+
 static cudaError_t dtw64_dispatch(const QueryBufs &b, const QueryArgs &a, const int64_t *offsets,
                                   int64_t count, double *out, int64_t count_for_grid, cudaStream_t s) {
     DtwPlan p;
     if (!plan_dtw<double>(a.m, a.r, false, &p)) return cudaErrorInvalidValue;
+    // anti-diagonal with more than one cell per lane of a warp: the
+    // multi-warp walk (the same arithmetic, the same result)
+    if (p.L == 32 && p.K >= 2) {
+#define DTWS_MW(KK)                                                                                       \
+        if (p.K == KK)                                                                                     \
+            return dtw64_mw_launch<PreShape<32, KK>::W, PreShape<32, KK>::K2>(b, a, offsets, count, out,  \
+                                                                               count_for_grid, s);
+        DTWS_MW(2) DTWS_MW(3) DTWS_MW(4) DTWS_MW(6) DTWS_MW(8) DTWS_MW(10) DTWS_MW(12) DTWS_MW(16)
+#undef DTWS_MW
+    }
     const int blocks = dtw_blocks(p, b.num_sms, count_for_grid);
 #define DTWS_CASE(LL, KK)                                                                                     \
     if (p.L == LL && p.K == KK) {                                                                             \
@@ -1478,70 +1758,110 @@ __global__ void k_final_select(QueryBufs b, QueryArgs a) {
 // Pre-score of the best Euclidean seed, run on a side stream while the
 // lower-bound scan streams: its FP32 DTW enters the result list (the survivor
 // pass skips it) and its extended-precision re-score waits for the final
-// stage.  One group of L lanes.
+// stage.  Paired mode (when both copies fit in shared memory): warp 0 runs
+// the FP32 DTW while warps 1..DfW run the re-score beside it, DfW warps wide
+// (the double-float walk's latency per anti-diagonal is what bounds the
+// stage).  Otherwise one warp runs both in turn.
 template <int L, int K>
 __global__ void k_prescore(QueryBufs b, QueryArgs a) {
+    using PS = PreShape<L, K>;
     extern __shared__ __align__(16) unsigned char smraw[];
     __shared__ double bc[2];
+    __shared__ DfXchg xchg;
     QueryState *st = b.st;
     if (!st->valid) return;
     const unsigned idx = prescored_window(st, a);
-    const int lane = threadIdx.x;
-    if (idx == 0xffffffffu || lane >= L) return;
-    const unsigned gmask = (L == 32) ? 0xffffffffu : ((1u << L) - 1u);
-    const int m = a.m, r = a.r, pad = diag_pad(r, L, K);
-    const size_t span = (size_t)((m + 2 * pad + 3) & ~3);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const bool pair = blockDim.x > 32;
+    if (idx == 0xffffffffu) return;
+    const int m = a.m, r = a.r;
+    const size_t span = pre_span(m, r, L, K);
     const float *xw = b.x + idx;
-    // FP32 DTW, as the survivor pass would compute it
-    float *q32 = (float *)smraw, *c32 = (float *)(smraw + span * 8);
-    const float INF = __int_as_float(0x7f800000);
-    fill_pads(q32, m, pad, INF, lane, L);
-    fill_pads(c32, m, pad, -INF, lane, L);
-    const float mh = b.mu_hi[idx], is = b.inv_sigma[idx], ls = b.mu_lo[idx] * is;
-    for (int j = lane; j < m; j += L) {
-        q32[pad + j] = b.qh32[j];
-        c32[pad + j] = fmaf(xw[j] - mh, is, -ls);
+    if (warp == 0) {
+        if (lane >= L) return;
+        const unsigned gmask = (L == 32) ? 0xffffffffu : ((1u << L) - 1u);
+        const int pad = diag_pad(r, L, K);
+        // FP32 DTW, as the survivor pass would compute it
+        float *q32 = (float *)smraw, *c32 = (float *)(smraw + span * 4);
+        const float INF = __int_as_float(0x7f800000);
+        fill_pads(q32, m, pad, INF, lane, L);
+        fill_pads(c32, m, pad, -INF, lane, L);
+        const float mh = b.mu_hi[idx], is = b.inv_sigma[idx], ls = b.mu_lo[idx] * is;
+        for (int j = lane; j < m; j += L) {
+            q32[pad + j] = b.qh32[j];
+            c32[pad + j] = fmaf(xw[j] - mh, is, -ls);
+        }
+        __syncwarp(gmask);
+        int cells = 0;
+        const float d32 =
+            dtw_diag<float, L, K, false>(q32 + pad, c32 + pad, nullptr, m, r, INF, gmask, lane, cells);
+        if (lane == 0) {
+            list_insert(st->res_keys, a.list_cap, make_key(key_quantize(d32, a.qgrid), idx));
+            atomicAdd(&st->ctr[kCtrDtwStarted], 1ull);
+            atomicAdd(&st->ctr[kCtrCells], (unsigned long long)cells);
+        }
+        __syncwarp(gmask);
+        if (pair) return;
+        // one warp: the re-score below reuses this memory
     }
-    __syncwarp(gmask);
-    int cells = 0;
-    const float d32 = dtw_diag<float, L, K, false>(q32 + pad, c32 + pad, nullptr, m, r, INF, gmask, lane, cells);
-    if (lane == 0) {
-        list_insert(st->res_keys, a.list_cap, make_key(key_quantize(d32, a.qgrid), idx));
-        atomicAdd(&st->ctr[kCtrDtwStarted], 1ull);
-        atomicAdd(&st->ctr[kCtrCells], (unsigned long long)cells);
-    }
-    __syncwarp(gmask);
-    // extended-precision re-score (FP64 statistics, double-float DTW)
-    double s = 0.0;
-    for (int j = lane; j < m; j += L) s += (double)xw[j];
+    // extended-precision re-score (FP64 statistics, double-float DTW) by the
+    // first re-score warp's lanes (the whole of warp 1 in paired mode, the
+    // L lanes of warp 0 otherwise)
+    constexpr int LS = PS::W > 1 ? 32 : L;  // lanes of the statistics warp
+    const int dw = pair ? warp - 1 : 0;     // this warp's index in the re-score group
+    const int nthr = pair ? 32 * PS::W : L;
+    const int t = dw * 32 + lane;           // thread index in the group
+    const bool stats_lane = dw == 0 && lane < LS;
+    if (!pair && lane >= L) return;
+    if (stats_lane) {
+        const unsigned smask = (LS == 32) ? 0xffffffffu : ((1u << LS) - 1u);
+        double s = 0.0;
+        for (int j = lane; j < m; j += LS) s += (double)xw[j];
 #pragma unroll
-    for (int o = L / 2; o > 0; o >>= 1) s += __shfl_xor_sync(gmask, s, o, L);
-    if (lane == 0) bc[0] = s / (double)m;
-    __syncwarp(gmask);
-    const double mu = bc[0];
-    double v = 0.0;
-    for (int j = lane; j < m; j += L) {
-        const double d = (double)xw[j] - mu;
-        v = fma(d, d, v);
-    }
+        for (int o = LS / 2; o > 0; o >>= 1) s += __shfl_xor_sync(smask, s, o, LS);
+        const double mu = s / (double)m;
+        double v = 0.0;
+        for (int j = lane; j < m; j += LS) {
+            const double d = (double)xw[j] - mu;
+            v = fma(d, d, v);
+        }
 #pragma unroll
-    for (int o = L / 2; o > 0; o >>= 1) v += __shfl_xor_sync(gmask, v, o, L);
-    if (lane == 0) {
-        const double var = v / (double)m, mm = mu * mu;
-        bc[1] = var <= 1e-24 * (mm > 1.0 ? mm : 1.0) ? 0.0 : 1.0 / sqrt(var);
+        for (int o = LS / 2; o > 0; o >>= 1) v += __shfl_xor_sync(smask, v, o, LS);
+        if (lane == 0) {
+            const double var = v / (double)m, mm = mu * mu;
+            bc[0] = mu;
+            bc[1] = var <= 1e-24 * (mm > 1.0 ? mm : 1.0) ? 0.0 : 1.0 / sqrt(var);
+        }
     }
-    __syncwarp(gmask);
-    const double inv = bc[1];
-    dfloat *qd = (dfloat *)smraw, *cd = (dfloat *)(smraw + span * 8);
-    fill_pads(qd, m, pad, dfloat{1e15f, 0.0f}, lane, L);
-    fill_pads(cd, m, pad, dfloat{-1e15f, 0.0f}, lane, L);
-    for (int j = lane; j < m; j += L) {
-        qd[pad + j] = df_from(b.qh64[j]);
-        cd[pad + j] = df_from(((double)xw[j] - mu) * inv);
+    // the group meets: named barrier 1 in paired mode, the warp otherwise
+    auto group_sync = [&]() {
+        if (pair) group_bar(1, 32 * PS::W);
+        else __syncwarp((L == 32) ? 0xffffffffu : ((1u << L) - 1u));
+    };
+    group_sync();
+    const double mu = bc[0], inv = bc[1];
+    // (paired with L < 32: one warp whose first L lanes walk, as unpaired)
+    const int lanes2 = (pair && L == 32) ? 32 * PS::W : L, k2 = pair ? PS::K2 : K;
+    const int pad2 = diag_pad(r, lanes2, k2);
+    const size_t span2 = pre_span(m, r, lanes2, k2);
+    unsigned char *dbase = smraw + (pair ? span * 8 : 0);
+    dfloat *qd = (dfloat *)dbase, *cd = (dfloat *)(dbase + span2 * 8);
+    fill_pads(qd, m, pad2, dfloat{1e15f, 0.0f}, t, nthr);
+    fill_pads(cd, m, pad2, dfloat{-1e15f, 0.0f}, t, nthr);
+    for (int j = t; j < m; j += nthr) {
+        qd[pad2 + j] = df_from(b.qh64[j]);
+        cd[pad2 + j] = df_from(((double)xw[j] - mu) * inv);
     }
-    __syncwarp(gmask);
-    const double d64 = dtw_diag_df<L, K>(qd + pad, cd + pad, m, r, gmask, lane);
-    if (lane == 0) {
+    group_sync();
+    double d64;
+    if (pair && PS::W > 1) {
+        d64 = dtw_diag_df_mw<PS::W, PS::K2>(qd + pad2, cd + pad2, m, r, dw, lane, xchg, 1);
+    } else {
+        const unsigned gmask = (L == 32) ? 0xffffffffu : ((1u << L) - 1u);
+        if (lane >= L) return;
+        d64 = dtw_diag_df<L, K>(qd + pad2, cd + pad2, m, r, gmask, lane);
+    }
+    if (t == 0) {
         st->pre_d64 = d64;
         __threadfence();
         st->pre_done = 1;
@@ -1552,14 +1872,20 @@ cudaError_t launch_prescore(const QueryBufs &b, const QueryArgs &a, cudaStream_t
     if (!a.prescore) return cudaSuccess;
     int L, K;
     diag_shape(a.r, &L, &K);
-    const int pad = diag_pad(a.r, L, K);
-    const size_t smem = (size_t)((a.m + 2 * pad + 3) & ~3) * 16;
 #define DTWS_CASE(LL, KK)                                                                           \
     if (L == LL && K == KK) {                                                                       \
+        using PS = PreShape<LL, KK>;                                                                \
+        /* paired: FP32 copy (8 B per element) beside the re-score's (16 B), */                    \
+        /* else one warp with the re-score reusing the FP32 copy's memory */                       \
+        const size_t s32 = pre_span(a.m, a.r, LL, KK) * 8;                                          \
+        const size_t sdf = pre_span(a.m, a.r, (LL < 32 ? LL : 32 * PS::W), PS::K2) * 16;           \
+        const bool pair = s32 + sdf <= (size_t)200 * 1024;                                          \
+        const size_t smem = pair ? s32 + sdf : pre_span(a.m, a.r, LL, KK) * 16;                     \
+        const int threads = pair ? 32 + 32 * PS::W : 32;                                            \
         cudaError_t e = cudaFuncSetAttribute(k_prescore<LL, KK>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
                                              (int)smem);                                            \
         if (e != cudaSuccess) return e;                                                             \
-        k_prescore<LL, KK><<<1, 32, smem, s>>>(b, a);                                               \
+        k_prescore<LL, KK><<<1, threads, smem, s>>>(b, a);                                          \
         return cudaGetLastError();                                                                  \
     }
     DTWS_CASE(1, 1) DTWS_CASE(2, 1) DTWS_CASE(4, 1) DTWS_CASE(8, 1) DTWS_CASE(16, 1)

@@ -175,7 +175,7 @@ __global__ void k_window_stats(const float *__restrict__ x, int64_t n, int m, co
                                const float *__restrict__ scale, int64_t nb,
                                float *__restrict__ mu_hi, float *__restrict__ mu_lo,
                                float *__restrict__ inv_sigma, float *__restrict__ smu_hi,
-                               float *__restrict__ smu_lo, float *__restrict__ sinv_sigma) {
+                               float *__restrict__ sinv_sigma) {
     const int64_t N = n - m + 1;
     const float sc = scale[0], isc = 1.0f / sc;  // powers of two
     const float *p1h = pf, *p1l = pf + n, *p2h = pf + 2 * n, *p2l = pf + 3 * n;
@@ -250,21 +250,21 @@ __global__ void k_window_stats(const float *__restrict__ x, int64_t n, int m, co
         mu_lo[i] = ml;
         inv_sigma[i] = is;
         if ((i & (kProxyStride - 1)) == 0) {  // every kProxyStride-th window, for the proxy scan
+            // (the mean's high part alone: the proxy only ranks proposals)
             smu_hi[i / kProxyStride] = mh;
-            smu_lo[i / kProxyStride] = ml;
             sinv_sigma[i / kProxyStride] = is;
         }
     }
 }
 
 cudaError_t launch_window_stats(const float *x, int64_t n, int m, const float *pf, const float *bf,
-                                const int *ok, const float *scale, float *mu_hi, float *mu_lo, float *inv_sigma, float *smu_hi,
-                                float *smu_lo, float *sinv_sigma, int num_sms, cudaStream_t s) {
+                                const int *ok, const float *scale, float *mu_hi, float *mu_lo, float *inv_sigma,
+                                float *smu_hi, float *sinv_sigma, int num_sms, cudaStream_t s) {
     const int64_t N = n - m + 1, nb = (n + kBlockB - 1) / kBlockB;
     int64_t blocks = (N + 255) / 256;
     if (blocks > (int64_t)num_sms * 16) blocks = (int64_t)num_sms * 16;
     k_window_stats<<<(unsigned)blocks, 256, 0, s>>>(x, n, m, pf, bf, ok, scale, nb, mu_hi, mu_lo, inv_sigma, smu_hi,
-                                                    smu_lo, sinv_sigma);
+                                                    sinv_sigma);
     return cudaGetLastError();
 }
 

@@ -42,6 +42,21 @@ def test_query_matches_oracle(walk, index, m, w, k, noise):
     _close(dist, od, m)
 
 
+@pytest.mark.parametrize("m,r", [(64, 5), (128, 17), (300, 70), (512, 51), (1024, 102), (700, 200),
+                                 (2048, 409)])
+def test_distances_are_the_extended_rescore(walk, index, m, r):
+    """The returned distances are the extended-precision re-scores (the
+    pre-scored seed's on the side stream, the rest in the final stage; one,
+    two, three or four warps per window): the FP64 oracle's DTW at the
+    returned offsets to FP32 rounding, and dtws_dtw_at_f64 there to an ulp."""
+    q, _ = synth.noisy_copy(walk, m, 300 + m, 400 + r, noise=0.3)
+    idx, dist = index.query(q, r, 3)
+    assert index.sync_status() == dtws.DTWS_OK
+    d64 = oracle.dtw_at(walk, q, r, idx)
+    np.testing.assert_allclose(dist, d64, rtol=2 ** -23, atol=0)
+    np.testing.assert_array_max_ulp(dist, index.dtw_at_f64(q, r, idx).astype(np.float32), maxulp=1)
+
+
 def test_random_query_not_a_copy(walk, index):
     """A query unrelated to the series: loose seeds, many survivors."""
     q = synth.random_walk(128, 999)

@@ -301,5 +301,5 @@ def test_fragment_worker_failure_propagates():
     q = synth.random_walk(10, 94)
     with pytest.raises(ValueError):
         # a fragment whose window range runs past the series is rejected by
-        # the oracle; the driver must re-raise instead of returning a result
+        # the oracle; search_fragments must re-raise instead of returning a result
         fragments.search_fragments(x, q, 2, 1, F=2, threads=2, first=500, count=600)

@@ -58,6 +58,8 @@ SPECS = {
     "rw1m": dict(n=1_000_000, m=128, w=0.05, k=1),
     # the learned-proposal workload's kind (walk + bursts, seeds 4/4/6), shortened to 2e7 samples
     "learn20m": dict(n=20_000_000, m=1024, w=0.10, k=1),
+    # the learned-proposal workload's series itself (2e8 samples), its first query
+    "learn200m": dict(n=200_000_000, m=1024, w=0.10, k=1),
 }
 
 
@@ -142,12 +144,12 @@ def make_workload(name: str, rank: int = 0, world: int = 1):
     def frag(k):
         if name in ("rw100m", "rw30m"):
             return synth.walk_with_bursts(n, 0 + 101 * k, 3 + 101 * k, 5 + 101 * k)
-        if name == "learn20m":
+        if name in ("learn20m", "learn200m"):
             return synth.walk_with_bursts(n, 4 + 101 * k, 4 + 101 * k, 6 + 101 * k)
         return synth.random_walk(n, 101 * k)
 
     x = frag(rank)
-    if name == "learn20m":
+    if name in ("learn20m", "learn200m"):
         qs, offs = synth.fixed_queries(frag(0) if rank != 0 else x, 1, m, 9)
         q, o = qs[0], offs[0]
     else:
@@ -415,6 +417,25 @@ def _mean_query_ms(ix, qds, r, k, dev, reps=1):
     return e0.elapsed_time(e1) / (len(qds) * reps)
 
 
+def _phase_sample(ix, qs, rs, k, count):
+    """Per-phase device times (events between the phases) and the cascade's
+    survivor counters of `count` single queries (query i with band rs[i]),
+    timing option on."""
+    from paper_1812_10302_gb300 import dtws
+    out = []
+    ix.set_options(timing=1)
+    for q, r in list(zip(qs, rs))[:count]:
+        ix.query(q, int(r), k)
+        st = ix.last_stats()
+        out.append({"m": int(len(q)), "r": int(r),
+                    "phase_ms": dict(zip(dtws.PHASES, [round(float(v), 4) for v in st["phase_ms"]])),
+                    "survivors": {c: int(st[s]) for c, s in (("kim", "pass_kim"), ("keogh_q", "pass_keogh_q"),
+                                                                ("keogh_s", "pass_keogh_s"),
+                                                                ("dtw_started", "dtw_started"))}})
+    ix.set_options(timing=0)
+    return out
+
+
 def learned_leg(dev):
     """Learned proposals on the learned-proposal workload (n = 2e8 walk with
     sine bursts, 64 noisy queries m = 1024, r = 102, top-1): mean ms per query
@@ -511,12 +532,17 @@ def batch_leg(dev):
         raise RuntimeError("device-side error in the batch")
     sec = float(np.median(ts))
     windows = sum(n - len(q) + 1 for q in qs)
+    # where a query's time goes: eight queries across the length range, alone
+    order = np.argsort([len(q) for q in qs])
+    pick = [int(order[j]) for j in np.linspace(0, len(qs) - 1, 8).round().astype(int)]
+    sample = _phase_sample(ix, [qs[j] for j in pick], [rs[j] for j in pick], k, 8)
     ix.close()
     return {"workload": "batch: random walk n=50000000, 256 noisy copies m~U{128..2048}, r=floor(w m), "
                         "w~U[0.05,0.2], top-10",
             "seconds_per_batch": sec, "queries_per_s": len(qs) / sec, "subsequences_per_s": windows / sec,
             "first_call_seconds": first, "lanes": 4, "graph": "captured on the first call, replayed",
-            "timing": "host wall clock around dtws_query_batch (synchronising; host queries and outputs)"}
+            "timing": "host wall clock around dtws_query_batch (synchronising; host queries and outputs)",
+            "single_query_sample": sample}
 
 
 def drift_leg(dev):
@@ -537,6 +563,7 @@ def drift_leg(dev):
     del x
     qds = [torch.from_numpy(q).to(dev) for q in qs]
     ms = _mean_query_ms(ix, qds, r, 1, dev)
+    sample = _phase_sample(ix, qds, [r] * len(qds), 1, 4)
     errs = []
     for q in qs:
         i, d = ix.query(q, r, 1)
@@ -548,7 +575,8 @@ def drift_leg(dev):
                         "m=1024, r=102, top-1",
             "ms_per_query": ms, "subsequences_per_s": (1_000_000_000 - 1023) / (ms * 1e-3),
             "create_seconds": create_s,
-            "fp32_dtw_rel_error_vs_extended": {"max": max(errs), "median": float(np.median(errs))}}
+            "fp32_dtw_rel_error_vs_extended": {"max": max(errs), "median": float(np.median(errs))},
+            "single_query_sample": sample}
 
 
 def main():

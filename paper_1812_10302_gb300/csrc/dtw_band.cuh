@@ -256,12 +256,22 @@ __device__ __forceinline__ void diag_step(const T (&qv)[K], const T (&cv)[K], T 
     }
 }
 
-// Cells of an anti-diagonal step inside the band and the matrix: positions p
-// with 0 <= p <= hi_band, 0 <= qbase - p < m, 0 <= cbase + p < m.
-__device__ __forceinline__ int diag_cells(int qbase, int cbase, int m, int hi_band) {
-    const int lo = max(0, max(qbase - (m - 1), -cbase));
-    const int hi = min(hi_band, min(qbase, m - 1 - cbase));
-    return hi >= lo ? hi - lo + 1 : 0;
+// Band cells (the band |i - j| <= r of Eq. 1 inside [0, m)^2) on the
+// anti-diagonals 0..A, in closed form.  G(B) counts the band's cells with
+// i + j <= B for B <= m - 1, where only i, j >= 0 bind: anti-diagonal a
+// holds a + 1 of them while a <= r, then r or r + 1 by parity.  Past the
+// middle the complement follows from the symmetry (i, j) -> (m-1-i, m-1-j).
+__host__ __device__ inline long long band_cells_upto(int A, int m, int r) {
+    if (r > m - 1) r = m - 1;
+    const long long T = (long long)m * (2 * r + 1) - (long long)r * (r + 1);
+    if (A < 0) return 0;
+    if (A >= 2 * m - 2) return T;
+    auto G = [r](long long B) -> long long {
+        if (B < 0) return 0;
+        if (B <= r) return (B + 1) * (B + 2) / 2;
+        return (long long)(r + 1) * (r + 2) / 2 + (B - r) * r + (B - r) / 2;
+    };
+    return A <= m - 1 ? G(A) : T - G(2LL * m - 3 - A);
 }
 
 // Register windows of the anti-diagonal walk: cell p of a step reads
@@ -306,7 +316,6 @@ __device__ T dtw_diag(const T *__restrict__ qp, const T *__restrict__ cp, const 
     // (bi, bj) = ((a - e_min)/2, (a + e_min)/2).  Along an (even, odd) pair
     // bi stays and bj grows by one; from pair to pair both grow by one.
     int a = 0, bi, bj;
-    int ncell = 0;  // lane 0's count
     if (r & 1) {  // a = 0 is odd: e_min = 1 - r
         const int qb = (r - 1) >> 1, cb = (1 - r) >> 1;
 #pragma unroll
@@ -315,7 +324,6 @@ __device__ T dtw_diag(const T *__restrict__ qp, const T *__restrict__ cp, const 
             cv[t] = cp[cb + (lane * K + t)];
         }
         diag_step<T, L, K, 1>(qv, cv, p1, p2, lane, r, gmask);
-        ncell += diag_cells(qb, cb, m, r - 1);
         a = 1;
         shift_q<T, L, K>(qv, qp, qb + 1, lane, gmask);
     } else {
@@ -330,10 +338,8 @@ __device__ T dtw_diag(const T *__restrict__ qp, const T *__restrict__ cp, const 
     bj = (a - r) >> 1;
     for (; a + 1 <= last; a += 2, ++bi, ++bj) {
         diag_step<T, L, K, 0>(qv, cv, p1, p2, lane, r, gmask);
-        ncell += diag_cells(bi, bj, m, r);
         shift_c<T, L, K>(cv, cp, bj + 1, lane, gmask);
         diag_step<T, L, K, 1>(qv, cv, p1, p2, lane, r, gmask);
-        ncell += diag_cells(bi, bj + 1, m, r - 1);
         shift_q<T, L, K>(qv, qp, bi + 1, lane, gmask);
         if (ABANDON && ((a >> 1) & 7) == 7) {
             // p1: anti-diagonal a+1 (rows bi - p), p2: a (rows bi - p)
@@ -347,16 +353,15 @@ __device__ T dtw_diag(const T *__restrict__ qp, const T *__restrict__ cp, const 
 #pragma unroll
             for (int o = L / 2; o > 0; o >>= 1) low = fminf(low, __shfl_xor_sync(gmask, low, o, L));
             if (low > (float)thr) {
-                if (lane == 0) cells += ncell;
+                if (lane == 0) cells += (int)band_cells_upto(a + 1, m, r);  // anti-diagonals 0..a+1
                 return INF;
             }
         }
     }
     if (a == last) {
         diag_step<T, L, K, 0>(qv, cv, p1, p2, lane, r, gmask);
-        ncell += diag_cells(bi, bj, m, r);
     }
-    if (lane == 0) cells += ncell;
+    if (lane == 0) cells += (int)band_cells_upto(last, m, r);
     // d(m-1, m-1): e = 0 on the last anti-diagonal
     const int pe = (r - ((last + r) & 1)) >> 1;
     T res = INF;

@@ -168,13 +168,16 @@ cudaError_t launch_qprep(const float *Q, const QueryBufs &b, const QueryArgs &a,
     size_t smem = (size_t)P * 8 + (size_t)a.m * 4;
     cudaError_t e = cudaFuncSetAttribute(k_qprep, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k_qprep<<<1, 1024, smem, s>>>(Q, b, a);
+    // the sort's compare-exchange steps take P/2 threads; a smaller block
+    // makes each of its barriers cheaper
+    const int threads = P / 2 < 128 ? 128 : (P / 2 > 1024 ? 1024 : P / 2);
+    k_qprep<<<1, threads, smem, s>>>(Q, b, a);
     return cudaGetLastError();
 }
 
 // ------------------------------------------------------------------ tile pipeline
-// A tile is kTile consecutive windows [i0, i0 + kTile).  Its samples
-// x[i0, i0 + kTile + m - 1) and its window statistics are staged in shared
+// A tile is W consecutive windows [i0, i0 + W).  Its samples
+// x[i0, i0 + W + m - 1) and its window statistics are staged in shared
 // memory by 1-D bulk copies (the TMA engine) completing on an mbarrier.  The
 // padded series and the statistics arrays are allocated so that every full
 // tile is in bounds (the library rounds both up to whole tiles plus kMMax).
@@ -191,12 +194,13 @@ cudaError_t launch_qprep(const float *Q, const QueryBufs &b, const QueryArgs &a,
 // Use u of a stage waits for phase u & 1 of its barriers.  The end is a stage
 // whose tile index is -1, completed without copies.
 //
-// Two stage layouts.  LbLayout: kTile windows with the statistics (mean as
+// Two stage layouts.  LbLayout<TW>: TW windows with the statistics (mean as
 // a hi + lo pair, 1/sigma) of every window (the lower-bound scan).
 // ProxyLayout: kProxyTile windows with the mean's high part and 1/sigma of
 // every kProxyStride-th window (the proxy scan; no ml array).
+template <int TW>
 struct LbLayout {
-    static constexpr int W = kTile, S = kTile, kStride = 1, NS = 3;
+    static constexpr int W = TW, S = TW, kStride = 1, NS = 3;
     __device__ static const float *mh(const QueryBufs &b) { return b.mu_hi; }
     __device__ static const float *ml(const QueryBufs &b) { return b.mu_lo; }
     __device__ static const float *is(const QueryBufs &b) { return b.inv_sigma; }
@@ -252,6 +256,7 @@ __device__ __forceinline__ void issue_tile(const Tile &t, const QueryBufs &b, in
 }
 
 constexpr int kScanConsumers = 8;                       // consumer warps
+constexpr int kLaneEqMin = 20;  // LB_KimFL passers in a row of 32 above which each lane takes its own Eq. 8
 constexpr int kScanThreads = (kScanConsumers + 1) * 32;  // + one producer warp
 
 // Runs process(tile, i0) in every consumer warp for each tile this CTA takes
@@ -557,40 +562,32 @@ cudaError_t launch_seed_scan(const QueryBufs &b, const QueryArgs &a, int proposa
 
 // The proposals: the `proposals` smallest of the per-CTA best windows of one
 // or two proposal scans (slots 0 .. ctas0-1 and kCtaSlots .. kCtaSlots +
-// ctas1-1), ascending, by a bitonic sort in shared memory.  The CTAs cover
-// disjoint windows, so the keys are distinct (empty slots sort last).
+// ctas1-1), ascending.  The CTAs cover disjoint windows, so the keys other
+// than the empty key are distinct: each key's rank is the number of keys
+// below it, and a key of rank < proposals goes to that slot (the list was
+// emptied by the query reset; empty keys are not written).
 __global__ void __launch_bounds__(1024) k_prop_merge(QueryBufs b, int n0, int n1, int proposals) {
     __shared__ unsigned long long keys[2 * kCtaSlots];
     QueryState *st = b.st;
     if (!st->valid) return;
     const int n = n0 + n1;
-    int size = 1;
-    while (size < n) size <<= 1;
-    for (int t = threadIdx.x; t < size; t += blockDim.x)
-        keys[t] = t < n0 ? st->cta_best[t] : (t < n ? st->cta_best[kCtaSlots + (t - n0)] : kEmptyKey);
+    for (int t = threadIdx.x; t < n; t += blockDim.x)
+        keys[t] = t < n0 ? st->cta_best[t] : st->cta_best[kCtaSlots + (t - n0)];
     __syncthreads();
-    for (int k = 2; k <= size; k <<= 1) {
-        for (int j = k >> 1; j > 0; j >>= 1) {
-            for (int t = threadIdx.x; t < size; t += blockDim.x) {
-                const int u = t ^ j;
-                if (u > t) {
-                    const unsigned long long x = keys[t], y = keys[u];
-                    if ((x > y) == ((t & k) == 0)) {
-                        keys[t] = y;
-                        keys[u] = x;
-                    }
-                }
-            }
-            __syncthreads();
-        }
+    for (int t = threadIdx.x; t < n; t += blockDim.x) {
+        const unsigned long long k = keys[t];
+        if (k == kEmptyKey) continue;
+        int rank = 0;
+        for (int u = 0; u < n; ++u) rank += keys[u] < k;
+        if (rank < proposals) st->prop_keys[rank] = k;
     }
-    for (int t = threadIdx.x; t < proposals; t += blockDim.x) st->prop_keys[t] = t < n ? keys[t] : kEmptyKey;
 }
 
 cudaError_t launch_prop_merge(const QueryBufs &b, int ctas0, int ctas1, int proposals, cudaStream_t s) {
     if (proposals <= 0 || ctas0 + ctas1 <= 0) return cudaSuccess;
     if (ctas0 > kCtaSlots || ctas1 > kCtaSlots || proposals > kPropMax) return cudaErrorInvalidValue;
-    k_prop_merge<<<1, 1024, 0, s>>>(b, ctas0, ctas1, proposals);
+    const int n = ctas0 + ctas1, threads = n < 1024 ? (n + 31) / 32 * 32 : 1024;
+    k_prop_merge<<<1, threads, 0, s>>>(b, ctas0, ctas1, proposals);
     return cudaGetLastError();
 }
 
@@ -1560,6 +1557,87 @@ __device__ __forceinline__ float warp_sum(float v) {
 // time: lanes take 32 consecutive terms of the |q_hat|-ordered LB_Keogh sums
 // and the warp abandons as soon as a chunk's running total exceeds thr.  No
 // thread waits on another warp's survivors.
+// The rare part of a row of 32 windows (entered only when some window
+// passed LB_KimFL): the windows that passed (bal) are bounded by
+// LB_Keogh of the window against the query envelope (Eq. 8) over the
+// kEqChunks * 32 largest-|q_hat| terms, and the survivors are appended as
+// (bound, offset) by one warp-aggregated atomic.  A dense row (a loose
+// bound) gives each passing lane its own window's terms; otherwise the warp
+// takes one window at a time, 32 terms per step.  Returns the survivors.
+__device__ __forceinline__ int lb_row_keogh(const Tile &t, const QueryBufs &b, QueryState *st, const int *o_s,
+                                         const float *u_s, const float *l_s, int m, float thr, unsigned bal,
+                                         int wrow, int lane, float kim, float mh, float is, float ls, int64_t i0) {
+    const int w = wrow + lane;
+    unsigned keep = 0;   // windows of this row that survive Eq. 8
+    float my_lb = 0.0f;  // lane t holds window t's bound when it survives
+    if (__popc(bal) >= kLaneEqMin) {
+        // the same terms in the same |q_hat| order, each lane abandoning once
+        // its sum exceeds thr (checked every 8 terms): 32 windows per step
+        // instead of one window and a shuffle reduction per chunk
+        const int nt = m < kEqChunks * 32 ? m : kEqChunks * 32;
+        float s2 = 0.0f;
+        bool alive = (bal >> lane) & 1u;
+        for (int j0 = 0; j0 < nt; j0 += 8) {
+            if (!__any_sync(0xffffffffu, alive)) break;
+            if (alive) {
+#pragma unroll
+                for (int v = 0; v < 8; ++v) {
+                    const int j = j0 + v;
+                    if (j < nt) {
+                        const bool sm = j < kEqSmem * 32;
+                        const int o = sm ? o_s[j] : (int)__ldg(b.ord + j);
+                        const float uq = sm ? u_s[j] : __ldg(b.sU + j), lq = sm ? l_s[j] : __ldg(b.sL + j);
+                        s2 += keogh_term(fmaf(t.xs[w + o] - mh, is, -ls), uq, lq);
+                    }
+                }
+                alive = !(s2 > thr);
+            }
+        }
+        keep = __ballot_sync(0xffffffffu, alive);
+        my_lb = fmaxf(kim, s2);
+    } else {
+        while (bal) {
+            const int src = __ffs(bal) - 1;
+            bal &= bal - 1;
+            const int ws = wrow + src;
+            const float smh = t.mh[ws], sis = t.is[ws], sls = t.ml[ws] * sis;
+            const float *xw = t.xs + ws;
+            // a window that survives these chunks (the neighbourhood of a
+            // match) goes to the DTW stage with the partial sum, itself a
+            // lower bound, rather than holding this warp for the full sum
+            float s2 = 0.0f;
+            for (int base = 0; base < m && base < kEqChunks * 32; base += 32) {
+                const int j = base + lane;
+                float term = 0.0f;
+                if (j < m) {
+                    const bool sm = base < kEqSmem * 32;
+                    const int o = sm ? o_s[j] : (int)__ldg(b.ord + j);
+                    const float uq = sm ? u_s[j] : __ldg(b.sU + j), lq = sm ? l_s[j] : __ldg(b.sL + j);
+                    term = keogh_term(fmaf(xw[o] - smh, sis, -sls), uq, lq);
+                }
+                s2 += warp_sum(term);
+                if (s2 > thr) break;
+            }
+            if (s2 > thr) continue;
+            keep |= 1u << src;
+            if (lane == src) my_lb = fmaxf(kim, s2);
+        }
+    }
+    // one append per row of 32 windows: a warp-aggregated atomic
+    if (keep) {
+        int base = 0;
+        if (lane == 0) base = atomicAdd(&st->n_cand, __popc(keep));
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if (keep & (1u << lane)) {
+            const int pos = base + __popc(keep & ((1u << lane) - 1u));
+            b.cand_lb[pos] = my_lb;
+            b.cand_idx[pos] = (unsigned)(i0 + w);
+        }
+    }
+    return __popc(keep);
+}
+
+template <int TW>
 __global__ void __launch_bounds__(kScanThreads) k_lb_scan(QueryBufs b, QueryArgs a, int stages) {
     extern __shared__ __align__(16) unsigned char smraw[];
     QueryState *st = b.st;
@@ -1569,7 +1647,7 @@ __global__ void __launch_bounds__(kScanThreads) k_lb_scan(QueryBufs b, QueryArgs
     if (blockIdx.x == 0 && threadIdx.x == 0) st->thr_scan = thr;
     const float qf = b.qh32[0], ql = b.qh32[m - 1];
     const int lane = lane_id(), warp = threadIdx.x >> 5;
-    constexpr int kPerWarp = kTile / kScanConsumers;
+    constexpr int kPerWarp = TW / kScanConsumers;
     // the ordered query terms the scan uses, in shared memory
     __shared__ int o_s[kEqSmem * 32];
     __shared__ float u_s[kEqSmem * 32], l_s[kEqSmem * 32];
@@ -1579,66 +1657,35 @@ __global__ void __launch_bounds__(kScanThreads) k_lb_scan(QueryBufs b, QueryArgs
         l_s[j] = j < m ? b.sL[j] : 0.0f;
     }
     unsigned long long c1 = 0, c2 = 0;
-    const int64_t ntiles = (a.N + kTile - 1) / kTile;
-    tile_pipeline<LbLayout>(smraw, b, m, ntiles, &st->tile_ctr[1], stages, [&](const Tile &t, int64_t i0) {
+    const int64_t ntiles = (a.N + TW - 1) / TW;
+    tile_pipeline<LbLayout<TW>>(smraw, b, m, ntiles, &st->tile_ctr[1], stages, [&](const Tile &t, int64_t i0) {
+        // 32-bit shared addresses of this lane's first window (row 0); the
+        // rows follow at constant offsets
+        const unsigned w0 = (unsigned)(warp * kPerWarp + lane);
+        const unsigned sa = smem_u32(t.mh) + 4u * w0, xa = smem_u32(t.xs) + 4u * w0;
+        const unsigned xl = xa + 4u * (unsigned)(m - 1);
+        const int64_t nrem = a.N - i0;  // windows of this tile that exist: w < nrem
+        // (one copy of the row body: the rare part below is inlined once)
 #pragma unroll 1
         for (int u = 0; u < kPerWarp / 32; ++u) {
-            const int w = warp * kPerWarp + u * 32 + lane;
+            const unsigned ro = (unsigned)u * 32u * 4u;
+            const int w = (int)w0 + u * 32;
             bool pass = false;
-            float kim = 0.0f;
-            if (i0 + w < a.N) {
-                const float mh = t.mh[w], is = t.is[w], ls = t.ml[w] * is;
-                const float d0 = qf - fmaf(t.xs[w] - mh, is, -ls);
-                const float d1 = ql - fmaf(t.xs[w + m - 1] - mh, is, -ls);
+            float kim = 0.0f, mh = 0.0f, is = 0.0f, ls = 0.0f;
+            if (w < nrem) {
+                const unsigned su = sa + ro;
+                mh = lds_at<0>(su);
+                const float ml = lds_at<TW * 4>(su);
+                is = lds_at<TW * 8>(su);
+                ls = ml * is;
+                const float d0 = qf - fmaf(lds_at<0>(xa + ro) - mh, is, -ls);
+                const float d1 = ql - fmaf(lds_at<0>(xl + ro) - mh, is, -ls);
                 kim = fmaf(d0, d0, d1 * d1);
                 pass = !(kim > thr);
             }
-            unsigned bal = __ballot_sync(0xffffffffu, pass);
+            const unsigned bal = __ballot_sync(0xffffffffu, pass);
             c1 += __popc(bal);
-            unsigned keep = 0;   // windows of this row of 32 that survive Eq. 8
-            float my_lb = 0.0f;  // lane t holds window t's bound when it survives
-            while (bal) {
-                const int src = __ffs(bal) - 1;
-                bal &= bal - 1;
-                const int ws = warp * kPerWarp + u * 32 + src;
-                const int64_t i = i0 + ws;
-                const float mh = t.mh[ws], is = t.is[ws], ls = t.ml[ws] * is;
-                const float *xw = t.xs + ws;
-                // LB_Keogh, window vs query envelope (Eq. 8), at most kEqChunks
-                // chunks of 32 terms here: a window that survives them (the
-                // neighbourhood of a match) goes to the DTW stage with the
-                // partial sum, itself a lower bound, rather than holding
-                // this warp for the full sum
-                float s2 = 0.0f;
-                for (int base = 0; base < m && base < kEqChunks * 32; base += 32) {
-                    const int j = base + lane;
-                    float term = 0.0f;
-                    if (j < m) {
-                        const bool sm = base < kEqSmem * 32;
-                        const int o = sm ? o_s[j] : (int)__ldg(b.ord + j);
-                        const float uq = sm ? u_s[j] : __ldg(b.sU + j), lq = sm ? l_s[j] : __ldg(b.sL + j);
-                        term = keogh_term(fmaf(xw[o] - mh, is, -ls), uq, lq);
-                    }
-                    s2 += warp_sum(term);
-                    if (s2 > thr) break;
-                }
-                if (s2 > thr) continue;
-                ++c2;
-                keep |= 1u << src;
-                if (lane == src) my_lb = fmaxf(kim, s2);
-                (void)i;
-            }
-            // one append per row of 32 windows: a warp-aggregated atomic
-            if (keep) {
-                int base = 0;
-                if (lane == 0) base = atomicAdd(&st->n_cand, __popc(keep));
-                base = __shfl_sync(0xffffffffu, base, 0);
-                if (keep & (1u << lane)) {
-                    const int pos = base + __popc(keep & ((1u << lane) - 1u));
-                    b.cand_lb[pos] = my_lb;
-                    b.cand_idx[pos] = (unsigned)(i0 + w);
-                }
-            }
+            if (bal) c2 += lb_row_keogh(t, b, st, o_s, u_s, l_s, m, thr, bal, w - lane, lane, kim, mh, is, ls, i0);
         }
     });
     if (lane == 0) {
@@ -1647,18 +1694,30 @@ __global__ void __launch_bounds__(kScanThreads) k_lb_scan(QueryBufs b, QueryArgs
     }
 }
 
-cudaError_t launch_lb_scan(const QueryBufs &b, const QueryArgs &a, cudaStream_t s) {
+template <int TW>
+static cudaError_t launch_lb_scan_t(const QueryBufs &b, const QueryArgs &a, cudaStream_t s) {
     size_t smem = 0;
-    const int stages = scan_stages((const void *)k_lb_scan, stage_bytes<LbLayout>(a.m), 3, &smem);
-    cudaError_t e = cudaFuncSetAttribute(k_lb_scan, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const int stages = scan_stages((const void *)k_lb_scan<TW>, stage_bytes<LbLayout<TW>>(a.m), 3, &smem);
+    cudaError_t e = cudaFuncSetAttribute(k_lb_scan<TW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    const int64_t tiles = (a.N + kTile - 1) / kTile;
-    int grid = scan_grid((const void *)k_lb_scan, kScanThreads, smem, b.num_sms, tiles);
+    const int64_t tiles = (a.N + TW - 1) / TW;
+    int grid = scan_grid((const void *)k_lb_scan<TW>, kScanThreads, smem, b.num_sms, tiles);
     // the scan is persistent and would occupy every CTA slot: leave one free
     // so the side-stream pre-score runs beside it instead of after it
     if (a.prescore && grid > b.num_sms) --grid;
-    k_lb_scan<<<grid, kScanThreads, smem, s>>>(b, a, stages);
+    k_lb_scan<TW><<<grid, kScanThreads, smem, s>>>(b, a, stages);
     return cudaGetLastError();
+}
+
+cudaError_t launch_lb_scan(const QueryBufs &b, const QueryArgs &a, cudaStream_t s) {
+    // Tile width by query length: a tile's stage holds its TW windows'
+    // statistics and TW + m - 1 samples (the m - 1 halo read from L2).  Up
+    // to m = 768 the 1024-window tile keeps 4 CTAs per SM with 3 stages;
+    // beyond it the stage grows and residency drops to 3, and the 512-window
+    // tile (more CTAs in flight, a larger halo share) is faster (measured:
+    // m = 512 0.293 ms vs 0.326 ms per 1e8 windows with 512; m = 1024
+    // 1.01 ms vs 1.28 ms per 2e8 with 1024).
+    return a.m <= 768 ? launch_lb_scan_t<kTile>(b, a, s) : launch_lb_scan_t<kTile / 2>(b, a, s);
 }
 
 // ------------------------------------------------------------------ survivor ordering
@@ -1698,13 +1757,29 @@ __global__ void __launch_bounds__(kBins) k_bin_scan(QueryState *st) {
     if (t == 0) st->work2 = 0;
 }
 
-__global__ void k_bin_scatter(QueryBufs b) {
+// Each CTA takes a contiguous chunk of the survivors, counts its bins in
+// shared memory, reserves each bin's range with one global atomic, and
+// scatters with shared-memory atomics (one global atomic per CTA and bin
+// instead of one per survivor: with a loose bound tens of millions of
+// survivors would otherwise queue on ~1000 addresses).  The order inside a
+// bin is arbitrary; the DTW stage takes bins in order.
+__global__ void __launch_bounds__(512) k_bin_scatter(QueryBufs b) {
+    __shared__ int h[kBins];
     QueryState *st = b.st;
-    const int n = st->n_cand;
+    const int64_t n = st->n_cand;
     const float thr = st->thr_scan;
-    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n; c += gridDim.x * blockDim.x) {
-        float lb = b.cand_lb[c];
-        int pos = atomicAdd(&st->bin_off[bin_of(lb, thr)], 1);
+    const int64_t per = (n + gridDim.x - 1) / gridDim.x;
+    const int64_t c0 = (int64_t)blockIdx.x * per, c1 = c0 + per < n ? c0 + per : n;
+    for (int t = threadIdx.x; t < kBins; t += blockDim.x) h[t] = 0;
+    __syncthreads();
+    for (int64_t c = c0 + threadIdx.x; c < c1; c += blockDim.x) atomicAdd(&h[bin_of(b.cand_lb[c], thr)], 1);
+    __syncthreads();
+    for (int t = threadIdx.x; t < kBins; t += blockDim.x)
+        if (h[t]) h[t] = atomicAdd(&st->bin_off[t], h[t]);
+    __syncthreads();
+    for (int64_t c = c0 + threadIdx.x; c < c1; c += blockDim.x) {
+        const float lb = b.cand_lb[c];
+        const int pos = atomicAdd(&h[bin_of(lb, thr)], 1);
         b.sort_lb[pos] = lb;
         b.sort_idx[pos] = b.cand_idx[c];
     }

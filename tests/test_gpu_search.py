@@ -103,6 +103,29 @@ def test_constant_windows_and_query():
         _close(dist, od, 64)
 
 
+def _band_cells(m, r):
+    """Cells of the band |i - j| <= r inside [0, m)^2, by enumeration."""
+    i = np.arange(m)[:, None]
+    return int(np.count_nonzero(np.abs(i - np.arange(m)[None, :]) <= min(r, m - 1)))
+
+
+@pytest.mark.parametrize("m,r", [(40, 0), (40, 7), (40, 8), (64, 33), (100, 99), (96, 40)])
+def test_cell_counter_without_pruning(m, r):
+    """With k equal to the number of windows nothing is pruned or abandoned,
+    so every DTW walks its whole band: the cell counter (closed form per
+    walk) is the walks started times the band's cell count."""
+    x = synth.random_walk(m + 40, 60 + m + r)  # 41 windows: k <= 64
+    q, _ = synth.noisy_copy(x, m, 61, 62)
+    N = x.size - m + 1
+    with dtws.Index(x) as ix:
+        idx, _ = ix.query(q, r, N)
+        assert ix.sync_status() == dtws.DTWS_OK
+        st = ix.last_stats()
+    assert sorted(idx.tolist()) == list(range(N))
+    assert st["dtw_abandoned"] == 0
+    assert st["dtw_cells"] == st["dtw_started"] * _band_cells(m, r)
+
+
 def test_k_equals_all_windows_and_m_equals_n():
     x = synth.random_walk(300, 8)
     q, _ = synth.noisy_copy(x, 250, 9, 10, noise=0.5)

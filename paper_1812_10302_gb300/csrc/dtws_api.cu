@@ -62,6 +62,8 @@ struct LearnEntry {
     int64_t used = 0, version = 0, rows = 0, rows2 = 0;
     void *E = nullptr;   // BF16 [rows][64]: windows at offsets j*b
     void *E2 = nullptr;  // BF16 [rows2][64]: windows at offsets j*b + b/2 (b >= 2)
+    void *Q = nullptr, *Q2 = nullptr;    // their int8 copies for the scan
+    float *S = nullptr, *S2 = nullptr;   // per int8 row: scale, squared norm (2 floats)
 };
 
 constexpr int kCacheSlots = 8;
@@ -279,8 +281,8 @@ cudaError_t need(T **p, size_t count) {
 }
 
 void free_learn(LearnEntry &e) {
-    cudaFree(e.E);
-    if (e.E2) cudaFree(e.E2);
+    for (void *p : {e.E, e.E2, e.Q, e.Q2, (void *)e.S, (void *)e.S2})
+        if (p) cudaFree(p);
     e = LearnEntry();
 }
 
@@ -330,20 +332,32 @@ dtws_status get_learn(dtws_t h, int m, const StatsEntry *se, cudaStream_t s, Lea
     e.rows = enc_rows(h, m);
     e.rows2 = enc_rows2(h, m);
     uint16_t *E = nullptr, *E2 = nullptr;
-    if (dalloc(&E, (size_t)e.rows * 64) != cudaSuccess ||
-        (e.rows2 > 0 && dalloc(&E2, (size_t)e.rows2 * 64) != cudaSuccess)) {
+    int8_t *Q = nullptr, *Q2 = nullptr;
+    float *S = nullptr, *S2 = nullptr;
+    bool ok = dalloc(&E, (size_t)e.rows * 64) == cudaSuccess && dalloc(&Q, (size_t)e.rows * 64) == cudaSuccess &&
+              dalloc(&S, (size_t)e.rows * 2) == cudaSuccess;
+    if (ok && e.rows2 > 0)
+        ok = dalloc(&E2, (size_t)e.rows2 * 64) == cudaSuccess && dalloc(&Q2, (size_t)e.rows2 * 64) == cudaSuccess &&
+             dalloc(&S2, (size_t)e.rows2 * 2) == cudaSuccess;
+    e.E = E;
+    e.E2 = E2;
+    e.Q = Q;
+    e.Q2 = Q2;
+    e.S = S;
+    e.S2 = S2;
+    if (!ok) {
         cudaGetLastError();
-        if (E) cudaFree(E);
+        free_learn(e);
         set_err("learned embeddings for m=%d: out of device memory", m);
         return DTWS_ENOMEM;
     }
-    e.E = E;
-    e.E2 = E2;
     CK(launch_enc_series(h->enc_blob, h->x, h->n, enc_block(m), se->inv_sigma, e.rows, e.E, h->num_sms, s));
+    CK(launch_enc_quant(e.E, e.rows, e.Q, e.S, s));
     if (e.rows2 > 0) {  // the same pass over the series shifted by the phase
         const int ph = enc_phase(m);
         CK(launch_enc_series(h->enc_blob, h->x + ph, h->n - ph, enc_block(m), se->inv_sigma + ph, e.rows2, e.E2,
                              h->num_sms, s));
+        CK(launch_enc_quant(e.E2, e.rows2, e.Q2, e.S2, s));
     }
     e.used = ++h->clock;
     h->learn.push_back(e);
@@ -491,9 +505,9 @@ dtws_status enqueue_search(dtws_t h, const Exec &e, const QueryArgs &a, const fl
     if (P > 0 && e.le) {
         int c0 = 0, c1 = 0;
         CK(launch_enc_query(h->enc_blob, b, a, s));
-        CK(launch_learn_scan(b, e.le->E, e.le->rows, enc_block(m), 0, 0, &c0, s));
+        CK(launch_learn_scan(b, e.le->Q, e.le->S, e.le->rows, enc_block(m), 0, 0, &c0, s));
         if (e.le->rows2 > 0) {
-            CK(launch_learn_scan(b, e.le->E2, e.le->rows2, enc_block(m), enc_phase(m), 1, &c1, s));
+            CK(launch_learn_scan(b, e.le->Q2, e.le->S2, e.le->rows2, enc_block(m), enc_phase(m), 1, &c1, s));
             ++launches;
         }
         CK(launch_prop_merge(b, c0, c1, P, s));

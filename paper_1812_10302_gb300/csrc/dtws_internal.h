@@ -99,8 +99,10 @@ cudaError_t launch_enc_series(const uint8_t *blob, const float *x, int64_t n, in
                               int64_t Nw, void *E, int num_sms, cudaStream_t s);
 cudaError_t launch_enc_query(const uint8_t *blob, const QueryBufs &b, const QueryArgs &a, cudaStream_t s);
 // windows at offsets j*stride + phase (j < Nw)
-cudaError_t launch_learn_scan(const QueryBufs &b, const void *E, int64_t Nw, int stride, int phase, int slot,
-                              int *ctas, cudaStream_t s);
+// int8 copy of BF16 embeddings for the scan: Q [rows][64], S [rows] = (scale, squared norm) as float2
+cudaError_t launch_enc_quant(const void *E, int64_t rows, void *Q, void *S, cudaStream_t s);
+cudaError_t launch_learn_scan(const QueryBufs &b, const void *Q, const void *S, int64_t Nw, int stride,
+                              int phase, int slot, int *ctas, cudaStream_t s);
 cudaError_t launch_prop_merge(const QueryBufs &b, int ctas0, int ctas1, int proposals, cudaStream_t s);
 cudaError_t launch_bf16_to_f32(const void *src, int64_t count, float *dst, cudaStream_t s);
 

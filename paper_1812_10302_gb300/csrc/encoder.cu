@@ -672,46 +672,116 @@ __global__ void __launch_bounds__(kSeqThreads) k_query_embed(const uint8_t *blob
     for (int i = threadIdx.x; i < DIM; i += blockDim.x) bq.st->e_q[i] = reinterpret_cast<const float *>(sm + SeqSmem::E)[i];
 }
 
-// Score every window at stride b by |e_q - E[j]|^2 (8 lanes per window, 8
-// dimensions each).  Each warp scans one contiguous segment of the windows
-// with eight 16-byte loads in flight per lane; each CTA writes its best
-// window (one barrier, at the end) to its slot for the proposal merge.
+// Per-row int8 copy of the embeddings for the scan: q = round(e * 127 / max|e|)
+// with the row's scale s = max|e| / 127 (q = 0, s = 0 for an all-zero row),
+// and the squared norm of the quantised row, s^2 * sum q^2: S[row] = (s, norm).
+// Eight lanes per row (8 values each), the row maximum by shuffles.
+__global__ void k_quant_rows(const bf16 *__restrict__ E, int64_t rows, int8_t *__restrict__ Q,
+                             float2 *__restrict__ S) {
+    const int lane = threadIdx.x & 31, sub = lane & 7;
+    const int64_t gw = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = (gridDim.x * (int64_t)blockDim.x) >> 5;
+    for (int64_t r0 = gw * 4; r0 < rows; r0 += nw * 4) {  // four rows per warp, warp-uniform
+        const int64_t r = r0 + (lane >> 3);
+        float v[8];
+        float mx = 0.0f;
+        if (r < rows) {
+            const uint4 raw = *reinterpret_cast<const uint4 *>(E + r * DIM + sub * 8);
+            const bf16 *h = reinterpret_cast<const bf16 *>(&raw);
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                v[k] = __bfloat162float(h[k]);
+                mx = fmaxf(mx, fabsf(v[k]));
+            }
+        } else {
+#pragma unroll
+            for (int k = 0; k < 8; ++k) v[k] = 0.0f;
+        }
+#pragma unroll
+        for (int o = 1; o < 8; o <<= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        const float inv = mx > 0.0f ? 127.0f / mx : 0.0f;
+        unsigned w[2] = {0u, 0u};
+        int q2 = 0;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            const int q = max(-127, min(127, __float2int_rn(v[k] * inv)));
+            q2 += q * q;
+            w[k >> 2] |= (unsigned)(q & 0xff) << (8 * (k & 3));
+        }
+#pragma unroll
+        for (int o = 1; o < 8; o <<= 1) q2 += __shfl_xor_sync(0xffffffffu, q2, o);
+        if (r < rows) {
+            *reinterpret_cast<uint2 *>(Q + r * DIM + sub * 8) = make_uint2(w[0], w[1]);
+            if (sub == 0) {
+                const float sc = mx * (1.0f / 127.0f);
+                S[r] = make_float2(sc, sc * sc * (float)q2);
+            }
+        }
+    }
+}
+
+// Score every window at stride b by |e_q - s_j v_j|^2, v_j, s_j the row's
+// int8 embedding and scale, expanded as |e_q|^2 - 2 s_j s_q (e8 . v_j) +
+// s_j^2 |v_j|^2 with e8, s_q the query embedding quantised the same way:
+// the dot product of two int8 vectors in four DP4A instructions per lane
+// (4 lanes per window, 16 dimensions each), |v_j|^2 stored with the row.
+// The expansion cancels for near matches (a few 1e-3 of |e_q|^2), which
+// only perturbs the order among the closest windows; negative results are
+// clamped to 0.  Each warp scans one contiguous segment of the windows with
+// eight 16-byte loads in flight per lane; each CTA writes its best window
+// (one barrier, at the end) to its slot for the proposal merge.
 constexpr int kLsThreads = 256, kLsU = 8;
-__global__ void __launch_bounds__(kLsThreads) k_learn_scan(QueryBufs bq, const bf16 *E, int64_t Nw, int b,
-                                                           int phase, int slot, int64_t seg) {
+__global__ void __launch_bounds__(kLsThreads) k_learn_scan(QueryBufs bq, const int8_t *Q, const float2 *S,
+                                                           int64_t Nw, int b, int phase, int slot, int64_t seg) {
     __shared__ unsigned long long wbest[kLsThreads / 32];
     QueryState *st = bq.st;
     if (!st->valid) return;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, sub = lane & 7, grp = lane >> 3;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, sub = lane & 3, grp = lane >> 2;
     const int64_t gwarp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-    float eq[8];
+    // the query's embedding: |e_q|^2, its int8 copy (this lane's 16 values)
+    float qn = 0.0f, qmx = 0.0f;
+    for (int i = 0; i < DIM; ++i) {
+        const float e = st->e_q[i];
+        qn = fmaf(e, e, qn);
+        qmx = fmaxf(qmx, fabsf(e));
+    }
+    const float qinv = qmx > 0.0f ? 127.0f / qmx : 0.0f, two_sq = 2.0f * qmx * (1.0f / 127.0f);
+    int e8[4];
 #pragma unroll
-    for (int i = 0; i < 8; ++i) eq[i] = st->e_q[sub * 8 + i];
+    for (int wi = 0; wi < 4; ++wi) {
+        unsigned wd = 0;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int q = max(-127, min(127, __float2int_rn(st->e_q[sub * 16 + wi * 4 + k] * qinv)));
+            wd |= (unsigned)(q & 0xff) << (8 * k);
+        }
+        e8[wi] = (int)wd;
+    }
     const int64_t lo = gwarp * seg, hi = lo + seg < Nw ? lo + seg : Nw;
     unsigned long long mine = ~0ull;
     // every lane runs the same number of steps (the shuffles below need the whole warp)
-    for (int64_t base = lo; base < hi; base += 4 * kLsU) {
+    for (int64_t base = lo; base < hi; base += 8 * kLsU) {
         const int64_t j0 = base + grp;
         uint4 v[kLsU];
+        float2 sn[kLsU];  // (scale, norm) of the row, loaded with it
 #pragma unroll
         for (int u = 0; u < kLsU; ++u) {
-            const int64_t j = j0 + 4 * u;
-            v[u] = j < hi ? *reinterpret_cast<const uint4 *>(E + j * DIM + sub * 8) : make_uint4(0, 0, 0, 0);
+            const int64_t j = j0 + 8 * u;
+            const bool in = j < hi;
+            v[u] = in ? *reinterpret_cast<const uint4 *>(Q + j * DIM + sub * 16) : make_uint4(0, 0, 0, 0);
+            sn[u] = in && sub == 0 ? S[j] : make_float2(0.0f, 0.0f);
         }
 #pragma unroll
         for (int u = 0; u < kLsU; ++u) {
-            const int64_t j = j0 + 4 * u;
-            const bf16 *h = reinterpret_cast<const bf16 *>(&v[u]);
-            float s = 0.0f;
-#pragma unroll
-            for (int i = 0; i < 8; ++i) {
-                const float d = eq[i] - __bfloat162float(h[i]);
-                s = fmaf(d, d, s);
-            }
-            s += __shfl_xor_sync(0xffffffffu, s, 1);
-            s += __shfl_xor_sync(0xffffffffu, s, 2);
-            s += __shfl_xor_sync(0xffffffffu, s, 4);
+            const int64_t j = j0 + 8 * u;
+            int dot = __dp4a((int)v[u].x, e8[0], 0);
+            dot = __dp4a((int)v[u].y, e8[1], dot);
+            dot = __dp4a((int)v[u].z, e8[2], dot);
+            dot = __dp4a((int)v[u].w, e8[3], dot);
+            dot += __shfl_xor_sync(0xffffffffu, dot, 1);
+            dot += __shfl_xor_sync(0xffffffffu, dot, 2);
             if (j < hi && sub == 0) {
+                const float s = fmaxf(0.0f, fmaf(-two_sq * sn[u].x, (float)dot, qn + sn[u].y));
                 const unsigned long long k = make_key(s, (unsigned)(j * b + phase));
                 mine = k < mine ? k : mine;
             }
@@ -811,8 +881,17 @@ cudaError_t launch_bf16_to_f32(const void *src, int64_t count, float *dst, cudaS
     return cudaGetLastError();
 }
 
-cudaError_t launch_learn_scan(const QueryBufs &b, const void *E, int64_t Nw, int stride, int phase, int slot,
-                              int *ctas, cudaStream_t s) {
+cudaError_t launch_enc_quant(const void *E, int64_t rows, void *Q, void *S, cudaStream_t s) {
+    if (rows <= 0) return cudaSuccess;
+    int64_t blocks = (rows * 8 + 255) / 256;
+    if (blocks > 4096) blocks = 4096;
+    enc::k_quant_rows<<<(unsigned)blocks, 256, 0, s>>>(reinterpret_cast<const enc::bf16 *>(E), rows,
+                                                       reinterpret_cast<int8_t *>(Q), reinterpret_cast<float2 *>(S));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_learn_scan(const QueryBufs &b, const void *Q, const void *S, int64_t Nw, int stride,
+                              int phase, int slot, int *ctas, cudaStream_t s) {
     // one wave: as many CTAs as are resident at once, each warp a segment of
     // >= 256 windows (a second wave would leave the first wave's SMs idle)
     int per_sm = 0;
@@ -829,7 +908,8 @@ cudaError_t launch_learn_scan(const QueryBufs &b, const void *E, int64_t Nw, int
     if (grid < 1) grid = 1;
     const int64_t warps = grid * (enc::kLsThreads / 32);
     const int64_t seg = ((Nw + warps - 1) / warps + 31) / 32 * 32;
-    enc::k_learn_scan<<<(unsigned)grid, enc::kLsThreads, 0, s>>>(b, reinterpret_cast<const enc::bf16 *>(E), Nw,
+    enc::k_learn_scan<<<(unsigned)grid, enc::kLsThreads, 0, s>>>(b, reinterpret_cast<const int8_t *>(Q),
+                                                                 reinterpret_cast<const float2 *>(S), Nw,
                                                                  stride, phase, slot, seg);
     *ctas = (int)grid;
     return cudaGetLastError();

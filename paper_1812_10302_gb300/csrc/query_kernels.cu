@@ -565,29 +565,40 @@ cudaError_t launch_seed_scan(const QueryBufs &b, const QueryArgs &a, int proposa
 // ctas1-1), ascending.  The CTAs cover disjoint windows, so the keys other
 // than the empty key are distinct: each key's rank is the number of keys
 // below it, and a key of rank < proposals goes to that slot (the list was
-// emptied by the query reset; empty keys are not written).
-__global__ void __launch_bounds__(1024) k_prop_merge(QueryBufs b, int n0, int n1, int proposals) {
-    __shared__ unsigned long long keys[2 * kCtaSlots];
+// emptied by the query reset; empty keys are not written).  128 keys per
+// CTA (one per thread), each CTA with its own copy of all the keys in shared
+// memory, eight keys per step in four independent 16-byte loads.
+constexpr int kMergeThreads = 128;
+__global__ void __launch_bounds__(kMergeThreads) k_prop_merge(QueryBufs b, int n0, int n1, int proposals) {
+    __shared__ __align__(16) unsigned long long keys[2 * kCtaSlots + 8];
     QueryState *st = b.st;
     if (!st->valid) return;
-    const int n = n0 + n1;
-    for (int t = threadIdx.x; t < n; t += blockDim.x)
-        keys[t] = t < n0 ? st->cta_best[t] : st->cta_best[kCtaSlots + (t - n0)];
+    const int n = n0 + n1, n8 = (n + 7) & ~7;
+    for (int t = threadIdx.x; t < n8; t += blockDim.x)
+        keys[t] = t < n0 ? st->cta_best[t] : (t < n ? st->cta_best[kCtaSlots + (t - n0)] : kEmptyKey);
     __syncthreads();
-    for (int t = threadIdx.x; t < n; t += blockDim.x) {
-        const unsigned long long k = keys[t];
-        if (k == kEmptyKey) continue;
-        int rank = 0;
-        for (int u = 0; u < n; ++u) rank += keys[u] < k;
-        if (rank < proposals) st->prop_keys[rank] = k;
+    const int t = blockIdx.x * kMergeThreads + threadIdx.x;
+    if (t >= n) return;
+    const unsigned long long k = keys[t];
+    if (k == kEmptyKey) return;
+    int r0 = 0, r1 = 0, r2 = 0, r3 = 0;
+    const ulonglong2 *k2 = reinterpret_cast<const ulonglong2 *>(keys);
+    for (int u = 0; u < n8 / 2; u += 4) {
+        const ulonglong2 a = k2[u], c = k2[u + 1], d = k2[u + 2], e = k2[u + 3];
+        r0 += (a.x < k) + (a.y < k);
+        r1 += (c.x < k) + (c.y < k);
+        r2 += (d.x < k) + (d.y < k);
+        r3 += (e.x < k) + (e.y < k);
     }
+    const int rank = r0 + r1 + r2 + r3;
+    if (rank < proposals) st->prop_keys[rank] = k;
 }
 
 cudaError_t launch_prop_merge(const QueryBufs &b, int ctas0, int ctas1, int proposals, cudaStream_t s) {
     if (proposals <= 0 || ctas0 + ctas1 <= 0) return cudaSuccess;
     if (ctas0 > kCtaSlots || ctas1 > kCtaSlots || proposals > kPropMax) return cudaErrorInvalidValue;
-    const int n = ctas0 + ctas1, threads = n < 1024 ? (n + 31) / 32 * 32 : 1024;
-    k_prop_merge<<<1, threads, 0, s>>>(b, ctas0, ctas1, proposals);
+    const int n = ctas0 + ctas1;
+    k_prop_merge<<<(n + kMergeThreads - 1) / kMergeThreads, kMergeThreads, 0, s>>>(b, ctas0, ctas1, proposals);
     return cudaGetLastError();
 }
 
@@ -606,57 +617,86 @@ __device__ __forceinline__ unsigned long long splitmix64(unsigned long long z) {
 // kProxyStride + 1 windows centred on it, since the proxy scan looked at
 // every kProxyStride-th window only.  Both lists hold distinct offsets: a repeated seed
 // would fill two of the k slots with one window.
-__device__ int distinct_append(unsigned *dst, int cap, const unsigned *src, int n, int lane, int *count) {
-    for (int base = 0; base < n; base += 32) {
-        const int t = base + lane;
+// Append the distinct values of src[0..n) (0xffffffff: none) to dst after
+// its first `start` entries, in first-occurrence order, up to cap entries in
+// all; returns the count.  Every thread of
+// the block takes elements t = threadIdx.x + c * blockDim.x and keeps t when
+// no earlier element equals it (the earlier elements are read in the same
+// order by all lanes: shared-memory broadcasts); the kept flags of a chunk
+// are placed by warp ballots and a prefix over the block's warps.
+__device__ int distinct_append(unsigned *dst, int cap, const unsigned *src, int n, int start, int *wcnt,
+                               int *total) {
+    const int lane = lane_id(), warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    if (threadIdx.x == 0) *total = start;
+    __syncthreads();
+    for (int c0 = 0; c0 < n; c0 += blockDim.x) {
+        const int t = c0 + threadIdx.x;
         bool keep = false;
-        if (t < n && src[t] != 0xffffffffu) {
-            keep = true;
-            for (int u = 0; u < t; ++u) keep &= src[u] != src[t];
+        unsigned v = 0xffffffffu;
+        if (t < n && (v = src[t]) != 0xffffffffu) {
+            // the earlier elements, four per 16-byte load (src is 16-byte
+            // aligned); the last group is checked element by element
+            const uint4 *s4 = reinterpret_cast<const uint4 *>(src);
+            const int full = t >> 2;
+            bool dup = false;
+            for (int g = 0; g < full; ++g) {
+                const uint4 q = s4[g];
+                dup |= (q.x == v) | (q.y == v) | (q.z == v) | (q.w == v);
+            }
+            for (int u = full << 2; u < t; ++u) dup |= src[u] == v;
+            keep = !dup;
         }
         const unsigned bal = __ballot_sync(0xffffffffu, keep);
-        const int pos = *count + __popc(bal & ((1u << lane) - 1u));
-        if (keep && pos < cap) dst[pos] = src[t];
-        __syncwarp();
-        if (lane == 0) *count += __popc(bal);
-        __syncwarp();
+        if (lane == 0) wcnt[warp] = __popc(bal);
+        __syncthreads();
+        if (threadIdx.x == 0) {  // exclusive prefix over the warps, then the chunk's total
+            int acc = *total;
+            for (int w = 0; w < nwarps; ++w) {
+                const int c = wcnt[w];
+                wcnt[w] = acc;
+                acc += c;
+            }
+            wcnt[nwarps] = acc;
+        }
+        __syncthreads();
+        const int pos = wcnt[warp] + __popc(bal & ((1u << lane) - 1u));
+        if (keep && pos < cap) dst[pos] = v;
+        __syncthreads();
+        if (threadIdx.x == 0) *total = wcnt[nwarps];
+        __syncthreads();
     }
-    return *count < cap ? *count : cap;
+    return *total < cap ? *total : cap;
 }
 
-__global__ void k_seed_gather(QueryBufs b, QueryArgs a, int n_random, int proposals, int H,
-                              unsigned long long rng) {
-    __shared__ unsigned cand[kEdMax];
-    __shared__ int nc;
+__global__ void __launch_bounds__(1024) k_seed_gather(QueryBufs b, QueryArgs a, int n_random, int proposals, int H,
+                                                      unsigned long long rng) {
+    __shared__ __align__(16) unsigned cand[kEdMax];
+    __shared__ int wcnt[33], total;
     if (!b.st->valid) return;
-    const int lane = threadIdx.x;  // one warp
     // exact-DTW seeds: random windows + proposals
-    for (int j = lane; j < n_random; j += 32)
+    for (int j = threadIdx.x; j < n_random; j += blockDim.x)
         cand[j] = (unsigned)(splitmix64(rng + (unsigned long long)j) % (unsigned long long)a.N);
-    for (int p = lane; p < proposals; p += 32) {
+    for (int p = threadIdx.x; p < proposals; p += blockDim.x) {
         const unsigned long long key = b.st->prop_keys[p];
         cand[n_random + p] = key != kEmptyKey ? key_idx(key) : 0xffffffffu;
     }
-    if (lane == 0) nc = 0;
-    __syncwarp();
-    const int ns = distinct_append(b.st->seed_off, kSeedMax, cand, n_random + proposals, lane, &nc);
+    __syncthreads();
+    const int ns = distinct_append(b.st->seed_off, kSeedMax, cand, n_random + proposals, 0, wcnt, &total);
     // Euclidean seeds: random windows + neighbourhoods of the proposals
-    for (int p = lane; p < proposals; p += 32) {
+    const int span = 2 * H + 1;
+    for (int e = threadIdx.x; e < proposals * span; e += blockDim.x) {
+        const int p = e / span, d = e - p * span - H;
         const unsigned long long key = b.st->prop_keys[p];
-        for (int d = -H; d <= H; ++d) {
-            unsigned o = 0xffffffffu;
-            if (key != kEmptyKey) {
-                const long long v = (long long)key_idx(key) + d;
-                if (v >= 0 && v < a.N) o = (unsigned)v;
-            }
-            cand[n_random + p * (2 * H + 1) + (d + H)] = o;
+        unsigned o = 0xffffffffu;
+        if (key != kEmptyKey) {
+            const long long v = (long long)key_idx(key) + d;
+            if (v >= 0 && v < a.N) o = (unsigned)v;
         }
+        cand[n_random + e] = o;
     }
-    __syncwarp();
-    if (lane == 0) nc = 0;
-    __syncwarp();
-    const int ne = distinct_append(b.st->ed_off, kEdMax, cand, n_random + proposals * (2 * H + 1), lane, &nc);
-    if (lane == 0) {
+    __syncthreads();
+    const int ne = distinct_append(b.st->ed_off, kEdMax, cand, n_random + proposals * span, 0, wcnt, &total);
+    if (threadIdx.x == 0) {
         b.st->n_seeds = a.k > 1 ? ns : 0;  // exact seeds only pay off for k > 1
         b.st->n_ed = ne;
         b.st->work = 0;
@@ -689,8 +729,8 @@ __global__ void k_seed_ed(QueryBufs b, QueryArgs a) {
 // shifts), so the offsets within +-k of the two best Euclidean seeds join
 // the exact-DTW seeds (one warp).
 __global__ void k_seed_expand(QueryBufs b, QueryArgs a) {
-    __shared__ unsigned cand[2 * (2 * kKMax + 1)];
-    __shared__ int nc;
+    __shared__ __align__(16) unsigned cand[2 * (2 * kKMax + 1)];
+    __shared__ int wcnt[33], total;
     QueryState *st = b.st;
     if (!st->valid || a.k < 2) return;
     const int lane = threadIdx.x;
@@ -711,9 +751,8 @@ __global__ void k_seed_expand(QueryBufs b, QueryArgs a) {
     for (int t = lane; t < 2 * W; t += 32)  // drop offsets that are seeds already
         for (int u = 0; u < have; ++u)
             if (cand[t] == st->seed_off[u]) cand[t] = 0xffffffffu;
-    if (lane == 0) nc = have;
     __syncwarp();
-    const int ns = distinct_append(st->seed_off, kSeedMax, cand, 2 * W, lane, &nc);
+    const int ns = distinct_append(st->seed_off, kSeedMax, cand, 2 * W, have, wcnt, &total);
     if (lane == 0) st->n_seeds = ns;
 }
 
@@ -729,7 +768,10 @@ cudaError_t launch_seed_ed(const QueryBufs &b, const QueryArgs &a, cudaStream_t 
 
 cudaError_t launch_seed_gather(const QueryBufs &b, const QueryArgs &a, int n_random, int proposals,
                                int half, unsigned long long rng, cudaStream_t s) {
-    k_seed_gather<<<1, 32, 0, s>>>(b, a, n_random, proposals, half, rng);
+    // one block: the distinctness test is O(n^2) over n <= kEdMax candidates
+    const int n = n_random + proposals * (2 * half + 1);
+    const int threads = n < 1024 ? (n < 32 ? 32 : (n + 31) / 32 * 32) : 1024;
+    k_seed_gather<<<1, threads, 0, s>>>(b, a, n_random, proposals, half, rng);
     return cudaGetLastError();
 }
 

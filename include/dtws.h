@@ -95,10 +95,13 @@ typedef struct {
     int32_t batch_lanes;    /* dtws_query_batch: queries in flight at once, each
                                lane with its own buffers and streams (1..16,
                                default 4; fewer when memory is short) */
-    int32_t batch_graph;    /* 1 (default): dtws_query_batch captures the batch
-                               into a CUDA graph once and replays it for later
-                               calls with the same arguments (not with the
-                               learned ordering) */
+    int32_t batch_graph;    /* 1 (default): repeated calls replay CUDA graphs.
+                               dtws_query_batch captures the batch into a
+                               graph once and replays it for later calls with
+                               the same arguments (not with the learned
+                               ordering); dtws_query does the same for one
+                               query (not while timing is on).  The query
+                               values may change between replays. */
     int64_t wait_limit_ns;  /* bound on every device-side wait, default 2e9 */
     uint64_t rng_seed;      /* seed of the random seed windows, default 0 */
 } dtws_options;

@@ -137,6 +137,9 @@ struct dtws_ctx {
     cudaStream_t cap_stream = nullptr;  // captures a batch (the caller's stream may be the legacy one)
     cudaGraphExec_t graph_exec = nullptr;
     std::vector<int64_t> graph_sig;  // what the cached graph was captured for
+    cudaGraphExec_t qgraph_exec = nullptr;  // the same for single queries
+    std::vector<int64_t> qgraph_sig;
+    int64_t qgraph_launches = 0;
     // learned proposal encoder
     uint8_t *enc_blob = nullptr;
     int64_t enc_version = 0;  // 0: no encoder installed
@@ -391,6 +394,7 @@ dtws_status ensure_candidates(dtws_t h) {
 
 QueryBufs make_bufs(dtws_t h, const StatsEntry *se, const EnvEntry *ee) {
     QueryBufs b;
+    memset(&b, 0, sizeof b);  // padding included: the bytes enter graph signatures
     b.st = h->st;
     b.x = h->x;
     b.mu_hi = se ? se->mu_hi : nullptr;
@@ -424,6 +428,7 @@ QueryBufs make_bufs(dtws_t h, const StatsEntry *se, const EnvEntry *ee) {
 
 QueryArgs make_args(dtws_t h, int m, int r, int k) {
     QueryArgs a;
+    memset(&a, 0, sizeof a);  // padding included: the bytes enter graph signatures
     a.N = h->n - m + 1;
     a.m = m;
     a.r = r > m - 1 ? m - 1 : r;
@@ -468,6 +473,14 @@ dtws_status check_query_args(dtws_t h, const float *Q, int32_t m, int32_t r, int
         }
     }
     return DTWS_OK;
+}
+
+// Append the bytes of a trivially copyable value to a signature.
+template <typename T>
+void sig_push(std::vector<int64_t> &sig, const T &v) {
+    int64_t w[(sizeof(T) + 7) / 8] = {};
+    memcpy(w, &v, sizeof(T));
+    sig.insert(sig.end(), w, w + (sizeof(T) + 7) / 8);
 }
 
 void record(dtws_t h, int i, cudaStream_t s) {
@@ -577,7 +590,56 @@ dtws_status run_query(dtws_t h, const float *Qd, int m, int r, int k, int64_t *i
     Exec e{make_bufs(h, se, ee), s, h->side, h->ev_fork, h->ev_join, le, true};
     const QueryArgs a = make_args(h, m, r, k);
     int64_t launches = 0;
-    if ((st = enqueue_search(h, e, a, Qd, idx_d, dist_d, &launches)) != DTWS_OK) return st;
+    // Repeated queries with the same arguments replay one CUDA graph of the
+    // search (the caches above are resolved first, on the caller's stream;
+    // no phase events are recorded in a graph).  The signature holds every
+    // value the captured kernels' arguments depend on.
+    const bool graph = h->opt.batch_graph && !h->opt.timing;
+    std::vector<int64_t> sig;
+    if (graph) {
+        sig = {(int64_t)(intptr_t)Qd, (int64_t)(intptr_t)idx_d, (int64_t)(intptr_t)dist_d,
+               (int64_t)(intptr_t)le, le ? le->version : 0};
+        sig_push(sig, h->opt);
+        sig_push(sig, e.b);
+        sig_push(sig, a);
+        if (h->qgraph_exec && sig == h->qgraph_sig) {
+            CK(cudaGraphLaunch(h->qgraph_exec, s));
+            launches = h->qgraph_launches;
+        } else {
+            if (!h->cap_stream) CK(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
+            if (!h->batch_fork) CK(cudaEventCreateWithFlags(&h->batch_fork, cudaEventDisableTiming));
+            // the capture stream starts after the caller's stream (the caches'
+            // kernels); the graph itself is launched on the caller's stream
+            CK(cudaEventRecord(h->batch_fork, s));
+            CK(cudaStreamWaitEvent(h->cap_stream, h->batch_fork, 0));
+            CK(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
+            Exec ec = e;
+            ec.s = h->cap_stream;
+            st = enqueue_search(h, ec, a, Qd, idx_d, dist_d, &launches);
+            cudaGraph_t g = nullptr;
+            const cudaError_t ce = cudaStreamEndCapture(h->cap_stream, &g);
+            if (st != DTWS_OK || ce != cudaSuccess) {
+                if (g) cudaGraphDestroy(g);
+                cudaGetLastError();
+                if (st != DTWS_OK) return st;
+                set_err("query graph capture: %s", cudaGetErrorString(ce));
+                return DTWS_ECUDA;
+            }
+            if (h->qgraph_exec) cudaGraphExecDestroy(h->qgraph_exec);
+            h->qgraph_exec = nullptr;
+            h->qgraph_sig.clear();
+            cudaGraphExec_t ex = nullptr;
+            const cudaError_t ie = cudaGraphInstantiate(&ex, g, 0);
+            cudaGraphDestroy(g);
+            CK(ie);
+            h->qgraph_exec = ex;
+            h->qgraph_sig = sig;
+            h->qgraph_launches = launches;
+            CK(cudaGraphLaunch(ex, s));
+        }
+    } else if ((st = enqueue_search(h, e, a, Qd, idx_d, dist_d, &launches)) != DTWS_OK) {
+        return st;
+    }
     h->last_stream = s;
     h->have_last = true;
     h->last_N = a.N;
@@ -604,7 +666,11 @@ void drop_graph(dtws_t h) {
     if (h->graph_exec) cudaGraphExecDestroy(h->graph_exec);
     h->graph_exec = nullptr;
     h->graph_sig.clear();
+    if (h->qgraph_exec) cudaGraphExecDestroy(h->qgraph_exec);
+    h->qgraph_exec = nullptr;
+    h->qgraph_sig.clear();
 }
+
 
 // Lanes with statistics slots for windows of at least m_min samples.
 dtws_status ensure_lanes(dtws_t h, int count, int m_min) {

@@ -215,6 +215,32 @@ def test_device_outputs_and_repeatability(walk, index):
     np.testing.assert_array_equal(hi, outs[0][0])
 
 
+def test_query_graph_replay_reads_new_values(walk):
+    """Repeated queries with the same arguments replay a captured CUDA graph:
+    new values in the same query and output buffers give the new query's
+    answer, and the graph-free path (batch_graph = 0) agrees."""
+    import torch
+    m, r, k = 256, 25, 3
+    qd = torch.empty(m, dtype=torch.float32, device="cuda")
+    idx = torch.empty(k, dtype=torch.int64, device="cuda")
+    dist = torch.empty(k, dtype=torch.float32, device="cuda")
+    with dtws.Index(walk) as ix:
+        for t in range(4):
+            q, _ = synth.noisy_copy(walk, m, 70 + t, 80 + t, noise=0.3)
+            qd.copy_(torch.from_numpy(q))
+            ix.query(qd, r, k, out=(idx, dist))
+            assert ix.sync_status() == dtws.DTWS_OK
+            gi, gd = idx.cpu().numpy(), dist.cpu().numpy()
+            oi, od = fragments.search_fragments(walk, q, r, k)
+            np.testing.assert_array_equal(gi, oi)
+            _close(gd, od, m)
+            ix.set_options(batch_graph=0)
+            ix.query(qd, r, k, out=(idx, dist))
+            np.testing.assert_array_equal(idx.cpu().numpy(), gi)
+            np.testing.assert_array_equal(dist.cpu().numpy(), gd)
+            ix.set_options(batch_graph=1)
+
+
 def test_stats_counters(walk, index):
     q, _ = synth.noisy_copy(walk, 128, 60, 61, noise=0.1)
     index.set_options(timing=1)

@@ -198,11 +198,26 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, unsigned parity) {
         : "memory");
     return ok != 0;
 }
-// Wait for phase `parity` of the barrier for at most limit_ns; false on timeout.
+// try_wait with a suspend-time hint: the thread sleeps in hardware until the
+// phase completes or about hint_ns pass, instead of polling
+__device__ __forceinline__ bool mbar_try_wait_sleep(uint64_t *bar, unsigned parity, unsigned hint_ns) {
+    unsigned ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity), "r"(hint_ns)
+        : "memory");
+    return ok != 0;
+}
+// Wait for phase `parity` of the barrier for at most limit_ns; false on
+// timeout.  The retries sleep (at most 20 us each), so a waiting warp takes
+// almost no issue slots from the warps that have work.
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, unsigned parity, long long limit_ns) {
     if (mbar_try_wait(bar, parity)) return true;
     long long t0 = global_ns();
-    while (!mbar_try_wait(bar, parity)) {
+    while (!mbar_try_wait_sleep(bar, parity, 20000u)) {
         if (global_ns() - t0 > limit_ns) return false;
     }
     return true;

@@ -60,6 +60,10 @@ SPECS = {
     "learn20m": dict(n=20_000_000, m=1024, w=0.10, k=1),
     # the learned-proposal workload's series itself (2e8 samples), its first query
     "learn200m": dict(n=200_000_000, m=1024, w=0.10, k=1),
+    # wide bands (r = 0.9 m, the regime of the paper's experiments) on 2e7 samples of the
+    # same kind: the anti-diagonal kernel (r <= 511) and the row-systolic one (r > 511)
+    "wide512": dict(n=20_000_000, m=512, w=0.90, k=1),
+    "wide1024": dict(n=20_000_000, m=1024, w=0.90, k=1),
 }
 
 
@@ -144,12 +148,12 @@ def make_workload(name: str, rank: int = 0, world: int = 1):
     def frag(k):
         if name in ("rw100m", "rw30m"):
             return synth.walk_with_bursts(n, 0 + 101 * k, 3 + 101 * k, 5 + 101 * k)
-        if name in ("learn20m", "learn200m"):
+        if name in ("learn20m", "learn200m", "wide512", "wide1024"):
             return synth.walk_with_bursts(n, 4 + 101 * k, 4 + 101 * k, 6 + 101 * k)
         return synth.random_walk(n, 101 * k)
 
     x = frag(rank)
-    if name in ("learn20m", "learn200m"):
+    if name in ("learn20m", "learn200m", "wide512", "wide1024"):
         qs, offs = synth.fixed_queries(frag(0) if rank != 0 else x, 1, m, 9)
         q, o = qs[0], offs[0]
     else:
@@ -334,7 +338,7 @@ def gpu_arm(args):
 
     hbm, peak_kind = load_peaks()
     lb_ms = float(phases[2])
-    lb_bytes = N * 16 + st["pass_keogh_s"] * 8
+    lb_bytes = N * 16 + st["pass_keogh_q"] * 8  # the scan writes (bound, offset) per survivor
     achieved = lb_bytes / (lb_ms * 1e-3) / 1e9 if lb_ms > 0 else None
     cpu = None
     if not args.no_cpu_baseline and world == 1 or (not args.no_cpu_baseline and rank == 0 and world == 1):

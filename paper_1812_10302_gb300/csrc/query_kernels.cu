@@ -1188,7 +1188,8 @@ __global__ void __launch_bounds__(256) k_dtw(QueryBufs b, QueryArgs a, const int
 
 // Re-score: per window two-pass FP64 statistics (Eq. 5), the normalised
 // values formed in FP64, and the banded DTW in double-float arithmetic
-// (about 48 significant bits; FP64 itself for bands wider than kDiagRMax).
+// (about 48 significant bits; FP64 itself, on the row-systolic kernel, where
+// the multi-warp walk k_dtw64_mw does not apply or fit).
 // No pruning.  Candidates: the margin list (offsets == null) or offsets.
 template <int L, int K>
 __global__ void __launch_bounds__(256) k_dtw64(QueryBufs b, QueryArgs a, const int64_t *offsets,
@@ -1486,7 +1487,7 @@ static cudaError_t dtw64_mw_launch(const QueryBufs &b, const QueryArgs &a, const
     const size_t hard = (size_t)200 * 1024;
     int groups = 8 / W;
     while (groups > 1 && bytes * (size_t)(1 + groups) > hard) --groups;
-    if (bytes * (size_t)(1 + groups) > hard) return cudaErrorInvalidValue;
+    if (bytes * (size_t)(1 + groups) > hard) return cudaErrorNotSupported;  // the caller falls back
     const size_t smem = bytes * (size_t)(1 + groups);
     int64_t want = (count_for_grid + groups - 1) / groups;
     const int64_t cap = (int64_t)b.num_sms * 4;
@@ -1504,14 +1505,26 @@ static cudaError_t dtw64_dispatch(const QueryBufs &b, const QueryArgs &a, const 
     if (!plan_dtw<double>(a.m, a.r, false, &p)) return cudaErrorInvalidValue;
     // anti-diagonal with more than one cell per lane of a warp: the
     // multi-warp walk (the same arithmetic, the same result)
+    cudaError_t mw = cudaErrorNotSupported;
     if (p.L == 32 && p.K >= 2) {
 #define DTWS_MW(KK)                                                                                       \
         if (p.K == KK)                                                                                     \
-            return dtw64_mw_launch<PreShape<32, KK>::W, PreShape<32, KK>::K2>(b, a, offsets, count, out,  \
-                                                                               count_for_grid, s);
+            mw = dtw64_mw_launch<PreShape<32, KK>::W, PreShape<32, KK>::K2>(b, a, offsets, count, out,    \
+                                                                             count_for_grid, s);
         DTWS_MW(2) DTWS_MW(3) DTWS_MW(4) DTWS_MW(6) DTWS_MW(8) DTWS_MW(10) DTWS_MW(12) DTWS_MW(16)
 #undef DTWS_MW
+    } else if (a.r > kDiagRMax && a.r < 4 * 32 * 16) {
+        // bands past the one-warp walks (r > 511, up to 2047): the double-float
+        // walk over four warps with up to 16 cells per lane, instead of FP64
+        // arithmetic, which this part issues at a small fraction of its FP32 rate
+        const int k2 = (a.r + 1 + 127) / 128;
+        if (k2 <= 6) mw = dtw64_mw_launch<4, 6>(b, a, offsets, count, out, count_for_grid, s);
+        else if (k2 <= 8) mw = dtw64_mw_launch<4, 8>(b, a, offsets, count, out, count_for_grid, s);
+        else if (k2 <= 12) mw = dtw64_mw_launch<4, 12>(b, a, offsets, count, out, count_for_grid, s);
+        else mw = dtw64_mw_launch<4, 16>(b, a, offsets, count, out, count_for_grid, s);
     }
+    if (mw != cudaErrorNotSupported) return mw;
+    // (the shared-memory copies do not fit: the one-group kernels below)
     const int blocks = dtw_blocks(p, b.num_sms, count_for_grid);
 #define DTWS_CASE(LL, KK)                                                                                     \
     if (p.L == LL && p.K == KK) {                                                                             \

@@ -89,9 +89,12 @@ def test_dtw_fp32_matches_oracle(series, index, m, r):
 
 
 # shapes of the double-float walk: one warp (r < 32), and 2, 3 or 4 warps with
-# 1 to 4 cells per lane (the widest band, the longest query)
+# 1 to 4 cells per lane (the widest band, the longest query); bands past 511
+# on four warps with 6 to 16 cells per lane; and FP64 where those copies do
+# not fit in shared memory (m = 8192, r = 2000)
 @pytest.mark.parametrize("m,r", [(32, 0), (64, 5), (128, 17), (512, 51), (333, 400), (300, 70), (1024, 102),
-                                 (700, 200), (2048, 409), (8192, 511)])
+                                 (700, 200), (2048, 409), (8192, 511), (700, 650), (1024, 921), (2048, 1400),
+                                 (4096, 2000), (8192, 2000)])
 def test_dtw_fp64_matches_oracle(series, index, m, r):
     q, _ = synth.noisy_copy(series, m, 30 + m, 31 + r, noise=0.3)
     offs = np.random.default_rng(m + 3 * r).integers(0, series.size - m + 1, 100)

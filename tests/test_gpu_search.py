@@ -43,7 +43,7 @@ def test_query_matches_oracle(walk, index, m, w, k, noise):
 
 
 @pytest.mark.parametrize("m,r", [(64, 5), (128, 17), (300, 70), (512, 51), (1024, 102), (700, 200),
-                                 (2048, 409)])
+                                 (2048, 409), (1024, 921)])
 def test_distances_are_the_extended_rescore(walk, index, m, r):
     """The returned distances are the extended-precision re-scores (the
     pre-scored seed's on the side stream, the rest in the final stage; one,

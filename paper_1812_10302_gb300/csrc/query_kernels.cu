@@ -1438,6 +1438,12 @@ static bool plan_dtw(int m, int r, bool tail, DtwPlan *p) {
         DTWS_TRY(32, 1) DTWS_TRY(32, 2) DTWS_TRY(32, 3) DTWS_TRY(32, 4) DTWS_TRY(32, 6) DTWS_TRY(32, 8) \
         DTWS_TRY(32, 10) DTWS_TRY(32, 12) DTWS_TRY(32, 16)
 #undef DTWS_TRY
+    } else if (std::is_same<T, float>::value && r <= kDiagRMaxF32) {
+        // wider bands in FP32: one warp with 24 or 32 cells per lane (the
+        // survivor, seed and given-offset kernels; the re-score has its own
+        // multi-warp walk)
+        if (r + 1 <= 32 * 24 && plan_fits<T, 32, 24>(m, r, tail, p)) return true;
+        if (plan_fits<T, 32, 32>(m, r, tail, p)) return true;
     }
     const int L = lanes_for(r);
 #define DTWS_TRY(LL) \
@@ -1473,7 +1479,7 @@ static cudaError_t dtw_dispatch(const QueryBufs &b, const QueryArgs &a, const in
     }
     DTWS_CASE(1, 1) DTWS_CASE(2, 1) DTWS_CASE(4, 1) DTWS_CASE(8, 1) DTWS_CASE(16, 1)
     DTWS_CASE(32, 1) DTWS_CASE(32, 2) DTWS_CASE(32, 3) DTWS_CASE(32, 4) DTWS_CASE(32, 6) DTWS_CASE(32, 8) \
-    DTWS_CASE(32, 10) DTWS_CASE(32, 12) DTWS_CASE(32, 16)
+    DTWS_CASE(32, 10) DTWS_CASE(32, 12) DTWS_CASE(32, 16) DTWS_CASE(32, 24) DTWS_CASE(32, 32)
     DTWS_CASE(1, 0) DTWS_CASE(2, 0) DTWS_CASE(4, 0) DTWS_CASE(8, 0) DTWS_CASE(16, 0) DTWS_CASE(32, 0)
 #undef DTWS_CASE
     return cudaErrorInvalidValue;

@@ -440,7 +440,7 @@ QueryArgs make_args(dtws_t h, int m, int r, int k) {
     float g = 1.17549435e-38f;
     while (g * 2.0f <= a.alpha * 0.25f) g *= 2.0f;
     a.qgrid = g;
-    a.prescore = a.r <= kDiagRMax ? 1 : 0;
+    a.prescore = a.r <= kDiagRMaxF32 ? 1 : 0;
     a.tune_l = a.tune_k = a.tune_w = 0;
     for (const auto &t : h->tune)
         if (t.m == m && t.r == a.r) {

@@ -1940,6 +1940,11 @@ __global__ void k_prescore(QueryBufs b, QueryArgs a) {
         if (pair) return;
         // one warp: the re-score below reuses this memory
     }
+    // (one-warp mode with more than 16 cells per lane: the FP32 result is in
+    // the list; the final stage re-scores the window like any other)
+    if constexpr (K > 16) {
+        if (!pair) return;
+    }
     // extended-precision re-score (FP64 statistics, double-float DTW) by the
     // first re-score warp's lanes (the whole of warp 1 in paired mode, the
     // L lanes of warp 0 otherwise)
@@ -1993,9 +1998,13 @@ __global__ void k_prescore(QueryBufs b, QueryArgs a) {
     if (pair && PS::W > 1) {
         d64 = dtw_diag_df_mw<PS::W, PS::K2>(qd + pad2, cd + pad2, m, r, dw, lane, xchg, 1);
     } else {
-        const unsigned gmask = (L == 32) ? 0xffffffffu : ((1u << L) - 1u);
-        if (lane >= L) return;
-        d64 = dtw_diag_df<L, K>(qd + pad2, cd + pad2, m, r, gmask, lane);
+        if constexpr (K <= 16) {
+            const unsigned gmask = (L == 32) ? 0xffffffffu : ((1u << L) - 1u);
+            if (lane >= L) return;
+            d64 = dtw_diag_df<L, K>(qd + pad2, cd + pad2, m, r, gmask, lane);
+        } else {
+            return;  // (not reached: K > 16 runs paired, with PS::W = 4)
+        }
     }
     if (t == 0) {
         st->pre_d64 = d64;
@@ -2008,6 +2017,10 @@ cudaError_t launch_prescore(const QueryBufs &b, const QueryArgs &a, cudaStream_t
     if (!a.prescore) return cudaSuccess;
     int L, K;
     diag_shape(a.r, &L, &K);
+    if (a.r > kDiagRMax) {  // the FP32 walk's wide shapes (one warp, 24 or 32 cells)
+        L = 32;
+        K = a.r + 1 <= 32 * 24 ? 24 : 32;
+    }
 #define DTWS_CASE(LL, KK)                                                                           \
     if (L == LL && K == KK) {                                                                       \
         using PS = PreShape<LL, KK>;                                                                \
@@ -2026,7 +2039,7 @@ cudaError_t launch_prescore(const QueryBufs &b, const QueryArgs &a, cudaStream_t
     }
     DTWS_CASE(1, 1) DTWS_CASE(2, 1) DTWS_CASE(4, 1) DTWS_CASE(8, 1) DTWS_CASE(16, 1)
     DTWS_CASE(32, 1) DTWS_CASE(32, 2) DTWS_CASE(32, 3) DTWS_CASE(32, 4) DTWS_CASE(32, 6) DTWS_CASE(32, 8) \
-    DTWS_CASE(32, 10) DTWS_CASE(32, 12) DTWS_CASE(32, 16)
+    DTWS_CASE(32, 10) DTWS_CASE(32, 12) DTWS_CASE(32, 16) DTWS_CASE(32, 24) DTWS_CASE(32, 32)
 #undef DTWS_CASE
     return cudaErrorInvalidValue;
 }

@@ -344,6 +344,22 @@ def gpu_arm(args):
     if not args.no_cpu_baseline and world == 1 or (not args.no_cpu_baseline and rank == 0 and world == 1):
         cpu = cpu_oracle_sample(x, q, r, k, true_off, args.cpu_windows)
     value = total_windows / (ms * 1e-3)
+    # The survivor DTW stage against its ALU ceiling: every SM's 128 FP32/ALU
+    # lanes at the maximum SM clock, 5 operations per band cell (subtract,
+    # multiply-add, two minimums, the band select); evaluated cells over the
+    # stage's event time.
+    dtw_roof = None
+    try:
+        dtw_ms = float(phases[4])
+        sms = torch.cuda.get_device_properties(dev).multi_processor_count
+        mhz = (clocks or {}).get("sm_max_mhz") or 2070.0
+        peak_cells = sms * 128 * mhz * 1e6 / 5.0
+        got = st["dtw_cells"] / (dtw_ms * 1e-3) if dtw_ms > 0 else None
+        dtw_roof = {"kernel": "k_dtw", "bound": "alu", "achieved": got, "peak": peak_cells, "unit": "cells/s",
+                    "frac": (got / peak_cells) if got else None, "ops_per_cell": 5,
+                    "peak_source": f"{sms} SMs x 128 lanes x {mhz:.0f} MHz / 5"}
+    except (KeyError, IndexError, TypeError, RuntimeError):
+        dtw_roof = None
     line = {
         "metric": "subsequences/s per query",
         "value": value,
@@ -375,6 +391,7 @@ def gpu_arm(args):
                      "unit": "GB/s", "frac": (achieved / hbm) if achieved else None,
                      "traffic": LB_SCAN_DRAM_BYTES_PER_WINDOW * N, "peak_source": peak_kind,
                      "algorithmic_bytes_per_launch": lb_bytes},
+        "dtw_roofline": dtw_roof,
         "clocks": clocks,
         "gpu_launches": launches,
         "e2e": {"value": total_windows / (e2e_ms * 1e-3), "unit": "subsequences/s",

@@ -229,3 +229,36 @@ def lbs_at(x, Q, r: int, offsets):
     outs = [np.empty(off.size, np.float64) for _ in range(4)]
     _load().orc_lbs_at(_p(x), x.size, _p(Q), Q.size, r, _p(off), off.size, *[_p(o) for o in outs])
     return tuple(outs)
+
+
+# ---------------------------------------------------------------- variants
+# (the paper is silent on both; they are defined here for the GPU path's
+# next steps and pinned in tests/test_oracle_variants.py)
+def search_brute_raw(x, Q, r: int, k: int):
+    """Eq. 3 without the z-normalisation of Eq. 5: banded DTW (Eq. 1) of the
+    raw query against every raw window, in FP64; the k smallest
+    (distance, offset) pairs, ties to the lower offset."""
+    x64, q64 = _f64(_f32(x)), _f64(_f32(Q))
+    m = q64.size
+    N = x64.size - m + 1
+    if m < 1 or N < 1 or k < 1:
+        raise ValueError("bad arguments")
+    d = np.array([dtw(q64, x64[i:i + m], r) for i in range(N)])
+    order = np.lexsort((np.arange(N), d))[:k]
+    return order.astype(np.int64), d[order]
+
+
+def exclusion_topk(dists, k: int, z: int):
+    """Top-k with an exclusion zone: take windows in (distance, offset) order,
+    skipping any window within z samples of one already taken, until k are
+    taken (fewer if the windows run out).  dists: the distance of every
+    window, by offset."""
+    d = np.asarray(dists, np.float64)
+    taken: list[int] = []
+    for i in np.lexsort((np.arange(d.size), d)):
+        if all(abs(int(i) - t) > z for t in taken):
+            taken.append(int(i))
+            if len(taken) == k:
+                break
+    idx = np.array(taken, np.int64)
+    return idx, d[idx]

@@ -1,0 +1,95 @@
+"""Pins of the oracle's variants (unnormalised DTW search, top-k with an
+exclusion zone) against closed forms, invariances and independent paths."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1812_10302_gb300 import synth
+
+
+def _sq_ed(x, q):
+    """Squared Euclidean distance of q to every window of x (NumPy)."""
+    x = x.astype(np.float64)
+    q = q.astype(np.float64)
+    w = np.lib.stride_tricks.sliding_window_view(x, q.size)
+    return ((w - q) ** 2).sum(axis=1)
+
+
+def test_raw_search_with_r0_is_squared_euclidean():
+    x = synth.random_walk(600, 1)
+    q = synth.random_walk(24, 2)
+    idx, dist = oracle.search_brute_raw(x, q, 0, 5)
+    ed = _sq_ed(x, q)
+    want = np.lexsort((np.arange(ed.size), ed))[:5]
+    np.testing.assert_array_equal(idx, want)
+    np.testing.assert_allclose(dist, ed[want], rtol=1e-12)
+
+
+def test_raw_dtw_is_at_most_euclidean_and_finds_a_planted_copy():
+    x = synth.random_walk(500, 3)
+    o = 217
+    q = x[o:o + 32].copy()
+    idx, dist = oracle.search_brute_raw(x, q, 3, 1)
+    assert idx[0] == o and dist[0] == 0.0
+    ed = _sq_ed(x, q)
+    for i in np.random.default_rng(4).integers(0, ed.size, 40):
+        assert oracle.dtw(q.astype(np.float64), x[i:i + 32].astype(np.float64), 3) <= ed[i] * (1 + 1e-12)
+
+
+def test_raw_search_translation_and_scale():
+    # values on a 2^-6 grid: the shifted and doubled inputs are exact in FP32
+    rng = np.random.default_rng(5)
+    x = (np.round(np.cumsum(rng.normal(0, 1, 400)) * 64) / 64).astype(np.float32)
+    q = (np.round(np.cumsum(rng.normal(0, 1, 20)) * 64) / 64).astype(np.float32)
+    i0, d0 = oracle.search_brute_raw(x, q, 4, 6)
+    i1, d1 = oracle.search_brute_raw(x + np.float32(8.0), q + np.float32(8.0), 4, 6)
+    i2, d2 = oracle.search_brute_raw(x * np.float32(2.0), q * np.float32(2.0), 4, 6)
+    np.testing.assert_array_equal(i1, i0)
+    np.testing.assert_allclose(d1, d0, rtol=1e-12)
+    np.testing.assert_array_equal(i2, i0)
+    np.testing.assert_allclose(d2, 4.0 * d0, rtol=1e-12)
+
+
+def test_exclusion_zone_zero_is_plain_topk_and_offsets_are_apart():
+    rng = np.random.default_rng(6)
+    d = rng.random(300)
+    d[50] = d[51]  # a tie: lower offset first
+    i0, _ = oracle.exclusion_topk(d, 10, 0)
+    np.testing.assert_array_equal(i0, np.lexsort((np.arange(d.size), d))[:10])
+    for z in (1, 5, 20):
+        idx, dist = oracle.exclusion_topk(d, 8, z)
+        assert np.all(np.abs(idx[:, None] - idx[None, :])[~np.eye(idx.size, dtype=bool)] > z)
+        assert np.all(np.diff(dist) >= 0)
+
+
+def test_exclusion_zone_returns_separate_planted_copies():
+    x = synth.random_walk(3000, 7)
+    ql = synth.random_walk(50, 8)
+    q = ql[5:45].copy()
+    # three planted copies far apart (with 5 samples of the pattern's own
+    # context on each side), one nearly exact: its shifted neighbours (the
+    # band absorbs a shift of one) beat the noisier copies
+    for o, s in ((300, 0.001), (1400, 0.5), (2500, 0.5)):
+        x[o - 5:o + 45] = ql + np.random.default_rng(o).normal(0, s, 50).astype(np.float32)
+    d = np.array([oracle.dtw(q.astype(np.float64), x[i:i + 40].astype(np.float64), 4)
+                  for i in range(x.size - 39)])
+    plain = np.lexsort((np.arange(d.size), d))[:3]
+    idx, _ = oracle.exclusion_topk(d, 3, 20)
+    # one answer at each copy (a noisy copy's best alignment may sit a sample off)
+    got = sorted(idx.tolist())
+    assert [abs(g - o) <= 2 for g, o in zip(got, (300, 1400, 2500))] == [True] * 3, got
+    assert np.ptp(plain) <= 3  # the plain top-3 are neighbours of one copy
+
+
+@pytest.mark.parametrize("seed", range(5))
+def test_exclusion_answer_lies_in_the_plain_top_k_2z_plus_1(seed):
+    rng = np.random.default_rng(seed)
+    d = np.cumsum(rng.normal(0, 1, 2000)) ** 2  # smooth: near windows have near distances
+    for k, z in ((3, 10), (5, 4), (2, 50)):
+        idx, _ = oracle.exclusion_topk(d, k, z)
+        K = k * (2 * z + 1)
+        top = np.lexsort((np.arange(d.size), d))[:K]
+        sub = np.full(d.size, np.inf)
+        sub[top] = d[top]
+        idx2, _ = oracle.exclusion_topk(sub, k, z)
+        np.testing.assert_array_equal(idx2, idx)

@@ -102,6 +102,15 @@ typedef struct {
                                ordering); dtws_query does the same for one
                                query (not while timing is on).  The query
                                values may change between replays. */
+    int32_t exclusion_zone; /* z >= 0 (default 0): dtws_query returns the k
+                               best windows of which no two lie within z
+                               samples of each other, taken greedily in
+                               (distance, offset) order.  Exact: that answer
+                               lies among the k*(2z+1) best windows, which
+                               the search finds first, so k*(2z+1) must not
+                               exceed DTWS_K_MAX.  Not for dtws_query_batch.
+                               Missing windows (the series too short) come
+                               back as offset -1, distance +inf. */
     int64_t wait_limit_ns;  /* bound on every device-side wait, default 2e9 */
     uint64_t rng_seed;      /* seed of the random seed windows, default 0 */
 } dtws_options;

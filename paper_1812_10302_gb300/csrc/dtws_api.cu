@@ -890,6 +890,7 @@ void dtws_default_options(dtws_options *o) {
     o->exact_envelope = 1;
     o->batch_lanes = 4;
     o->batch_graph = 1;
+    o->exclusion_zone = 0;
     o->wait_limit_ns = 2000000000LL;
     o->rng_seed = 0;
 }
@@ -1010,7 +1011,7 @@ dtws_status dtws_set_options(dtws_t h, const dtws_options *o) {
         o->seed_random > 64 || o->seed_proposals < 0 || o->seed_proposals > kPropMax ||
         o->proxy_terms < 1 || o->proxy_terms > 16 || o->wait_limit_ns <= 0 ||
         (o->exact_envelope != 0 && o->exact_envelope != 1) || o->batch_lanes < 1 || o->batch_lanes > 16 ||
-        (o->batch_graph != 0 && o->batch_graph != 1) ||
+        (o->batch_graph != 0 && o->batch_graph != 1) || o->exclusion_zone < 0 ||
         (o->ordering != DTWS_ORDER_PLAIN && o->ordering != DTWS_ORDER_LEARNED)) {
         set_err("option out of range");
         return DTWS_EINVAL;
@@ -1030,10 +1031,25 @@ dtws_status dtws_query(dtws_t h, const float *Q, int32_t m, int32_t r, int32_t k
     dtws_status st = check_query_args(h, Q, m, r, k);
     if (st != DTWS_OK) return st;
     if (!out_idx || !out_dist) { set_err("null output"); return DTWS_EINVAL; }
+    // with an exclusion zone z the search finds the K = k(2z+1) best windows
+    // (capped at N), among which the greedy answer lies
+    const int z = h->opt.exclusion_zone;
+    int K = k;
+    if (z > 0) {
+        const int64_t want = (int64_t)k * (2 * (int64_t)z + 1), N = h->n - m + 1;
+        if (want > DTWS_K_MAX) {
+            set_err("exclusion_zone=%d with k=%d needs the %lld best windows (at most %d)", z, k,
+                    (long long)want, DTWS_K_MAX);
+            return DTWS_EINVAL;
+        }
+        K = (int)(want < N ? want : N);
+    }
     cudaStream_t s = (cudaStream_t)stream;
     const bool qdev = is_device_ptr(Q), idev = is_device_ptr(out_idx), ddev = is_device_ptr(out_dist);
     const size_t qb = (size_t)m * 4, ib = (size_t)k * 8, db = (size_t)k * 4;
-    if ((st = ensure_stage(h, 256 + round_up(qb, 256) + round_up(ib, 256) + round_up(db, 256))) != DTWS_OK)
+    const size_t kib = (size_t)K * 8, kdb = (size_t)K * 4;  // the K-list (exclusion zone only)
+    if ((st = ensure_stage(h, 256 + round_up(qb, 256) + round_up(ib, 256) + round_up(db, 256) +
+                                  round_up(kib, 256) + round_up(kdb, 256))) != DTWS_OK)
         return st;
     char *sp = (char *)h->stage;
     const float *Qd = Q;
@@ -1043,7 +1059,15 @@ dtws_status dtws_query(dtws_t h, const float *Q, int32_t m, int32_t r, int32_t k
     }
     int64_t *idx_d = idev ? out_idx : (int64_t *)(sp + round_up(qb, 256));
     float *dist_d = ddev ? out_dist : (float *)(sp + round_up(qb, 256) + round_up(ib, 256));
-    if ((st = run_query(h, Qd, m, r, k, idx_d, dist_d, s)) != DTWS_OK) return st;
+    if (z > 0) {
+        char *kp = sp + round_up(qb, 256) + round_up(ib, 256) + round_up(db, 256);
+        int64_t *kidx = (int64_t *)kp;
+        float *kdist = (float *)(kp + round_up(kib, 256));
+        if ((st = run_query(h, Qd, m, r, K, kidx, kdist, s)) != DTWS_OK) return st;
+        CK(launch_exclusion_select(kidx, kdist, K, k, z, idx_d, dist_d, s));
+    } else if ((st = run_query(h, Qd, m, r, k, idx_d, dist_d, s)) != DTWS_OK) {
+        return st;
+    }
     if (!idev) CK(cudaMemcpyAsync(out_idx, idx_d, ib, cudaMemcpyDeviceToHost, s));
     if (!ddev) CK(cudaMemcpyAsync(out_dist, dist_d, db, cudaMemcpyDeviceToHost, s));
     if (!idev || !ddev) CK(cudaStreamSynchronize(s));
@@ -1058,6 +1082,7 @@ dtws_status dtws_query_batch(dtws_t h, const float *Q_cat, const int64_t *q_off,
         return DTWS_EINVAL;
     }
     if (q_off[0] != 0) { set_err("q_off[0] != 0"); return DTWS_EINVAL; }
+    if (h->opt.exclusion_zone > 0) { set_err("exclusion_zone is for dtws_query only"); return DTWS_EINVAL; }
     for (int q = 0; q < nq; ++q) {
         if (q_off[q + 1] - q_off[q] != m_arr[q]) { set_err("q_off/m mismatch at %d", q); return DTWS_EINVAL; }
         dtws_status st = check_query_args(h, Q_cat, m_arr[q], r_arr[q], k);

@@ -104,6 +104,9 @@ cudaError_t launch_enc_quant(const void *E, int64_t rows, void *Q, void *S, cuda
 cudaError_t launch_learn_scan(const QueryBufs &b, const void *Q, const void *S, int64_t Nw, int stride,
                               int phase, int slot, int *ctas, cudaStream_t s);
 cudaError_t launch_prop_merge(const QueryBufs &b, int ctas0, int ctas1, int proposals, cudaStream_t s);
+// greedy exclusion-zone selection of k of the K ordered results (idx, dist)
+cudaError_t launch_exclusion_select(const int64_t *idx, const float *dist, int K, int k, int z, int64_t *out_idx,
+                                    float *out_dist, cudaStream_t s);
 cudaError_t launch_bf16_to_f32(const void *src, int64_t count, float *dst, cudaStream_t s);
 
 }  // namespace dtws

@@ -2044,6 +2044,46 @@ cudaError_t launch_prescore(const QueryBufs &b, const QueryArgs &a, cudaStream_t
     return cudaErrorInvalidValue;
 }
 
+// Top-k with an exclusion zone: the search's K best windows in (distance,
+// offset) order are taken one by one, skipping any window within z samples
+// of one already taken, until k are taken; the rest of the output (a series
+// too short for k such windows) is offset -1, distance +inf.  K <= 64: one
+// thread.
+__global__ void k_exclusion_select(const int64_t *idx, const float *dist, int K, int k, int z, int64_t *out_idx,
+                                   float *out_dist) {
+    if (threadIdx.x != 0) return;
+    int64_t taken[kKMax];
+    int n = 0;
+    for (int j = 0; j < K && n < k; ++j) {
+        const int64_t i = idx[j];
+        if (i < 0) continue;
+        bool ok = true;
+        for (int t = 0; t < n; ++t) {
+            const int64_t d = taken[t] - i;
+            if (d <= z && d >= -z) {
+                ok = false;
+                break;
+            }
+        }
+        if (!ok) continue;
+        taken[n] = i;
+        out_idx[n] = i;
+        out_dist[n] = dist[j];
+        ++n;
+    }
+    for (; n < k; ++n) {
+        out_idx[n] = -1;
+        out_dist[n] = __int_as_float(0x7f800000);
+    }
+}
+
+cudaError_t launch_exclusion_select(const int64_t *idx, const float *dist, int K, int k, int z, int64_t *out_idx,
+                                    float *out_dist, cudaStream_t s) {
+    if (K > kKMax || k > kKMax) return cudaErrorInvalidValue;
+    k_exclusion_select<<<1, 32, 0, s>>>(idx, dist, K, k, z, out_idx, out_dist);
+    return cudaGetLastError();
+}
+
 __global__ void k_final_sort(QueryBufs b, QueryArgs a, int64_t *out_idx, float *out_dist) {
     QueryState *st = b.st;
     const int nm = st->valid ? st->n_margin : 0;

@@ -56,6 +56,7 @@ class dtws_options(ctypes.Structure):
         ("exact_envelope", ctypes.c_int32),
         ("batch_lanes", ctypes.c_int32),
         ("batch_graph", ctypes.c_int32),
+        ("exclusion_zone", ctypes.c_int32),
         ("wait_limit_ns", ctypes.c_int64),
         ("rng_seed", ctypes.c_uint64),
     ]

@@ -72,6 +72,31 @@ def test_wide_band_queries_match_oracle(m, r, k):
     _close(dist, od, m)
 
 
+@pytest.mark.parametrize("m,r,k,z", [(64, 6, 3, 10), (128, 12, 4, 7), (100, 20, 2, 15)])
+def test_exclusion_zone_matches_oracle(m, r, k, z):
+    """Top-k with an exclusion zone: the oracle's greedy selection over the
+    FP64 DTW of every window; k(2z+1) beyond the result list is refused, and
+    so is a batch."""
+    x = synth.random_walk(20_000, 90 + m)
+    q, _ = synth.noisy_copy(x, m, 91 + m, 92 + m, noise=0.3)
+    with dtws.Index(x) as ix:
+        ix.set_options(exclusion_zone=z)
+        idx, dist = ix.query(q, r, k)
+        assert ix.sync_status() == dtws.DTWS_OK
+        idx2, dist2 = ix.query(q, r, k)  # (replayed graph)
+        with pytest.raises(dtws.DtwsError):
+            ix.query(q, r, k + 1 if (k + 1) * (2 * z + 1) > 64 else 64)
+        with pytest.raises(dtws.DtwsError):
+            ix.query_batch([q, q], [r, r], k=k)
+    np.testing.assert_array_equal(idx2, idx)
+    np.testing.assert_array_equal(dist2, dist)
+    d = oracle.dtw_at(x, q, r, np.arange(x.size - m + 1))
+    oi, od = oracle.exclusion_topk(d, k, z)
+    np.testing.assert_array_equal(idx, oi)
+    _close(dist, od, m)
+    assert np.all(np.abs(idx[:, None] - idx[None, :])[~np.eye(k, dtype=bool)] > z)
+
+
 def test_random_query_not_a_copy(walk, index):
     """A query unrelated to the series: loose seeds, many survivors."""
     q = synth.random_walk(128, 999)

@@ -60,6 +60,42 @@ def test_default_options_and_strerror(lib):
     assert dtws.strerror(dtws.DTWS_EOVERFLOW).startswith("more near-ties")
 
 
+def _c_layout(tmp_path, struct, fields):
+    """sizeof and offsetof of each field as a C compiler lays the header's struct out."""
+    src = tmp_path / f"{struct}.c"
+    src.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "dtws.h"\nint main(void) {\n'
+                   f'    printf("%zu\\n", sizeof({struct}));\n' +
+                   "".join(f'    printf("%zu\\n", offsetof({struct}, {f}));\n' for f in fields) +
+                   "    return 0;\n}\n")
+    exe = tmp_path / struct
+    try:
+        subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True,
+                       capture_output=True)
+    except (OSError, subprocess.CalledProcessError) as e:
+        pytest.skip(f"no C compiler: {e}")
+    return [int(v) for v in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()]
+
+
+@pytest.mark.parametrize("struct", ["dtws_options", "dtws_query_stats", "dtws_adam"])
+def test_binding_structs_match_the_header_layout(struct, tmp_path):
+    """The binding's ctypes mirror of each ABI struct has the header's size
+    and every field at the header's offset."""
+    import ctypes
+    from paper_1812_10302_gb300 import dtws
+    cls = getattr(dtws, struct)
+    fields = [f for f, _ in cls._fields_]
+    got = _c_layout(tmp_path, struct, fields)
+    assert got[0] == ctypes.sizeof(cls)
+    assert got[1:] == [getattr(cls, f).offset for f in fields]
+
+
+def test_option_defaults(lib):
+    from paper_1812_10302_gb300 import dtws
+    o = dtws.dtws_default_options()
+    assert (o.ordering, o.timing, o.exact_envelope, o.batch_lanes, o.batch_graph, o.exclusion_zone,
+            o.rng_seed) == (dtws.DTWS_ORDER_PLAIN, 0, 1, 4, 1, 0, 0)
+
+
 def test_create_rejects_bad_arguments_without_device_work(lib):
     import ctypes
     from paper_1812_10302_gb300 import dtws

@@ -173,7 +173,12 @@ dtws_status dtws_get_options(dtws_t h, dtws_options *opt);
  * A window (or query) whose variance is <= 1e-24*max(1, mean^2) normalises
  * to all zeros.  Per-series data for this m (window statistics) and r
  * (series envelope) are computed on first use and cached in the handle.
- * Errors: DTWS_EINVAL synchronously; DTWS_ENONFINITE via dtws_sync_status.
+ * With options.exclusion_zone = z > 0 the k results are more than z
+ * samples apart (see dtws_options).  With options.batch_graph = 1 a call
+ * whose arguments (pointers, m, r, k, options) repeat the previous one's
+ * replays the captured search; the query values may differ.
+ * Errors: DTWS_EINVAL synchronously (also k*(2z+1) > DTWS_K_MAX with an
+ * exclusion zone); DTWS_ENONFINITE via dtws_sync_status.
  */
 dtws_status dtws_query(dtws_t h, const float *Q, int32_t m, int32_t r, int32_t k,
                        int64_t *out_idx, float *out_dist, void *stream);

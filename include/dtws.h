@@ -9,7 +9,9 @@
  * Distances are squared (no square root, Sec. 2.2, Eq. 4 remark).  This
  * library returns the k smallest (distance, offset) pairs in lexicographic
  * order, so ties go to the lowest offset; neighbouring offsets of one match
- * may fill the list (no exclusion zone).
+ * may fill the list (no exclusion zone, unless options.exclusion_zone
+ * asks for one).  options.unnormalised = 1 drops the z-normalisation and
+ * compares raw values (an API variant the paper does not treat).
  *
  * Notation: n = series length, m = query length, r = band half-width in
  * samples, N = n - m + 1 windows, offsets are 0-based in [0, N).
@@ -43,7 +45,9 @@ typedef enum {
     DTWS_EINVAL = 1,      /* bad argument (null pointer, size out of range) */
     DTWS_ENOMEM = 2,      /* device or host allocation failed */
     DTWS_ECUDA = 3,       /* a CUDA runtime call failed */
-    DTWS_ENONFINITE = 4,  /* NaN or +-Inf in the series or the query */
+    DTWS_ENONFINITE = 4,  /* NaN or +-Inf in the series or the query (with
+                             unnormalised DTW: also a query value beyond
+                             +-2^32) */
     DTWS_ETIMEOUT = 5,    /* a bounded device-side wait ran out */
     DTWS_ENOTIMPL = 6,    /* not implemented */
     DTWS_EOVERFLOW = 7    /* more near-ties than the re-score list holds; the
@@ -111,6 +115,24 @@ typedef struct {
                                exceed DTWS_K_MAX.  Not for dtws_query_batch.
                                Missing windows (the series too short) come
                                back as offset -1, distance +inf. */
+    int32_t unnormalised;   /* 1: DTW of the raw values (no z-normalisation of
+                               the windows or the query, Eq. 5 skipped);
+                               default 0.  dtws_query and the building
+                               blocks at given offsets only; not with the
+                               learned ordering (its embeddings are of
+                               normalised windows).  The series and the
+                               query must lie within +-2^32 (so that every
+                               squared path sum stays far inside FP32's
+                               range): dtws_query returns DTWS_EINVAL for
+                               such a series, dtws_sync_status
+                               DTWS_ENONFINITE for such a query.
+                               Distances are then in squared units of the
+                               data, and so is alpha_per_m: the raw values
+                               enter the differences unscaled, so the FP32
+                               errors are relative and delta covers them;
+                               keep alpha_per_m*m well below the distances
+                               of interest (near-ties within it are
+                               re-scored, DTWS_EOVERFLOW beyond k + 64). */
     int64_t wait_limit_ns;  /* bound on every device-side wait, default 2e9 */
     uint64_t rng_seed;      /* seed of the random seed windows, default 0 */
 } dtws_options;
@@ -177,8 +199,10 @@ dtws_status dtws_get_options(dtws_t h, dtws_options *opt);
  * samples apart (see dtws_options).  With options.batch_graph = 1 a call
  * whose arguments (pointers, m, r, k, options) repeat the previous one's
  * replays the captured search; the query values may differ.
+ * With options.unnormalised = 1 neither side is normalised (raw values).
  * Errors: DTWS_EINVAL synchronously (also k*(2z+1) > DTWS_K_MAX with an
- * exclusion zone); DTWS_ENONFINITE via dtws_sync_status.
+ * exclusion zone; unnormalised DTW with the learned ordering or with a
+ * series beyond +-2^32); DTWS_ENONFINITE via dtws_sync_status.
  */
 dtws_status dtws_query(dtws_t h, const float *Q, int32_t m, int32_t r, int32_t k,
                        int64_t *out_idx, float *out_dist, void *stream);
@@ -234,7 +258,9 @@ dtws_status dtws_series_envelope(dtws_t h, int32_t r, float *U, float *L, void *
 
 /* FP32 banded DTW (Eq. 1 + band) of the z-normalised query against the
    z-normalised windows at offsets[0..count) (int64, each in [0, N)), no
-   pruning: the search's DTW kernel.  out: FP32 [count]. */
+   pruning: the search's DTW kernel.  out: FP32 [count].  With
+   options.unnormalised = 1 (here and in the two calls below) the raw query
+   and windows. */
 dtws_status dtws_dtw_at(dtws_t h, const float *Q, int32_t m, int32_t r,
                         const int64_t *offsets, int64_t count, float *out, void *stream);
 

@@ -103,7 +103,10 @@ struct dtws_ctx {
     float *pscale = nullptr;             // [0]: the series' power-of-two scale; [1]: scratch
     float *envst = nullptr;              // block envelope (sparse table)
     int64_t nblk = 0;
+    unsigned *absmax = nullptr;          // max |x| as FP32 bits (device), and its host copy:
+    float xabs = 0.0f;
     std::vector<StatsEntry> stats;
+    StatsEntry ident;                    // unnormalised DTW: mean 0, 1/sigma 1 for every window
     std::vector<EnvEntry> env;
     int64_t clock = 0;
     QueryState *st = nullptr;
@@ -239,6 +242,43 @@ dtws_status get_stats(dtws_t h, int m, cudaStream_t s, StatsEntry **out, bool *c
     *out = &h->stats.back();
     *computed = true;
     return DTWS_OK;
+}
+
+// Unnormalised DTW: statistics arrays with mean 0 and 1/sigma 1 for every
+// window, so every kernel's (x - mu) * (1/sigma) is x itself, exactly.  One
+// entry sized for m = 2 (the most windows) serves every m.
+dtws_status get_ident(dtws_t h, cudaStream_t s, StatsEntry **out, bool *computed) {
+    *computed = false;
+    if (!h->ident.mu_hi) {
+        StatsEntry e;
+        const int64_t N = h->n - 1;
+        const int64_t cap = round_up(N, kProxyTile) + kProxyTile;
+        const int64_t scap = cap / kProxyStride;
+        cudaError_t a1 = dalloc(&e.mu_hi, cap), a2 = dalloc(&e.mu_lo, cap), a3 = dalloc(&e.inv_sigma, cap);
+        cudaError_t a4 = dalloc(&e.smu_hi, scap), a6 = dalloc(&e.sinv_sigma, scap);
+        if (a1 != cudaSuccess || a2 != cudaSuccess || a3 != cudaSuccess || a4 != cudaSuccess ||
+            a6 != cudaSuccess) {
+            free_stats(e);
+            cudaGetLastError();
+            set_err("unnormalised statistics: out of device memory");
+            return DTWS_ENOMEM;
+        }
+        CK(cudaMemsetAsync(e.mu_hi, 0, cap * 4, s));
+        CK(cudaMemsetAsync(e.mu_lo, 0, cap * 4, s));
+        CK(cudaMemsetAsync(e.smu_hi, 0, scap * 4, s));
+        CK(launch_fill(e.inv_sigma, cap, 1.0f, h->num_sms, s));
+        CK(launch_fill(e.sinv_sigma, scap, 1.0f, h->num_sms, s));
+        h->ident = e;
+        *computed = true;
+    }
+    *out = &h->ident;
+    return DTWS_OK;
+}
+
+// The statistics a query reads: the window statistics for m, or the
+// identity ones for unnormalised DTW.
+dtws_status query_stats(dtws_t h, int m, cudaStream_t s, StatsEntry **out, bool *computed) {
+    return h->opt.unnormalised ? get_ident(h, s, out, computed) : get_stats(h, m, s, out, computed);
 }
 
 dtws_status get_env(dtws_t h, int r, cudaStream_t s, EnvEntry **out, bool *computed) {
@@ -426,7 +466,7 @@ QueryBufs make_bufs(dtws_t h, const StatsEntry *se, const EnvEntry *ee) {
     return b;
 }
 
-QueryArgs make_args(dtws_t h, int m, int r, int k) {
+QueryArgs make_args(dtws_t h, int m, int r, int k, bool raw) {
     QueryArgs a;
     memset(&a, 0, sizeof a);  // padding included: the bytes enter graph signatures
     a.N = h->n - m + 1;
@@ -436,6 +476,10 @@ QueryArgs make_args(dtws_t h, int m, int r, int k) {
     a.list_cap = k + 64 < kListMax ? k + 64 : kListMax;
     a.delta = h->opt.delta;
     a.alpha = h->opt.alpha_per_m * (float)m;
+    // Raw values (unnormalised DTW) enter the differences unscaled, so every
+    // FP32 error is relative to its term and delta covers it; alpha keeps
+    // its meaning, in squared units of the data.
+    a.raw = raw ? 1 : 0;
     // largest power of two <= alpha/4 (alpha 0: FP32's smallest normal)
     float g = 1.17549435e-38f;
     while (g * 2.0f <= a.alpha * 0.25f) g *= 2.0f;
@@ -450,6 +494,7 @@ QueryArgs make_args(dtws_t h, int m, int r, int k) {
         }
     return a;
 }
+QueryArgs make_args(dtws_t h, int m, int r, int k) { return make_args(h, m, r, k, h->opt.unnormalised != 0); }
 
 dtws_status check_query_args(dtws_t h, const float *Q, int32_t m, int32_t r, int32_t k) {
     if (!h || !Q) { set_err("null handle or query"); return DTWS_EINVAL; }
@@ -462,6 +507,16 @@ dtws_status check_query_args(dtws_t h, const float *Q, int32_t m, int32_t r, int
     if (k < 1 || k > DTWS_K_MAX || (int64_t)k > N) {
         set_err("k=%d out of range [1, min(N, %d)]", k, DTWS_K_MAX);
         return DTWS_EINVAL;
+    }
+    if (h->opt.unnormalised) {
+        if (h->opt.ordering == DTWS_ORDER_LEARNED) {
+            set_err("unnormalised DTW with the learned ordering (its embeddings are of normalised windows)");
+            return DTWS_EINVAL;
+        }
+        if (!(h->xabs <= kRawAbsMax)) {
+            set_err("unnormalised DTW needs |x| <= 2^32 (the series reaches %g)", (double)h->xabs);
+            return DTWS_EINVAL;
+        }
     }
     if (h->opt.ordering == DTWS_ORDER_LEARNED) {
         if (!h->enc_version) { set_err("learned ordering without an encoder (dtws_set_encoder)"); return DTWS_EINVAL; }
@@ -571,7 +626,7 @@ dtws_status run_query(dtws_t h, const float *Qd, int m, int r, int k, int64_t *i
     StatsEntry *se;
     EnvEntry *ee = nullptr;
     bool c1, c2 = false;
-    if ((st = get_stats(h, m, s, &se, &c1)) != DTWS_OK) return st;
+    if ((st = query_stats(h, m, s, &se, &c1)) != DTWS_OK) return st;
     record(h, 6, s);
     const int rr = r > m - 1 ? m - 1 : r;
     if (h->opt.exact_envelope) {
@@ -891,6 +946,7 @@ void dtws_default_options(dtws_options *o) {
     o->batch_lanes = 4;
     o->batch_graph = 1;
     o->exclusion_zone = 0;
+    o->unnormalised = 0;
     o->wait_limit_ns = 2000000000LL;
     o->rng_seed = 0;
 }
@@ -918,6 +974,7 @@ dtws_status dtws_destroy(dtws_t h) {
     cudaSetDevice(h->device);
     cudaDeviceSynchronize();
     for (auto &e : h->stats) free_stats(e);
+    free_stats(h->ident);
     for (auto &e : h->env) free_env(e);
     for (auto &e : h->learn) free_learn(e);
     if (h->enc_blob) cudaFree(h->enc_blob);
@@ -925,7 +982,7 @@ dtws_status dtws_destroy(dtws_t h) {
     for (auto &l : h->lanes) free_lane(l);
     if (h->batch_fork) cudaEventDestroy(h->batch_fork);
     if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
-    void *ptrs[] = {h->x, h->pf, h->bf, h->pok, h->pscale, h->envst, h->st, h->status, h->qh32, h->Uq,
+    void *ptrs[] = {h->x, h->pf, h->bf, h->pok, h->pscale, h->envst, h->absmax, h->st, h->status, h->qh32, h->Uq,
                     h->Lq, h->sq, h->sU, h->sL, h->qh64, h->ord, h->cand_lb, h->sort_lb,
                     h->cand_idx, h->sort_idx, h->stage};
     for (void *p : ptrs)
@@ -976,13 +1033,18 @@ dtws_status dtws_create(const float *series, int64_t n, void *stream, dtws_t *ou
     h->nblk = (n + kEnvG - 1) / kEnvG;
     CKF(dalloc(&h->envst, 2 * (size_t)kEnvLevels * h->nblk));
     CKF(dalloc(&h->status, 1));
+    CKF(dalloc(&h->absmax, 1));
     CKF(cudaMemsetAsync(h->x, 0, h->n_alloc * 4, s));
     CKF(cudaMemcpyAsync(h->x, series, n * 4, cudaMemcpyDefault, s));
     CKF(cudaMemsetAsync(h->status, 0, 4, s));
-    CKF(launch_check_finite(h->x, n, h->status, s));
+    CKF(cudaMemsetAsync(h->absmax, 0, 4, s));
+    CKF(launch_check_finite(h->x, n, h->status, h->absmax, s));
     int flag = 0;
+    unsigned amax = 0;
     CKF(cudaMemcpyAsync(&flag, h->status, 4, cudaMemcpyDeviceToHost, s));
+    CKF(cudaMemcpyAsync(&amax, h->absmax, 4, cudaMemcpyDeviceToHost, s));
     CKF(cudaStreamSynchronize(s));
+    memcpy(&h->xabs, &amax, 4);
     if (flag) {
         set_err("series contains NaN or Inf");
         return fail(DTWS_ENONFINITE);
@@ -1012,6 +1074,7 @@ dtws_status dtws_set_options(dtws_t h, const dtws_options *o) {
         o->proxy_terms < 1 || o->proxy_terms > 16 || o->wait_limit_ns <= 0 ||
         (o->exact_envelope != 0 && o->exact_envelope != 1) || o->batch_lanes < 1 || o->batch_lanes > 16 ||
         (o->batch_graph != 0 && o->batch_graph != 1) || o->exclusion_zone < 0 ||
+        (o->unnormalised != 0 && o->unnormalised != 1) ||
         (o->ordering != DTWS_ORDER_PLAIN && o->ordering != DTWS_ORDER_LEARNED)) {
         set_err("option out of range");
         return DTWS_EINVAL;
@@ -1083,6 +1146,7 @@ dtws_status dtws_query_batch(dtws_t h, const float *Q_cat, const int64_t *q_off,
     }
     if (q_off[0] != 0) { set_err("q_off[0] != 0"); return DTWS_EINVAL; }
     if (h->opt.exclusion_zone > 0) { set_err("exclusion_zone is for dtws_query only"); return DTWS_EINVAL; }
+    if (h->opt.unnormalised) { set_err("unnormalised DTW is for dtws_query only"); return DTWS_EINVAL; }
     for (int q = 0; q < nq; ++q) {
         if (q_off[q + 1] - q_off[q] != m_arr[q]) { set_err("q_off/m mismatch at %d", q); return DTWS_EINVAL; }
         dtws_status st = check_query_args(h, Q_cat, m_arr[q], r_arr[q], k);
@@ -1167,6 +1231,7 @@ dtws_status dtws_clear_cache(dtws_t h) {
     if (!h) return DTWS_EINVAL;
     CK(cudaDeviceSynchronize());
     for (auto &e : h->stats) free_stats(e);
+    free_stats(h->ident);
     for (auto &e : h->env) free_env(e);
     for (auto &e : h->learn) free_learn(e);
     drop_graph(h);
@@ -1225,7 +1290,8 @@ dtws_status dtws_autotune(dtws_t h, const int32_t *m_arr, const int32_t *r_arr, 
         bool c;
         if ((st = get_stats(h, m, s, &se, &c)) != DTWS_OK) return cleanup(st);
         const QueryBufs b = make_bufs(h, se, nullptr);
-        QueryArgs a = make_args(h, m, r, 1);
+        // shapes are timed on normalised windows whatever the options say
+        QueryArgs a = make_args(h, m, r, 1, false);
         a.tune_l = a.tune_k = a.tune_w = 0;
         // the query: a window of the series; the samples: evenly spread windows
         const int64_t N = h->n - m + 1;
@@ -1421,7 +1487,7 @@ static dtws_status at_prepare(dtws_t h, const float *Q, int32_t m, int32_t r, co
     StatsEntry *se;
     EnvEntry *ee = nullptr;
     bool c;
-    if ((st = get_stats(h, m, s, &se, &c)) != DTWS_OK) return st;
+    if ((st = query_stats(h, m, s, &se, &c)) != DTWS_OK) return st;
     const int rr = r > m - 1 ? m - 1 : r;
     if (need_env && (st = get_env(h, rr, s, &ee, &c)) != DTWS_OK) return st;
     if ((st = ensure_workspace(h)) != DTWS_OK) return st;

@@ -42,6 +42,10 @@ constexpr int kBins = 1024;         // survivor ordering bins
 constexpr int kDiagRMax = 511;      // widest band of the anti-diagonal DTW kernels (all shapes)
 constexpr int kDiagRMaxF32 = 1023;  // widest band of the FP32 anti-diagonal kernels (24, 32 cells per lane)
 constexpr uint64_t kEmptyKey = ~0ull;
+// Unnormalised DTW: the largest |value| accepted.  Path sums then stay
+// below 2^66 * 2 * 8192 = 2^80, far under the 1e30 boundary of the
+// double-float walk and the ~4e30 cost of its +-1e15 pads.
+constexpr float kRawAbsMax = 4294967296.0f;  // 2^32
 
 // status bits (device word in the handle)
 constexpr int kStNonFinite = 1;
@@ -94,6 +98,8 @@ struct QueryArgs {
     float qgrid;        // key grid: a power of two <= alpha/4
     int prescore;       // 1: the best Euclidean seed is scored on a side stream
     int tune_l, tune_k, tune_w;  // survivor DTW shape chosen by the autotuner (0: default)
+    int raw;            // 1: unnormalised DTW (the query and the re-scored windows are
+                        // taken as they are: mean 0, 1/sigma 1)
 };
 
 

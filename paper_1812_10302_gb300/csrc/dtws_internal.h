@@ -14,7 +14,8 @@ namespace dtws {
 void set_error_detail(const char *fmt, ...);
 
 // ---- series level (series_kernels.cu)
-cudaError_t launch_check_finite(const float *x, int64_t n, int *flag, cudaStream_t s);
+cudaError_t launch_check_finite(const float *x, int64_t n, int *flag, unsigned *absmax, cudaStream_t s);
+cudaError_t launch_fill(float *p, int64_t count, float v, int num_sms, cudaStream_t s);
 // pf: 4*n floats (P1 hi, P1 lo, P2 hi, P2 lo); bf: 5*nb floats (T1 hi, lo,
 // T2 hi, lo, anchors); ok: nb flags; nb = ceil(n / kBlockB); maxabs: one
 // word of scratch; scale: one float (the series' power-of-two scale)

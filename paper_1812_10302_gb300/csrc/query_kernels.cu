@@ -74,7 +74,8 @@ __global__ void __launch_bounds__(1024) k_qprep(const float *__restrict__ Q, Que
     if (threadIdx.x == 0) bad = 0;
     __syncthreads();
     bool nf = false;
-    for (int j = threadIdx.x; j < m; j += blockDim.x) nf |= !isfinite(Q[j]);
+    for (int j = threadIdx.x; j < m; j += blockDim.x)
+        nf |= !isfinite(Q[j]) || (a.raw && fabsf(Q[j]) > kRawAbsMax);
     if (nf) atomicOr(&bad, 1);
     __syncthreads();
     if (bad) {
@@ -88,8 +89,14 @@ __global__ void __launch_bounds__(1024) k_qprep(const float *__restrict__ Q, Que
     // One warp does the FP64 work: this part's FP64 units retire about one
     // lane operation per cycle per SM, so FP64 shuffle reductions in every
     // warp of the block would cost far more than the sums themselves.
+    // Unnormalised DTW takes the query as it is.
     __shared__ double mu_s, isg_s;
-    if (threadIdx.x < 32) {
+    if (threadIdx.x < 32 && a.raw) {
+        for (int j = threadIdx.x; j < m; j += 32) {
+            b.qh64[j] = (double)Q[j];
+            qs[j] = Q[j];
+        }
+    } else if (threadIdx.x < 32) {
         double s = 0.0;
         for (int j = threadIdx.x; j < m; j += 32) s += (double)Q[j];
 #pragma unroll
@@ -1254,8 +1261,8 @@ __global__ void __launch_bounds__(256) k_dtw64(QueryBufs b, QueryArgs a, const i
         // one division and square root per group (long FP64 sequences)
         if (lane == 0) {
             const double mu = s / (double)m, var = v / (double)m, mm = mu * mu;
-            bc[2 * gid] = mu;
-            bc[2 * gid + 1] = var <= 1e-24 * (mm > 1.0 ? mm : 1.0) ? 0.0 : 1.0 / sqrt(var);
+            bc[2 * gid] = a.raw ? 0.0 : mu;
+            bc[2 * gid + 1] = a.raw ? 1.0 : var <= 1e-24 * (mm > 1.0 ? mm : 1.0) ? 0.0 : 1.0 / sqrt(var);
         }
         __syncwarp(gmask);
         const double mu = bc[2 * gid], inv = bc[2 * gid + 1];
@@ -1364,8 +1371,8 @@ __global__ void __launch_bounds__(256) k_dtw64_mw(QueryBufs b, QueryArgs a, cons
             for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
             if (lane == 0) {
                 const double mu = sum / (double)m, var = v / (double)m, mm = mu * mu;
-                bc[2 * g] = mu;
-                bc[2 * g + 1] = var <= 1e-24 * (mm > 1.0 ? mm : 1.0) ? 0.0 : 1.0 / sqrt(var);
+                bc[2 * g] = a.raw ? 0.0 : mu;
+                bc[2 * g + 1] = a.raw ? 1.0 : var <= 1e-24 * (mm > 1.0 ? mm : 1.0) ? 0.0 : 1.0 / sqrt(var);
             }
         }
         group_bar(bar, nthr);
@@ -1970,8 +1977,8 @@ __global__ void k_prescore(QueryBufs b, QueryArgs a) {
         for (int o = LS / 2; o > 0; o >>= 1) v += __shfl_xor_sync(smask, v, o, LS);
         if (lane == 0) {
             const double var = v / (double)m, mm = mu * mu;
-            bc[0] = mu;
-            bc[1] = var <= 1e-24 * (mm > 1.0 ? mm : 1.0) ? 0.0 : 1.0 / sqrt(var);
+            bc[0] = a.raw ? 0.0 : mu;
+            bc[1] = a.raw ? 1.0 : var <= 1e-24 * (mm > 1.0 ? mm : 1.0) ? 0.0 : 1.0 / sqrt(var);
         }
     }
     // the group meets: named barrier 1 in paired mode, the warp otherwise

@@ -13,18 +13,41 @@
 namespace dtws {
 
 // ------------------------------------------------------------------ finite
-__global__ void k_check_finite(const float *__restrict__ x, int64_t n, int *flag) {
+// Also the largest |x| (as its FP32 bit pattern, which orders like the value
+// for non-negative floats; meaningful when no value is NaN or Inf).
+__global__ void k_check_finite(const float *__restrict__ x, int64_t n, int *flag, unsigned *absmax) {
     bool bad = false;
+    unsigned amax = 0u;
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n;
-         t += (int64_t)gridDim.x * blockDim.x)
-        bad |= !isfinite(x[t]);
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const float v = x[t];
+        bad |= !isfinite(v);
+        amax = max(amax, __float_as_uint(fabsf(v)));
+    }
     if (__any_sync(0xffffffffu, bad) && lane_id() == 0) atomicOr(flag, 1);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) amax = max(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+    if (lane_id() == 0 && amax) atomicMax(absmax, amax);
 }
 
-cudaError_t launch_check_finite(const float *x, int64_t n, int *flag, cudaStream_t s) {
+cudaError_t launch_check_finite(const float *x, int64_t n, int *flag, unsigned *absmax, cudaStream_t s) {
     int blocks = (int)((n + 255) / 256);
     if (blocks > 4096) blocks = 4096;
-    k_check_finite<<<blocks, 256, 0, s>>>(x, n, flag);
+    k_check_finite<<<blocks, 256, 0, s>>>(x, n, flag, absmax);
+    return cudaGetLastError();
+}
+
+__global__ void k_fill(float *__restrict__ p, int64_t count, float v) {
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < count;
+         t += (int64_t)gridDim.x * blockDim.x)
+        p[t] = v;
+}
+
+cudaError_t launch_fill(float *p, int64_t count, float v, int num_sms, cudaStream_t s) {
+    if (count <= 0) return cudaSuccess;
+    int64_t blocks = (count + 255) / 256;
+    if (blocks > 8LL * num_sms) blocks = 8LL * num_sms;
+    k_fill<<<(int)blocks, 256, 0, s>>>(p, count, v);
     return cudaGetLastError();
 }
 

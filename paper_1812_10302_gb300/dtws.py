@@ -57,6 +57,7 @@ class dtws_options(ctypes.Structure):
         ("batch_lanes", ctypes.c_int32),
         ("batch_graph", ctypes.c_int32),
         ("exclusion_zone", ctypes.c_int32),
+        ("unnormalised", ctypes.c_int32),
         ("wait_limit_ns", ctypes.c_int64),
         ("rng_seed", ctypes.c_uint64),
     ]

@@ -90,10 +90,13 @@ def test_binding_structs_match_the_header_layout(struct, tmp_path):
 
 
 def test_option_defaults(lib):
+    from ctypes import sizeof as ctypes_sizeof
     from paper_1812_10302_gb300 import dtws
     o = dtws.dtws_default_options()
     assert (o.ordering, o.timing, o.exact_envelope, o.batch_lanes, o.batch_graph, o.exclusion_zone,
-            o.rng_seed) == (dtws.DTWS_ORDER_PLAIN, 0, 1, 4, 1, 0, 0)
+            o.unnormalised, o.rng_seed) == (dtws.DTWS_ORDER_PLAIN, 0, 1, 4, 1, 0, 0, 0)
+    # the new field filled the padding before wait_limit_ns: the struct did not grow
+    assert ctypes_sizeof(dtws.dtws_options) == 64
 
 
 def test_create_rejects_bad_arguments_without_device_work(lib):

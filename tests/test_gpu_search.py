@@ -97,6 +97,72 @@ def test_exclusion_zone_matches_oracle(m, r, k, z):
     assert np.all(np.abs(idx[:, None] - idx[None, :])[~np.eye(k, dtype=bool)] > z)
 
 
+@pytest.mark.parametrize("m,r,k,shift,scale", [(64, 6, 3, 500.0, 3.0), (128, 25, 1, -1.0e4, 50.0),
+                                               (200, 20, 5, 0.0, 0.05)])
+def test_unnormalised_matches_oracle(m, r, k, shift, scale):
+    """Unnormalised DTW (raw values, Eq. 5 skipped): the oracle's FP64 brute
+    force over every raw window.  The building blocks at given offsets take
+    the raw values too: FP32 and extended DTW against the oracle's DTW, the
+    lower bounds admissible.  Switching the option back (a new graph
+    signature) gives the normalised answer again."""
+    x = (synth.random_walk(6_000, 70 + m).astype(np.float64) * scale + shift).astype(np.float32)
+    q, _ = synth.noisy_copy(x, m, 71 + m, 72 + m, noise=0.3 * scale)
+    offs = np.arange(0, x.size - m + 1, 97, dtype=np.int64)
+    with dtws.Index(x) as ix:
+        ni, nd = ix.query(q, r, k)
+        ix.set_options(unnormalised=1)
+        idx, dist = ix.query(q, r, k)
+        assert ix.sync_status() == dtws.DTWS_OK
+        idx2, dist2 = ix.query(q, r, k)  # (replayed graph)
+        d32 = ix.dtw_at(q, r, offs)
+        d64 = ix.dtw_at_f64(q, r, offs)
+        lbs = ix.lower_bounds_at(q, r, offs)
+        ix.set_options(unnormalised=0)
+        ni2, nd2 = ix.query(q, r, k)
+        assert ix.sync_status() == dtws.DTWS_OK
+    oi, od = oracle.search_brute_raw(x, q, r, k)
+    np.testing.assert_array_equal(idx, oi)
+    np.testing.assert_allclose(dist, od, rtol=1e-4, atol=0)
+    np.testing.assert_array_equal(idx2, idx)
+    np.testing.assert_array_equal(dist2, dist)
+    np.testing.assert_array_equal(ni2, ni)
+    np.testing.assert_array_equal(nd2, nd)
+    want = np.array([oracle.dtw(q, x[o:o + m], r) for o in offs])
+    np.testing.assert_allclose(d32, want, rtol=1e-4, atol=0)
+    np.testing.assert_allclose(d64, want, rtol=1e-9, atol=0)
+    for lb in lbs:
+        assert np.all(np.asarray(lb, np.float64) <= want * (1 + 1e-5))
+
+
+def test_unnormalised_refusals():
+    """Unnormalised DTW refuses the learned ordering (embeddings of
+    normalised windows), the batch, a series beyond +-2^32; a query beyond
+    +-2^32 is reported by dtws_sync_status."""
+    x = synth.random_walk(4_000, 81)
+    q, _ = synth.noisy_copy(x, 64, 82, 83, noise=0.3)
+    with dtws.Index(x) as ix:
+        ix.set_options(unnormalised=1)
+        with pytest.raises(dtws.DtwsError):
+            ix.query_batch([q, q], [6, 6], k=1)
+        bad = q.copy()
+        bad[5] = 1e10
+        ix.query(bad, 6, 1)
+        assert ix.sync_status() == dtws.DTWS_ENONFINITE
+        ix.query(q, 6, 1)
+        assert ix.sync_status() == dtws.DTWS_OK
+        ix.set_options(ordering=dtws.DTWS_ORDER_LEARNED)
+        with pytest.raises(dtws.DtwsError):
+            ix.query(q, 6, 1)
+    spiked = x.copy()
+    spiked[100] = 5e9
+    with dtws.Index(spiked) as ix:
+        ix.query(q, 6, 1)  # normalised: fine
+        assert ix.sync_status() == dtws.DTWS_OK
+        ix.set_options(unnormalised=1)
+        with pytest.raises(dtws.DtwsError):
+            ix.query(q, 6, 1)
+
+
 def test_random_query_not_a_copy(walk, index):
     """A query unrelated to the series: loose seeds, many survivors."""
     q = synth.random_walk(128, 999)

@@ -54,7 +54,7 @@ typedef enum {
                              returned order among near-ties may be inexact */
 } dtws_status;
 
-/* Limits of this build. */
+/* Limits of the library. */
 #define DTWS_M_MAX 8192      /* longest query (and block length of the
                                 anchored prefix sums, see dtws_create) */
 #define DTWS_K_MAX 64        /* largest k */

@@ -230,13 +230,20 @@ dtws_status get_stats(dtws_t h, int m, cudaStream_t s, StatsEntry **out, bool *c
         set_err("window statistics for m=%d: out of device memory", m);
         return DTWS_ENOMEM;
     }
-    CK(cudaMemsetAsync(e.mu_hi, 0, cap * 4, s));
-    CK(cudaMemsetAsync(e.mu_lo, 0, cap * 4, s));
-    CK(cudaMemsetAsync(e.inv_sigma, 0, cap * 4, s));
-    CK(cudaMemsetAsync(e.smu_hi, 0, scap * 4, s));
-    CK(cudaMemsetAsync(e.sinv_sigma, 0, scap * 4, s));
-    CK(launch_window_stats(h->x, h->n, m, h->pf, h->bf, h->pok, h->pscale, e.mu_hi, e.mu_lo, e.inv_sigma, e.smu_hi,
-                           e.sinv_sigma, h->num_sms, s));
+    cudaError_t ce = cudaMemsetAsync(e.mu_hi, 0, cap * 4, s);
+    if (ce == cudaSuccess) ce = cudaMemsetAsync(e.mu_lo, 0, cap * 4, s);
+    if (ce == cudaSuccess) ce = cudaMemsetAsync(e.inv_sigma, 0, cap * 4, s);
+    if (ce == cudaSuccess) ce = cudaMemsetAsync(e.smu_hi, 0, scap * 4, s);
+    if (ce == cudaSuccess) ce = cudaMemsetAsync(e.sinv_sigma, 0, scap * 4, s);
+    if (ce == cudaSuccess)
+        ce = launch_window_stats(h->x, h->n, m, h->pf, h->bf, h->pok, h->pscale, e.mu_hi, e.mu_lo, e.inv_sigma,
+                                 e.smu_hi, e.sinv_sigma, h->num_sms, s);
+    if (ce != cudaSuccess) {  // nothing half-initialised stays in the cache
+        free_stats(e);
+        cudaGetLastError();
+        set_err("window statistics for m=%d: %s", m, cudaGetErrorString(ce));
+        return DTWS_ECUDA;
+    }
     e.used = ++h->clock;
     h->stats.push_back(e);
     *out = &h->stats.back();
@@ -263,11 +270,17 @@ dtws_status get_ident(dtws_t h, cudaStream_t s, StatsEntry **out, bool *computed
             set_err("unnormalised statistics: out of device memory");
             return DTWS_ENOMEM;
         }
-        CK(cudaMemsetAsync(e.mu_hi, 0, cap * 4, s));
-        CK(cudaMemsetAsync(e.mu_lo, 0, cap * 4, s));
-        CK(cudaMemsetAsync(e.smu_hi, 0, scap * 4, s));
-        CK(launch_fill(e.inv_sigma, cap, 1.0f, h->num_sms, s));
-        CK(launch_fill(e.sinv_sigma, scap, 1.0f, h->num_sms, s));
+        cudaError_t ce = cudaMemsetAsync(e.mu_hi, 0, cap * 4, s);
+        if (ce == cudaSuccess) ce = cudaMemsetAsync(e.mu_lo, 0, cap * 4, s);
+        if (ce == cudaSuccess) ce = cudaMemsetAsync(e.smu_hi, 0, scap * 4, s);
+        if (ce == cudaSuccess) ce = launch_fill(e.inv_sigma, cap, 1.0f, h->num_sms, s);
+        if (ce == cudaSuccess) ce = launch_fill(e.sinv_sigma, scap, 1.0f, h->num_sms, s);
+        if (ce != cudaSuccess) {
+            free_stats(e);
+            cudaGetLastError();
+            set_err("unnormalised statistics: %s", cudaGetErrorString(ce));
+            return DTWS_ECUDA;
+        }
         h->ident = e;
         *computed = true;
     }
@@ -306,9 +319,15 @@ dtws_status get_env(dtws_t h, int r, cudaStream_t s, EnvEntry **out, bool *compu
         set_err("series envelope for r=%d: out of device memory", r);
         return DTWS_ENOMEM;
     }
-    CK(cudaMemsetAsync(e.U, 0, h->n_alloc * 4, s));
-    CK(cudaMemsetAsync(e.L, 0, h->n_alloc * 4, s));
-    CK(launch_envelope(h->x, h->n, r, e.U, e.L, s));
+    cudaError_t ce = cudaMemsetAsync(e.U, 0, h->n_alloc * 4, s);
+    if (ce == cudaSuccess) ce = cudaMemsetAsync(e.L, 0, h->n_alloc * 4, s);
+    if (ce == cudaSuccess) ce = launch_envelope(h->x, h->n, r, e.U, e.L, s);
+    if (ce != cudaSuccess) {
+        free_env(e);
+        cudaGetLastError();
+        set_err("series envelope for r=%d: %s", r, cudaGetErrorString(ce));
+        return DTWS_ECUDA;
+    }
     e.used = ++h->clock;
     h->env.push_back(e);
     *out = &h->env.back();
@@ -394,13 +413,20 @@ dtws_status get_learn(dtws_t h, int m, const StatsEntry *se, cudaStream_t s, Lea
         set_err("learned embeddings for m=%d: out of device memory", m);
         return DTWS_ENOMEM;
     }
-    CK(launch_enc_series(h->enc_blob, h->x, h->n, enc_block(m), se->inv_sigma, e.rows, e.E, h->num_sms, s));
-    CK(launch_enc_quant(e.E, e.rows, e.Q, e.S, s));
-    if (e.rows2 > 0) {  // the same pass over the series shifted by the phase
+    cudaError_t ce = launch_enc_series(h->enc_blob, h->x, h->n, enc_block(m), se->inv_sigma, e.rows, e.E,
+                                       h->num_sms, s);
+    if (ce == cudaSuccess) ce = launch_enc_quant(e.E, e.rows, e.Q, e.S, s);
+    if (ce == cudaSuccess && e.rows2 > 0) {  // the same pass over the series shifted by the phase
         const int ph = enc_phase(m);
-        CK(launch_enc_series(h->enc_blob, h->x + ph, h->n - ph, enc_block(m), se->inv_sigma + ph, e.rows2, e.E2,
-                             h->num_sms, s));
-        CK(launch_enc_quant(e.E2, e.rows2, e.Q2, e.S2, s));
+        ce = launch_enc_series(h->enc_blob, h->x + ph, h->n - ph, enc_block(m), se->inv_sigma + ph, e.rows2, e.E2,
+                               h->num_sms, s);
+        if (ce == cudaSuccess) ce = launch_enc_quant(e.E2, e.rows2, e.Q2, e.S2, s);
+    }
+    if (ce != cudaSuccess) {
+        free_learn(e);
+        cudaGetLastError();
+        set_err("learned embeddings for m=%d: %s", m, cudaGetErrorString(ce));
+        return DTWS_ECUDA;
     }
     e.used = ++h->clock;
     h->learn.push_back(e);

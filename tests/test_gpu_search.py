@@ -134,6 +134,22 @@ def test_unnormalised_matches_oracle(m, r, k, shift, scale):
         assert np.all(np.asarray(lb, np.float64) <= want * (1 + 1e-5))
 
 
+def test_unnormalised_with_exclusion_zone():
+    """Both options at once: the oracle's greedy selection over the FP64 DTW
+    of every raw window."""
+    x = (synth.random_walk(8_000, 95).astype(np.float64) * 2.0 + 100.0).astype(np.float32)
+    m, r, k, z = 96, 10, 3, 8
+    q, _ = synth.noisy_copy(x, m, 96, 97, noise=0.6)
+    with dtws.Index(x) as ix:
+        ix.set_options(unnormalised=1, exclusion_zone=z)
+        idx, dist = ix.query(q, r, k)
+        assert ix.sync_status() == dtws.DTWS_OK
+    d = np.array([oracle.dtw(q, x[o:o + m], r) for o in range(x.size - m + 1)])
+    oi, od = oracle.exclusion_topk(d, k, z)
+    np.testing.assert_array_equal(idx, oi)
+    np.testing.assert_allclose(dist, od, rtol=1e-4, atol=0)
+
+
 def test_unnormalised_refusals():
     """Unnormalised DTW refuses the learned ordering (embeddings of
     normalised windows), the batch, a series beyond +-2^32; a query beyond

@@ -1,20 +1,33 @@
 // query_kernels.cu -- per-query kernels of the search (arxiv 1812.10302):
 //
 //   k_query_reset   clear the device query state
-//   k_qprep         z-normalise Q (Sec. 2.2, Eq. 5; FP64 two-pass), its
-//                   envelope (Eq. 9) and the order of |q_hat| (largest first)
-//   k_seed_scan     proxy scan: per tile, the window with the smallest partial
-//                   squared distance on the largest-|q_hat| positions
+//   k_qprep         z-normalise Q (Sec. 2.2, Eq. 5; FP64 two-pass; taken as
+//                   it is for unnormalised DTW), its envelope (Eq. 9) and the
+//                   order of |q_hat| (largest first)
+//   k_seed_scan     proxy scan: each CTA's window with the smallest squared
+//                   distance on evenly spaced query positions, to its slot
+//   k_prop_merge    the P best of the per-CTA slots (rank selection)
 //   k_seed_gather   seed offsets = seeded random windows (the paper's random
-//                   first bsf, Algorithm 1) + the proxy proposals
-//   k_dtw<SEED>     DTW of the seeds -> k-th seed distance = first bsf
-//   k_lb_scan       fused cascade per tile (Sec. 2.2, Eqs. 6-10): LB_KimFL,
-//                   LB_Keogh vs the query envelope, LB_Keogh vs the series
-//                   envelope, with in-CTA compaction between the stages
+//                   first bsf, Algorithm 1) + the proposals
+//   k_seed_ed       Euclidean distance of each seed (an upper bound of the
+//                   banded DTW) -> first bsf
+//   k_seed_expand   k > 1: offsets within +-k of the two best Euclidean
+//                   seeds join the seeds, distinct
+//   k_dtw<SEED>     exact DTW of the seeds when k > 1
+//   k_prescore      the best seed's FP32 DTW and its extended re-score, on a
+//                   side stream during the scan
+//   k_lb_scan       LB_KimFL (Eq. 7) and LB_Keogh vs the query envelope
+//                   (Eq. 8) per window of a bulk-copied tile; survivors
+//                   appended by warp ballot
 //   k_bin_*         order the survivors by lower bound (counting sort)
-//   k_dtw<SURV>     banded DTW (Eq. 1 + band) of the survivors in that order,
-//                   early abandon, lock-free top-k list
-//   k_final_*       FP64 re-score of the top-k and its near-ties, output
+//   k_dtw<SURV>     LB_Keogh vs the series envelope (Eq. 10) as a pre-check,
+//                   then banded DTW (Eq. 1 + band) of the survivors in that
+//                   order, early abandon, lock-free top-k list
+//   k_final_select  the top-k and every near-tie within the margin
+//   k_dtw64*        their extended-precision re-score (FP64 statistics,
+//                   double-float DTW)
+//   k_final_sort    order by (re-scored distance, offset), output
+//   k_exclusion_select  greedy top-k with an exclusion zone over the K best
 //
 // Pruning (Eq. 6, strict): a window is dropped when a lower bound exceeds
 // thr = bsf*(1+delta) + alpha, bsf being the k-th best distance found so far.

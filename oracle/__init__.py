@@ -262,3 +262,31 @@ def exclusion_topk(dists, k: int, z: int):
                 break
     idx = np.array(taken, np.int64)
     return idx, d[idx]
+
+
+def separated_kth(dists, k: int, sep: int, order=None) -> float:
+    """A pruning threshold for top-k with an exclusion zone z (``exclusion_topk``),
+    taken from windows found so far: insert the windows ``order`` (offsets,
+    default every window by offset) one at a time into a set that keeps, of
+    any two windows within ``sep`` samples of each other, the one with the
+    smaller (distance, offset); return the k-th smallest distance in the set
+    (inf if it holds fewer than k).  The kept windows are pairwise more than
+    ``sep`` apart.  With sep = 2z the result is an upper bound of the k-th
+    distance of the exclusion-zone answer: each window that the greedy
+    selection takes, or that it skips because of a taken window, accounts for
+    at most one kept window (two kept windows within z of one taken window
+    would be at most 2z apart), so the selection has taken k windows before
+    its distances pass the k-th kept one.  With sep = z it is not a bound
+    (one taken window can shut out two kept ones)."""
+    d = np.asarray(dists, np.float64)
+    kept: dict[int, float] = {}
+    for w in (range(d.size) if order is None else order):
+        w = int(w)
+        near = [v for v in kept if abs(v - w) <= sep]
+        if any((kept[v], v) < (d[w], w) for v in near):
+            continue
+        for v in near:
+            del kept[v]
+        kept[w] = float(d[w])
+    vals = sorted(kept.values())
+    return vals[k - 1] if len(vals) >= k else INF

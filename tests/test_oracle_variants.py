@@ -93,3 +93,49 @@ def test_exclusion_answer_lies_in_the_plain_top_k_2z_plus_1(seed):
         sub[top] = d[top]
         idx2, _ = oracle.exclusion_topk(sub, k, z)
         np.testing.assert_array_equal(idx2, idx)
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_two_z_separated_set_bounds_the_exclusion_answer(seed):
+    """Any windows found so far, kept pairwise more than 2z apart, give a
+    threshold no smaller than the exclusion-zone answer's k-th distance,
+    whatever the order and subset in which they are found."""
+    rng = np.random.default_rng(100 + seed)
+    n = 600
+    d = np.cumsum(rng.normal(0, 1, n)) ** 2 if seed % 2 else rng.random(n)
+    for k, z in ((1, 3), (3, 10), (5, 4), (2, 40), (4, 25)):
+        _, dist = oracle.exclusion_topk(d, k, z)
+        if dist.size < k:
+            continue
+        for trial in range(4):
+            found = rng.permutation(n)[: int(n * (0.3 + 0.2 * trial))]
+            t = oracle.separated_kth(d, k, 2 * z, order=found)
+            assert t >= dist[k - 1]
+        # all windows found, in offset order: the same holds
+        assert oracle.separated_kth(d, k, 2 * z) >= dist[k - 1]
+
+
+def test_z_separated_set_is_not_a_bound():
+    """The threshold needs 2z: with windows kept only z apart, one taken
+    window can shut out two kept ones."""
+    z = 5
+    d = np.full(200, 100.0) + np.arange(200) * 1e-3
+    d[50], d[50 - z], d[50 + z] = 1.0, 2.0, 2.0
+    _, dist = oracle.exclusion_topk(d, 2, z)
+    assert dist[1] >= 100.0  # 45 and 55 lie within z of the first pick, 50
+    found = [50 - z, 50 + z]  # found before 50
+    assert oracle.separated_kth(d, 2, z, order=found) == 2.0 < dist[1]
+    assert oracle.separated_kth(d, 2, 2 * z, order=found) == np.inf
+    assert oracle.separated_kth(d, 2, 2 * z, order=found + [50]) >= dist[1]
+
+
+def test_separated_set_keeps_the_better_neighbour():
+    d = np.array([5.0, 3.0, 4.0, 1.0, 9.0, 9.0, 9.0, 2.0])
+    # sep 1: kept {3 (1.0), 7 (2.0), 1 (3.0), 5 (9.0)} -> sorted 1, 2, 3, 9
+    assert oracle.separated_kth(d, 1, 1) == 1.0
+    assert oracle.separated_kth(d, 3, 1) == 3.0
+    assert oracle.separated_kth(d, 4, 1) == 9.0
+    assert oracle.separated_kth(d, 5, 1) == np.inf
+    # insertion order does not matter for sep 1 here: the kept set is the same
+    assert oracle.separated_kth(d, 3, 1, order=[7, 6, 5, 4, 3, 2, 1, 0]) == 3.0
+

@@ -139,3 +139,61 @@ def test_separated_set_keeps_the_better_neighbour():
     # insertion order does not matter for sep 1 here: the kept set is the same
     assert oracle.separated_kth(d, 3, 1, order=[7, 6, 5, 4, 3, 2, 1, 0]) == 3.0
 
+
+def _exclusion_search(d, lb, k, z, sep):
+    """The search procedure for wide exclusion zones, simulated on the host:
+    windows come in lower-bound order (admissible bounds), each one whose
+    bound is within the threshold is scored, scored windows within the
+    threshold go to a buffer and to the list kept ``sep`` apart, the
+    threshold is the smallest k-th distance that list has had; at the end
+    the buffer, filtered by the final threshold, is taken greedily.
+    Returns (offsets, distances, final threshold, windows scored)."""
+    n = d.size
+    thr, found, buf, scored = np.inf, [], [], 0
+    for w in np.lexsort((np.arange(n), lb)):
+        if lb[w] > thr:
+            continue  # pruned
+        scored += 1
+        if d[w] <= thr:
+            buf.append(int(w))
+            found.append(int(w))
+            thr = min(thr, oracle.separated_kth(d, k, sep, order=found))
+    keep = np.array([w for w in buf if d[w] <= thr], np.int64)
+    sub = np.full(n, np.inf)
+    sub[keep] = d[keep]
+    idx, dist = oracle.exclusion_topk(sub, k, z)
+    return idx, dist, thr, scored
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_exclusion_search_with_the_2z_threshold_is_exact(seed):
+    """The simulated search with the list kept 2z apart returns the
+    exclusion-zone answer over every window, and prunes."""
+    rng = np.random.default_rng(200 + seed)
+    n = 500
+    d = np.cumsum(rng.normal(0, 1, n)) ** 2 + rng.random(n) if seed % 2 else rng.random(n) * 10
+    lb = d * rng.uniform(0.3, 1.0, n)
+    for k, z in ((2, 30), (4, 12), (3, 60)):
+        want_i, want_d = oracle.exclusion_topk(d, k, z)
+        got_i, got_d, thr, scored = _exclusion_search(d, lb, k, z, 2 * z)
+        np.testing.assert_array_equal(got_i, want_i)
+        np.testing.assert_array_equal(got_d, want_d)
+        assert thr >= want_d[-1]
+        assert scored < n  # the threshold pruned something
+
+
+def test_exclusion_search_with_a_z_threshold_loses_a_match():
+    """The same search with the list kept only z apart prunes the second
+    match: the two windows beside the best one are found first and set a
+    threshold that the best one then invalidates."""
+    z = 5
+    d = np.full(200, 100.0) + np.arange(200) * 1e-3
+    d[50], d[50 - z], d[50 + z] = 1.0, 2.0, 2.0
+    lb = d * 0.9
+    lb[50] = 1.95  # scored after its neighbours
+    want_i, want_d = oracle.exclusion_topk(d, 2, z)
+    got_i, got_d, _, _ = _exclusion_search(d, lb, 2, z, 2 * z)
+    np.testing.assert_array_equal(got_i, want_i)
+    np.testing.assert_array_equal(got_d, want_d)
+    _, bad_d, _, _ = _exclusion_search(d, lb, 2, z, z)
+    assert want_d[1] < np.inf and bad_d[1] == np.inf  # the second match was pruned

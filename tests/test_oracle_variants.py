@@ -140,14 +140,32 @@ def test_separated_set_keeps_the_better_neighbour():
     assert oracle.separated_kth(d, 3, 1, order=[7, 6, 5, 4, 3, 2, 1, 0]) == 3.0
 
 
-def _exclusion_search(d, lb, k, z, sep):
+def _bucket_kth(d, k, z, found):
+    """The lock-free form of the threshold: offsets cut into buckets of
+    2z + 1; windows in different buckets of the same parity are at least
+    2z + 2 apart.  Per parity, the first window found in each bucket enters a
+    list once; the k-th smallest of either list bounds the answer (each entry
+    is a real window's distance, the entries pairwise more than 2z apart)."""
+    W = 2 * z + 1
+    first = {}
+    for w in found:
+        first.setdefault(w // W, float(d[w]))
+    best = np.inf
+    for parity in (0, 1):
+        vals = sorted(v for b, v in first.items() if b % 2 == parity)
+        if len(vals) >= k:
+            best = min(best, vals[k - 1])
+    return best
+
+
+def _exclusion_search(d, lb, k, z, sep, buckets=False):
     """The search procedure for wide exclusion zones, simulated on the host:
     windows come in lower-bound order (admissible bounds), each one whose
     bound is within the threshold is scored, scored windows within the
-    threshold go to a buffer and to the list kept ``sep`` apart, the
-    threshold is the smallest k-th distance that list has had; at the end
-    the buffer, filtered by the final threshold, is taken greedily.
-    Returns (offsets, distances, final threshold, windows scored)."""
+    threshold go to a buffer and to the list kept ``sep`` apart (or to the
+    bucket lists), the threshold is the smallest k-th distance that list has
+    had; at the end the buffer, filtered by the final threshold, is taken
+    greedily.  Returns (offsets, distances, final threshold, windows scored)."""
     n = d.size
     thr, found, buf, scored = np.inf, [], [], 0
     for w in np.lexsort((np.arange(n), lb)):
@@ -157,7 +175,8 @@ def _exclusion_search(d, lb, k, z, sep):
         if d[w] <= thr:
             buf.append(int(w))
             found.append(int(w))
-            thr = min(thr, oracle.separated_kth(d, k, sep, order=found))
+            t = _bucket_kth(d, k, z, found) if buckets else oracle.separated_kth(d, k, sep, order=found)
+            thr = min(thr, t)
     keep = np.array([w for w in buf if d[w] <= thr], np.int64)
     sub = np.full(n, np.inf)
     sub[keep] = d[keep]
@@ -167,19 +186,21 @@ def _exclusion_search(d, lb, k, z, sep):
 
 @pytest.mark.parametrize("seed", range(4))
 def test_exclusion_search_with_the_2z_threshold_is_exact(seed):
-    """The simulated search with the list kept 2z apart returns the
-    exclusion-zone answer over every window, and prunes."""
+    """The simulated search with the list kept 2z apart, and with its
+    lock-free bucket form, returns the exclusion-zone answer over every
+    window, and prunes."""
     rng = np.random.default_rng(200 + seed)
     n = 500
     d = np.cumsum(rng.normal(0, 1, n)) ** 2 + rng.random(n) if seed % 2 else rng.random(n) * 10
     lb = d * rng.uniform(0.3, 1.0, n)
     for k, z in ((2, 30), (4, 12), (3, 60)):
         want_i, want_d = oracle.exclusion_topk(d, k, z)
-        got_i, got_d, thr, scored = _exclusion_search(d, lb, k, z, 2 * z)
-        np.testing.assert_array_equal(got_i, want_i)
-        np.testing.assert_array_equal(got_d, want_d)
-        assert thr >= want_d[-1]
-        assert scored < n  # the threshold pruned something
+        for buckets in (False, True):
+            got_i, got_d, thr, scored = _exclusion_search(d, lb, k, z, 2 * z, buckets)
+            np.testing.assert_array_equal(got_i, want_i)
+            np.testing.assert_array_equal(got_d, want_d)
+            assert thr >= want_d[-1]
+            assert scored < n  # the threshold pruned something
 
 
 def test_exclusion_search_with_a_z_threshold_loses_a_match():
@@ -192,8 +213,9 @@ def test_exclusion_search_with_a_z_threshold_loses_a_match():
     lb = d * 0.9
     lb[50] = 1.95  # scored after its neighbours
     want_i, want_d = oracle.exclusion_topk(d, 2, z)
-    got_i, got_d, _, _ = _exclusion_search(d, lb, 2, z, 2 * z)
-    np.testing.assert_array_equal(got_i, want_i)
-    np.testing.assert_array_equal(got_d, want_d)
+    for buckets in (False, True):
+        got_i, got_d, _, _ = _exclusion_search(d, lb, 2, z, 2 * z, buckets)
+        np.testing.assert_array_equal(got_i, want_i)
+        np.testing.assert_array_equal(got_d, want_d)
     _, bad_d, _, _ = _exclusion_search(d, lb, 2, z, z)
     assert want_d[1] < np.inf and bad_d[1] == np.inf  # the second match was pruned

@@ -248,6 +248,19 @@ def _stream_ptr(stream) -> int:
     return int(stream.cuda_stream)
 
 
+def apply_options(o: dtws_options, kw: dict) -> dtws_options:
+    """Set the named fields of a dtws_options; an unknown name raises
+    (a ctypes structure would otherwise take it as a plain attribute and the
+    library would never see it)."""
+    fields = {f for f, _ in dtws_options._fields_}
+    unknown = sorted(set(kw) - fields)
+    if unknown:
+        raise KeyError(f"unknown dtws_options field(s): {', '.join(unknown)}")
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return o
+
+
 class _Arg:
     """Pointer to an array's data: a contiguous torch tensor (any device) or
     a NumPy array kept alive for the call."""
@@ -298,8 +311,7 @@ class Index:
 
     def set_options(self, **kw):
         o = dtws_get_options(self.h)
-        for k, v in kw.items():
-            setattr(o, k, v)
+        apply_options(o, kw)
         dtws_set_options(self.h, o)
 
     def options(self) -> dict:

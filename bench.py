@@ -164,25 +164,33 @@ def make_workload(name: str, rank: int = 0, world: int = 1):
 
 
 # ------------------------------------------------------------------ CPU oracle
-def cpu_oracle_sample(x, q, r, k, true_off, budget_windows: int):
-    """Oracle cascade (FP64) over a window range around the true offset,
-    fragment-parallel over the host cores (Eq. 11)."""
-    import oracle  # test infrastructure: the CPU baseline leg only
+def cpu_oracle_sample(x, q, r, k, first: int, count: int):
+    """Oracle cascade (FP64, anchored window statistics) over the windows
+    [first, first + count), fragment-parallel over the host cores (Eq. 11)."""
+    import oracle  # test infrastructure: the CPU baseline legs only
     from oracle import fragments
     m = q.size
     N = x.size - m + 1
-    cnt = min(budget_windows, N)
-    first = max(0, min(true_off - cnt // 2, N - cnt))
+    cnt = max(1, min(count, N - first))
     cores = fragments.host_threads()
     t0 = time.perf_counter()
     idx, dist = fragments.search_fragments(x, q, r, k, threads=cores, F=cores * 4, first=first,
                                            count=cnt, stats="anchored")
     dt = time.perf_counter() - t0
     _ = oracle
+    whole = first == 0 and cnt == N
+    what = "all windows" if whole else f"windows [{first}, {first + cnt})"
     return dict(value=cnt / dt, unit="subsequences/s", cores=cores, kind="oracle",
-                sample=f"windows [{first}, {first + cnt}) of the same series and query "
-                       f"(FP64 UCR-style cascade, anchored stats, Eq. 11 fragments over "
-                       f"{cores} threads)", seconds=dt, idx=int(idx[0]), dist=float(dist[0]))
+                sample=f"{what} of the same series and query (FP64 UCR-style cascade, anchored stats, "
+                       f"Eq. 11 fragments over {cores} threads)", seconds=dt, windows=cnt,
+                idx=[int(v) for v in idx], dist=[float(v) for v in dist])
+
+
+def cpu_oracle_fp64_at(x, qs, r, answers):
+    """The FP64 oracle's DTW at the windows the GPU returned (CPU oracle leg:
+    the reference values of the FP32 error the drift workload reports)."""
+    import oracle  # test infrastructure: the CPU baseline legs only
+    return [float(oracle.dtw_at(x, q, r, [int(i)])[0]) for q, i in zip(qs, answers)]
 
 
 def reference_arm(args):
@@ -190,14 +198,18 @@ def reference_arm(args):
     if rank != 0:
         return 0
     x, q, r, k, o = make_workload(args.workload)
-    # size each step so that the whole warm-up + timed run takes about 150 s of host time
-    probe = cpu_oracle_sample(x, q, r, k, o, 1_000_000)
-    rate = 1_000_000 / probe["seconds"]
-    budget = int(min(args.cpu_windows, max(1_000_000, rate * 150.0 / (args.warmup + args.steps))))
+    # each step searches the first `budget` windows of the series (a slice
+    # that starts at window 0, not one centred on the answer); sized so that
+    # the whole warm-up + timed run takes about 150 s of host time
+    probe = cpu_oracle_sample(x, q, r, k, 0, 1_000_000)
+    rate = probe["windows"] / probe["seconds"]
+    budget = int(max(1_000_000, rate * 150.0 / (args.warmup + args.steps)))
+    if args.cpu_windows:
+        budget = min(budget, args.cpu_windows)
     times = []
     res = None
     for s in range(args.warmup + args.steps):
-        res = cpu_oracle_sample(x, q, r, k, o, budget)
+        res = cpu_oracle_sample(x, q, r, k, 0, budget)
         if s >= args.warmup:
             times.append(res["seconds"])
     ms = 1e3 * statistics.mean(times)
@@ -341,8 +353,14 @@ def gpu_arm(args):
     lb_bytes = N * 16 + st["pass_keogh_q"] * 8  # the scan writes (bound, offset) per survivor
     achieved = lb_bytes / (lb_ms * 1e-3) / 1e9 if lb_ms > 0 else None
     cpu = None
-    if not args.no_cpu_baseline and world == 1 or (not args.no_cpu_baseline and rank == 0 and world == 1):
-        cpu = cpu_oracle_sample(x, q, r, k, true_off, args.cpu_windows)
+    if not args.no_cpu_baseline and world == 1:
+        # the oracle over every window of the same series and query (or the
+        # first --cpu-windows of them when that is smaller), and whether it
+        # returns the GPU's answer
+        cpu = cpu_oracle_sample(x, q, r, k, 0, args.cpu_windows or N)
+        cpu["agrees_with_gpu"] = (cpu["windows"] == N and cpu["idx"] == [int(v) for v in idx_h] and
+                                  all(abs(a - b) <= 1e-4 * max(abs(b), 1e-6 * m) for a, b in
+                                      zip(map(float, dist_h), cpu["dist"])))
     value = total_windows / (ms * 1e-3)
     # The survivor DTW stage against its ALU ceiling: every SM's 128 FP32/ALU
     # lanes at the maximum SM clock, 5 operations per band cell (subtract,
@@ -402,6 +420,8 @@ def gpu_arm(args):
     }
     if cpu is not None:
         line["cpu_baseline"]["seconds"] = cpu["seconds"]
+        line["cpu_baseline"]["answer"] = {"offsets": cpu["idx"], "dist": cpu["dist"],
+                                          "agrees_with_gpu": cpu["agrees_with_gpu"]}
     ix.close()
     if world == 1 and not args.no_extras:
         del qd, idx_d, dist_d
@@ -410,7 +430,7 @@ def gpu_arm(args):
         torch.cuda.empty_cache()
         line["batch"] = batch_leg(dev)
         torch.cuda.empty_cache()
-        line["drift"] = drift_leg(dev)
+        line["drift"] = drift_leg(dev, fp64_oracle=not args.no_cpu_baseline)
     print(json.dumps(line))
     return 0
 
@@ -566,12 +586,12 @@ def batch_leg(dev):
             "single_query_sample": sample}
 
 
-def drift_leg(dev):
+def drift_leg(dev, fp64_oracle: bool = True):
     """The precision-stress workload (n = 1e9 walk with drift 1e-3 and
     variance regimes, 32 noisy queries m = 1024, r = 102, top-1): mean ms per
-    query, and per query the relative difference between the FP32 DTW at the
-    answer and the library's extended-precision re-score of it (the FP64
-    oracle comparison of the same workload is in the test suite)."""
+    query and, per query, the relative error against the FP64 oracle's DTW at
+    the returned window of (a) the FP32 DTW the search prunes with and (b) the
+    returned (extended-precision re-scored) distance."""
     import torch
 
     from paper_1812_10302_gb300 import dtws, synth
@@ -581,23 +601,27 @@ def drift_leg(dev):
     ix = dtws.Index(torch.from_numpy(x).to(dev))
     torch.cuda.synchronize(dev)
     create_s = time.perf_counter() - t0
-    del x
     qds = [torch.from_numpy(q).to(dev) for q in qs]
     ms = _mean_query_ms(ix, qds, r, 1, dev)
     sample = _phase_sample(ix, qds, [r] * len(qds), 1, 4)
-    errs = []
+    ans, f32, ret = [], [], []
     for q in qs:
         i, d = ix.query(q, r, 1)
-        f32 = ix.dtw_at(q, r, i)
-        f64 = ix.dtw_at_f64(q, r, i)
-        errs.append(abs(float(f32[0]) - float(f64[0])) / max(float(f64[0]), 1e-30))
+        ans.append(int(i[0]))
+        ret.append(float(d[0]))
+        f32.append(float(ix.dtw_at(q, r, i)[0]))
     ix.close()
-    return {"workload": "drift: walk with drift 1e-3 and variance regimes, n=1000000000, 32 noisy copies "
-                        "m=1024, r=102, top-1",
-            "ms_per_query": ms, "subsequences_per_s": (1_000_000_000 - 1023) / (ms * 1e-3),
-            "create_seconds": create_s,
-            "fp32_dtw_rel_error_vs_extended": {"max": max(errs), "median": float(np.median(errs))},
-            "single_query_sample": sample}
+    out = {"workload": "drift: walk with drift 1e-3 and variance regimes, n=1000000000, 32 noisy copies "
+                       "m=1024, r=102, top-1",
+           "ms_per_query": ms, "subsequences_per_s": (1_000_000_000 - 1023) / (ms * 1e-3),
+           "create_seconds": create_s, "single_query_sample": sample}
+    if fp64_oracle:
+        ref = cpu_oracle_fp64_at(x, qs, r, ans)
+        e32 = [abs(a - b) / max(b, 1e-30) for a, b in zip(f32, ref)]
+        eret = [abs(a - b) / max(b, 1e-30) for a, b in zip(ret, ref)]
+        out["fp32_dtw_rel_error_vs_fp64_oracle"] = {"max": max(e32), "median": float(np.median(e32))}
+        out["returned_dist_rel_error_vs_fp64_oracle"] = {"max": max(eret), "median": float(np.median(eret))}
+    return out
 
 
 def main():
@@ -607,8 +631,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="dtws", choices=["dtws", "reference"])
     ap.add_argument("--workload", default="rw100m", choices=sorted(SPECS))
-    ap.add_argument("--cpu-windows", type=int, default=20_000_000,
-                    help="windows in the CPU oracle's bounded sample")
+    ap.add_argument("--cpu-windows", type=int, default=0,
+                    help="windows in the CPU oracle's sample (0: every window for the GPU arm's "
+                         "cpu_baseline; the reference arm sizes its steps itself, at most this many "
+                         "when given)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ordering", default="proxy", choices=["proxy", "learned", "random"],
                     help="seeding of the timed queries: proxy scan (default), learned proposals, or "

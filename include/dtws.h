@@ -408,10 +408,12 @@ dtws_status dtws_trainer_destroy(dtws_trainer_t t);
  * through its own pool, or the deployment fixes its memory at start-up).
  * Inputs and outputs are the caller's DEVICE arrays: series FP32 [n],
  * Q FP32 [m] (raw), offsets int64 [count] (each in [0, n-m]), out FP32
- * [count]; nothing is staged.  Result: the FP32 banded DTW (Eq. 1 + band) of
+ * [count]; nothing is staged.  Result: the FP32 Sakoe-Chiba-banded DTW of
  * the z-normalised query against each z-normalised window, each window's
- * statistics computed two-pass in FP64; an offset out of range, or a
- * non-finite query, gives NaN.
+ * mean and deviation computed two-pass in FP64, the same quantity as
+ * dtws_dtw_at; an offset out of range, or a non-finite query, gives NaN.
+ * count may be any value >= 0 (the work cursor is 64-bit); count == 0
+ * returns at once.
  * Working memory is one fixed device array inside the library (about 33 KB,
  * held by every GPU that loads the library until the process exits).  Its
  * device address is looked up on the first call made on each device, so
@@ -419,7 +421,10 @@ dtws_status dtws_trainer_destroy(dtws_trainer_t t);
  * array: each call resets what it uses, and calls whose work overlaps on the
  * GPU race, so do not run two at once.
  * Errors (synchronous): DTWS_EINVAL for null or host pointers, n or r out of
- * range, or m beyond DTWS_NOALLOC_M_MAX (the scratch size); DTWS_ECUDA.
+ * range, m beyond DTWS_NOALLOC_M_MAX (the scratch size), or a query length
+ * and band whose one-warp shared memory (4 m + 8 (r + 1) bytes) exceeds the
+ * device's per-block limit (not reached on GB300 within DTWS_NOALLOC_M_MAX);
+ * DTWS_ECUDA.
  */
 dtws_status dtws_dtw_at_noalloc(const float *series, int64_t n, const float *Q, int32_t m,
                                 int32_t r, const int64_t *offsets, int64_t count, float *out,

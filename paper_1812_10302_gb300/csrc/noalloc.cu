@@ -29,8 +29,15 @@
 
 namespace {
 
-constexpr int kNoAllocCursor = DTWS_NOALLOC_M_MAX;      // int slot after q_hat
+constexpr int kNoAllocCursor = DTWS_NOALLOC_M_MAX;      // 64-bit slot after q_hat (8-byte aligned)
 constexpr int kNoAllocFloats = DTWS_NOALLOC_M_MAX + 64;  // q_hat, cursor, padding
+
+// The largest launch this entry point makes is one warp (a group of 32
+// lanes) at m = DTWS_NOALLOC_M_MAX and r = m - 1: the normalised query
+// (4 m bytes) plus one ring of 2r + 2 floats (8 m bytes).  It must fit the
+// 227 KB a CTA may opt into on this part; the run-time check below also
+// compares it with the device's own limit.
+static_assert(12 * DTWS_NOALLOC_M_MAX <= 227 * 1024, "scratch query length too long for one warp's shared memory");
 
 }  // namespace
 
@@ -52,7 +59,7 @@ __global__ void __launch_bounds__(1024) k_noalloc_prep(const float *__restrict__
     for (int j = threadIdx.x; j < m; j += blockDim.x) nf |= !isfinite(Q[j]);
     if (nf) atomicOr(&bad, 1);
     __syncthreads();
-    if (threadIdx.x == 0) ((int *)scratch)[kNoAllocCursor] = 0;
+    if (threadIdx.x == 0) *(unsigned long long *)(scratch + kNoAllocCursor) = 0ull;
     if (bad) {
         if (threadIdx.x == 0) scratch[0] = __int_as_float(0x7fc00000);
         return;
@@ -100,12 +107,14 @@ __global__ void __launch_bounds__(256) k_noalloc_dtw(const float *__restrict__ x
     const int gid = warp * (32 / L) + g;
     const unsigned gmask = (L == 32) ? 0xffffffffu : (((1u << L) - 1u) << (g * L));
     float *ring = qs + ((m + 3) & ~3) + gid * (W + 1);
-    int *cursor = (int *)scratch + kNoAllocCursor;
+    // 64-bit cursor: count may exceed INT_MAX
+    unsigned long long *cursor = (unsigned long long *)(scratch + kNoAllocCursor);
     while (true) {
-        int c = 0;
-        if (lane == 0) c = atomicAdd(cursor, 1);
-        c = __shfl_sync(gmask, c, 0, L);
-        if (c >= count) break;
+        unsigned long long cu = 0;
+        if (lane == 0) cu = atomicAdd(cursor, 1ull);
+        cu = __shfl_sync(gmask, cu, 0, L);
+        if (cu >= (unsigned long long)count) break;
+        const int64_t c = (int64_t)cu;
         const int64_t o = offsets[c];
         if (qbad || o < 0 || o >= N) {
             if (lane == 0) out[c] = __int_as_float(0x7fc00000);
@@ -174,18 +183,23 @@ bool on_device(const void *p) {
     return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
 }
 
+// Shared memory of a k_noalloc_dtw CTA of `warps` warps: the normalised
+// query and one ring of W + 1 floats per lane group.
+inline size_t noalloc_smem(int m, int r, int L, int warps) {
+    const size_t qbytes = (size_t)((m + 3) & ~3) * 4;
+    const size_t per_warp = (size_t)(32 / L) * (2 * r + 2) * 4;
+    return qbytes + (size_t)warps * per_warp;
+}
+
 template <int L>
 cudaError_t launch_noalloc_dtw(const float *x, int64_t n, int m, int r, const int64_t *offsets,
                                int64_t count, float *out, float *scratch, cudaStream_t s) {
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const int W = 2 * r + 1;
-    const size_t qbytes = (size_t)((m + 3) & ~3) * 4;
-    const size_t per_warp = (size_t)(32 / L) * (W + 1) * 4;
     int warps = 8;
-    while (warps > 1 && qbytes + warps * per_warp > 100 * 1024) --warps;
-    const size_t smem = qbytes + warps * per_warp;
+    while (warps > 1 && noalloc_smem(m, r, L, warps) > 100 * 1024) --warps;
+    const size_t smem = noalloc_smem(m, r, L, warps);
     const int groups = warps * (32 / L);
     int64_t blocks = (count + groups - 1) / groups;
     if (blocks > (int64_t)sms * 4) blocks = (int64_t)sms * 4;
@@ -231,6 +245,17 @@ extern "C" dtws_status dtws_dtw_at_noalloc(const float *series, int64_t n, const
     if (st != DTWS_OK) return st;
     if (count == 0) return DTWS_OK;
     const int rr = r > m - 1 ? m - 1 : r;
+    {  // one warp's shared memory must fit the device's per-block limit
+        int dev = 0, optin = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+        const size_t need = noalloc_smem(m, rr, lanes_for(rr), 1);
+        if (optin > 0 && need > (size_t)optin) {
+            set_error_detail("dtws_dtw_at_noalloc: m=%d, r=%d need %zu bytes of shared memory per warp, "
+                             "beyond the device's %d", m, rr, need, optin);
+            return DTWS_EINVAL;
+        }
+    }
     cudaStream_t s = (cudaStream_t)stream;
     k_noalloc_prep<<<1, 1024, 0, s>>>(Q, m, scratch);
     cudaError_t e = cudaGetLastError();

@@ -1,9 +1,11 @@
 """Parity at the full workload sizes, in the launch configuration bench.py
 times (default options, series and query on the device).
 
-The 1e6-sample workload is checked exactly against the oracle's full
-search.  For the larger ones the oracle cannot search everything in a test,
-so each answer is checked through facts it can compute one by one:
+The 1e6- and 1e8-sample workloads (the latter is the one bench.py times)
+are checked exactly against the oracle's search of every window (the Eq. 11
+fragment cascade over the host cores).  For the batch and the 1e9-sample
+series the oracle cannot search everything in a test, so each answer is
+checked through facts it can compute one by one:
 * the returned distances equal the oracle's FP64 DTW at the returned offsets;
 * an exact oracle search of a fragment around the planted match, merged with
   the returned list, leaves the returned list unchanged (no window of the
@@ -76,8 +78,12 @@ def test_rw100m_bench_configuration(rw100m):
     assert ix.sync_status() == dtws.DTWS_OK
     idx, dist = idx_d.cpu().numpy(), dist_d.cpu().numpy()
     ix.close()
-    _check_fragment_merge(x, q, r, 1, idx, dist, o, 100_000)
-    _check_samples(x, q, r, float(dist[0]), 3000, 1)
+    # the oracle's exact search over all 99,999,489 windows (FP64 cascade,
+    # anchored window statistics, Eq. 11 fragments over the host cores)
+    oi, od = fragments.search_fragments(x, q, r, 1, stats="anchored")
+    np.testing.assert_array_equal(idx, oi)
+    _close(dist, od, q.size)
+    _close(dist, oracle.dtw_at(x, q, r, idx), q.size)
 
 
 def test_batch_workload():
@@ -107,7 +113,8 @@ def test_drift_1e9_precision():
             q = qs[t]
             idx, dist = ix.query(q, r, 1)
             assert ix.sync_status() == dtws.DTWS_OK
-            _check_fragment_merge(x, q, r, 1, idx, dist, offs[t], 2_000)
+            # an exact oracle search of the 4e6 windows around the planted copy
+            _check_fragment_merge(x, q, r, 1, idx, dist, offs[t], 2_000_000)
             od = oracle.dtw_at(x, q, r, idx)
             f32 = ix.dtw_at(q, r, idx)
             errs.append(abs(float(f32[0]) - od[0]) / od[0])

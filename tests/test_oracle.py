@@ -209,6 +209,44 @@ def test_lower_bounds_are_admissible():
             for t, o in enumerate(offs[:20]):
                 ed = np.sum((qh - oracle.znorm(x[o:o + m])) ** 2)
                 assert abs(kq[t] - ed) <= 1e-9 * ed and abs(kc[t] - ed) <= 1e-9 * ed
+                # with r = 0 the series-wide envelope at j is the sample
+                # itself, so Eq. 10 over it is the squared ED as well
+                assert abs(ks[t] - ed) <= 1e-9 * ed
+
+
+def test_series_envelope_bound_hand_values():
+    """Eq. 10 against the series-wide envelope: hand-worked values, one of
+    which differs from the window-clipped reading (a slip that clips to the
+    window would give 2.5 instead of 0)."""
+    for c in GOLD["lb_keogh_series"]:
+        _, _, kc, ks = oracle.lbs_at(np.array(c["x"], np.float32), np.array(c["q"], np.float32), c["r"],
+                                     [c["offset"]])
+        want = c["keogh_series"] if "keogh_series" in c else 3.5 - 2 * np.sqrt(3.0)
+        assert abs(ks[0] - want) <= 1e-12, (c, ks[0])
+        if "keogh_clipped" in c:
+            assert abs(kc[0] - c["keogh_clipped"]) <= 1e-12, (c, kc[0])
+
+
+def test_series_envelope_bound_matches_scipy_definition():
+    """Eq. 10 with the series-wide envelope restated with SciPy filters (max /
+    min over [t-r, t+r] clipped to the series = mode 'nearest') and NumPy
+    normalisation, at windows near both series ends and in the interior."""
+    x = synth.random_walk(5_000, 41)
+    rng = np.random.default_rng(42)
+    for m, r in ((16, 1), (40, 5), (100, 30), (64, 63)):
+        q, _ = synth.noisy_copy(x, m, 43 + m, 44 + m, noise=0.4)
+        offs = np.concatenate([[0, 1, 2, x.size - m, x.size - m - 1], rng.integers(0, x.size - m + 1, 40)])
+        _, _, _, ks = oracle.lbs_at(x, q, r, offs)
+        U = maximum_filter1d(x.astype(np.float64), 2 * r + 1, mode="nearest")
+        L = minimum_filter1d(x.astype(np.float64), 2 * r + 1, mode="nearest")
+        qd = q.astype(np.float64)
+        qh = (qd - qd.mean()) / qd.std()
+        for t, o in enumerate(offs):
+            w = x[o:o + m].astype(np.float64)
+            mu, sg = w.mean(), w.std()
+            u, lo = (U[o:o + m] - mu) / sg, (L[o:o + m] - mu) / sg
+            want = np.sum(np.maximum(qh - u, 0) ** 2 + np.maximum(lo - qh, 0) ** 2)
+            assert abs(ks[t] - want) <= 1e-9 * max(1.0, want), (m, r, o, ks[t], want)
 
 
 # ------------------------------------------------------------------ search

@@ -217,43 +217,22 @@ __device__ T dtw_band(const T *__restrict__ qs, const float *__restrict__ xw, co
 // Early abandon (ABANDON): every warping path visits anti-diagonal a or a+1,
 // so min over the cells of two consecutive anti-diagonals of d(cell) plus a
 // lower bound of the rows after the cell's row bounds DTW from below.  The
-// rows' bound is cbs[i] = sum_{i' >= i} of the row's LB_Keogh term (q_hat_i'
-// against the window's envelope), in shared memory; tested every 16 steps.
-// cp: the group's normalised window (nullptr: read and normalise from xw).
+// rows' bound is a suffix sum of the rows' LB_Keogh terms (q_hat_i' against
+// the window's envelope), kept every kTailG rows in shared memory
+// (tail_suffix); tested once per unrolled iteration (at least 16 steps).
 // Padding on each side of the query / window arrays the anti-diagonal kernel
 // reads: cell indices run r/2 + L*K past either end.  The query is padded
 // with +inf and the window with -inf, so every cell outside [0, m)^2 costs
 // +inf (never NaN) and needs no bounds test.
 __host__ __device__ inline int diag_pad(int r, int L, int K) { return (r >> 1) + L * K + 4; }
 
-// One anti-diagonal step of dtw_diag: lane cell t (position p = lane*K + t
-// along the anti-diagonal) takes its left / up neighbours from the previous
-// anti-diagonal (p1, with one value from the adjacent lane), its diagonal
-// one from the one before (p2), and the query / window values from the
-// register windows qv, cv.
-template <typename T, int L, int K, int ODD>
-__device__ __forceinline__ void diag_step(const T (&qv)[K], const T (&cv)[K], T (&p1)[K], T (&p2)[K], int lane,
-                                          int r, unsigned gmask) {
-    const T INF = tinf<T>();
-    // the one neighbour held by the adjacent lane: p-1 (even) / p+1 (odd)
-    T nb = __shfl_sync(gmask, ODD ? p1[0] : p1[K - 1], ODD ? ((lane + 1) & (L - 1)) : ((lane - 1) & (L - 1)), L);
-    if (ODD ? (lane == L - 1) : (lane == 0)) nb = INF;
-    T cur[K];
-#pragma unroll
-    for (int t = 0; t < K; ++t) {
-        const int p = lane * K + t;
-        const T left = ODD ? p1[t] : (t == 0 ? nb : p1[t > 0 ? t - 1 : 0]);
-        const T up = ODD ? (t == K - 1 ? nb : p1[t < K - 1 ? t + 1 : 0]) : p1[t];
-        const T d = qv[t] - cv[t];
-        T v = tfma(d, d, tmin(tmin(left, up), p2[t]));
-        if (ODD ? (p >= r) : (p > r)) v = INF;  // past the band's cells on this anti-diagonal
-        cur[t] = v;
-    }
-#pragma unroll
-    for (int t = 0; t < K; ++t) {
-        p2[t] = p1[t];
-        p1[t] = cur[t];
-    }
+// Three-input minimum (one instruction on sm_100 and later).  The DTW
+// values are never NaN (out-of-band cells are +inf), so its NaN rule does
+// not matter here.
+__device__ __forceinline__ float min3f(float a, float b, float c) {
+    float r;
+    asm("min.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+    return r;
 }
 
 // Band cells (the band |i - j| <= r of Eq. 1 inside [0, m)^2) on the
@@ -274,58 +253,143 @@ __host__ __device__ inline long long band_cells_upto(int A, int m, int r) {
     return A <= m - 1 ? G(A) : T - G(2LL * m - 3 - A);
 }
 
+// Anti-diagonal pairs per unrolled iteration of dtw_diag: a multiple of K
+// (the register windows rotate by one slot per pair, so after K pairs every
+// value is back in its own register) and at least 8.
+__host__ __device__ constexpr int diag_unroll(int K) { return K * ((8 + K - 1) / K); }
+
+// Rows per entry of the coarse tail bound cbs that dtw_diag reads: entry g
+// holds the bound of the rows from kTailG*g on.
+constexpr int kTailG = 8;
+__host__ __device__ inline int tail_entries(int m) { return (m + kTailG - 1) / kTailG + 1; }
+
+// One anti-diagonal step of dtw_diag: lane cell t (position p = lane*K + t
+// along the anti-diagonal) takes its left / up neighbours from the previous
+// anti-diagonal (p1, with one value from the adjacent lane), its diagonal
+// one from the one before (p2), and the query / window values from the
+// register windows, whose logical element t sits in physical slot
+// (t - QP) mod K (query) and (t + CP) mod K (window).
+//
+// Cells past the band: with every cell past the band held at +inf, an
+// even (a + r) step's cells p > r see only such cells, and an odd step's
+// cells p > r as well; the odd step's cell p = r alone has a neighbour in
+// the band (its left, cell r of the even anti-diagonal), so only that cell
+// is forced to +inf, by the per-lane penalty pen (K <= 8) or a compare.
+template <int L, int K, int ODD, int QP, int CP>
+__device__ __forceinline__ void diag_step(const float (&qv)[K], const float (&cv)[K], float (&p1)[K],
+                                          float (&p2)[K], const float (&pen)[K], int lane, int r, unsigned gmask) {
+    const float INF = __int_as_float(0x7f800000);
+    // the one neighbour held by the adjacent lane: p-1 (even) / p+1 (odd)
+    float nb = __shfl_sync(gmask, ODD ? p1[0] : p1[K - 1], ODD ? ((lane + 1) & (L - 1)) : ((lane - 1) & (L - 1)), L);
+    if (ODD ? (lane == L - 1) : (lane == 0)) nb = INF;
+    float cur[K];
+#pragma unroll
+    for (int t = 0; t < K; ++t) {
+        const float left = ODD ? p1[t] : (t == 0 ? nb : p1[t > 0 ? t - 1 : 0]);
+        const float up = ODD ? (t == K - 1 ? nb : p1[t < K - 1 ? t + 1 : 0]) : p1[t];
+        const float d = qv[((t - QP) % K + K) % K] - cv[(t + CP) % K];
+        float v = fmaf(d, d, min3f(left, up, p2[t]));
+        if (ODD) {
+            if constexpr (K <= 8) v = fmaxf(v, pen[t]);
+            else if (lane * K + t == r) v = INF;
+        }
+        cur[t] = v;
+    }
+#pragma unroll
+    for (int t = 0; t < K; ++t) {
+        p2[t] = p1[t];
+        p1[t] = cur[t];
+    }
+}
+
 // Register windows of the anti-diagonal walk: cell p of a step reads
 // q[qbase - p] and c[cbase + p].  After an even step cbase grows by one (the
 // window values move one cell down, the last lane loads the new one); after
 // an odd step qbase grows by one (the query values move one cell up, lane 0
-// loads the new one).
-template <typename T, int L, int K>
-__device__ __forceinline__ void shift_c(T (&cv)[K], const T *cp, int cbase_new, int lane, unsigned gmask) {
-    const T from_next = __shfl_down_sync(gmask, cv[0], 1, L);
-    const T fresh = cp[cbase_new + L * K - 1];
+// loads the new one).  The move is a rotation: the slot whose value leaves
+// the lane takes the arriving one, and the phase (CP, QP) advances.
+template <int L, int K, int CP>
+__device__ __forceinline__ void rot_c(float (&cv)[K], const float *cp, int cbase_new, int lane, unsigned gmask) {
+    constexpr int s = CP % K;  // logical 0: leaves downwards, becomes logical K-1
+    const float from_next = __shfl_down_sync(gmask, cv[s], 1, L);
+    const float fresh = cp[cbase_new + L * K - 1];
+    cv[s] = lane == L - 1 ? fresh : from_next;
+}
+template <int L, int K, int QP>
+__device__ __forceinline__ void rot_q(float (&qv)[K], const float *qp, int qbase_new, int lane, unsigned gmask) {
+    constexpr int s = ((K - 1 - QP) % K + K) % K;  // logical K-1: leaves upwards, becomes logical 0
+    const float from_prev = __shfl_up_sync(gmask, qv[s], 1, L);
+    const float fresh = qp[qbase_new];
+    qv[s] = lane == 0 ? fresh : from_prev;
+}
+
+// The same moves without rotation (phase 0 before and after): the values
+// move one register along, the leaving one goes to the adjacent lane.
+template <int L, int K>
+__device__ __forceinline__ void shift_c(float (&cv)[K], const float *cp, int cbase_new, int lane, unsigned gmask) {
+    const float from_next = __shfl_down_sync(gmask, cv[0], 1, L);
+    const float fresh = cp[cbase_new + L * K - 1];
 #pragma unroll
     for (int t = 0; t < K - 1; ++t) cv[t] = cv[t + 1];
     cv[K - 1] = lane == L - 1 ? fresh : from_next;
 }
-template <typename T, int L, int K>
-__device__ __forceinline__ void shift_q(T (&qv)[K], const T *qp, int qbase_new, int lane, unsigned gmask) {
-    const T from_prev = __shfl_up_sync(gmask, qv[K - 1], 1, L);
-    const T fresh = qp[qbase_new];
+template <int L, int K>
+__device__ __forceinline__ void shift_q(float (&qv)[K], const float *qp, int qbase_new, int lane, unsigned gmask) {
+    const float from_prev = __shfl_up_sync(gmask, qv[K - 1], 1, L);
+    const float fresh = qp[qbase_new];
 #pragma unroll
     for (int t = K - 1; t > 0; --t) qv[t] = qv[t - 1];
     qv[0] = lane == 0 ? fresh : from_prev;
 }
 
+// The end of the walk: d(m-1, m-1) is cell pe of the last anti-diagonal.
+template <int K>
+__device__ __forceinline__ float diag_result(const float (&p1)[K], int lane, int pe) {
+    float res = __int_as_float(0x7f800000);
+#pragma unroll
+    for (int t = 0; t < K; ++t)
+        if (lane * K + t == pe) res = p1[t];
+    return res;
+}
+
 // qp, cp: the query and the group's normalised window, each padded by
 // diag_pad(r, L, K) elements (+inf / -inf) on both sides, pointing at
-// element 0.  cbs: the rows' tail bound for ABANDON (or nullptr).  cells:
-// lane 0 accumulates the cells evaluated (in the band and the matrix).
+// element 0.  cbs: the rows' coarse tail bound for ABANDON (or nullptr):
+// cbs[g] bounds the cost of the rows kTailG*g .. m-1 from below, so the
+// rows after row i are bounded by cbs[ceil((i+1)/kTailG)] (fewer rows, a
+// smaller sum).  cells: lane 0 accumulates the cells evaluated (in the band
+// and the matrix).  The walk takes diag_unroll(K) anti-diagonal pairs per
+// iteration; the abandon test runs once per iteration.
 template <typename T, int L, int K, bool ABANDON>
 __device__ T dtw_diag(const T *__restrict__ qp, const T *__restrict__ cp, const float *cbs, int m, int r, T thr,
                       unsigned gmask, int lane, int &cells) {
-    const T INF = tinf<T>();
+    static_assert(sizeof(T) == 4, "the FP32 walk");
+    constexpr int U = diag_unroll(K);
+    const float INF = __int_as_float(0x7f800000);
     const int p0 = (r - (r & 1)) >> 1;
-    T p1[K], p2[K], qv[K], cv[K];
+    float p1[K], p2[K], qv[K], cv[K], pen[K];
 #pragma unroll
     for (int t = 0; t < K; ++t) {
         p1[t] = INF;
-        p2[t] = (lane * K + t == p0) ? (T)0 : INF;
+        p2[t] = (lane * K + t == p0) ? 0.0f : INF;
+        pen[t] = (lane * K + t == r) ? INF : 0.0f;
     }
     const int last = 2 * m - 2;
+    const int pe_even = r >> 1, pe_odd = (r - 1) >> 1;  // cell e = 0 by the parity of (last + r)
     // anti-diagonal a has e_min = -r + ((a + r) & 1); its first cell is
     // (bi, bj) = ((a - e_min)/2, (a + e_min)/2).  Along an (even, odd) pair
     // bi stays and bj grows by one; from pair to pair both grow by one.
-    int a = 0, bi, bj;
-    if (r & 1) {  // a = 0 is odd: e_min = 1 - r
+    int a = 0;
+    if (r & 1) {  // a = 0 is odd: e_min = 1 - r; one odd step, then the query window shifts
         const int qb = (r - 1) >> 1, cb = (1 - r) >> 1;
 #pragma unroll
         for (int t = 0; t < K; ++t) {
             qv[t] = qp[qb - (lane * K + t)];
             cv[t] = cp[cb + (lane * K + t)];
         }
-        diag_step<T, L, K, 1>(qv, cv, p1, p2, lane, r, gmask);
+        diag_step<L, K, 1, 0, 0>(qv, cv, p1, p2, pen, lane, r, gmask);
         a = 1;
-        shift_q<T, L, K>(qv, qp, qb + 1, lane, gmask);
+        shift_q<L, K>(qv, qp, qb + 1, lane, gmask);
     } else {
         const int qb = r >> 1, cb = -(r >> 1);
 #pragma unroll
@@ -334,41 +398,58 @@ __device__ T dtw_diag(const T *__restrict__ qp, const T *__restrict__ cp, const 
             cv[t] = cp[cb + (lane * K + t)];
         }
     }
-    bi = (a + r) >> 1;
-    bj = (a - r) >> 1;
-    for (; a + 1 <= last; a += 2, ++bi, ++bj) {
-        diag_step<T, L, K, 0>(qv, cv, p1, p2, lane, r, gmask);
-        shift_c<T, L, K>(cv, cp, bj + 1, lane, gmask);
-        diag_step<T, L, K, 1>(qv, cv, p1, p2, lane, r, gmask);
-        shift_q<T, L, K>(qv, qp, bi + 1, lane, gmask);
-        if (ABANDON && ((a >> 1) & 7) == 7) {
-            // p1: anti-diagonal a+1 (rows bi - p), p2: a (rows bi - p)
-            float low = __int_as_float(0x7f800000);
+    int bi = (a + r) >> 1, bj = (a - r) >> 1;
+    float res = INF;
+    // iterations that end before the last anti-diagonal need no end test
+    while (a + 2 * U - 1 < last) {
+        static_for<U>([&](auto uc) {
+            constexpr int u = decltype(uc)::value;
+            diag_step<L, K, 0, u % K, u % K>(qv, cv, p1, p2, pen, lane, r, gmask);
+            rot_c<L, K, u % K>(cv, cp, bj + u + 1, lane, gmask);
+            diag_step<L, K, 1, u % K, (u + 1) % K>(qv, cv, p1, p2, pen, lane, r, gmask);
+            rot_q<L, K, u % K>(qv, qp, bi + u + 1, lane, gmask);
+        });
+        a += 2 * U;
+        bi += U;
+        bj += U;
+        if (ABANDON) {
+            // p1: anti-diagonal a-1, p2: a-2, both on rows bi - 1 - p
+            float low = INF;
 #pragma unroll
             for (int t = 0; t < K; ++t) {
-                const int i = bi - (lane * K + t);
-                const float tail = (cbs && i >= 0 && i < m) ? cbs[i + 1] : 0.0f;
-                low = fminf(low, fminf((float)p1[t], (float)p2[t]) + tail);
+                const int i = bi - 1 - (lane * K + t);
+                const float tail = (cbs && i >= 0 && i < m) ? cbs[(i + kTailG) / kTailG] : 0.0f;
+                low = fminf(low, fminf(p1[t], p2[t]) + tail);
             }
 #pragma unroll
             for (int o = L / 2; o > 0; o >>= 1) low = fminf(low, __shfl_xor_sync(gmask, low, o, L));
             if (low > (float)thr) {
-                if (lane == 0) cells += (int)band_cells_upto(a + 1, m, r);  // anti-diagonals 0..a+1
-                return INF;
+                if (lane == 0) cells += (int)band_cells_upto(a - 1, m, r);  // anti-diagonals 0..a-1
+                return (T)INF;
             }
         }
     }
-    if (a == last) {
-        diag_step<T, L, K, 0>(qv, cv, p1, p2, lane, r, gmask);
+    // the rest (fewer than U pairs), one pair at a time: the rotation phase
+    // is 0 here (the loop above took whole multiples of K pairs), so the
+    // windows shift by register moves and keep that phase
+    for (;; a += 2, ++bi, ++bj) {
+        diag_step<L, K, 0, 0, 0>(qv, cv, p1, p2, pen, lane, r, gmask);
+        if (a == last) {
+            res = diag_result<K>(p1, lane, pe_even);
+            break;
+        }
+        shift_c<L, K>(cv, cp, bj + 1, lane, gmask);
+        diag_step<L, K, 1, 0, 0>(qv, cv, p1, p2, pen, lane, r, gmask);
+        if (a + 1 == last) {
+            res = diag_result<K>(p1, lane, pe_odd);
+            break;
+        }
+        shift_q<L, K>(qv, qp, bi + 1, lane, gmask);
     }
     if (lane == 0) cells += (int)band_cells_upto(last, m, r);
     // d(m-1, m-1): e = 0 on the last anti-diagonal
-    const int pe = (r - ((last + r) & 1)) >> 1;
-    T res = INF;
-#pragma unroll
-    for (int t = 0; t < K; ++t)
-        if (lane * K + t == pe) res = p1[t];
-    return __shfl_sync(gmask, res, pe / K, L);
+    const int pe = ((last + r) & 1) ? pe_odd : pe_even;
+    return (T)__shfl_sync(gmask, res, pe / K, L);
 }
 
 // Knuth's error-free transformations (TwoSum, FastTwoSum, FMA-based
@@ -655,11 +736,12 @@ __device__ double dtw_diag_df_mw(const dfloat *__restrict__ qs, const dfloat *__
     return (double)res.hi + (double)res.lo;
 }
 
-// Suffix sums of the rows' LB_Keogh terms for the abandon test of dtw_diag:
-// cbs[i] = sum_{i' >= i} (q_hat_i' against the window's normalised envelope
-// interval at i')^2, cbs[m] = 0, shrunk by 1e-5 of the total so FP32
-// rounding of the sums can only weaken the bound.  Rows are taken L at a
-// time (coalesced loads), from the last chunk to the first, with a suffix
+// Suffix sums of the rows' LB_Keogh terms for the abandon test of dtw_diag,
+// kept every kTailG rows: cbs[g] = sum_{i >= kTailG*g} (q_hat_i against the
+// window's normalised envelope interval at i)^2, cbs[tail_entries(m) - 1] =
+// 0, shrunk by 1e-5 of the total so FP32 rounding of the sums can only
+// weaken the bound.  cbs[0] is the whole Eq. 10 bound.  Rows are taken L at
+// a time (coalesced loads), from the last chunk to the first, with a suffix
 // scan across the group per chunk.
 template <int L>
 __device__ void tail_suffix(const TailCtx &tc, float *cbs, int m, unsigned gmask, int lane) {
@@ -673,12 +755,14 @@ __device__ void tail_suffix(const TailCtx &tc, float *cbs, int m, unsigned gmask
             const float u = __shfl_down_sync(gmask, v, o, L);
             if (lane + o < L) v += u;
         }
-        if (i < m) cbs[i] = carry + v;
+        if (i < m && (i % kTailG) == 0) cbs[i / kTailG] = carry + v;
         carry += __shfl_sync(gmask, v, 0, L);
     }
+    __syncwarp(gmask);  // entries written by other lanes of the group
     const float slack = 1e-5f * carry;
-    for (int i = lane; i < m; i += L) cbs[i] = fmaxf(0.0f, cbs[i] - slack);
-    if (lane == 0) cbs[m] = 0.0f;
+    const int ne = tail_entries(m);
+    for (int g = lane; g < ne - 1; g += L) cbs[g] = fmaxf(0.0f, cbs[g] - slack);
+    if (lane == 0) cbs[ne - 1] = 0.0f;
     __syncwarp(gmask);
 }
 
@@ -704,6 +788,23 @@ __host__ __device__ inline void diag_shape(int r, int *L, int *K) {
             break;
         }
     *K = k;  // 0 < K <= 16 for r <= 511
+}
+
+// Cells per lane for the FP32 anti-diagonal kernel: as diag_shape, except
+// that bands of 4 < r+1 <= 32 cells take two cells per lane on half as many
+// lanes (a power of two), so that each lane's pair of shuffles and window
+// loads per anti-diagonal pair serves two cells and a warp walks two or
+// more candidates at once.
+__host__ __device__ inline void diag_shape_f32(int r, int *L, int *K) {
+    const int need = r + 1;
+    if (need > 4 && need <= 32) {
+        int l = 1;
+        while (2 * l < need) l *= 2;
+        *L = l;
+        *K = 2;
+        return;
+    }
+    diag_shape(r, L, K);
 }
 
 // Lanes per group for band half-width r: the largest power of two <= r

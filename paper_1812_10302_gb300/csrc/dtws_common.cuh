@@ -9,9 +9,22 @@
 #pragma once
 
 #include <cstdint>
+#include <type_traits>
+#include <utility>
 #include <cuda_runtime.h>
 
 namespace dtws {
+
+// Compile-time loop: f(std::integral_constant<int, I>{}) for I = 0..N-1, so
+// the body can use I as a template argument (register indices, rotations).
+template <typename F, int... I>
+__device__ __forceinline__ void static_for_impl(F &&f, std::integer_sequence<int, I...>) {
+    (f(std::integral_constant<int, I>{}), ...);
+}
+template <int N, typename F>
+__device__ __forceinline__ void static_for(F &&f) {
+    static_for_impl(f, std::make_integer_sequence<int, N>{});
+}
 
 // ---------------------------------------------------------------- limits
 constexpr int kBlockB = 8192;       // anchored prefix block length (= DTWS_M_MAX)

@@ -36,12 +36,9 @@
 #include <utility>
 #include <type_traits>
 
-#include "dtw_band.cuh"
-#include "dtws_internal.h"
+#include "dtw_kernels.cuh"
 
 namespace dtws {
-
-#define DINF __int_as_float(0x7f800000)
 
 // ------------------------------------------------------------------ reset
 __global__ void k_query_reset(QueryState *st) {
@@ -423,14 +420,6 @@ __device__ __forceinline__ float lds_at(unsigned addr) {
     asm volatile("ld.shared.f32 %0, [%1+%2];" : "=f"(v) : "r"(addr), "n"(OFF));
     return v;
 }
-template <typename F, int... I>
-__device__ __forceinline__ void static_for_impl(F &&f, std::integer_sequence<int, I...>) {
-    (f(std::integral_constant<int, I>{}), ...);
-}
-template <int N, typename F>
-__device__ __forceinline__ void static_for(F &&f) {
-    static_for_impl(f, std::make_integer_sequence<int, N>{});
-}
 
 template <int TERMS>
 __global__ void __launch_bounds__(kScanThreads) k_seed_scan(QueryBufs b, QueryArgs a, int proposals, int stages) {
@@ -795,26 +784,6 @@ cudaError_t launch_seed_gather(const QueryBufs &b, const QueryArgs &a, int n_ran
     return cudaGetLastError();
 }
 
-// Bin of a survivor's lower bound for the counting sort (see launch_order):
-// with a finite scan threshold the bins split [0, thr] evenly; otherwise
-// they follow the float's exponent and leading mantissa bits (monotone for
-// lb >= 0).
-__device__ __forceinline__ int bin_of(float lb, float thr) {
-    if (thr < DINF) {
-        int bn = (int)(lb * ((float)kBins / thr));
-        return bn < 0 ? 0 : (bn >= kBins ? kBins - 1 : bn);
-    }
-    return (int)(__float_as_uint(lb) >> 21);
-}
-
-// A value that every bound in bins >= k (bin_of with the same thr) is at
-// least: the bin's lower edge, lowered by 2^-20 to cover the rounding of the
-// product in bin_of.
-__device__ __forceinline__ float bin_floor(int k, float thr) {
-    if (thr < DINF) return ((float)k / ((float)kBins / thr)) * (1.0f - 9.5367431640625e-07f);
-    return __uint_as_float((unsigned)k << 21);
-}
-
 // ------------------------------------------------------------------ wait self-test
 // One thread waits, bounded, on a fresh mbarrier that nothing arrives on:
 // the wait runs out after wait_ns and records the timeout status the same way
@@ -831,379 +800,6 @@ __global__ void k_wait_selftest(int *status, long long wait_ns) {
 cudaError_t launch_wait_selftest(int *status, long long wait_ns, cudaStream_t s) {
     k_wait_selftest<<<1, 32, 0, s>>>(status, wait_ns);
     return cudaGetLastError();
-}
-
-// ------------------------------------------------------------------ DTW kernels
-enum DtwMode { kModeSeed = 0, kModeSurv = 1, kModeOut = 2 };
-
-// Shared memory of a DTW CTA: the query [pad + m + pad] then, per group,
-// its staged normalised window [pad + m + pad] (when staged), the rows' tail
-// bound [m4 + 4] (FP32; anti-diagonal kernel with abandon) and the ring
-// [W + 1] (row-systolic kernel, K == 0).  pad = diag_pad(r, L, K) for the
-// anti-diagonal kernel, 0 for the row-systolic one.
-template <typename T>
-struct DtwSmem {
-    int m, m4, W, pad;
-    bool staged, tail, ring;
-    __host__ __device__ size_t span() const { return (size_t)((m + 2 * pad + 3) & ~3); }
-    __host__ __device__ size_t group_bytes() const {
-        return (staged ? span() * sizeof(T) : 0) + (tail ? (size_t)(m4 + 4) * 4 : 0) +
-               (ring ? (size_t)(W + 1) * sizeof(T) : 0);
-    }
-    __host__ __device__ size_t q_bytes() const { return span() * sizeof(T); }
-};
-
-template <typename T, int L, int K>
-__host__ __device__ inline DtwSmem<T> dtw_smem(int m, int r, bool staged, bool tail) {
-    DtwSmem<T> d;
-    d.m = m;
-    d.m4 = (m + 3) & ~3;
-    d.W = 2 * r + 1;
-    d.pad = K > 0 ? diag_pad(r, L, K) : 0;
-    d.staged = staged;
-    d.tail = staged && tail && K > 0;
-    d.ring = K == 0;
-    return d;
-}
-
-// Fill [base, base + pad) and [base + pad + m, base + 2 pad + m) with v.
-template <typename T>
-__device__ __forceinline__ void fill_pads(T *base, int m, int pad, T v, int tid, int nthreads) {
-    for (int t = tid; t < 2 * pad; t += nthreads) base[t < pad ? t : m + t] = v;
-}
-
-// FP32 DTW over a candidate list (MODE: seeds, survivors, or given offsets).
-// Groups of L lanes pull candidates from a device cursor.  K > 0: the
-// anti-diagonal kernel with K cells per lane (window staged in shared
-// memory); K == 0: the row-systolic kernel (staged when it fits).
-template <int L, int K, int MODE>
-__global__ void __launch_bounds__(256) k_dtw(QueryBufs b, QueryArgs a, const int64_t *offsets,
-                                             int64_t count_host, float *out, int staged) {
-    extern __shared__ __align__(16) unsigned char smraw[];
-    QueryState *st = b.st;
-    if (!st->valid) return;
-    const int m = a.m, r = a.r;
-    const bool has_env = b.U != nullptr || b.stmax != nullptr;
-    const DtwSmem<float> lay = dtw_smem<float, L, K>(m, r, staged != 0, MODE == kModeSurv && has_env);
-    const float INF = DINF;
-    float *qbase = (float *)smraw, *qs = qbase + lay.pad;
-    for (int t = threadIdx.x; t < m; t += blockDim.x) qs[t] = b.qh32[t];
-    fill_pads(qbase, m, lay.pad, INF, threadIdx.x, blockDim.x);
-    const int warp = threadIdx.x >> 5, ln = lane_id();
-    const int g = ln / L, lane = ln % L;
-    const int gid = warp * (32 / L) + g;
-    const unsigned gmask = (L == 32) ? 0xffffffffu : (((1u << L) - 1u) << (g * L));
-    unsigned char *gbase = smraw + lay.q_bytes() + (size_t)gid * lay.group_bytes();
-    float *cbuf = nullptr;
-    if (lay.staged) {
-        fill_pads((float *)gbase, m, lay.pad, -INF, lane, L);
-        cbuf = (float *)gbase + lay.pad;
-    }
-    float *cbs = lay.tail ? (float *)(gbase + (lay.staged ? lay.span() * 4 : 0)) : nullptr;
-    float *ring = lay.ring ? (float *)(gbase + (lay.staged ? lay.span() * 4 : 0) +
-                                       (lay.tail ? (size_t)(lay.m4 + 4) * 4 : 0))
-                           : nullptr;
-    // survivor pass: the seeds' offsets (already evaluated by the seed pass)
-    // and the first 128 query positions in |q_hat| order with q_hat and the
-    // query envelope there (the pre-check reads them for every candidate)
-    __shared__ unsigned seeds_s[kSeedMax];
-    __shared__ int n_seeds_s;
-    __shared__ int ord_s[128];
-    __shared__ float sq_s[128], su_s[128], sl_s[128];
-    if (MODE == kModeSurv) {
-        if (threadIdx.x == 0) n_seeds_s = st->n_seeds;
-        for (int t = threadIdx.x; t < st->n_seeds; t += blockDim.x) seeds_s[t] = st->seed_off[t];
-        for (int t = threadIdx.x; t < 128; t += blockDim.x) {
-            const bool in = t < m;
-            ord_s[t] = in ? (int)b.ord[t] : 0;
-            sq_s[t] = in ? b.sq[t] : 0.0f;
-            su_s[t] = in ? b.sU[t] : 0.0f;
-            sl_s[t] = in ? b.sL[t] : 0.0f;
-        }
-    }
-    __syncthreads();
-    int *cursor = MODE == kModeSurv ? &st->work2 : &st->work;
-    const float thr_scan = MODE == kModeSurv ? st->thr_scan : 0.0f;
-    const unsigned pre = MODE == kModeSurv ? prescored_window(st, a) : 0xffffffffu;
-    const int64_t count = MODE == kModeSeed ? (int64_t)st->n_seeds
-                        : MODE == kModeSurv ? (int64_t)st->n_cand : count_host;
-    long long cells_acc = 0;
-    int started = 0, abandoned = 0, passed_s = 0;
-    // survivor pass, two schedules chosen per launch (the same for every
-    // group): with many survivors (more than 64 per group) a group takes L
-    // candidates per cursor step and each lane runs the pre-check (bin floor,
-    // seeds, Eq. 10 and Eq. 8 with early abandon) for its own candidate, the
-    // ones that pass then being scored one at a time by the whole group;
-    // with few survivors a group takes one candidate at a time and pre-checks
-    // it cooperatively, L terms per step (shorter critical path when most of
-    // them sit near the best match).
-    unsigned pend = 0, my_idx = 0;
-    float my_mh = 0.0f, my_is = 0.0f, my_ls = 0.0f;
-    bool stop = false;
-    const unsigned lmask = L == 32 ? 0xffffffffu : ((1u << L) - 1u);
-    const bool lanewise = MODE == kModeSurv && count > (int64_t)gridDim.x * (blockDim.x / L) * 64;
-    while (true) {
-        int c = 0, psrc = 0;
-        unsigned idx;
-        float lb = 0.0f;
-        bool coop = false;  // the one-candidate schedule's cooperative pre-check is still due
-        if (MODE == kModeSurv && lanewise) {
-            if (!pend) {
-                if (stop) break;
-                int c0 = 0;
-                if (lane == 0) c0 = atomicAdd(cursor, L);
-                c0 = __shfl_sync(gmask, c0, 0, L);
-                if (c0 >= count) break;
-                const int cc = c0 + lane;
-                const bool valid = cc < count;
-                const unsigned id = valid ? b.sort_idx[cc] : 0u;
-                const float lbv = valid ? b.sort_lb[cc] : DINF;
-                float th = 0.0f;
-                if (lane == 0) th = current_thr(st, a);
-                th = __shfl_sync(gmask, th, 0, L);
-                bool pass = valid && !(lbv > th);
-                // survivors are in ascending bins and thr only shrinks: once a
-                // candidate's bin floor is above thr, so is every later one's
-                const bool done = valid && lbv > th && bin_floor(bin_of(lbv, thr_scan), thr_scan) > th;
-                if (pass) {  // scored already: by the seed pass or on the side stream
-                    bool seen = id == pre;
-                    for (int t = 0; t < n_seeds_s; ++t) seen |= seeds_s[t] == id;
-                    pass = !seen;
-                }
-                float pmh = 0.0f, pis = 0.0f, pls = 0.0f;
-                if (pass) {
-                    pmh = b.mu_hi[id];
-                    pis = b.inv_sigma[id];
-                    pls = b.mu_lo[id] * pis;
-                }
-                if (pass && has_env) {
-                    // Eq. 10 (q_hat against the window's envelope) and Eq. 8
-                    // (the window against the query's envelope; the scan took
-                    // only its first terms) with early abandon, terms in
-                    // |q_hat| descending order until either partial sum passes
-                    // thr -- each is a lower bound on its own (rows and
-                    // columns of the same warping path).  Past 128 terms the
-                    // full Eq. 10 below (row order, with the suffix sums the
-                    // DTW needs) takes over.
-                    TailCtx pc;
-                    pc.Uw = b.U ? b.U + id : nullptr;
-                    pc.Lw = b.L ? b.L + id : nullptr;
-                    pc.stmax = b.stmax;
-                    pc.stmin = b.stmin;
-                    pc.nblk = b.nblk;
-                    pc.n = b.n;
-                    pc.t0 = id;
-                    pc.r = r;
-                    const float *xp = b.x + id;
-                    const int budget = m < 128 ? m : 128;
-                    float acc = 0.0f, acc8 = 0.0f;
-                    // 8 terms per step: their loads are issued together, the
-                    // abandon test runs once per step
-                    constexpr int kB = 8;
-                    for (int j0 = 0; j0 < budget; j0 += kB) {
-                        float xv[kB], uv[kB], lv[kB];
-#pragma unroll
-                        for (int t = 0; t < kB; ++t) {
-                            const int j = j0 + t < budget ? j0 + t : budget - 1;
-                            const int pos = ord_s[j];
-                            xv[t] = xp[pos];
-                            env_at(pc, pos, uv[t], lv[t]);
-                        }
-#pragma unroll
-                        for (int t = 0; t < kB; ++t) {
-                            if (j0 + t >= budget) break;
-                            const int j = j0 + t;
-                            const float u = fmaf(uv[t] - pmh, pis, -pls), l = fmaf(lv[t] - pmh, pis, -pls);
-                            const float q = sq_s[j];
-                            const float dq = fmaxf(q - u, 0.0f) + fmaxf(l - q, 0.0f);
-                            const float cv = fmaf(xv[t] - pmh, pis, -pls);
-                            const float e = fmaxf(cv - su_s[j], 0.0f) + fmaxf(sl_s[j] - cv, 0.0f);
-                            acc = fmaf(dq, dq, acc);
-                            acc8 = fmaf(e, e, acc8);
-                        }
-                        if (acc > th || acc8 > th) {
-                            pass = false;
-                            break;
-                        }
-                    }
-                }
-                my_idx = id;
-                my_mh = pmh;
-                my_is = pis;
-                my_ls = pls;
-                const int gshift = (ln / L) * L;
-                pend = (__ballot_sync(gmask, pass) >> gshift) & lmask;
-                stop = ((__ballot_sync(gmask, done) >> gshift) & lmask) != 0u;
-                continue;
-            }
-            psrc = __ffs(pend) - 1;
-            pend &= pend - 1;
-            idx = __shfl_sync(gmask, my_idx, psrc, L);
-        } else {
-            if (lane == 0) c = atomicAdd(cursor, 1);
-            c = __shfl_sync(gmask, c, 0, L);
-            if (c >= count) break;
-            if (MODE == kModeSurv) {
-                idx = b.sort_idx[c];
-                lb = b.sort_lb[c];
-                coop = true;
-            }
-        }
-        if (MODE == kModeSeed) {
-            idx = st->seed_off[c];
-        } else if (MODE == kModeOut) {
-            const int64_t o = offsets[c];
-            if (o < 0 || o >= a.N) {  // caller's device offsets are checked here
-                if (lane == 0) out[c] = __int_as_float(0x7fc00000);
-                continue;
-            }
-            idx = (unsigned)o;
-        }
-        // the threshold moves while other groups insert: read it once (lane
-        // 0) so every lane of the group takes the same branches
-        float thr = DINF;
-        if (MODE == kModeSeed) {
-            const float kth = list_kth(st->seed_keys, a.k);
-            thr = kth < DINF ? fmaf(kth, 1.0f + a.delta, a.alpha) : DINF;
-        } else if (MODE == kModeSurv) {
-            thr = current_thr(st, a);
-        }
-        thr = __shfl_sync(gmask, thr, 0, L);
-        if (coop) {
-            if (lb > thr) {
-                // see the batch schedule: past this bin floor nothing is left
-                if (bin_floor(bin_of(lb, thr_scan), thr_scan) > thr) break;
-                continue;
-            }
-            bool seen = idx == pre;  // scored already: by the seed pass or on the side stream
-            for (int t = lane; t < n_seeds_s; t += L) seen |= seeds_s[t] == idx;
-            if (__any_sync(gmask, seen)) continue;
-        }
-        float mh, is, ls;
-        if (MODE == kModeSurv && !coop) {  // pre-checked by its lane: take its statistics
-            mh = __shfl_sync(gmask, my_mh, psrc, L);
-            is = __shfl_sync(gmask, my_is, psrc, L);
-            ls = __shfl_sync(gmask, my_ls, psrc, L);
-        } else {
-            mh = b.mu_hi[idx];
-            is = b.inv_sigma[idx];
-            ls = b.mu_lo[idx] * is;
-        }
-        const float *xw = b.x + idx;
-        TailCtx tc;
-        tc.Uw = b.U ? b.U + idx : nullptr;
-        tc.Lw = b.L ? b.L + idx : nullptr;
-        tc.stmax = b.stmax;
-        tc.stmin = b.stmin;
-        tc.nblk = b.nblk;
-        tc.n = b.n;
-        tc.t0 = idx;
-        tc.r = r;
-        tc.qs = qs;
-        tc.mh = mh;
-        tc.is = is;
-        tc.ls = ls;
-        if (coop && has_env) {
-            // the same pre-check as the batch schedule's, L terms per step
-            // over the group (the sums are reduced, so every lane takes the
-            // same exit)
-            float acc = 0.0f, acc8 = 0.0f;
-            bool pruned = false;
-            const int budget = m < 128 ? m : 128;
-            for (int c0 = 0; c0 < budget; c0 += L) {
-                const int j = c0 + lane;
-                float v = 0.0f, v8 = 0.0f;
-                if (j < budget) {
-                    const int pos = ord_s[j];
-                    const float x = xw[pos];
-                    float U, Lo;
-                    env_at(tc, pos, U, Lo);
-                    const float u = fmaf(U - mh, is, -ls), l = fmaf(Lo - mh, is, -ls), q = sq_s[j];
-                    const float dq = fmaxf(q - u, 0.0f) + fmaxf(l - q, 0.0f);
-                    v = dq * dq;
-                    const float cv = fmaf(x - mh, is, -ls);
-                    const float e = fmaxf(cv - su_s[j], 0.0f) + fmaxf(sl_s[j] - cv, 0.0f);
-                    v8 = e * e;
-                }
-#pragma unroll
-                for (int o = L / 2; o > 0; o >>= 1) {
-                    v += __shfl_xor_sync(gmask, v, o, L);
-                    v8 += __shfl_xor_sync(gmask, v8, o, L);
-                }
-                acc += v;
-                acc8 += v8;
-                if (acc > thr || acc8 > thr) {
-                    pruned = true;
-                    break;
-                }
-            }
-            if (pruned) continue;
-        }
-        if (cbuf) {  // the group's normalised copy of the window
-            for (int j = lane; j < m; j += L) cbuf[j] = fmaf(xw[j] - mh, is, -ls);
-        }
-        if (cbs) {
-            tail_suffix<L>(tc, cbs, m, gmask, lane);
-            // cbs[0] is LB_Keogh of q_hat against the window's envelope
-            // (Eq. 10 with the series-wide envelope): the third bound
-            if (cbs[0] > thr) continue;
-            if (lane == 0) ++passed_s;
-        }
-        __syncwarp(gmask);
-        int cells = 0;
-        float d;
-        if constexpr (K == 0) {
-            if (MODE == kModeOut)
-                d = dtw_band<float, L, false>(qs, xw, cbuf, mh, is, ls, nullptr, ring, m, r, thr, gmask, lane,
-                                              cells);
-            else
-                d = dtw_band<float, L, true>(qs, xw, cbuf, mh, is, ls,
-                                             (has_env && MODE == kModeSurv) ? &tc : nullptr, ring, m, r, thr,
-                                             gmask, lane, cells);
-        } else {
-            if (MODE == kModeOut)
-                d = dtw_diag<float, L, K, false>(qs, cbuf, nullptr, m, r, thr, gmask, lane, cells);
-            else
-                d = dtw_diag<float, L, K, true>(qs, cbuf, cbs, m, r, thr, gmask, lane, cells);
-        }
-        cells_acc += cells;
-        if (lane == 0) {
-            ++started;
-            if (!(d < DINF)) ++abandoned;
-            if (MODE == kModeOut) out[c] = d;
-            else if (MODE == kModeSeed) {
-                if (d < DINF) {
-                    // a finished seed is also a result candidate; the survivor
-                    // pass skips the seeds, so each window enters once
-                    const unsigned long long key = make_key(key_quantize(d, a.qgrid), idx);
-                    list_insert(st->seed_keys, a.k, key);
-                    list_insert(st->res_keys, a.list_cap, key);
-                }
-            } else if (d <= thr) {
-                list_insert(st->res_keys, a.list_cap, make_key(key_quantize(d, a.qgrid), idx));
-            }
-        }
-        __syncwarp(gmask);
-    }
-    if (MODE != kModeOut) {
-        // counters: one atomic per warp
-        unsigned long long cs = (unsigned long long)cells_acc;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) cs += __shfl_xor_sync(0xffffffffu, cs, o);
-        int ns = started, na = abandoned, np = passed_s;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            ns += __shfl_xor_sync(0xffffffffu, ns, o);
-            na += __shfl_xor_sync(0xffffffffu, na, o);
-            np += __shfl_xor_sync(0xffffffffu, np, o);
-        }
-        if (ln == 0) {
-            atomicAdd(&st->ctr[kCtrCells], cs);
-            atomicAdd(&st->ctr[kCtrDtwStarted], (unsigned long long)ns);
-            atomicAdd(&st->ctr[kCtrDtwAbandoned], (unsigned long long)na);
-            if (np) atomicAdd(&st->ctr[kCtrKeoghS], (unsigned long long)np);
-        }
-    }
 }
 
 // Re-score: per window two-pass FP64 statistics (Eq. 5), the normalised
@@ -1301,19 +897,6 @@ __global__ void __launch_bounds__(256) k_dtw64(QueryBufs b, QueryArgs a, const i
     }
 }
 
-// Shape of the double-float re-score walk.
-template <int L, int K>
-struct PreShape {
-    // the double-float walk for the FP32 walk's shape (L lanes, K cells):
-    // as many warps as the FP32 walk has cells per lane (at most 4), the
-    // r+1 <= L*K cells spread over them
-    static constexpr int W = (L < 32) ? 1 : (K <= 4 ? K : 4);
-    static constexpr int K2 = (L < 32 || K <= 4) ? 1 : (K * 32 + 127) / 128;
-};
-__host__ __device__ inline size_t pre_span(int m, int r, int lanes, int k) {
-    return (size_t)((m + 2 * diag_pad(r, lanes, k) + 3) & ~3);
-}
-
 // The re-score with the anti-diagonal walk spread over W warps per window
 // (dtw_diag_df_mw): G = blockDim.x / (32 W) groups per CTA, group g owning
 // named barrier 1 + g; the query's double-float copy is shared, each group
@@ -1400,111 +983,6 @@ __global__ void __launch_bounds__(256) k_dtw64_mw(QueryBufs b, QueryArgs a, cons
     }
 }
 
-// Kernel choice and CTA shape.  The anti-diagonal kernel (K > 0) is used
-// when r <= kDiagRMax and one warp's groups can stage their windows;
-// otherwise the row-systolic kernel (K == 0), staged when it fits.  Warps
-// per CTA shrink until the CTA fits in ~100 KB (two CTAs per SM).
-struct DtwPlan {
-    int L, K, staged, warps;
-    size_t smem;
-};
-
-template <typename T, int L, int K>
-static bool plan_fits(int m, int r, bool tail, DtwPlan *p) {
-    const size_t budget = 100 * 1024, hard = 200 * 1024;
-    for (int staged = 1; staged >= (K > 0 ? 1 : 0); --staged) {
-        const DtwSmem<T> lay = dtw_smem<T, L, K>(m, r, staged != 0, tail);
-        auto total = [&](int w) { return lay.q_bytes() + (size_t)w * (32 / L) * lay.group_bytes(); };
-        int warps = 8;
-        while (warps > 1 && total(warps) > budget) --warps;
-        if (total(warps) <= hard) {
-            *p = DtwPlan{L, K, staged, warps, total(warps)};
-            return true;
-        }
-    }
-    return false;
-}
-
-// A given shape (K > 0: anti-diagonal with L*K >= r+1 lanes' cells; K == 0:
-// row-systolic with lanes_for(r) lanes) if it is instantiated and fits;
-// warps <= 0 keeps the largest count within the shared-memory budget.
-template <typename T>
-static bool plan_shape(int m, int r, bool tail, int L, int K, int warps, DtwPlan *p) {
-    if (K > 0 && (r > kDiagRMax || L * K < r + 1)) return false;
-    if (K == 0 && L != lanes_for(r)) return false;
-    bool ok = false;
-#define DTWS_TRY(LL, KK) \
-    if (!ok && L == LL && K == KK) ok = plan_fits<T, LL, KK>(m, r, tail, p);
-    DTWS_TRY(1, 1) DTWS_TRY(2, 1) DTWS_TRY(4, 1) DTWS_TRY(8, 1) DTWS_TRY(16, 1)
-    DTWS_TRY(32, 1) DTWS_TRY(32, 2) DTWS_TRY(32, 3) DTWS_TRY(32, 4) DTWS_TRY(32, 6) DTWS_TRY(32, 8) \
-        DTWS_TRY(32, 10) DTWS_TRY(32, 12) DTWS_TRY(32, 16)
-    DTWS_TRY(1, 0) DTWS_TRY(2, 0) DTWS_TRY(4, 0) DTWS_TRY(8, 0) DTWS_TRY(16, 0) DTWS_TRY(32, 0)
-#undef DTWS_TRY
-    if (!ok) return false;
-    // fewer warps than the budget allows: the allocation for more groups
-    // stays valid (each group addresses only its own slice)
-    if (warps > 0 && warps < p->warps) p->warps = warps;
-    return true;
-}
-
-template <typename T>
-static bool plan_dtw(int m, int r, bool tail, DtwPlan *p) {
-    if (r <= kDiagRMax) {
-        int L, K;
-        diag_shape(r, &L, &K);
-#define DTWS_TRY(LL, KK) \
-    if (L == LL && K == KK && plan_fits<T, LL, KK>(m, r, tail, p)) return true;
-        DTWS_TRY(1, 1) DTWS_TRY(2, 1) DTWS_TRY(4, 1) DTWS_TRY(8, 1) DTWS_TRY(16, 1)
-        DTWS_TRY(32, 1) DTWS_TRY(32, 2) DTWS_TRY(32, 3) DTWS_TRY(32, 4) DTWS_TRY(32, 6) DTWS_TRY(32, 8) \
-        DTWS_TRY(32, 10) DTWS_TRY(32, 12) DTWS_TRY(32, 16)
-#undef DTWS_TRY
-    } else if (std::is_same<T, float>::value && r <= kDiagRMaxF32) {
-        // wider bands in FP32: one warp with 24 or 32 cells per lane (the
-        // survivor, seed and given-offset kernels; the re-score has its own
-        // multi-warp walk)
-        if (r + 1 <= 32 * 24 && plan_fits<T, 32, 24>(m, r, tail, p)) return true;
-        if (plan_fits<T, 32, 32>(m, r, tail, p)) return true;
-    }
-    const int L = lanes_for(r);
-#define DTWS_TRY(LL) \
-    if (L == LL) return plan_fits<T, LL, 0>(m, r, tail, p);
-    DTWS_TRY(1) DTWS_TRY(2) DTWS_TRY(4) DTWS_TRY(8) DTWS_TRY(16) DTWS_TRY(32)
-#undef DTWS_TRY
-    return false;
-}
-
-static int dtw_blocks(const DtwPlan &p, int num_sms, int64_t count) {
-    const int groups = p.warps * (32 / p.L);
-    int64_t want = (count + groups - 1) / groups;
-    const int64_t cap = (int64_t)num_sms * 4;
-    if (want < 1) want = 1;
-    return (int)(want < cap ? want : cap);
-}
-
-template <int MODE>
-static cudaError_t dtw_dispatch(const QueryBufs &b, const QueryArgs &a, const int64_t *offsets,
-                                int64_t count, float *out, int64_t count_for_grid, cudaStream_t s) {
-    DtwPlan p;
-    const bool tail = MODE == kModeSurv && (b.U != nullptr || b.stmax != nullptr);
-    const bool tuned = a.tune_l > 0 && plan_shape<float>(a.m, a.r, tail, a.tune_l, a.tune_k, a.tune_w, &p);
-    if (!tuned && !plan_dtw<float>(a.m, a.r, tail, &p)) return cudaErrorInvalidValue;
-    const int blocks = dtw_blocks(p, b.num_sms, count_for_grid);
-#define DTWS_CASE(LL, KK)                                                                                     \
-    if (p.L == LL && p.K == KK) {                                                                             \
-        cudaError_t e = cudaFuncSetAttribute(k_dtw<LL, KK, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
-                                             (int)p.smem);                                                    \
-        if (e != cudaSuccess) return e;                                                                       \
-        k_dtw<LL, KK, MODE><<<blocks, p.warps * 32, p.smem, s>>>(b, a, offsets, count, out, p.staged);        \
-        return cudaGetLastError();                                                                            \
-    }
-    DTWS_CASE(1, 1) DTWS_CASE(2, 1) DTWS_CASE(4, 1) DTWS_CASE(8, 1) DTWS_CASE(16, 1)
-    DTWS_CASE(32, 1) DTWS_CASE(32, 2) DTWS_CASE(32, 3) DTWS_CASE(32, 4) DTWS_CASE(32, 6) DTWS_CASE(32, 8) \
-    DTWS_CASE(32, 10) DTWS_CASE(32, 12) DTWS_CASE(32, 16) DTWS_CASE(32, 24) DTWS_CASE(32, 32)
-    DTWS_CASE(1, 0) DTWS_CASE(2, 0) DTWS_CASE(4, 0) DTWS_CASE(8, 0) DTWS_CASE(16, 0) DTWS_CASE(32, 0)
-#undef DTWS_CASE
-    return cudaErrorInvalidValue;
-}
-
 template <int W, int K>
 static cudaError_t dtw64_mw_launch(const QueryBufs &b, const QueryArgs &a, const int64_t *offsets, int64_t count,
                                    double *out, int64_t count_for_grid, cudaStream_t s) {
@@ -1568,35 +1046,9 @@ static cudaError_t dtw64_dispatch(const QueryBufs &b, const QueryArgs &a, const 
     return cudaErrorInvalidValue;
 }
 
-cudaError_t launch_dtw_seeds(const QueryBufs &b, const QueryArgs &a, cudaStream_t s) {
-    return dtw_dispatch<kModeSeed>(b, a, nullptr, 0, nullptr, kSeedMax, s);
-}
-
-cudaError_t launch_dtw_survivors(const QueryBufs &b, const QueryArgs &a, cudaStream_t s) {
-    return dtw_dispatch<kModeSurv>(b, a, nullptr, 0, nullptr, (int64_t)b.num_sms * 1024, s);
-}
-
+namespace {
 __global__ void k_reset_cursor(QueryState *st) { st->work = 0; }
-
-cudaError_t launch_dtw_at(const QueryBufs &b, const QueryArgs &a, const int64_t *offsets,
-                          int64_t count, float *out, cudaStream_t s) {
-    k_reset_cursor<<<1, 1, 0, s>>>(b.st);
-    return dtw_dispatch<kModeOut>(b, a, offsets, count, out, count, s);
-}
-
-bool dtw_shape_valid(int m, int r, int L, int K, int warps) {
-    DtwPlan p;
-    return plan_shape<float>(m, r, true, L, K, warps, &p) && plan_shape<float>(m, r, false, L, K, warps, &p);
-}
-
-cudaError_t launch_dtw_at_shape(const QueryBufs &b, QueryArgs a, const int64_t *offsets, int64_t count, float *out,
-                                int L, int K, int warps, cudaStream_t s) {
-    a.tune_l = L;
-    a.tune_k = K;
-    a.tune_w = warps;
-    k_reset_cursor<<<1, 1, 0, s>>>(b.st);
-    return dtw_dispatch<kModeOut>(b, a, offsets, count, out, count, s);
-}
+}  // namespace
 
 cudaError_t launch_dtw_at_f64(const QueryBufs &b, const QueryArgs &a, const int64_t *offsets,
                               int64_t count, double *out, cudaStream_t s) {
@@ -1909,159 +1361,6 @@ __global__ void k_final_select(QueryBufs b, QueryArgs a) {
     if (count == a.list_cap && key_dist(st->res_keys[count - 1]) <= lim) atomicOr(b.status, kStOverflow);
     st->n_margin = nm;
     st->ctr[kCtrRescored] = (unsigned long long)nm;
-}
-
-// Pre-score of the best Euclidean seed, run on a side stream while the
-// lower-bound scan streams: its FP32 DTW enters the result list (the survivor
-// pass skips it) and its extended-precision re-score waits for the final
-// stage.  Paired mode (when both copies fit in shared memory): warp 0 runs
-// the FP32 DTW while warps 1..DfW run the re-score beside it, DfW warps wide
-// (the double-float walk's latency per anti-diagonal is what bounds the
-// stage).  Otherwise one warp runs both in turn.
-template <int L, int K>
-__global__ void k_prescore(QueryBufs b, QueryArgs a) {
-    using PS = PreShape<L, K>;
-    extern __shared__ __align__(16) unsigned char smraw[];
-    __shared__ double bc[2];
-    __shared__ DfXchg xchg;
-    QueryState *st = b.st;
-    if (!st->valid) return;
-    const unsigned idx = prescored_window(st, a);
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const bool pair = blockDim.x > 32;
-    if (idx == 0xffffffffu) return;
-    const int m = a.m, r = a.r;
-    const size_t span = pre_span(m, r, L, K);
-    const float *xw = b.x + idx;
-    if (warp == 0) {
-        if (lane >= L) return;
-        const unsigned gmask = (L == 32) ? 0xffffffffu : ((1u << L) - 1u);
-        const int pad = diag_pad(r, L, K);
-        // FP32 DTW, as the survivor pass would compute it
-        float *q32 = (float *)smraw, *c32 = (float *)(smraw + span * 4);
-        const float INF = __int_as_float(0x7f800000);
-        fill_pads(q32, m, pad, INF, lane, L);
-        fill_pads(c32, m, pad, -INF, lane, L);
-        const float mh = b.mu_hi[idx], is = b.inv_sigma[idx], ls = b.mu_lo[idx] * is;
-        for (int j = lane; j < m; j += L) {
-            q32[pad + j] = b.qh32[j];
-            c32[pad + j] = fmaf(xw[j] - mh, is, -ls);
-        }
-        __syncwarp(gmask);
-        int cells = 0;
-        const float d32 =
-            dtw_diag<float, L, K, false>(q32 + pad, c32 + pad, nullptr, m, r, INF, gmask, lane, cells);
-        if (lane == 0) {
-            list_insert(st->res_keys, a.list_cap, make_key(key_quantize(d32, a.qgrid), idx));
-            atomicAdd(&st->ctr[kCtrDtwStarted], 1ull);
-            atomicAdd(&st->ctr[kCtrCells], (unsigned long long)cells);
-        }
-        __syncwarp(gmask);
-        if (pair) return;
-        // one warp: the re-score below reuses this memory
-    }
-    // (one-warp mode with more than 16 cells per lane: the FP32 result is in
-    // the list; the final stage re-scores the window like any other)
-    if constexpr (K > 16) {
-        if (!pair) return;
-    }
-    // extended-precision re-score (FP64 statistics, double-float DTW) by the
-    // first re-score warp's lanes (the whole of warp 1 in paired mode, the
-    // L lanes of warp 0 otherwise)
-    constexpr int LS = PS::W > 1 ? 32 : L;  // lanes of the statistics warp
-    const int dw = pair ? warp - 1 : 0;     // this warp's index in the re-score group
-    const int nthr = pair ? 32 * PS::W : L;
-    const int t = dw * 32 + lane;           // thread index in the group
-    const bool stats_lane = dw == 0 && lane < LS;
-    if (!pair && lane >= L) return;
-    if (stats_lane) {
-        const unsigned smask = (LS == 32) ? 0xffffffffu : ((1u << LS) - 1u);
-        double s = 0.0;
-        for (int j = lane; j < m; j += LS) s += (double)xw[j];
-#pragma unroll
-        for (int o = LS / 2; o > 0; o >>= 1) s += __shfl_xor_sync(smask, s, o, LS);
-        const double mu = s / (double)m;
-        double v = 0.0;
-        for (int j = lane; j < m; j += LS) {
-            const double d = (double)xw[j] - mu;
-            v = fma(d, d, v);
-        }
-#pragma unroll
-        for (int o = LS / 2; o > 0; o >>= 1) v += __shfl_xor_sync(smask, v, o, LS);
-        if (lane == 0) {
-            const double var = v / (double)m, mm = mu * mu;
-            bc[0] = a.raw ? 0.0 : mu;
-            bc[1] = a.raw ? 1.0 : var <= 1e-24 * (mm > 1.0 ? mm : 1.0) ? 0.0 : 1.0 / sqrt(var);
-        }
-    }
-    // the group meets: named barrier 1 in paired mode, the warp otherwise
-    auto group_sync = [&]() {
-        if (pair) group_bar(1, 32 * PS::W);
-        else __syncwarp((L == 32) ? 0xffffffffu : ((1u << L) - 1u));
-    };
-    group_sync();
-    const double mu = bc[0], inv = bc[1];
-    // (paired with L < 32: one warp whose first L lanes walk, as unpaired)
-    const int lanes2 = (pair && L == 32) ? 32 * PS::W : L, k2 = pair ? PS::K2 : K;
-    const int pad2 = diag_pad(r, lanes2, k2);
-    const size_t span2 = pre_span(m, r, lanes2, k2);
-    unsigned char *dbase = smraw + (pair ? span * 8 : 0);
-    dfloat *qd = (dfloat *)dbase, *cd = (dfloat *)(dbase + span2 * 8);
-    fill_pads(qd, m, pad2, dfloat{1e15f, 0.0f}, t, nthr);
-    fill_pads(cd, m, pad2, dfloat{-1e15f, 0.0f}, t, nthr);
-    for (int j = t; j < m; j += nthr) {
-        qd[pad2 + j] = df_from(b.qh64[j]);
-        cd[pad2 + j] = df_from(((double)xw[j] - mu) * inv);
-    }
-    group_sync();
-    double d64;
-    if (pair && PS::W > 1) {
-        d64 = dtw_diag_df_mw<PS::W, PS::K2>(qd + pad2, cd + pad2, m, r, dw, lane, xchg, 1);
-    } else {
-        if constexpr (K <= 16) {
-            const unsigned gmask = (L == 32) ? 0xffffffffu : ((1u << L) - 1u);
-            if (lane >= L) return;
-            d64 = dtw_diag_df<L, K>(qd + pad2, cd + pad2, m, r, gmask, lane);
-        } else {
-            return;  // (not reached: K > 16 runs paired, with PS::W = 4)
-        }
-    }
-    if (t == 0) {
-        st->pre_d64 = d64;
-        __threadfence();
-        st->pre_done = 1;
-    }
-}
-
-cudaError_t launch_prescore(const QueryBufs &b, const QueryArgs &a, cudaStream_t s) {
-    if (!a.prescore) return cudaSuccess;
-    int L, K;
-    diag_shape(a.r, &L, &K);
-    if (a.r > kDiagRMax) {  // the FP32 walk's wide shapes (one warp, 24 or 32 cells)
-        L = 32;
-        K = a.r + 1 <= 32 * 24 ? 24 : 32;
-    }
-#define DTWS_CASE(LL, KK)                                                                           \
-    if (L == LL && K == KK) {                                                                       \
-        using PS = PreShape<LL, KK>;                                                                \
-        /* paired: FP32 copy (8 B per element) beside the re-score's (16 B), */                    \
-        /* else one warp with the re-score reusing the FP32 copy's memory */                       \
-        const size_t s32 = pre_span(a.m, a.r, LL, KK) * 8;                                          \
-        const size_t sdf = pre_span(a.m, a.r, (LL < 32 ? LL : 32 * PS::W), PS::K2) * 16;           \
-        const bool pair = s32 + sdf <= (size_t)200 * 1024;                                          \
-        const size_t smem = pair ? s32 + sdf : pre_span(a.m, a.r, LL, KK) * 16;                     \
-        const int threads = pair ? 32 + 32 * PS::W : 32;                                            \
-        cudaError_t e = cudaFuncSetAttribute(k_prescore<LL, KK>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
-                                             (int)smem);                                            \
-        if (e != cudaSuccess) return e;                                                             \
-        k_prescore<LL, KK><<<1, threads, smem, s>>>(b, a);                                          \
-        return cudaGetLastError();                                                                  \
-    }
-    DTWS_CASE(1, 1) DTWS_CASE(2, 1) DTWS_CASE(4, 1) DTWS_CASE(8, 1) DTWS_CASE(16, 1)
-    DTWS_CASE(32, 1) DTWS_CASE(32, 2) DTWS_CASE(32, 3) DTWS_CASE(32, 4) DTWS_CASE(32, 6) DTWS_CASE(32, 8) \
-    DTWS_CASE(32, 10) DTWS_CASE(32, 12) DTWS_CASE(32, 16) DTWS_CASE(32, 24) DTWS_CASE(32, 32)
-#undef DTWS_CASE
-    return cudaErrorInvalidValue;
 }
 
 // Top-k with an exclusion zone: the search's K best windows in (distance,

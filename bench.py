@@ -62,9 +62,10 @@ SPECS = {
     # the learned-proposal workload's series itself (2e8 samples), its first query
     "learn200m": dict(n=200_000_000, m=1024, w=0.10, k=1),
     # wide bands (r = 0.9 m, the regime of the paper's experiments) on 2e7 samples of the
-    # same kind: the anti-diagonal kernel (r <= 511) and the row-systolic one (r > 511)
+    # same kind: the one-warp walk (r <= 511) and the four-warp walk (511 < r <= 2047)
     "wide512": dict(n=20_000_000, m=512, w=0.90, k=1),
     "wide1024": dict(n=20_000_000, m=1024, w=0.90, k=1),
+    "wide2048": dict(n=20_000_000, m=2048, w=0.90, k=1),
 }
 
 
@@ -149,12 +150,12 @@ def make_workload(name: str, rank: int = 0, world: int = 1):
     def frag(k):
         if name in ("rw100m", "rw30m"):
             return synth.walk_with_bursts(n, 0 + 101 * k, 3 + 101 * k, 5 + 101 * k)
-        if name in ("learn20m", "learn200m", "wide512", "wide1024"):
+        if name in ("learn20m", "learn200m", "wide512", "wide1024", "wide2048"):
             return synth.walk_with_bursts(n, 4 + 101 * k, 4 + 101 * k, 6 + 101 * k)
         return synth.random_walk(n, 101 * k)
 
     x = frag(rank)
-    if name in ("learn20m", "learn200m", "wide512", "wide1024"):
+    if name in ("learn20m", "learn200m", "wide512", "wide1024", "wide2048"):
         qs, offs = synth.fixed_queries(frag(0) if rank != 0 else x, 1, m, 9)
         q, o = qs[0], offs[0]
     else:
@@ -434,6 +435,8 @@ def gpu_arm(args):
         line["batch"] = batch_leg(dev)
         torch.cuda.empty_cache()
         line["drift"] = drift_leg(dev, fp64_oracle=not args.no_cpu_baseline)
+        torch.cuda.empty_cache()
+        line["wide"] = wide_leg(dev)
     print(json.dumps(line))
     return 0
 
@@ -624,6 +627,35 @@ def drift_leg(dev, fp64_oracle: bool = True):
         eret = [abs(a - b) / max(b, 1e-30) for a, b in zip(ret, ref)]
         out["fp32_dtw_rel_error_vs_fp64_oracle"] = {"max": max(e32), "median": float(np.median(e32))}
         out["returned_dist_rel_error_vs_fp64_oracle"] = {"max": max(eret), "median": float(np.median(eret))}
+    return out
+
+
+def wide_leg(dev):
+    """Wide bands, the regime of the paper's experiments (r = 0.9 m): the
+    wide1024 (m = 1024, r = 921) and wide2048 (m = 2048, r = 1843) workloads
+    on 2e7 samples, one noisy query each: mean ms per query after the
+    per-series data is built, phase times, and the survivor DTW stage's
+    evaluated cells per second."""
+    import torch
+
+    from paper_1812_10302_gb300 import dtws
+    out = {}
+    for name in ("wide1024", "wide2048"):
+        x, q, r, k, o = make_workload(name)
+        ix = dtws.Index(torch.from_numpy(x).to(dev))
+        qd = torch.from_numpy(q).to(dev)
+        ms = _mean_query_ms(ix, [qd], r, k, dev, reps=5)
+        idx, dist = ix.query(q, r, k)
+        sample = _phase_sample(ix, [qd], [r], k, 1)[0]
+        st = ix.last_stats()
+        ix.close()
+        dtw_ms = sample["phase_ms"]["dtw"]
+        out[name] = {"n": int(x.size), "m": int(q.size), "r": int(r), "ms_per_query": ms,
+                     "subsequences_per_s": (x.size - q.size + 1) / (ms * 1e-3),
+                     "dtw_cells_evaluated": int(st["dtw_cells"]),
+                     "dtw_cells_per_s": (st["dtw_cells"] / (dtw_ms * 1e-3)) if dtw_ms > 0 else None,
+                     "phase_ms": sample["phase_ms"], "survivors": sample["survivors"],
+                     "result": {"offset": int(idx[0]), "dist": float(dist[0]), "planted_offset": int(o)}}
     return out
 
 

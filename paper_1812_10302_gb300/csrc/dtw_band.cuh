@@ -226,6 +226,12 @@ __device__ T dtw_band(const T *__restrict__ qs, const float *__restrict__ xw, co
 // +inf (never NaN) and needs no bounds test.
 __host__ __device__ inline int diag_pad(int r, int L, int K) { return (r >> 1) + L * K + 4; }
 
+// Named barrier `id` over `nthreads` threads (a multiple of 32): the warps
+// of one lane group meet without stopping the rest of the CTA.
+__device__ __forceinline__ void group_bar(int id, int nthreads) {
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
+}
+
 // Three-input minimum (one instruction on sm_100 and later).  The DTW
 // values are never NaN (out-of-band cells are +inf), so its NaN rule does
 // not matter here.
@@ -452,6 +458,203 @@ __device__ T dtw_diag(const T *__restrict__ qp, const T *__restrict__ cp, const 
     return (T)__shfl_sync(gmask, res, pe / K, L);
 }
 
+// ------------------------------------------------------------------ multi-warp FP32 walk
+// dtw_diag with the r+1 cells of an anti-diagonal spread over W warps of one
+// group (32 W lanes, K cells each): bands up to 32 W K - 1 (2047 with four
+// warps of 16 cells).  Inside a warp the neighbour cell arrives by shuffle;
+// across a warp boundary through shared memory: after each step every warp's
+// first and last lane publish their newest cell into the other half of a
+// double buffer and the group meets at its named barrier, so a step's reads
+// (this half) never race the next step's writes (the other half).  The
+// register windows rotate as in dtw_diag; each warp's boundary lane loads
+// its fresh value from the padded arrays instead of a neighbour warp.
+struct MwXchg {
+    float first[2][8], last[2][8];  // [buffer][warp]: lane 0's p1[0], lane 31's p1[K-1]
+    float red[2][8];                // per-warp partial sums / minima
+    float res;
+};
+
+template <int W, int K, int ODD, int QP, int CP>
+__device__ __forceinline__ void diag_step_mw(const float (&qv)[K], const float (&cv)[K], float (&p1)[K],
+                                             float (&p2)[K], const float (&pen)[K], int gl, int lane, int w, int r,
+                                             const MwXchg &x, int buf) {
+    const float INF = __int_as_float(0x7f800000);
+    float nb = __shfl_sync(0xffffffffu, ODD ? p1[0] : p1[K - 1], ODD ? ((lane + 1) & 31) : ((lane - 1) & 31));
+    if (ODD) {
+        if (lane == 31) nb = (w == W - 1) ? INF : x.first[buf][w + 1];
+    } else {
+        if (lane == 0) nb = (w == 0) ? INF : x.last[buf][w - 1];
+    }
+    float cur[K];
+#pragma unroll
+    for (int t = 0; t < K; ++t) {
+        const float left = ODD ? p1[t] : (t == 0 ? nb : p1[t > 0 ? t - 1 : 0]);
+        const float up = ODD ? (t == K - 1 ? nb : p1[t < K - 1 ? t + 1 : 0]) : p1[t];
+        const float d = qv[((t - QP) % K + K) % K] - cv[(t + CP) % K];
+        float v = fmaf(d, d, min3f(left, up, p2[t]));
+        if (ODD) {
+            if constexpr (K <= 8) v = fmaxf(v, pen[t]);
+            else if (gl * K + t == r) v = INF;
+        }
+        cur[t] = v;
+    }
+#pragma unroll
+    for (int t = 0; t < K; ++t) {
+        p2[t] = p1[t];
+        p1[t] = cur[t];
+    }
+}
+
+template <int W, int K>
+__device__ __forceinline__ void mw_publish(const float (&p1)[K], int lane, int w, MwXchg &x, int &buf, int bar) {
+    const int nbuf = buf ^ 1;
+    if (lane == 0) x.first[nbuf][w] = p1[0];
+    if (lane == 31) x.last[nbuf][w] = p1[K - 1];
+    group_bar(bar, 32 * W);
+    buf = nbuf;
+}
+
+template <int K, int CP>
+__device__ __forceinline__ void rot_c_mw(float (&cv)[K], const float *cp, int cbase_new, int gl, int lane) {
+    constexpr int s = CP % K;
+    const float from_next = __shfl_down_sync(0xffffffffu, cv[s], 1);
+    const float fresh = cp[cbase_new + (gl + 1) * K - 1];
+    cv[s] = lane == 31 ? fresh : from_next;
+}
+template <int K, int QP>
+__device__ __forceinline__ void rot_q_mw(float (&qv)[K], const float *qp, int qbase_new, int gl, int lane) {
+    constexpr int s = ((K - 1 - QP) % K + K) % K;
+    const float from_prev = __shfl_up_sync(0xffffffffu, qv[s], 1);
+    const float fresh = qp[qbase_new - gl * K];
+    qv[s] = lane == 0 ? fresh : from_prev;
+}
+template <int K>
+__device__ __forceinline__ void shift_c_mw(float (&cv)[K], const float *cp, int cbase_new, int gl, int lane) {
+    const float from_next = __shfl_down_sync(0xffffffffu, cv[0], 1);
+    const float fresh = cp[cbase_new + (gl + 1) * K - 1];
+#pragma unroll
+    for (int t = 0; t < K - 1; ++t) cv[t] = cv[t + 1];
+    cv[K - 1] = lane == 31 ? fresh : from_next;
+}
+template <int K>
+__device__ __forceinline__ void shift_q_mw(float (&qv)[K], const float *qp, int qbase_new, int gl, int lane) {
+    const float from_prev = __shfl_up_sync(0xffffffffu, qv[K - 1], 1);
+    const float fresh = qp[qbase_new - gl * K];
+#pragma unroll
+    for (int t = K - 1; t > 0; --t) qv[t] = qv[t - 1];
+    qv[0] = lane == 0 ? fresh : from_prev;
+}
+
+// qp, cp: element 0 of the query / the group's normalised window, padded by
+// diag_pad(r, 32*W, K) on both sides (+inf / -inf); cbs: the coarse tail
+// bound (as dtw_diag) or nullptr.  Called by all 32 W threads of warps
+// w = 0..W-1 of the group; bar: the group's named barrier.  Every thread
+// returns the distance (+inf when abandoned); thread 0 of the group adds the
+// cells evaluated to `cells`.
+template <int W, int K, bool ABANDON>
+__device__ float dtw_diag_mw(const float *__restrict__ qp, const float *__restrict__ cp, const float *cbs, int m,
+                             int r, float thr, int w, int lane, MwXchg &x, int bar, int &cells) {
+    static_assert(W >= 2 && W <= 8, "two to eight warps");
+    constexpr int U = diag_unroll(K);
+    const float INF = __int_as_float(0x7f800000);
+    const int gl = w * 32 + lane;
+    const int p0 = (r - (r & 1)) >> 1;
+    float p1[K], p2[K], qv[K], cv[K], pen[K];
+#pragma unroll
+    for (int t = 0; t < K; ++t) {
+        p1[t] = INF;
+        p2[t] = (gl * K + t == p0) ? 0.0f : INF;
+        pen[t] = (gl * K + t == r) ? INF : 0.0f;
+    }
+    int buf = 1;
+    mw_publish<W, K>(p1, lane, w, x, buf, bar);  // buffer 0 := the all-inf anti-diagonal -1
+    const int last = 2 * m - 2;
+    const int pe_even = r >> 1, pe_odd = (r - 1) >> 1;
+    int a = 0;
+    if (r & 1) {
+        const int qb = (r - 1) >> 1, cb = (1 - r) >> 1;
+#pragma unroll
+        for (int t = 0; t < K; ++t) {
+            qv[t] = qp[qb - (gl * K + t)];
+            cv[t] = cp[cb + (gl * K + t)];
+        }
+        diag_step_mw<W, K, 1, 0, 0>(qv, cv, p1, p2, pen, gl, lane, w, r, x, buf);
+        mw_publish<W, K>(p1, lane, w, x, buf, bar);
+        a = 1;
+        shift_q_mw<K>(qv, qp, qb + 1, gl, lane);
+    } else {
+        const int qb = r >> 1, cb = -(r >> 1);
+#pragma unroll
+        for (int t = 0; t < K; ++t) {
+            qv[t] = qp[qb - (gl * K + t)];
+            cv[t] = cp[cb + (gl * K + t)];
+        }
+    }
+    int bi = (a + r) >> 1, bj = (a - r) >> 1;
+    while (a + 2 * U - 1 < last) {
+        static_for<U>([&](auto uc) {
+            constexpr int u = decltype(uc)::value;
+            diag_step_mw<W, K, 0, u % K, u % K>(qv, cv, p1, p2, pen, gl, lane, w, r, x, buf);
+            mw_publish<W, K>(p1, lane, w, x, buf, bar);
+            rot_c_mw<K, u % K>(cv, cp, bj + u + 1, gl, lane);
+            diag_step_mw<W, K, 1, u % K, (u + 1) % K>(qv, cv, p1, p2, pen, gl, lane, w, r, x, buf);
+            mw_publish<W, K>(p1, lane, w, x, buf, bar);
+            rot_q_mw<K, u % K>(qv, qp, bi + u + 1, gl, lane);
+        });
+        a += 2 * U;
+        bi += U;
+        bj += U;
+        if (ABANDON) {
+            float low = INF;
+#pragma unroll
+            for (int t = 0; t < K; ++t) {
+                const int i = bi - 1 - (gl * K + t);
+                const float tail = (cbs && i >= 0 && i < m) ? cbs[(i + kTailG) / kTailG] : 0.0f;
+                low = fminf(low, fminf(p1[t], p2[t]) + tail);
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) low = fminf(low, __shfl_xor_sync(0xffffffffu, low, o));
+            if (lane == 0) x.red[0][w] = low;
+            group_bar(bar, 32 * W);
+#pragma unroll
+            for (int v = 0; v < W; ++v) low = fminf(low, x.red[0][v]);
+            if (low > thr) {
+                if (gl == 0) cells += (int)band_cells_upto(a - 1, m, r);
+                group_bar(bar, 32 * W);  // x.red is read before anyone writes it again
+                return INF;
+            }
+        }
+    }
+    bool at_end = false;
+    for (;; a += 2, ++bi, ++bj) {
+        diag_step_mw<W, K, 0, 0, 0>(qv, cv, p1, p2, pen, gl, lane, w, r, x, buf);
+        mw_publish<W, K>(p1, lane, w, x, buf, bar);
+        if (a == last) {
+#pragma unroll
+            for (int t = 0; t < K; ++t)
+                if (gl * K + t == pe_even) x.res = p1[t];
+            at_end = true;
+        }
+        if (at_end) break;
+        shift_c_mw<K>(cv, cp, bj + 1, gl, lane);
+        diag_step_mw<W, K, 1, 0, 0>(qv, cv, p1, p2, pen, gl, lane, w, r, x, buf);
+        mw_publish<W, K>(p1, lane, w, x, buf, bar);
+        if (a + 1 == last) {
+#pragma unroll
+            for (int t = 0; t < K; ++t)
+                if (gl * K + t == pe_odd) x.res = p1[t];
+            at_end = true;
+        }
+        if (at_end) break;
+        shift_q_mw<K>(qv, qp, bi + 1, gl, lane);
+    }
+    group_bar(bar, 32 * W);
+    const float res = x.res;
+    if (gl == 0) cells += (int)band_cells_upto(last, m, r);
+    group_bar(bar, 32 * W);  // x.res is read before the next walk writes it
+    return res;
+}
+
 // Knuth's error-free transformations (TwoSum, FastTwoSum, FMA-based
 // products).  It runs on the FP32 pipes, which on this part issue far more
 // than its FP64 units; accumulated relative error over a DTW is ~1e-14.
@@ -611,9 +814,6 @@ struct DfXchg {
     dfloat res;
 };
 
-__device__ __forceinline__ void group_bar(int id, int nthreads) {
-    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
-}
 
 template <int W, int K, int ODD>
 __device__ __forceinline__ void diag_step_df_mw(const dfloat (&qv)[K], const dfloat (&cv)[K], dfloat (&p1)[K],

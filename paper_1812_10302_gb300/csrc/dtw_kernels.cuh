@@ -18,6 +18,11 @@
 
 namespace dtws {
 
+// the multi-warp FP32 kernel for bands past one warp (k_dtw_mw below): four
+// warps per candidate, up to 16 cells per lane
+constexpr int kWideW = 4;
+constexpr int kWideRMax = 32 * kWideW * 16 - 1;  // 2047
+
 // Bin of a survivor's lower bound for the counting sort (see launch_order):
 // with a finite scan threshold the bins split [0, thr] evenly; otherwise
 // they follow the float's exponent and leading mantissa bits (monotone for
@@ -499,13 +504,9 @@ static bool plan_dtw(int m, int r, bool tail, DtwPlan *p) {
         DTWS_TRY(32, 1) DTWS_TRY(32, 2) DTWS_TRY(32, 3) DTWS_TRY(32, 4) DTWS_TRY(32, 6) DTWS_TRY(32, 8) \
         DTWS_TRY(32, 10) DTWS_TRY(32, 12) DTWS_TRY(32, 16)
 #undef DTWS_TRY
-    } else if (std::is_same<T, float>::value && r <= kDiagRMaxF32) {
-        // wider bands in FP32: one warp with 24 or 32 cells per lane (the
-        // survivor, seed and given-offset kernels; the re-score has its own
-        // multi-warp walk)
-        if (r + 1 <= 32 * 24 && plan_fits<T, 32, 24>(m, r, tail, p)) return true;
-        if (plan_fits<T, 32, 32>(m, r, tail, p)) return true;
     }
+    // (FP32 bands kDiagRMax < r <= kWideRMax go to the multi-warp kernel,
+    // dtw_wide_launch; the row-systolic kernel below takes the rest)
     const int L = lanes_for(r);
 #define DTWS_TRY(LL) \
     if (L == LL) return plan_fits<T, LL, 0>(m, r, tail, p);
@@ -522,12 +523,18 @@ inline int dtw_blocks(const DtwPlan &p, int num_sms, int64_t count) {
     return (int)(want < cap ? want : cap);
 }
 
+// Launch of the wide-band kernel for one mode (instantiated in dtw_wide.cu).
+template <int MODE>
+cudaError_t dtw_wide_launch(const QueryBufs &b, const QueryArgs &a, const int64_t *offsets, int64_t count,
+                            float *out, int64_t count_for_grid, cudaStream_t s);
 template <int MODE>
 static cudaError_t dtw_dispatch(const QueryBufs &b, const QueryArgs &a, const int64_t *offsets,
                                 int64_t count, float *out, int64_t count_for_grid, cudaStream_t s) {
     DtwPlan p;
     const bool tail = MODE == kModeSurv && (b.U != nullptr || b.stmax != nullptr);
     const bool tuned = a.tune_l > 0 && plan_shape<float>(a.m, a.r, tail, a.tune_l, a.tune_k, a.tune_w, &p);
+    if (!tuned && a.r > kDiagRMax && a.r <= kWideRMax)
+        return dtw_wide_launch<MODE>(b, a, offsets, count, out, count_for_grid, s);
     if (!tuned && !plan_dtw<float>(a.m, a.r, tail, &p)) return cudaErrorInvalidValue;
     const int blocks = dtw_blocks(p, b.num_sms, count_for_grid);
 #define DTWS_CASE(LL, KK)                                                                                     \
@@ -541,10 +548,234 @@ static cudaError_t dtw_dispatch(const QueryBufs &b, const QueryArgs &a, const in
     DTWS_CASE(1, 1) DTWS_CASE(2, 1) DTWS_CASE(4, 1) DTWS_CASE(8, 1) DTWS_CASE(16, 1)
     DTWS_CASE(4, 2) DTWS_CASE(8, 2) DTWS_CASE(16, 2)
     DTWS_CASE(32, 1) DTWS_CASE(32, 2) DTWS_CASE(32, 3) DTWS_CASE(32, 4) DTWS_CASE(32, 6) DTWS_CASE(32, 8) \
-    DTWS_CASE(32, 10) DTWS_CASE(32, 12) DTWS_CASE(32, 16) DTWS_CASE(32, 24) DTWS_CASE(32, 32)
+    DTWS_CASE(32, 10) DTWS_CASE(32, 12) DTWS_CASE(32, 16)
     DTWS_CASE(1, 0) DTWS_CASE(2, 0) DTWS_CASE(4, 0) DTWS_CASE(8, 0) DTWS_CASE(16, 0) DTWS_CASE(32, 0)
 #undef DTWS_CASE
     return cudaErrorInvalidValue;
 }
+
+
+// ------------------------------------------------------------------ wide bands
+// The FP32 DTW kernel for bands past the one-warp walks (kDiagRMax < r <=
+// 2047): a group of W = 4 warps per candidate (dtw_diag_mw, K cells per
+// lane, 128 K >= r + 1), two groups per CTA of 256 threads (one when the
+// copies do not fit).  The same three modes and the same per-candidate
+// steps as k_dtw (one candidate at a time per group, the pre-check of the
+// survivor mode over the group's 128 threads); group decisions come from
+// values every thread of the group reads after the group's barrier, so all
+// its threads take the same branches.
+
+__host__ __device__ inline int wide_k(int r) {
+    const int need = (r + 1 + 32 * kWideW - 1) / (32 * kWideW);
+    return need <= 6 ? 6 : need <= 8 ? 8 : need <= 12 ? 12 : 16;
+}
+__host__ __device__ inline size_t wide_span(int m, int r, int K) {
+    return (size_t)((m + 2 * diag_pad(r, 32 * kWideW, K) + 3) & ~3);
+}
+__host__ __device__ inline size_t wide_tail(int m) { return (size_t)((tail_entries(m) + 3) & ~3); }
+
+template <int W, int K, int MODE>
+__global__ void __launch_bounds__(256, 2) k_dtw_mw(QueryBufs b, QueryArgs a, const int64_t *offsets,
+                                                   int64_t count_host, float *out) {
+    constexpr int GMAX = 8 / W;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    __shared__ MwXchg xch[GMAX];
+    __shared__ int cur_s[GMAX][2];
+    __shared__ float thr_s[GMAX][2];
+    __shared__ unsigned seeds_s[kSeedMax];
+    __shared__ int n_seeds_s;
+    __shared__ int ord_s[128];
+    __shared__ float sq_s[128], su_s[128], sl_s[128];
+    QueryState *st = b.st;
+    if (!st->valid) return;
+    const int m = a.m, r = a.r;
+    const bool has_env = MODE == kModeSurv && (b.U != nullptr || b.stmax != nullptr);
+    const int G = (int)(blockDim.x / (32 * W));
+    const int pad = diag_pad(r, 32 * W, K);
+    const size_t span = wide_span(m, r, K), tailn = wide_tail(m);
+    float *qs = (float *)smraw + pad;
+    for (int t = threadIdx.x; t < m; t += blockDim.x) qs[t] = b.qh32[t];
+    fill_pads((float *)smraw, m, pad, DINF, threadIdx.x, blockDim.x);
+    const int warp = threadIdx.x >> 5, lane = lane_id();
+    const int g = warp / W, w = warp % W, t = w * 32 + lane;
+    const int nthr = 32 * W, bar = 1 + g;
+    float *gbase = (float *)smraw + span + (size_t)g * (span + tailn);
+    float *cd = gbase + pad;
+    float *cbs = gbase + span;
+    if (g < G) fill_pads(gbase, m, pad, -DINF, t, nthr);
+    if (MODE == kModeSurv) {
+        if (threadIdx.x == 0) n_seeds_s = st->n_seeds;
+        for (int i = threadIdx.x; i < st->n_seeds; i += blockDim.x) seeds_s[i] = st->seed_off[i];
+        for (int i = threadIdx.x; i < 128; i += blockDim.x) {
+            const bool in = i < m;
+            ord_s[i] = in ? (int)b.ord[i] : 0;
+            sq_s[i] = in ? b.sq[i] : 0.0f;
+            su_s[i] = in ? b.sU[i] : 0.0f;
+            sl_s[i] = in ? b.sL[i] : 0.0f;
+        }
+    }
+    __syncthreads();
+    if (g >= G) return;
+    int *cursor = MODE == kModeSurv ? &st->work2 : &st->work;
+    const float thr_scan = MODE == kModeSurv ? st->thr_scan : 0.0f;
+    const unsigned pre = MODE == kModeSurv ? prescored_window(st, a) : 0xffffffffu;
+    const int64_t count = MODE == kModeSeed ? (int64_t)st->n_seeds
+                        : MODE == kModeSurv ? (int64_t)st->n_cand : count_host;
+    long long cells_acc = 0;
+    int started = 0, abandoned = 0, passed_s = 0;
+    int cells = 0;
+    for (int it = 0;; it ^= 1) {
+        // cur_s / thr_s alternate between two slots: a slot is written again
+        // only after the next iteration's barrier, which every thread of the
+        // group reaches after reading it
+        if (t == 0) {
+            cur_s[g][it] = atomicAdd(cursor, 1);
+            float th = DINF;
+            if (MODE == kModeSeed) {
+                const float kth = list_kth(st->seed_keys, a.k);
+                th = kth < DINF ? fmaf(kth, 1.0f + a.delta, a.alpha) : DINF;
+            } else if (MODE == kModeSurv) {
+                th = current_thr(st, a);
+            }
+            thr_s[g][it] = th;
+        }
+        group_bar(bar, nthr);
+        const int c = cur_s[g][it];
+        if (c >= count) break;
+        const float thr = thr_s[g][it];
+        unsigned idx = 0;
+        if (MODE == kModeSeed) {
+            idx = st->seed_off[c];
+        } else if (MODE == kModeOut) {
+            const int64_t o = offsets[c];
+            if (o < 0 || o >= a.N) {
+                if (t == 0) out[c] = __int_as_float(0x7fc00000);
+                continue;
+            }
+            idx = (unsigned)o;
+        } else {
+            idx = b.sort_idx[c];
+            const float lb = b.sort_lb[c];
+            if (lb > thr) {
+                // survivors are in ascending bins and thr only shrinks
+                if (bin_floor(bin_of(lb, thr_scan), thr_scan) > thr) break;
+                continue;
+            }
+            bool seen = idx == pre;  // scored already: by the seed pass or on the side stream
+            for (int i = 0; i < n_seeds_s; ++i) seen |= seeds_s[i] == idx;
+            if (seen) continue;
+        }
+        const float mh = b.mu_hi[idx], is = b.inv_sigma[idx], ls = b.mu_lo[idx] * is;
+        const float *xw = b.x + idx;
+        TailCtx tc;
+        tc.Uw = b.U ? b.U + idx : nullptr;
+        tc.Lw = b.L ? b.L + idx : nullptr;
+        tc.stmax = b.stmax;
+        tc.stmin = b.stmin;
+        tc.nblk = b.nblk;
+        tc.n = b.n;
+        tc.t0 = idx;
+        tc.r = r;
+        tc.qs = qs;
+        tc.mh = mh;
+        tc.is = is;
+        tc.ls = ls;
+        if (has_env) {
+            // Eq. 10 and Eq. 8 over the 128 largest-|q_hat| rows (one pass:
+            // 128 threads, one term each), reduced over the group
+            const int budget = m < 128 ? m : 128;
+            float v = 0.0f, v8 = 0.0f;
+            for (int j = t; j < budget; j += nthr) {
+                const int pos = ord_s[j];
+                float U, Lo;
+                env_at(tc, pos, U, Lo);
+                const float u = fmaf(U - mh, is, -ls), l = fmaf(Lo - mh, is, -ls), q = sq_s[j];
+                const float dq = fmaxf(q - u, 0.0f) + fmaxf(l - q, 0.0f);
+                v = fmaf(dq, dq, v);
+                const float cv = fmaf(xw[pos] - mh, is, -ls);
+                const float e = fmaxf(cv - su_s[j], 0.0f) + fmaxf(sl_s[j] - cv, 0.0f);
+                v8 = fmaf(e, e, v8);
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                v += __shfl_xor_sync(0xffffffffu, v, o);
+                v8 += __shfl_xor_sync(0xffffffffu, v8, o);
+            }
+            if (lane == 0) {
+                xch[g].red[0][w] = v;
+                xch[g].red[1][w] = v8;
+            }
+            group_bar(bar, nthr);
+            float acc = 0.0f, acc8 = 0.0f;
+#pragma unroll
+            for (int u = 0; u < W; ++u) {
+                acc += xch[g].red[0][u];
+                acc8 += xch[g].red[1][u];
+            }
+            if (acc > thr || acc8 > thr) continue;
+        }
+        for (int j = t; j < m; j += nthr) cd[j] = fmaf(xw[j] - mh, is, -ls);
+        if (has_env) {
+            // the coarse tail bound: kTailG-row sums, then a suffix scan by
+            // the group's first warp
+            const int ne = tail_entries(m);
+            for (int gi = t; gi < ne - 1; gi += nthr) {
+                float sum = 0.0f;
+                const int i1 = (gi + 1) * kTailG < m ? (gi + 1) * kTailG : m;
+                for (int i = gi * kTailG; i < i1; ++i) sum += tail_term(tc, i);
+                cbs[gi] = sum;
+            }
+            group_bar(bar, nthr);
+            if (w == 0) {
+                float carry = 0.0f;
+                for (int c0 = ((ne - 1 + 31) / 32 - 1) * 32; c0 >= 0; c0 -= 32) {
+                    const int gi = c0 + lane;
+                    float v = gi < ne - 1 ? cbs[gi] : 0.0f;
+#pragma unroll
+                    for (int o = 1; o < 32; o <<= 1) {
+                        const float u = __shfl_down_sync(0xffffffffu, v, o);
+                        if (lane + o < 32) v += u;
+                    }
+                    if (gi < ne - 1) cbs[gi] = carry + v;
+                    carry += __shfl_sync(0xffffffffu, v, 0);
+                }
+                __syncwarp();
+                const float slack = 1e-5f * carry;
+                for (int gi = lane; gi < ne - 1; gi += 32) cbs[gi] = fmaxf(0.0f, cbs[gi] - slack);
+                if (lane == 0) cbs[ne - 1] = 0.0f;
+            }
+        }
+        group_bar(bar, nthr);
+        if (has_env) {
+            if (cbs[0] > thr) continue;  // Eq. 10 over every row
+            if (t == 0) ++passed_s;
+        }
+        const float d = dtw_diag_mw<W, K, MODE != kModeOut>(qs, cd, has_env ? cbs : nullptr, m, r, thr, w, lane,
+                                                            xch[g], bar, cells);
+        if (t == 0) {
+            ++started;
+            if (!(d < DINF)) ++abandoned;
+            if (MODE == kModeOut) {
+                out[c] = d;
+            } else if (MODE == kModeSeed) {
+                if (d < DINF) {
+                    const unsigned long long key = make_key(key_quantize(d, a.qgrid), idx);
+                    list_insert(st->seed_keys, a.k, key);
+                    list_insert(st->res_keys, a.list_cap, key);
+                }
+            } else if (d <= thr) {
+                list_insert(st->res_keys, a.list_cap, make_key(key_quantize(d, a.qgrid), idx));
+            }
+        }
+    }
+    cells_acc = cells;
+    if (MODE != kModeOut && t == 0) {
+        atomicAdd(&st->ctr[kCtrCells], (unsigned long long)cells_acc);
+        atomicAdd(&st->ctr[kCtrDtwStarted], (unsigned long long)started);
+        atomicAdd(&st->ctr[kCtrDtwAbandoned], (unsigned long long)abandoned);
+        if (passed_s) atomicAdd(&st->ctr[kCtrKeoghS], (unsigned long long)passed_s);
+    }
+}
+
 
 }  // namespace dtws

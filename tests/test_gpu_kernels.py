@@ -77,9 +77,10 @@ def test_lower_bounds_match_oracle_and_are_admissible(series, index, m, r):
         assert np.all(g <= d * (1 + DELTA) + 1e-6 * m)
 
 
-@pytest.mark.parametrize("m,r", [(32, 0), (32, 1), (48, 2), (64, 3), (64, 5), (100, 8), (128, 17),
-                                 (256, 40), (512, 51), (700, 127), (64, 63), (1024, 102),
-                                 (700, 650), (1024, 921), (2048, 1000), (2048, 1500)])
+@pytest.mark.parametrize("m,r", [(32, 0), (32, 1), (48, 2), (64, 3), (64, 5), (100, 8), (128, 17), (70, 31),
+                                 (256, 40), (512, 51), (700, 127), (64, 63), (1024, 102), (900, 511),
+                                 (700, 650), (1024, 921), (2048, 1000), (2048, 1500), (2048, 1100),
+                                 (2048, 2047), (3000, 2047), (2048, 600), (1600, 1535), (3000, 2100)])
 def test_dtw_fp32_matches_oracle(series, index, m, r):
     q, _ = synth.noisy_copy(series, m, 20 + m, 21 + r, noise=0.3)
     offs = np.random.default_rng(m * 7 + r).integers(0, series.size - m + 1, 300)

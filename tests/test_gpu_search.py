@@ -57,11 +57,12 @@ def test_distances_are_the_extended_rescore(walk, index, m, r):
     np.testing.assert_array_max_ulp(dist, index.dtw_at_f64(q, r, idx).astype(np.float32), maxulp=1)
 
 
-@pytest.mark.parametrize("m,r,k", [(700, 630, 3), (1100, 990, 1), (1500, 1499, 2)])
+@pytest.mark.parametrize("m,r,k", [(700, 630, 3), (1100, 990, 1), (1500, 1499, 2), (1400, 1100, 2),
+                                   (2048, 1843, 1), (2048, 2047, 3), (2500, 2100, 1)])
 def test_wide_band_queries_match_oracle(m, r, k):
-    """Bands of 0.9 m and more: the FP32 anti-diagonal walk with 24 or 32
-    cells per lane (r <= 1023), the row-systolic kernel beyond, and the
-    four-warp double-float re-score."""
+    """Bands of 0.9 m and more: the FP32 walk on four warps per candidate
+    (kDiagRMax < r <= 2047, up to 16 cells per lane), the row-systolic
+    kernel beyond, and the four-warp double-float re-score."""
     x = synth.random_walk(6_000, 40 + m)
     q, _ = synth.noisy_copy(x, m, 41 + m, 42 + m, noise=0.3)
     with dtws.Index(x) as ix:

@@ -109,12 +109,22 @@ typedef struct {
     int32_t exclusion_zone; /* z >= 0 (default 0): dtws_query returns the k
                                best windows of which no two lie within z
                                samples of each other, taken greedily in
-                               (distance, offset) order.  Exact: that answer
-                               lies among the k*(2z+1) best windows, which
-                               the search finds first, so k*(2z+1) must not
-                               exceed DTWS_K_MAX.  Not for dtws_query_batch.
-                               Missing windows (the series too short) come
-                               back as offset -1, distance +inf. */
+                               (distance, offset) order.  Exact.  When
+                               k*(2z+1) <= DTWS_K_MAX the answer lies among
+                               the k*(2z+1) best windows, which the search
+                               finds first; otherwise (e.g. z ~ m/2 with
+                               k > 1) the search prunes against the k-th
+                               distance of windows found more than 2z apart
+                               (offsets cut into buckets of 2z+1, one window
+                               per bucket, two lists by bucket parity), keeps
+                               every window scored within its threshold in a
+                               candidate buffer, and at the end re-scores
+                               those within the final threshold and takes
+                               them greedily (DTWS_EOVERFLOW if the buffer of
+                               2^20 or the re-score list of 8192 fills).
+                               Not for dtws_query_batch.  Missing windows
+                               (the series too short) come back as offset
+                               -1, distance +inf. */
     int32_t unnormalised;   /* 1: DTW of the raw values (no z-normalisation of
                                the windows or the query, Eq. 5 skipped);
                                default 0.  dtws_query and the building
@@ -200,9 +210,9 @@ dtws_status dtws_get_options(dtws_t h, dtws_options *opt);
  * whose arguments (pointers, m, r, k, options) repeat the previous one's
  * replays the captured search; the query values may differ.
  * With options.unnormalised = 1 neither side is normalised (raw values).
- * Errors: DTWS_EINVAL synchronously (also k*(2z+1) > DTWS_K_MAX with an
- * exclusion zone; unnormalised DTW with the learned ordering or with a
- * series beyond +-2^32); DTWS_ENONFINITE via dtws_sync_status.
+ * Errors: DTWS_EINVAL synchronously (also unnormalised DTW with the learned
+ * ordering or with a series beyond +-2^32); DTWS_ENONFINITE and
+ * DTWS_EOVERFLOW via dtws_sync_status.
  */
 dtws_status dtws_query(dtws_t h, const float *Q, int32_t m, int32_t r, int32_t k,
                        int64_t *out_idx, float *out_dist, void *stream);
@@ -239,6 +249,15 @@ const char *dtws_last_error_detail(void);
    by this library fail as if the device were out of memory (the calls that
    need them return DTWS_ENOMEM and release what they allocated). */
 void dtws_debug_fail_next_allocs(int count);
+
+/* Test hook for the wide exclusion zone (the paper has no counterpart):
+   capacities of its candidate buffer (windows scored within the threshold,
+   default 2^20) and re-score list (windows within the final threshold,
+   default 8192) from the next query on; a query that fills either reports
+   DTWS_EOVERFLOW from dtws_sync_status (its answer may then be inexact).
+   Synchronises the device.  Errors: DTWS_EINVAL (buf_cap < 1, sel_cap
+   outside [1, 16384]), DTWS_ECUDA. */
+dtws_status dtws_debug_set_xz_capacity(dtws_t h, int32_t buf_cap, int32_t sel_cap);
 
 /* ---- building blocks, exposed for element-wise checking and reuse ---- */
 

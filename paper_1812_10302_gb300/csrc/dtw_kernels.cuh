@@ -399,7 +399,9 @@ __global__ void __launch_bounds__(256, dtw_min_blocks(K)) k_dtw(QueryBufs b, Que
                     list_insert(st->res_keys, a.list_cap, key);
                 }
             } else if (d <= thr) {
-                list_insert(st->res_keys, a.list_cap, make_key(key_quantize(d, a.qgrid), idx));
+                const unsigned long long key = make_key(key_quantize(d, a.qgrid), idx);
+                list_insert(st->res_keys, a.list_cap, key);
+                if (a.xz_z > 0) xz_offer(b, a, key, true);
             }
         }
         __syncwarp(gmask);
@@ -764,7 +766,9 @@ __global__ void __launch_bounds__(256, 2) k_dtw_mw(QueryBufs b, QueryArgs a, con
                     list_insert(st->res_keys, a.list_cap, key);
                 }
             } else if (d <= thr) {
-                list_insert(st->res_keys, a.list_cap, make_key(key_quantize(d, a.qgrid), idx));
+                const unsigned long long key = make_key(key_quantize(d, a.qgrid), idx);
+                list_insert(st->res_keys, a.list_cap, key);
+                if (a.xz_z > 0) xz_offer(b, a, key, true);
             }
         }
     }

@@ -147,6 +147,15 @@ struct dtws_ctx {
     uint8_t *enc_blob = nullptr;
     int64_t enc_version = 0;  // 0: no encoder installed
     std::vector<LearnEntry> learn;
+    // wide exclusion zone: bucket keys (grown to the largest bucket count
+    // met), the candidate buffer and the re-score list (capacities settable
+    // for tests with dtws_debug_set_xz_capacity)
+    unsigned long long *xz_bkey = nullptr;
+    int64_t xz_bkey_cap = 0;
+    unsigned long long *xz_buf = nullptr;
+    unsigned *xz_sel = nullptr;
+    double *xz_d64 = nullptr;
+    int xz_cap = 1 << 20, xz_sel_cap = 8192;
 };
 
 namespace {
@@ -489,7 +498,40 @@ QueryBufs make_bufs(dtws_t h, const StatsEntry *se, const EnvEntry *ee) {
     b.status = h->status;
     b.wait_ns = h->opt.wait_limit_ns;
     b.num_sms = h->num_sms;
+    b.xz_bkey = h->xz_bkey;
+    b.xz_buf = h->xz_buf;
+    b.xz_sel = h->xz_sel;
+    b.xz_d64 = h->xz_d64;
+    b.xz_cap = h->xz_cap;
+    b.xz_sel_cap = h->xz_sel_cap;
     return b;
+}
+
+// Buckets of a wide exclusion zone z over N windows: offsets cut into runs
+// of 2z+1.
+int64_t xz_buckets(int64_t N, int z) { return (N - 1) / (2 * (int64_t)z + 1) + 1; }
+
+void drop_graph(dtws_t h);
+
+// The wide exclusion zone's device buffers for `buckets` buckets.
+dtws_status ensure_xz(dtws_t h, int64_t buckets) {
+    if (!h->xz_buf) {
+        CK(dalloc(&h->xz_buf, (size_t)h->xz_cap));
+        CK(dalloc(&h->xz_sel, (size_t)h->xz_sel_cap));
+        CK(dalloc(&h->xz_d64, (size_t)h->xz_sel_cap));
+    }
+    if (h->xz_bkey_cap < buckets) {
+        if (h->xz_bkey) {
+            CK(cudaDeviceSynchronize());
+            drop_graph(h);
+            cudaFree(h->xz_bkey);
+            h->xz_bkey = nullptr;
+            h->xz_bkey_cap = 0;
+        }
+        CK(dalloc(&h->xz_bkey, (size_t)buckets));
+        h->xz_bkey_cap = buckets;
+    }
+    return DTWS_OK;
 }
 
 QueryArgs make_args(dtws_t h, int m, int r, int k, bool raw) {
@@ -587,12 +629,18 @@ dtws_status enqueue_search(dtws_t h, const Exec &e, const QueryArgs &a, const fl
     const QueryBufs &b = e.b;
     cudaStream_t s = e.s;
     const int m = a.m, k = a.k;
-    const int P = h->opt.seed_proposals, R = h->opt.seed_random;
+    // a wide exclusion zone needs k seeds in separate buckets of each parity
+    // for a first threshold: all the proposals the list holds
+    const int P = (a.xz_z > 0 && h->opt.seed_proposals > 0) ? kPropMax : h->opt.seed_proposals;
+    const int R = h->opt.seed_random;
     int64_t launches = 0;
     auto rec = [&](int i) {
         if (e.timing) record(h, i, s);
     };
     CK(launch_query_reset(b, a, s));
+    if (a.xz_z > 0) {  // every bucket empty
+        CK(cudaMemsetAsync(b.xz_bkey, 0xff, (size_t)xz_buckets(a.N, a.xz_z) * 8, s));
+    }
     CK(launch_qprep(Qd, b, a, s));
     rec(0);
     int half = kProxyStride / 2;
@@ -615,7 +663,9 @@ dtws_status enqueue_search(dtws_t h, const Exec &e, const QueryArgs &a, const fl
     }
     CK(launch_seed_gather(b, a, R, P, half, h->opt.rng_seed, s));
     CK(launch_seed_ed(b, a, s));
-    if (k > 1) {  // exact DTW seeds tighten a k-th bound the Euclidean seeds leave loose
+    if (k > 1 && a.xz_z == 0) {  // exact DTW seeds tighten a k-th bound the Euclidean seeds leave loose
+        // (the neighbours of one match, which is all these seeds are, bound
+        // nothing with an exclusion zone)
         CK(launch_seed_expand(b, a, s));
         CK(launch_dtw_seeds(b, a, s));
         launches += 2;
@@ -636,7 +686,8 @@ dtws_status enqueue_search(dtws_t h, const Exec &e, const QueryArgs &a, const fl
     CK(launch_dtw_survivors(b, a, s));
     rec(4);
     if (a.prescore) CK(cudaStreamWaitEvent(s, e.ev_join, 0));
-    CK(launch_finalize(b, a, idx_d, dist_d, s));
+    if (a.xz_z > 0) CK(launch_xz_finalize(b, a, idx_d, dist_d, s));
+    else CK(launch_finalize(b, a, idx_d, dist_d, s));
     rec(5);
     launches += 2 + 2 + 1 + 3 + 1 + 3;  // reset, qprep, gather, ED seeds, scan, order x3, DTW, final x3
     *launches_out = launches;
@@ -645,7 +696,7 @@ dtws_status enqueue_search(dtws_t h, const Exec &e, const QueryArgs &a, const fl
 
 // One query on the handle's own buffers (dtws_query).
 dtws_status run_query(dtws_t h, const float *Qd, int m, int r, int k, int64_t *idx_d, float *dist_d,
-                      cudaStream_t s) {
+                      cudaStream_t s, int xz_z = 0) {
     dtws_status st;
     for (bool &v : h->ev_recorded) v = false;
     record(h, 8, s);
@@ -668,8 +719,10 @@ dtws_status run_query(dtws_t h, const float *Qd, int m, int r, int k, int64_t *i
     bool c3 = false;
     if (h->opt.seed_proposals > 0 && h->opt.ordering == DTWS_ORDER_LEARNED)
         if ((st = get_learn(h, m, se, s, &le, &c3)) != DTWS_OK) return st;
+    if (xz_z > 0 && (st = ensure_xz(h, xz_buckets(h->n - m + 1, xz_z))) != DTWS_OK) return st;
     Exec e{make_bufs(h, se, ee), s, h->side, h->ev_fork, h->ev_join, le, true};
-    const QueryArgs a = make_args(h, m, r, k);
+    QueryArgs a = make_args(h, m, r, k);
+    a.xz_z = xz_z;
     int64_t launches = 0;
     // Repeated queries with the same arguments replay one CUDA graph of the
     // search (the caches above are resolved first, on the caller's stream;
@@ -995,6 +1048,25 @@ const char *dtws_last_error_detail(void) { return g_err; }
 
 void dtws_debug_fail_next_allocs(int count) { g_fail_allocs = count < 0 ? 0 : count; }
 
+dtws_status dtws_debug_set_xz_capacity(dtws_t h, int32_t buf_cap, int32_t sel_cap) {
+    if (!h || buf_cap < 1 || sel_cap < 1 || sel_cap > 16384) {
+        set_err("dtws_debug_set_xz_capacity: need buf_cap >= 1 and 1 <= sel_cap <= 16384");
+        return DTWS_EINVAL;
+    }
+    CK(cudaSetDevice(h->device));
+    CK(cudaDeviceSynchronize());
+    drop_graph(h);
+    void *ptrs[] = {h->xz_buf, h->xz_sel, h->xz_d64};
+    for (void *p : ptrs)
+        if (p) cudaFree(p);
+    h->xz_buf = nullptr;
+    h->xz_sel = nullptr;
+    h->xz_d64 = nullptr;
+    h->xz_cap = buf_cap;
+    h->xz_sel_cap = sel_cap;
+    return DTWS_OK;
+}
+
 dtws_status dtws_destroy(dtws_t h) {
     if (!h) return DTWS_EINVAL;
     cudaSetDevice(h->device);
@@ -1010,7 +1082,7 @@ dtws_status dtws_destroy(dtws_t h) {
     if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
     void *ptrs[] = {h->x, h->pf, h->bf, h->pok, h->pscale, h->envst, h->absmax, h->st, h->status, h->qh32, h->Uq,
                     h->Lq, h->sq, h->sU, h->sL, h->qh64, h->ord, h->cand_lb, h->sort_lb,
-                    h->cand_idx, h->sort_idx, h->stage};
+                    h->cand_idx, h->sort_idx, h->stage, h->xz_bkey, h->xz_buf, h->xz_sel, h->xz_d64};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (h->ev_ok)
@@ -1122,16 +1194,17 @@ dtws_status dtws_query(dtws_t h, const float *Q, int32_t m, int32_t r, int32_t k
     if (!out_idx || !out_dist) { set_err("null output"); return DTWS_EINVAL; }
     // with an exclusion zone z the search finds the K = k(2z+1) best windows
     // (capped at N), among which the greedy answer lies
+    // With an exclusion zone z: when k(2z+1) fits the result list, the search
+    // finds the K = k(2z+1) best windows (capped at N), among which the greedy
+    // answer lies; otherwise the wide form (a threshold from windows more
+    // than 2z apart, a candidate buffer, greedy selection at the end).
     const int z = h->opt.exclusion_zone;
     int K = k;
+    bool wide = false;
     if (z > 0) {
         const int64_t want = (int64_t)k * (2 * (int64_t)z + 1), N = h->n - m + 1;
-        if (want > DTWS_K_MAX) {
-            set_err("exclusion_zone=%d with k=%d needs the %lld best windows (at most %d)", z, k,
-                    (long long)want, DTWS_K_MAX);
-            return DTWS_EINVAL;
-        }
-        K = (int)(want < N ? want : N);
+        if (want > DTWS_K_MAX) wide = true;
+        else K = (int)(want < N ? want : N);
     }
     cudaStream_t s = (cudaStream_t)stream;
     const bool qdev = is_device_ptr(Q), idev = is_device_ptr(out_idx), ddev = is_device_ptr(out_dist);
@@ -1148,7 +1221,9 @@ dtws_status dtws_query(dtws_t h, const float *Q, int32_t m, int32_t r, int32_t k
     }
     int64_t *idx_d = idev ? out_idx : (int64_t *)(sp + round_up(qb, 256));
     float *dist_d = ddev ? out_dist : (float *)(sp + round_up(qb, 256) + round_up(ib, 256));
-    if (z > 0) {
+    if (wide) {
+        if ((st = run_query(h, Qd, m, r, k, idx_d, dist_d, s, z)) != DTWS_OK) return st;
+    } else if (z > 0) {
         char *kp = sp + round_up(qb, 256) + round_up(ib, 256) + round_up(db, 256);
         int64_t *kidx = (int64_t *)kp;
         float *kdist = (float *)(kp + round_up(kib, 256));

@@ -100,6 +100,11 @@ struct QueryState {
     int valid;                             // 0 when the query is non-finite
     int hist[kBins];
     int bin_off[kBins];
+    // wide exclusion zone (QueryArgs::xz_z > 0): per bucket parity, the
+    // sorted keys of the first window found in each bucket of 2z+1 offsets
+    unsigned long long xz_keys[2][kKMax];
+    int xz_count;                          // windows appended to the candidate buffer
+    int xz_nsel;                           // of them within the final threshold
 };
 
 // Scalars of one query, passed by value to every kernel.
@@ -113,6 +118,9 @@ struct QueryArgs {
     int tune_l, tune_k, tune_w;  // survivor DTW shape chosen by the autotuner (0: default)
     int raw;            // 1: unnormalised DTW (the query and the re-scored windows are
                         // taken as they are: mean 0, 1/sigma 1)
+    int xz_z;           // > 0: top-k with this exclusion zone, wide form (the
+                        // threshold from separated windows, a candidate buffer,
+                        // greedy selection at the end); 0: plain top-k
 };
 
 
@@ -172,11 +180,24 @@ __device__ __forceinline__ float list_kth(const unsigned long long *slots, int k
 // Current pruning threshold: bsf*(1+delta)+alpha, bsf = the smallest of the
 // k-th seed DTW, the k-th survivor DTW found so far and the k-th squared
 // Euclidean distance of the seed windows (+inf while fewer than k exist).
+//
+// With a wide exclusion zone z (a.xz_z > 0) those lists bound nothing (a
+// match's neighbours fill them); the bound is the smaller k-th of the two
+// bucket lists instead: buckets of 2z+1 offsets, one window per bucket, so
+// the windows of one parity's list are pairwise more than 2z apart, and the
+// k-th distance of any k windows pairwise more than 2z apart bounds the
+// answer's k-th distance from above (a window the greedy selection takes
+// shuts out at most one of them).
 __device__ __forceinline__ float current_thr(const QueryState *st, const QueryArgs &a) {
-    // each list holds distinct windows, so each k-th value bounds the true
-    // k-th distance from above
-    float b = fminf(fminf(list_kth(st->seed_keys, a.k), list_kth(st->res_keys, a.k)),
-                    list_kth(st->ed_keys, a.k));
+    float b;
+    if (a.xz_z > 0) {
+        b = fminf(list_kth(st->xz_keys[0], a.k), list_kth(st->xz_keys[1], a.k));
+    } else {
+        // each list holds distinct windows, so each k-th value bounds the true
+        // k-th distance from above
+        b = fminf(fminf(list_kth(st->seed_keys, a.k), list_kth(st->res_keys, a.k)),
+                  list_kth(st->ed_keys, a.k));
+    }
     if (!(b < __int_as_float(0x7f800000))) return __int_as_float(0x7f800000);
     return fmaf(b, 1.0f + a.delta, a.alpha);
 }

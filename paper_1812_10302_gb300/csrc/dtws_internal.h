@@ -47,7 +47,32 @@ struct QueryBufs {
     int *status;
     long long wait_ns;
     int num_sms;
+    // wide exclusion zone (QueryArgs::xz_z > 0): one key per bucket of 2z+1
+    // offsets (EMPTY = none yet), the candidate buffer of windows scored
+    // within the threshold, and the re-score list of those within the final
+    // threshold (offsets, extended-precision distances)
+    unsigned long long *xz_bkey;
+    unsigned long long *xz_buf;
+    unsigned *xz_sel;
+    double *xz_d64;
+    int xz_cap, xz_sel_cap;
 };
+
+// Offer a scored window (key: its quantised distance and offset) to the wide
+// exclusion-zone state: the first window of its bucket enters the bucket
+// list of the bucket's parity; with `append` it also joins the candidate
+// buffer (DTWS_EOVERFLOW when full).
+__device__ __forceinline__ void xz_offer(const QueryBufs &b, const QueryArgs &a, unsigned long long key, bool append) {
+    QueryState *st = b.st;
+    const unsigned idx = key_idx(key);
+    const unsigned bucket = idx / (unsigned)(2 * a.xz_z + 1);
+    if (atomicCAS(&b.xz_bkey[bucket], kEmptyKey, key) == kEmptyKey) list_insert(st->xz_keys[bucket & 1u], a.k, key);
+    if (append) {
+        const int i = atomicAdd(&st->xz_count, 1);
+        if (i < b.xz_cap) b.xz_buf[i] = key;
+        else atomicOr(b.status, kStOverflow);
+    }
+}
 
 cudaError_t launch_query_reset(const QueryBufs &b, const QueryArgs &a, cudaStream_t s);
 cudaError_t launch_qprep(const float *Q, const QueryBufs &b, const QueryArgs &a, cudaStream_t s);
@@ -68,6 +93,10 @@ cudaError_t launch_order(const QueryBufs &b, const QueryArgs &a, cudaStream_t s)
 cudaError_t launch_dtw_survivors(const QueryBufs &b, const QueryArgs &a, cudaStream_t s);
 cudaError_t launch_finalize(const QueryBufs &b, const QueryArgs &a, int64_t *out_idx,
                             float *out_dist, cudaStream_t s);
+// wide exclusion zone: the candidates within the final threshold,
+// re-scored, sorted, taken greedily (k results; -1 / +inf where missing)
+cudaError_t launch_xz_finalize(const QueryBufs &b, const QueryArgs &a, int64_t *out_idx, float *out_dist,
+                               cudaStream_t s);
 
 // element-wise building blocks
 cudaError_t launch_dtw_at(const QueryBufs &b, const QueryArgs &a, const int64_t *offsets,

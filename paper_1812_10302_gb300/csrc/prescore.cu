@@ -44,7 +44,9 @@ __global__ void k_prescore(QueryBufs b, QueryArgs a) {
         const float d32 =
             dtw_diag<float, L, K, false>(q32 + pad, c32 + pad, nullptr, m, r, INF, gmask, lane, cells);
         if (lane == 0) {
-            list_insert(st->res_keys, a.list_cap, make_key(key_quantize(d32, a.qgrid), idx));
+            const unsigned long long key = make_key(key_quantize(d32, a.qgrid), idx);
+            list_insert(st->res_keys, a.list_cap, key);
+            if (a.xz_z > 0 && d32 < DINF) xz_offer(b, a, key, true);
             atomicAdd(&st->ctr[kCtrDtwStarted], 1ull);
             atomicAdd(&st->ctr[kCtrCells], (unsigned long long)cells);
         }

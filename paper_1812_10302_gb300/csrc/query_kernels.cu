@@ -48,7 +48,10 @@ __global__ void k_query_reset(QueryState *st) {
     for (int t = threadIdx.x; t < kKMax; t += blockDim.x) st->ed_keys[t] = kEmptyKey;
     for (int t = threadIdx.x; t < kBins; t += blockDim.x) st->hist[t] = 0;
     for (int t = threadIdx.x; t < kCtrN; t += blockDim.x) st->ctr[t] = 0;
+    for (int t = threadIdx.x; t < 2 * kKMax; t += blockDim.x) st->xz_keys[t / kKMax][t % kKMax] = kEmptyKey;
     if (threadIdx.x == 0) {
+        st->xz_count = 0;
+        st->xz_nsel = 0;
         st->n_seeds = 0;
         st->n_cand = 0;
         st->work = 0;
@@ -706,7 +709,9 @@ __global__ void __launch_bounds__(1024) k_seed_gather(QueryBufs b, QueryArgs a, 
     __syncthreads();
     const int ne = distinct_append(b.st->ed_off, kEdMax, cand, n_random + proposals * span, 0, wcnt, &total);
     if (threadIdx.x == 0) {
-        b.st->n_seeds = a.k > 1 ? ns : 0;  // exact seeds only pay off for k > 1
+        // exact seeds only pay off for k > 1, and not with a wide exclusion
+        // zone (no seed pass runs then, so the survivor pass must not skip them)
+        b.st->n_seeds = (a.k > 1 && a.xz_z == 0) ? ns : 0;
         b.st->n_ed = ne;
         b.st->work = 0;
     }
@@ -730,7 +735,13 @@ __global__ void k_seed_ed(QueryBufs b, QueryArgs a) {
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    if (lane == 0) list_insert(st->ed_keys, a.k, make_key(key_quantize(acc, a.qgrid), idx));
+    if (lane == 0) {
+        const unsigned long long key = make_key(key_quantize(acc, a.qgrid), idx);
+        list_insert(st->ed_keys, a.k, key);
+        // the Euclidean distance bounds the window's DTW from above, so it
+        // may stand for the window in a bucket list (never in the buffer)
+        if (a.xz_z > 0) xz_offer(b, a, key, false);
+    }
 }
 
 // k > 1: the k-th best distance needs k good windows.  The windows nearest
@@ -835,7 +846,9 @@ __global__ void __launch_bounds__(256) k_dtw64(QueryBufs b, QueryArgs a, const i
     if (K > 0) fill_pads((dfloat *)gbase, m, lay.pad, dfloat{-1e15f, 0.0f}, lane, L);
     double *ring = lay.ring ? (double *)(gbase + (lay.staged ? lay.span() * 8 : 0)) : nullptr;
     __syncthreads();
-    const int64_t count = offsets ? count_host : (int64_t)st->n_margin;
+    const int64_t count = offsets ? count_host
+                        : a.xz_z > 0 ? (int64_t)min(st->xz_nsel, b.xz_sel_cap)
+                                     : (int64_t)st->n_margin;
     __shared__ double bc[2 * 8 * 32];  // per group: mu, 1/sigma
     // (the margin list's first margin_skip entries were re-scored already)
     while (true) {
@@ -852,7 +865,7 @@ __global__ void __launch_bounds__(256) k_dtw64(QueryBufs b, QueryArgs a, const i
             }
             idx = (unsigned)o;
         } else {
-            idx = st->margin_idx[c];
+            idx = a.xz_z > 0 ? b.xz_sel[c] : st->margin_idx[c];
         }
         const float *xw = b.x + idx;
         double s = 0.0;
@@ -891,6 +904,7 @@ __global__ void __launch_bounds__(256) k_dtw64(QueryBufs b, QueryArgs a, const i
         }
         if (lane == 0) {
             if (offsets) out[c] = d;
+            else if (a.xz_z > 0) b.xz_d64[c] = d;
             else st->margin_d64[c] = d;
         }
         __syncwarp(gmask);
@@ -929,7 +943,9 @@ __global__ void __launch_bounds__(256) k_dtw64_mw(QueryBufs b, QueryArgs a, cons
     if (g < G) fill_pads(cbase, m, pad, dfloat{-1e15f, 0.0f}, t, nthr);
     __syncthreads();
     if (g >= G) return;
-    const int64_t count = offsets ? count_host : (int64_t)st->n_margin;
+    const int64_t count = offsets ? count_host
+                        : a.xz_z > 0 ? (int64_t)min(st->xz_nsel, b.xz_sel_cap)
+                                     : (int64_t)st->n_margin;
     while (true) {
         // (the previous window's last barrier lies between every thread's
         // read of cur[g] and this write)
@@ -944,7 +960,7 @@ __global__ void __launch_bounds__(256) k_dtw64_mw(QueryBufs b, QueryArgs a, cons
             bad = o < 0 || o >= a.N;
             idx = bad ? 0u : (unsigned)o;
         } else {
-            idx = st->margin_idx[c];
+            idx = a.xz_z > 0 ? b.xz_sel[c] : st->margin_idx[c];
         }
         if (bad) {
             if (t == 0) out[c] = __longlong_as_double(0x7ff8000000000000ll);
@@ -978,6 +994,7 @@ __global__ void __launch_bounds__(256) k_dtw64_mw(QueryBufs b, QueryArgs a, cons
         const double d = dtw_diag_df_mw<W, K>(qd, cd, m, r, w, lane, xch[g], bar);
         if (t == 0) {
             if (offsets) out[c] = d;
+            else if (a.xz_z > 0) b.xz_d64[c] = d;
             else st->margin_d64[c] = d;
         }
     }
@@ -1433,6 +1450,123 @@ cudaError_t launch_finalize(const QueryBufs &b, const QueryArgs &a, int64_t *out
     cudaError_t e = dtw64_dispatch(b, a, nullptr, 0, nullptr, kListMax, s);
     if (e != cudaSuccess) return e;
     k_final_sort<<<1, kListMax, 0, s>>>(b, a, out_idx, out_dist);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ wide exclusion zone
+// The end of a search with a wide exclusion zone z.  Every window whose FP32
+// DTW was within the threshold when it was computed is in the candidate
+// buffer; the final threshold (the smaller k-th of the bucket lists, with
+// the margin) bounds the answer's k-th distance, so the windows of the
+// answer, and every window that could shut one of them out, are among the
+// buffer's windows within it.  Those are re-scored in extended precision,
+// ordered by (re-scored distance, offset) and taken greedily, skipping any
+// window within z samples of one already taken -- the definition of the
+// answer, applied to a superset of its windows.
+__global__ void __launch_bounds__(1024) k_xz_compact(QueryBufs b, QueryArgs a) {
+    QueryState *st = b.st;
+    __shared__ int cnt;
+    if (threadIdx.x == 0) {
+        cnt = 0;
+        st->work = 0;
+    }
+    __syncthreads();
+    if (!st->valid) {
+        if (threadIdx.x == 0) st->xz_nsel = 0;
+        return;
+    }
+    const float thr = current_thr(st, a);
+    const int n = min(st->xz_count, b.xz_cap);
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const unsigned long long key = b.xz_buf[i];
+        if (key_dist(key) <= thr) {
+            const int j = atomicAdd(&cnt, 1);
+            if (j < b.xz_sel_cap) b.xz_sel[j] = key_idx(key);
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        st->xz_nsel = cnt;
+        if (cnt > b.xz_sel_cap) atomicOr(b.status, kStOverflow);  // answers may be inexact
+        st->ctr[kCtrRescored] = (unsigned long long)min(cnt, b.xz_sel_cap);
+    }
+}
+
+// Sort the re-scored candidates by (distance, offset) in shared memory
+// (bitonic, padded to a power of two), then one warp takes them greedily.
+__global__ void __launch_bounds__(1024) k_xz_select(QueryBufs b, QueryArgs a, int64_t *out_idx, float *out_dist) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    __shared__ unsigned taken[kKMax];
+    __shared__ float takend[kKMax];
+    QueryState *st = b.st;
+    const int n = st->valid ? min(st->xz_nsel, b.xz_sel_cap) : 0;
+    int P = 1;
+    while (P < n) P <<= 1;
+    int Pmax = 1;
+    while (Pmax < b.xz_sel_cap) Pmax <<= 1;
+    double *sd = (double *)smraw;
+    unsigned *so = (unsigned *)(sd + Pmax);
+    for (int j = threadIdx.x; j < P; j += blockDim.x) {
+        sd[j] = j < n ? b.xz_d64[j] : __longlong_as_double(0x7ff0000000000000ll);
+        so[j] = j < n ? b.xz_sel[j] : 0xffffffffu;
+    }
+    __syncthreads();
+    for (int size = 2; size <= P; size <<= 1) {
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            for (int t = threadIdx.x; t < P / 2; t += blockDim.x) {
+                const int lo = 2 * t - (t & (stride - 1)), hi = lo + stride;
+                const bool asc = (lo & size) == 0;
+                const double d0 = sd[lo], d1 = sd[hi];
+                const unsigned o0 = so[lo], o1 = so[hi];
+                const bool gt = d0 > d1 || (d0 == d1 && o0 > o1);
+                if (gt == asc) {
+                    sd[lo] = d1;
+                    sd[hi] = d0;
+                    so[lo] = o1;
+                    so[hi] = o0;
+                }
+            }
+            __syncthreads();
+        }
+    }
+    if (threadIdx.x >= 32) return;
+    const int lane = threadIdx.x;
+    int nt = 0;
+    for (int j = 0; j < n && nt < a.k; ++j) {
+        const unsigned o = so[j];
+        if (j > 0 && so[j - 1] == o) continue;  // the same window twice
+        bool near = false;
+        for (int t = lane; t < nt; t += 32) {
+            const long long dd = (long long)taken[t] - (long long)o;
+            near |= (dd < 0 ? -dd : dd) <= a.xz_z;
+        }
+        if (__any_sync(0xffffffffu, near)) continue;
+        if (lane == 0) {
+            taken[nt] = o;
+            takend[nt] = (float)sd[j];
+        }
+        ++nt;
+        __syncwarp();
+    }
+    for (int t = lane; t < a.k; t += 32) {
+        out_idx[t] = t < nt ? (int64_t)taken[t] : -1;
+        out_dist[t] = t < nt ? takend[t] : DINF;
+    }
+}
+
+cudaError_t launch_xz_finalize(const QueryBufs &b, const QueryArgs &a, int64_t *out_idx, float *out_dist,
+                               cudaStream_t s) {
+    k_xz_compact<<<1, 1024, 0, s>>>(b, a);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    e = dtw64_dispatch(b, a, nullptr, 0, nullptr, b.xz_sel_cap, s);
+    if (e != cudaSuccess) return e;
+    int Pmax = 1;
+    while (Pmax < b.xz_sel_cap) Pmax <<= 1;
+    const size_t smem = (size_t)Pmax * 12;
+    e = cudaFuncSetAttribute(k_xz_select, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_xz_select<<<1, 1024, smem, s>>>(b, a, out_idx, out_dist);
     return cudaGetLastError();
 }
 

@@ -104,6 +104,7 @@ _SIGS = {
     "dtws_strerror": (ctypes.c_char_p, [_S]),
     "dtws_last_error_detail": (ctypes.c_char_p, []),
     "dtws_debug_fail_next_allocs": (None, [ctypes.c_int]),
+    "dtws_debug_set_xz_capacity": (_S, [_P, _I32, _I32]),
     "dtws_window_stats": (_S, [_P, _I32, _P, _P, _P, _P]),
     "dtws_series_envelope": (_S, [_P, _I32, _P, _P, _P]),
     "dtws_dtw_at": (_S, [_P, _P, _I32, _I32, _P, _I64, _P, _P]),
@@ -388,6 +389,11 @@ class Index:
         _check(self._lib.dtws_dtw_at_f64(self.h, q.ptr, q.size, r, o.ptr, o.size, out.ctypes.data,
                                          _stream_ptr(stream)), "dtws_dtw_at_f64")
         return out
+
+    def debug_set_xz_capacity(self, buf_cap: int, sel_cap: int):
+        """Test hook: capacities of the wide exclusion zone's candidate buffer
+        and re-score list (see dtws.h)."""
+        _check(self._lib.dtws_debug_set_xz_capacity(self.h, buf_cap, sel_cap), "dtws_debug_set_xz_capacity")
 
     def debug_wait_selftest(self, wait_ns: int, stream=None):
         _check(self._lib.dtws_debug_wait_selftest(self.h, wait_ns, _stream_ptr(stream)), "dtws_debug_wait_selftest")

@@ -73,11 +73,103 @@ def test_wide_band_queries_match_oracle(m, r, k):
     _close(dist, od, m)
 
 
+def _exclusion_want(x, q, r, k, z):
+    m = q.size
+    d = oracle.dtw_at(x, q, r, np.arange(x.size - m + 1))
+    wi, wd = oracle.exclusion_topk(d, k, z)
+    out_i = np.full(k, -1, np.int64)
+    out_d = np.full(k, np.inf)
+    out_i[:wi.size] = wi
+    out_d[:wd.size] = wd
+    return out_i, out_d
+
+
+@pytest.mark.parametrize("m,r,k,z", [(128, 12, 3, 64), (128, 12, 10, 64), (96, 9, 5, 48), (64, 6, 10, 20),
+                                     (200, 40, 4, 100)])
+def test_wide_exclusion_zone_matches_oracle(m, r, k, z):
+    """Exclusion zones wider than the result list covers (k(2z+1) > 64, e.g.
+    z = m/2): the bucket-list threshold, the candidate buffer and the final
+    greedy selection against the oracle's greedy selection over the FP64 DTW
+    of every window; a replayed graph gives the same answer."""
+    x = synth.random_walk(30_000, 500 + m + z)
+    q, _ = synth.noisy_copy(x, m, 501 + m, 502 + k, noise=0.3)
+    want_i, want_d = _exclusion_want(x, q, r, k, z)
+    with dtws.Index(x) as ix:
+        ix.set_options(exclusion_zone=z)
+        idx, dist = ix.query(q, r, k)
+        assert ix.sync_status() == dtws.DTWS_OK
+        idx2, dist2 = ix.query(q, r, k)
+        assert ix.sync_status() == dtws.DTWS_OK
+    np.testing.assert_array_equal(idx, want_i)
+    _close(dist, want_d, m)
+    np.testing.assert_array_equal(idx2, idx)
+    np.testing.assert_array_equal(dist2, dist)
+    assert np.all(np.abs(np.diff(np.sort(idx))) > z)
+
+
+def test_wide_exclusion_zone_with_decoys_inside_the_zone():
+    """An exact copy of the query, two close copies z samples on either side
+    of it (inside its zone, so the answer may not take them) and a noisier
+    copy far away: the answer is the exact copy and the far one.  The two
+    decoys are 2z apart, so a threshold from windows kept only z apart would
+    prune the far copy."""
+    m, r, z, k = 64, 6, 80, 2
+    x = synth.random_walk(40_000, 610).astype(np.float64)
+    rng = np.random.default_rng(611)
+    P, F = 20_000, 33_000
+    base = x[P:P + m].copy()
+    for o, noise in ((P - z, 0.02), (P + z, 0.02), (F, 0.4)):
+        x[o:o + m] = base + rng.normal(0, noise, m) + (x[o] - base[0])
+    x = x.astype(np.float32)
+    q = x[P:P + m].copy()
+    want_i, want_d = _exclusion_want(x, q, r, k, z)
+    assert want_i.tolist() == [P, F]
+    with dtws.Index(x) as ix:
+        ix.set_options(exclusion_zone=z)
+        idx, dist = ix.query(q, r, k)
+        assert ix.sync_status() == dtws.DTWS_OK
+    np.testing.assert_array_equal(idx, want_i)
+    _close(dist, want_d, m)
+
+
+def test_wide_exclusion_zone_short_series_and_overflow():
+    """A series too short for k windows more than z apart: the missing ones
+    come back as -1 / +inf.  Buffers smaller than the candidates: the query
+    reports DTWS_EOVERFLOW, and with the default capacities again it answers
+    exactly."""
+    x = synth.random_walk(400, 620)
+    q, _ = synth.noisy_copy(x, 64, 621, 622, noise=0.2)
+    want_i, want_d = _exclusion_want(x, q, 6, 4, 120)
+    assert want_i[-1] == -1
+    y = synth.random_walk(30_000, 623)
+    qy, _ = synth.noisy_copy(y, 128, 624, 625, noise=0.3)
+    want_yi, want_yd = _exclusion_want(y, qy, 12, 5, 64)
+    with dtws.Index(x) as ix:
+        ix.set_options(exclusion_zone=120)
+        idx, dist = ix.query(q, 6, 4)
+        assert ix.sync_status() == dtws.DTWS_OK
+    np.testing.assert_array_equal(idx, want_i)
+    assert np.all(np.isinf(dist[want_i < 0]))
+    _close(dist[want_i >= 0], want_d[want_i >= 0], 64)
+    with dtws.Index(y) as ix:
+        ix.set_options(exclusion_zone=64)
+        ix.debug_set_xz_capacity(4, 4)
+        ix.query(qy, 12, 5)
+        assert ix.sync_status() == dtws.DTWS_EOVERFLOW
+        ix.debug_set_xz_capacity(1 << 20, 8192)
+        idx, dist = ix.query(qy, 12, 5)
+        assert ix.sync_status() == dtws.DTWS_OK
+        with pytest.raises(dtws.DtwsError):
+            ix.debug_set_xz_capacity(1, 20000)
+    np.testing.assert_array_equal(idx, want_yi)
+    _close(dist, want_yd, 128)
+
+
 @pytest.mark.parametrize("m,r,k,z", [(64, 6, 3, 10), (128, 12, 4, 7), (100, 20, 2, 15)])
 def test_exclusion_zone_matches_oracle(m, r, k, z):
-    """Top-k with an exclusion zone: the oracle's greedy selection over the
-    FP64 DTW of every window; k(2z+1) beyond the result list is refused, and
-    so is a batch."""
+    """Top-k with an exclusion zone whose k(2z+1) best windows fit the result
+    list: the oracle's greedy selection over the FP64 DTW of every window; a
+    batch is refused."""
     x = synth.random_walk(20_000, 90 + m)
     q, _ = synth.noisy_copy(x, m, 91 + m, 92 + m, noise=0.3)
     with dtws.Index(x) as ix:
@@ -85,8 +177,6 @@ def test_exclusion_zone_matches_oracle(m, r, k, z):
         idx, dist = ix.query(q, r, k)
         assert ix.sync_status() == dtws.DTWS_OK
         idx2, dist2 = ix.query(q, r, k)  # (replayed graph)
-        with pytest.raises(dtws.DtwsError):
-            ix.query(q, r, k + 1 if (k + 1) * (2 * z + 1) > 64 else 64)
         with pytest.raises(dtws.DtwsError):
             ix.query_batch([q, q], [r, r], k=k)
     np.testing.assert_array_equal(idx2, idx)

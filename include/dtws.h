@@ -259,6 +259,15 @@ void dtws_debug_fail_next_allocs(int count);
    outside [1, 16384]), DTWS_ECUDA. */
 dtws_status dtws_debug_set_xz_capacity(dtws_t h, int32_t buf_cap, int32_t sel_cap);
 
+/* Test hook for dtws_query_batch (the paper has no counterpart): capacity of
+   the survivor pool of the batch's persistent DTW stage, in survivors, from
+   the next batch on; 0 = no pool (every query runs its survivor pass on its
+   lane), -1 = the default (the batch's window count, at most 2^27).  A query
+   whose survivors do not fit runs its survivor pass on its lane; the answers
+   are the same either way.  Synchronises the device.  Errors: DTWS_EINVAL
+   (cap < -1), DTWS_ECUDA. */
+dtws_status dtws_debug_set_pool_capacity(dtws_t h, int64_t cap);
+
 /* ---- building blocks, exposed for element-wise checking and reuse ---- */
 
 /*
@@ -308,6 +317,17 @@ dtws_status dtws_lower_bounds_at(dtws_t h, const float *Q, int32_t m, int32_t r,
    kernel of the library spins forever; this entry point exercises that path
    without a fault or a hang.  Errors: DTWS_EINVAL, DTWS_ECUDA. */
 dtws_status dtws_debug_wait_selftest(dtws_t h, int64_t wait_ns, void *stream);
+
+/* Failure-detection self-test of the one lock in the library (the paper has
+   no counterpart): the wide exclusion zone's bucket lists are rewritten under
+   a spin lock whose wait is bounded by options.wait_limit_ns.  Here one
+   device thread holds the lock while another offers a window to the same
+   list; after wait_ns (1 .. 1e10) the offer gives up, drops the window (which
+   only loosens the pruning bound) and records a timeout that the next
+   dtws_sync_status(h, stream) returns as DTWS_ETIMEOUT; then the lock is
+   released.  Overwrites the handle's query state (run it between queries).
+   Errors: DTWS_EINVAL, DTWS_ENOMEM, DTWS_ECUDA. */
+dtws_status dtws_debug_lock_selftest(dtws_t h, int64_t wait_ns, void *stream);
 
 /* ---- autotuner (the paper has no counterpart) ----
  *

@@ -95,12 +95,19 @@ __host__ __device__ constexpr int dtw_min_blocks(int K) {
     return (K >= 1 && K <= 2) ? 4 : (K >= 1 && K <= 4) ? 3 : (K >= 16) ? 1 : 2;
 }
 
+// The body of k_dtw for one query (the CTA's part of its candidate stream);
+// the persistent batch stage (k_dtw_pool) runs it for one query after
+// another.  In survivor mode with b.surv_mh set, the survivors' window
+// statistics come from per-survivor arrays (indexed like sort_idx) instead
+// of the per-window statistics; without it, a query whose survivors were
+// handed to the persistent stage (st->deferred) is left to that stage.
 template <int L, int K, int MODE>
-__global__ void __launch_bounds__(256, dtw_min_blocks(K)) k_dtw(QueryBufs b, QueryArgs a, const int64_t *offsets,
-                                             int64_t count_host, float *out, int staged) {
+__device__ __forceinline__ void dtw_body(const QueryBufs &b, const QueryArgs &a, const int64_t *offsets,
+                                         int64_t count_host, float *out, int staged) {
     extern __shared__ __align__(16) unsigned char smraw[];
     QueryState *st = b.st;
     if (!st->valid) return;
+    if (MODE == kModeSurv && b.surv_mh == nullptr && st->deferred) return;
     const int m = a.m, r = a.r;
     const bool has_env = b.U != nullptr || b.stmax != nullptr;
     const DtwSmem<float> lay = dtw_smem<float, L, K>(m, r, staged != 0, MODE == kModeSurv && has_env);
@@ -190,7 +197,11 @@ __global__ void __launch_bounds__(256, dtw_min_blocks(K)) k_dtw(QueryBufs b, Que
                     pass = !seen;
                 }
                 float pmh = 0.0f, pis = 0.0f, pls = 0.0f;
-                if (pass) {
+                if (pass && b.surv_mh) {
+                    pmh = b.surv_mh[cc];
+                    pis = b.surv_is[cc];
+                    pls = b.surv_ls[cc];
+                } else if (pass) {
                     pmh = b.mu_hi[id];
                     pis = b.inv_sigma[id];
                     pls = b.mu_lo[id] * pis;
@@ -303,6 +314,10 @@ __global__ void __launch_bounds__(256, dtw_min_blocks(K)) k_dtw(QueryBufs b, Que
             mh = __shfl_sync(gmask, my_mh, psrc, L);
             is = __shfl_sync(gmask, my_is, psrc, L);
             ls = __shfl_sync(gmask, my_ls, psrc, L);
+        } else if (MODE == kModeSurv && b.surv_mh) {
+            mh = b.surv_mh[c];
+            is = b.surv_is[c];
+            ls = b.surv_ls[c];
         } else {
             mh = b.mu_hi[idx];
             is = b.inv_sigma[idx];
@@ -424,6 +439,48 @@ __global__ void __launch_bounds__(256, dtw_min_blocks(K)) k_dtw(QueryBufs b, Que
             atomicAdd(&st->ctr[kCtrDtwAbandoned], (unsigned long long)na);
             if (np) atomicAdd(&st->ctr[kCtrKeoghS], (unsigned long long)np);
         }
+    }
+}
+
+template <int L, int K, int MODE>
+__global__ void __launch_bounds__(256, dtw_min_blocks(K)) k_dtw(QueryBufs b, QueryArgs a, const int64_t *offsets,
+                                                              int64_t count_host, float *out, int staged) {
+    dtw_body<L, K, MODE>(b, a, offsets, count_host, out, staged);
+}
+
+// The persistent survivor-DTW stage of a batch (one launch per kernel shape
+// in the batch): every CTA walks the list of the shape's deferred queries in
+// order and runs the survivor pass of each with the others, pulling that
+// query's survivors from its cursor; a CTA whose share of one query is done
+// moves on to the next at once, so no launch boundary or tail separates the
+// queries.  base: the series, envelopes and status of the handle, with
+// sort_idx / sort_lb / surv_* pointing at the survivor pool (each query's
+// survivors at st->pool_off).
+template <int L, int K>
+__global__ void __launch_bounds__(256, dtw_min_blocks(K)) k_dtw_pool(QueryBufs base, const PoolQuery *pq,
+                                                                   const int *list, int nlist, int staged) {
+    for (int j = 0; j < nlist; ++j) {
+        const PoolQuery &p = pq[list[j]];
+        QueryState *st = p.st;
+        if (!st->deferred) continue;
+        const long long off = st->pool_off;
+        QueryBufs b = base;
+        b.st = st;
+        b.qh32 = p.qh32;
+        b.ord = p.ord;
+        b.sq = p.sq;
+        b.sU = p.sU;
+        b.sL = p.sL;
+        b.U = p.U;
+        b.L = p.L;
+        b.sort_idx = base.sort_idx + off;
+        b.sort_lb = base.sort_lb + off;
+        b.surv_mh = base.surv_mh + off;
+        b.surv_is = base.surv_is + off;
+        b.surv_ls = base.surv_ls + off;
+        const QueryArgs a = p.a;
+        dtw_body<L, K, kModeSurv>(b, a, nullptr, 0, nullptr, staged);
+        __syncthreads();  // shared copies of this query are read before the next query's are written
     }
 }
 

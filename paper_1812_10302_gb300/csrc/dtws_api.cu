@@ -147,11 +147,21 @@ struct dtws_ctx {
     uint8_t *enc_blob = nullptr;
     int64_t enc_version = 0;  // 0: no encoder installed
     std::vector<LearnEntry> learn;
-    // wide exclusion zone: bucket keys (grown to the largest bucket count
-    // met), the candidate buffer and the re-score list (capacities settable
-    // for tests with dtws_debug_set_xz_capacity)
-    unsigned long long *xz_bkey = nullptr;
-    int64_t xz_bkey_cap = 0;
+    // batch: per-query states and query buffers, the survivor pool of the
+    // persistent stage, its query table and shape lists
+    QueryState *bq_st = nullptr;
+    int bq_cap = 0;
+    float *bq_f = nullptr;           // qh32, Uq, Lq, sq, sU, sL: 6 runs of bq_fcap
+    double *bq_d = nullptr;          // qh64
+    unsigned short *bq_o = nullptr;  // ord
+    int64_t bq_fcap = 0;
+    SurvPool pool{};
+    long long pool_limit = -1;  // test hook: survivor pool capacity (-1: sized for the batch)
+    PoolQuery *pq_dev = nullptr;
+    int *plist_dev = nullptr;
+    int pq_cap = 0;
+    // wide exclusion zone: the candidate buffer and the re-score list
+    // (capacities settable for tests with dtws_debug_set_xz_capacity)
     unsigned long long *xz_buf = nullptr;
     unsigned *xz_sel = nullptr;
     double *xz_d64 = nullptr;
@@ -498,7 +508,6 @@ QueryBufs make_bufs(dtws_t h, const StatsEntry *se, const EnvEntry *ee) {
     b.status = h->status;
     b.wait_ns = h->opt.wait_limit_ns;
     b.num_sms = h->num_sms;
-    b.xz_bkey = h->xz_bkey;
     b.xz_buf = h->xz_buf;
     b.xz_sel = h->xz_sel;
     b.xz_d64 = h->xz_d64;
@@ -507,29 +516,12 @@ QueryBufs make_bufs(dtws_t h, const StatsEntry *se, const EnvEntry *ee) {
     return b;
 }
 
-// Buckets of a wide exclusion zone z over N windows: offsets cut into runs
-// of 2z+1.
-int64_t xz_buckets(int64_t N, int z) { return (N - 1) / (2 * (int64_t)z + 1) + 1; }
-
-void drop_graph(dtws_t h);
-
-// The wide exclusion zone's device buffers for `buckets` buckets.
-dtws_status ensure_xz(dtws_t h, int64_t buckets) {
+// The wide exclusion zone's device buffers.
+dtws_status ensure_xz(dtws_t h) {
     if (!h->xz_buf) {
         CK(dalloc(&h->xz_buf, (size_t)h->xz_cap));
         CK(dalloc(&h->xz_sel, (size_t)h->xz_sel_cap));
         CK(dalloc(&h->xz_d64, (size_t)h->xz_sel_cap));
-    }
-    if (h->xz_bkey_cap < buckets) {
-        if (h->xz_bkey) {
-            CK(cudaDeviceSynchronize());
-            drop_graph(h);
-            cudaFree(h->xz_bkey);
-            h->xz_bkey = nullptr;
-            h->xz_bkey_cap = 0;
-        }
-        CK(dalloc(&h->xz_bkey, (size_t)buckets));
-        h->xz_bkey_cap = buckets;
     }
     return DTWS_OK;
 }
@@ -620,6 +612,10 @@ struct Exec {
     cudaEvent_t ev_fork, ev_join;
     const LearnEntry *le;  // learned ordering: the embeddings for m (or null)
     bool timing;           // record the handle's phase events
+    // batch stages: 0 the whole query; 1 up to the survivor pass (its
+    // survivors handed to the pool when `pool` is set); 2 the final stage
+    int stage = 0;
+    const SurvPool *pool = nullptr;
 };
 
 // Enqueue the kernels of one query (Sec. 2.2's cascade, re-planned for the
@@ -629,6 +625,11 @@ dtws_status enqueue_search(dtws_t h, const Exec &e, const QueryArgs &a, const fl
     const QueryBufs &b = e.b;
     cudaStream_t s = e.s;
     const int m = a.m, k = a.k;
+    if (e.stage == 2) {  // the final stage of a batch query (after the persistent stage)
+        CK(launch_finalize(b, a, idx_d, dist_d, s));
+        *launches_out = 3;
+        return DTWS_OK;
+    }
     // a wide exclusion zone needs k seeds in separate buckets of each parity
     // for a first threshold: all the proposals the list holds
     const int P = (a.xz_z > 0 && h->opt.seed_proposals > 0) ? kPropMax : h->opt.seed_proposals;
@@ -638,9 +639,6 @@ dtws_status enqueue_search(dtws_t h, const Exec &e, const QueryArgs &a, const fl
         if (e.timing) record(h, i, s);
     };
     CK(launch_query_reset(b, a, s));
-    if (a.xz_z > 0) {  // every bucket empty
-        CK(cudaMemsetAsync(b.xz_bkey, 0xff, (size_t)xz_buckets(a.N, a.xz_z) * 8, s));
-    }
     CK(launch_qprep(Qd, b, a, s));
     rec(0);
     int half = kProxyStride / 2;
@@ -683,9 +681,18 @@ dtws_status enqueue_search(dtws_t h, const Exec &e, const QueryArgs &a, const fl
     rec(2);
     CK(launch_order(b, a, s));
     rec(3);
+    if (e.pool) {  // batch: the survivors go to the persistent stage (unless the pool is full)
+        CK(launch_defer(b, *e.pool, s));
+        launches += 2;
+    }
     CK(launch_dtw_survivors(b, a, s));
     rec(4);
     if (a.prescore) CK(cudaStreamWaitEvent(s, e.ev_join, 0));
+    if (e.stage == 1) {
+        launches += 2 + 2 + 1 + 3 + 1;  // reset, qprep, gather, ED seeds, scan, order x3, DTW
+        *launches_out = launches;
+        return DTWS_OK;
+    }
     if (a.xz_z > 0) CK(launch_xz_finalize(b, a, idx_d, dist_d, s));
     else CK(launch_finalize(b, a, idx_d, dist_d, s));
     rec(5);
@@ -719,7 +726,7 @@ dtws_status run_query(dtws_t h, const float *Qd, int m, int r, int k, int64_t *i
     bool c3 = false;
     if (h->opt.seed_proposals > 0 && h->opt.ordering == DTWS_ORDER_LEARNED)
         if ((st = get_learn(h, m, se, s, &le, &c3)) != DTWS_OK) return st;
-    if (xz_z > 0 && (st = ensure_xz(h, xz_buckets(h->n - m + 1, xz_z))) != DTWS_OK) return st;
+    if (xz_z > 0 && (st = ensure_xz(h)) != DTWS_OK) return st;
     Exec e{make_bufs(h, se, ee), s, h->side, h->ev_fork, h->ev_join, le, true};
     QueryArgs a = make_args(h, m, r, k);
     a.xz_z = xz_z;
@@ -889,20 +896,107 @@ QueryBufs lane_bufs(dtws_t h, const Lane &l, const EnvEntry *ee) {
     return b;
 }
 
+// Per-query device state of a batch of nq queries with sum_m samples in all,
+// and the survivor pool of the persistent stage (pool_cap survivors).
+dtws_status ensure_batch(dtws_t h, int nq, int64_t sum_m, long long pool_cap) {
+    if (h->bq_cap < nq) {
+        if (h->bq_st) {
+            CK(cudaDeviceSynchronize());
+            drop_graph(h);
+            cudaFree(h->bq_st);
+            cudaFree(h->pq_dev);
+            cudaFree(h->plist_dev);
+            h->bq_st = nullptr;
+            h->pq_dev = nullptr;
+            h->plist_dev = nullptr;
+            h->bq_cap = h->pq_cap = 0;
+        }
+        CK(dalloc(&h->bq_st, (size_t)nq));
+        CK(dalloc(&h->pq_dev, (size_t)nq));
+        CK(dalloc(&h->plist_dev, (size_t)nq));
+        h->bq_cap = h->pq_cap = nq;
+    }
+    if (h->bq_fcap < sum_m) {
+        if (h->bq_f) {
+            CK(cudaDeviceSynchronize());
+            drop_graph(h);
+            cudaFree(h->bq_f);
+            cudaFree(h->bq_d);
+            cudaFree(h->bq_o);
+            h->bq_f = nullptr;
+            h->bq_d = nullptr;
+            h->bq_o = nullptr;
+            h->bq_fcap = 0;
+        }
+        CK(dalloc(&h->bq_f, (size_t)sum_m * 6));
+        CK(dalloc(&h->bq_d, (size_t)sum_m));
+        CK(dalloc(&h->bq_o, (size_t)sum_m));
+        h->bq_fcap = sum_m;
+    }
+    if (h->pool.cap != pool_cap && (h->pool.cap < pool_cap || h->pool_limit >= 0)) {
+        if (h->pool.idx || h->pool.cap) {
+            CK(cudaDeviceSynchronize());
+            drop_graph(h);
+            void *ptrs[] = {h->pool.idx, h->pool.lb, h->pool.mh, h->pool.is, h->pool.ls, h->pool.cursor};
+            for (void *p : ptrs) cudaFree(p);
+            h->pool = SurvPool{};
+        }
+        if (pool_cap <= 0) return DTWS_OK;  // no pool: every query keeps its survivors
+        SurvPool p{};
+        cudaError_t e = cudaSuccess;
+        auto al = [&](cudaError_t r) {
+            if (e == cudaSuccess) e = r;
+        };
+        al(dalloc(&p.idx, (size_t)pool_cap));
+        al(dalloc(&p.lb, (size_t)pool_cap));
+        al(dalloc(&p.mh, (size_t)pool_cap));
+        al(dalloc(&p.is, (size_t)pool_cap));
+        al(dalloc(&p.ls, (size_t)pool_cap));
+        al(dalloc(&p.cursor, 1));
+        if (e != cudaSuccess) {
+            void *ptrs[] = {p.idx, p.lb, p.mh, p.is, p.ls, p.cursor};
+            for (void *q : ptrs)
+                if (q) cudaFree(q);
+            cudaGetLastError();
+            return DTWS_OK;  // no pool: every query keeps its survivors (h->pool.cap stays 0)
+        }
+        p.cap = pool_cap;
+        h->pool = p;
+    }
+    return DTWS_OK;
+}
+
 // Many queries (dtws_query_batch): queries sorted by (m, r) and dealt
 // round-robin to the lanes; each lane computes the window statistics of a
 // new m into its slot, in stream order, and uses the exact envelope of r
-// when one is cached, else the block envelope.  Unless the learned ordering
-// is on, the whole batch is captured once into a CUDA graph, kept, and
-// replayed by later calls with the same arguments.
+// when one is cached, else the block envelope.  Three stages:
+//   1. per query, on its lane: query preparation, seeding, the lower-bound
+//      scan and the survivor ordering, then the survivors and their window
+//      statistics go to the batch's survivor pool (a query whose survivors do
+//      not fit, or whose band takes another kernel, runs its survivor pass
+//      here instead);
+//   2. one persistent launch per kernel shape runs the survivor DTW of all the
+//      batch's queries of that shape (k_dtw_pool);
+//   3. per query, on its lane: the final stage.
+// Each query has its own device state.  Unless the learned ordering is on,
+// the whole batch is captured once into a CUDA graph, kept, and replayed by
+// later calls with the same arguments.
 dtws_status run_batch(dtws_t h, const float *Qd, const int64_t *q_off, const int32_t *m_arr, const int32_t *r_arr,
                       int32_t nq, int32_t k, int64_t *idx_d, float *dist_d, cudaStream_t s) {
     dtws_status st;
     const bool learned = h->opt.seed_proposals > 0 && h->opt.ordering == DTWS_ORDER_LEARNED;
     const int nl = std::max(1, std::min<int>(h->opt.batch_lanes, nq));
     int m_min = m_arr[0];
-    for (int q = 1; q < nq; ++q) m_min = std::min<int>(m_min, m_arr[q]);
+    int64_t sum_m = 0, sum_N = 0;
+    for (int q = 0; q < nq; ++q) {
+        m_min = std::min<int>(m_min, m_arr[q]);
+        sum_m += m_arr[q];
+        sum_N += h->n - m_arr[q] + 1;
+    }
     if ((st = ensure_lanes(h, nl, m_min)) != DTWS_OK) return st;
+    long long pool_want = std::min<long long>(1ll << 27, std::max<long long>(1, sum_N));
+    if (h->pool_limit >= 0) pool_want = h->pool_limit;
+    if ((st = ensure_batch(h, nq, sum_m, pool_want)) != DTWS_OK) return st;
     const int L = std::min<int>(nl, (int)h->lanes.size());
     std::vector<int> order(nq);
     for (int q = 0; q < nq; ++q) order[q] = q;
@@ -921,11 +1015,83 @@ dtws_status run_batch(dtws_t h, const float *Qd, const int64_t *q_off, const int
             sig.push_back(((int64_t)m_arr[q] << 32) | (uint32_t)r_arr[q]);
         }
         for (auto &en : h->env) sig.push_back(((int64_t)en.r << 32) | (int64_t)(intptr_t)en.U);
+        sig.push_back((int64_t)(intptr_t)h->pool.idx);
+        sig.push_back(h->pool.cap);
         if (h->graph_exec && sig == h->graph_sig) {
             CK(cudaGraphLaunch(h->graph_exec, s));
             h->last_stream = s;
             return DTWS_OK;
         }
+    }
+    // per query: its buffers, arguments, lane, and whether its survivors go
+    // to the persistent stage (the pool exists and the band takes a one-warp
+    // anti-diagonal shape at its default); the persistent stage's query table
+    // and per-shape lists are uploaded before any kernel is enqueued
+    std::vector<int64_t> qoff(nq + 1, 0);
+    for (int q = 0; q < nq; ++q) qoff[q + 1] = qoff[q] + m_arr[q];
+    std::vector<QueryBufs> qb(nq);
+    std::vector<QueryArgs> qa(nq);
+    std::vector<PoolQuery> pq(nq);
+    std::vector<char> deferq(nq, 0);
+    struct Shape {
+        int L, K, m_max, r_max;
+        std::vector<int> list;
+    };
+    std::vector<Shape> shapes;
+    const int64_t F = h->bq_fcap;
+    for (int j = 0; j < nq; ++j) {
+        const int q = order[j], li = j % L;
+        Lane &l = h->lanes[li];
+        const int m = m_arr[q], r = r_arr[q], rr = r > m - 1 ? m - 1 : r;
+        const EnvEntry *ee = nullptr;
+        for (auto &en : h->env)
+            if (en.r == rr) ee = &en;
+        QueryBufs b = lane_bufs(h, l, ee);
+        b.st = h->bq_st + q;
+        float *f = h->bq_f + qoff[q];
+        b.qh32 = f;
+        b.Uq = f + F;
+        b.Lq = f + 2 * F;
+        b.sq = f + 3 * F;
+        b.sU = f + 4 * F;
+        b.sL = f + 5 * F;
+        b.qh64 = h->bq_d + qoff[q];
+        b.ord = h->bq_o + qoff[q];
+        qb[q] = b;
+        qa[q] = make_args(h, m, r, k);
+        pq[q] = PoolQuery{b.st, b.qh32, b.ord, b.sq, b.sU, b.sL, b.U, b.L, qa[q]};
+        int sL = 0, sK = 0;
+        if (h->pool.cap > 0 && qa[q].tune_l == 0 && pool_shape(qa[q].r, &sL, &sK)) {
+            deferq[q] = 1;
+            Shape *sh = nullptr;
+            for (auto &x : shapes)
+                if (x.L == sL && x.K == sK) sh = &x;
+            if (!sh) {
+                shapes.push_back(Shape{sL, sK, 0, 0, {}});
+                sh = &shapes.back();
+            }
+            sh->m_max = std::max(sh->m_max, m);
+            sh->r_max = std::max(sh->r_max, qa[q].r);
+            sh->list.push_back(q);
+        }
+    }
+    std::vector<int> lists;
+    std::vector<int> list_off;
+    for (auto &x : shapes) {
+        list_off.push_back((int)lists.size());
+        lists.insert(lists.end(), x.list.begin(), x.list.end());
+    }
+    // in the caller's stream order (after any earlier batch that read them),
+    // before a capture starts; the pageable source is staged at the call.  A
+    // batch without a graph rewrites the tables a cached graph reads.
+    if (!graph) drop_graph(h);
+    CK(cudaMemcpyAsync(h->pq_dev, pq.data(), sizeof(PoolQuery) * (size_t)nq, cudaMemcpyHostToDevice, s));
+    if (!lists.empty())
+        CK(cudaMemcpyAsync(h->plist_dev, lists.data(), sizeof(int) * lists.size(), cudaMemcpyHostToDevice, s));
+    if (graph) {
+        // the capture stream starts after the caller's stream (the uploads)
+        CK(cudaEventRecord(h->batch_fork, s));
+        CK(cudaStreamWaitEvent(h->cap_stream, h->batch_fork, 0));
         CK(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
     }
     // the stream the batch forks from and joins into: the capture stream, or the caller's
@@ -947,14 +1113,28 @@ dtws_status run_batch(dtws_t h, const float *Qd, const int64_t *q_off, const int
             return fail(DTWS_ECUDA);                                                   \
         }                                                                              \
     } while (0)
-    CKB(cudaEventRecord(h->batch_fork, root));
+    auto fork = [&]() -> cudaError_t {
+        cudaError_t e = cudaEventRecord(h->batch_fork, root);
+        for (int i = 0; i < L && e == cudaSuccess; ++i) e = cudaStreamWaitEvent(h->lanes[i].stream, h->batch_fork, 0);
+        return e;
+    };
+    auto join = [&]() -> cudaError_t {
+        cudaError_t e = cudaSuccess;
+        for (int i = 0; i < L && e == cudaSuccess; ++i) {
+            e = cudaEventRecord(h->lanes[i].ev_done, h->lanes[i].stream);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(root, h->lanes[i].ev_done, 0);
+        }
+        return e;
+    };
+    if (h->pool.cap > 0) CKB(cudaMemsetAsync(h->pool.cursor, 0, sizeof(unsigned long long), root));
+    CKB(fork());
     std::vector<int> lane_m(L, -1);
-    for (int i = 0; i < L; ++i) CKB(cudaStreamWaitEvent(h->lanes[i].stream, h->batch_fork, 0));
     int64_t launches = 0;
+    // stage 1
     for (int j = 0; j < nq; ++j) {
         const int q = order[j], li = j % L;
         Lane &l = h->lanes[li];
-        const int m = m_arr[q], r = r_arr[q], rr = r > m - 1 ? m - 1 : r;
+        const int m = m_arr[q];
         if (lane_m[li] != m) {
             CKB(launch_window_stats(h->x, h->n, m, h->pf, h->bf, h->pok, h->pscale, l.stats.mu_hi, l.stats.mu_lo,
                                     l.stats.inv_sigma, l.stats.smu_hi, l.stats.sinv_sigma,
@@ -962,9 +1142,6 @@ dtws_status run_batch(dtws_t h, const float *Qd, const int64_t *q_off, const int
             lane_m[li] = m;
             ++launches;
         }
-        const EnvEntry *ee = nullptr;
-        for (auto &en : h->env)
-            if (en.r == rr) ee = &en;
         LearnEntry *le = nullptr;
         if (learned) {
             bool c3;
@@ -974,18 +1151,37 @@ dtws_status run_batch(dtws_t h, const float *Qd, const int64_t *q_off, const int
             if ((st = get_stats(h, m, l.stream, &se, &c1)) != DTWS_OK) return fail(st);
             if ((st = get_learn(h, m, se, l.stream, &le, &c3)) != DTWS_OK) return fail(st);
         }
-        Exec e{lane_bufs(h, l, ee), l.stream, l.side, l.ev_fork, l.ev_join, le, false};
-        const QueryArgs a = make_args(h, m, r, k);
+        Exec e{qb[q], l.stream, l.side, l.ev_fork, l.ev_join, le, false, 1, deferq[q] ? &h->pool : nullptr};
         int64_t n_l = 0;
-        if ((st = enqueue_search(h, e, a, Qd + q_off[q], idx_d + (int64_t)q * k, dist_d + (int64_t)q * k, &n_l)) !=
-            DTWS_OK)
+        if ((st = enqueue_search(h, e, qa[q], Qd + q_off[q], idx_d + (int64_t)q * k, dist_d + (int64_t)q * k,
+                                 &n_l)) != DTWS_OK)
             return fail(st);
         launches += n_l;
     }
-    for (int i = 0; i < L; ++i) {
-        CKB(cudaEventRecord(h->lanes[i].ev_done, h->lanes[i].stream));
-        CKB(cudaStreamWaitEvent(root, h->lanes[i].ev_done, 0));
+    CKB(join());
+    // stage 2: the persistent survivor-DTW launches, one per shape
+    {
+        QueryBufs base = make_bufs(h, nullptr, nullptr);
+        for (size_t c = 0; c < shapes.size(); ++c) {
+            const Shape &x = shapes[c];
+            CKB(launch_dtw_pool(base, h->pool, h->pq_dev, h->plist_dev + list_off[c], (int)x.list.size(), x.L, x.K,
+                                x.m_max, x.r_max, root));
+            ++launches;
+        }
     }
+    // stage 3
+    CKB(fork());
+    for (int j = 0; j < nq; ++j) {
+        const int q = order[j], li = j % L;
+        Lane &l = h->lanes[li];
+        Exec e{qb[q], l.stream, l.side, l.ev_fork, l.ev_join, nullptr, false, 2, nullptr};
+        int64_t n_l = 0;
+        if ((st = enqueue_search(h, e, qa[q], Qd + q_off[q], idx_d + (int64_t)q * k, dist_d + (int64_t)q * k,
+                                 &n_l)) != DTWS_OK)
+            return fail(st);
+        launches += n_l;
+    }
+    CKB(join());
 #undef CKB
     if (graph) {
         cudaGraph_t g = nullptr;
@@ -1003,7 +1199,7 @@ dtws_status run_batch(dtws_t h, const float *Qd, const int64_t *q_off, const int
     h->have_last = true;
     h->last_N = h->n - m_arr[order[nq - 1]] + 1;
     h->last_launches = launches;
-    h->last_st = h->lanes[(nq - 1) % L].st;
+    h->last_st = h->bq_st + order[nq - 1];
     return DTWS_OK;
 }
 
@@ -1048,6 +1244,18 @@ const char *dtws_last_error_detail(void) { return g_err; }
 
 void dtws_debug_fail_next_allocs(int count) { g_fail_allocs = count < 0 ? 0 : count; }
 
+dtws_status dtws_debug_set_pool_capacity(dtws_t h, int64_t cap) {
+    if (!h || cap < -1) {
+        set_err("dtws_debug_set_pool_capacity: need cap >= -1");
+        return DTWS_EINVAL;
+    }
+    CK(cudaSetDevice(h->device));
+    CK(cudaDeviceSynchronize());
+    drop_graph(h);
+    h->pool_limit = cap;
+    return DTWS_OK;
+}
+
 dtws_status dtws_debug_set_xz_capacity(dtws_t h, int32_t buf_cap, int32_t sel_cap) {
     if (!h || buf_cap < 1 || sel_cap < 1 || sel_cap > 16384) {
         set_err("dtws_debug_set_xz_capacity: need buf_cap >= 1 and 1 <= sel_cap <= 16384");
@@ -1082,7 +1290,8 @@ dtws_status dtws_destroy(dtws_t h) {
     if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
     void *ptrs[] = {h->x, h->pf, h->bf, h->pok, h->pscale, h->envst, h->absmax, h->st, h->status, h->qh32, h->Uq,
                     h->Lq, h->sq, h->sU, h->sL, h->qh64, h->ord, h->cand_lb, h->sort_lb,
-                    h->cand_idx, h->sort_idx, h->stage, h->xz_bkey, h->xz_buf, h->xz_sel, h->xz_d64};
+                    h->cand_idx, h->sort_idx, h->stage, h->xz_buf, h->xz_sel, h->xz_d64, h->bq_st, h->bq_f, h->bq_d, h->bq_o, h->pool.idx,
+                    h->pool.lb, h->pool.mh, h->pool.is, h->pool.ls, h->pool.cursor, h->pq_dev, h->plist_dev};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (h->ev_ok)
@@ -1339,6 +1548,22 @@ dtws_status dtws_clear_cache(dtws_t h) {
     h->stats.clear();
     h->env.clear();
     h->learn.clear();
+    return DTWS_OK;
+}
+
+dtws_status dtws_debug_lock_selftest(dtws_t h, int64_t wait_ns, void *stream) {
+    if (!h || wait_ns < 1 || wait_ns > 10000000000LL) {
+        set_err("dtws_debug_lock_selftest: null handle or wait_ns outside [1, 1e10]");
+        return DTWS_EINVAL;
+    }
+    dtws_status st;
+    if ((st = ensure_workspace(h)) != DTWS_OK) return st;
+    if ((st = ensure_xz(h)) != DTWS_OK) return st;
+    QueryBufs b = make_bufs(h, nullptr, nullptr);
+    b.wait_ns = wait_ns;
+    QueryArgs a = make_args(h, 2, 0, 1);
+    a.xz_z = 1;
+    CK(launch_lock_selftest(b, a, (cudaStream_t)stream));
     return DTWS_OK;
 }
 

@@ -100,11 +100,16 @@ struct QueryState {
     int valid;                             // 0 when the query is non-finite
     int hist[kBins];
     int bin_off[kBins];
-    // wide exclusion zone (QueryArgs::xz_z > 0): per bucket parity, the
-    // sorted keys of the first window found in each bucket of 2z+1 offsets
+    // wide exclusion zone (QueryArgs::xz_z > 0): per bucket parity, the k
+    // smallest keys with at most one window per bucket of 2z+1 offsets
+    // (each bucket's best found so far), updated under xz_lock[parity]
     unsigned long long xz_keys[2][kKMax];
+    int xz_lock[2];
     int xz_count;                          // windows appended to the candidate buffer
     int xz_nsel;                           // of them within the final threshold
+    // batch: the survivors went to the persistent stage's pool at pool_off
+    int deferred;
+    long long pool_off;
 };
 
 // Scalars of one query, passed by value to every kernel.

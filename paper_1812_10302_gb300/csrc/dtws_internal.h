@@ -47,32 +47,103 @@ struct QueryBufs {
     int *status;
     long long wait_ns;
     int num_sms;
-    // wide exclusion zone (QueryArgs::xz_z > 0): one key per bucket of 2z+1
-    // offsets (EMPTY = none yet), the candidate buffer of windows scored
-    // within the threshold, and the re-score list of those within the final
-    // threshold (offsets, extended-precision distances)
-    unsigned long long *xz_bkey;
+    // survivor pass of the persistent batch stage: the survivors' window
+    // statistics (mean high part, 1/sigma, mean low part * 1/sigma), indexed
+    // like sort_idx; null elsewhere
+    const float *surv_mh, *surv_is, *surv_ls;
+    // wide exclusion zone (QueryArgs::xz_z > 0): the candidate buffer of
+    // windows scored within the threshold, and the re-score list of those
+    // within the final threshold (offsets, extended-precision distances)
     unsigned long long *xz_buf;
     unsigned *xz_sel;
     double *xz_d64;
     int xz_cap, xz_sel_cap;
 };
 
-// Offer a scored window (key: its quantised distance and offset) to the wide
-// exclusion-zone state: the first window of its bucket enters the bucket
-// list of the bucket's parity; with `append` it also joins the candidate
+// Offer a scored window (key: its quantised distance and offset) to the bucket
+// list of its bucket's parity: offsets are cut into buckets of 2z+1, so
+// windows in different buckets of one parity are more than 2z apart, and the
+// list keeps the k smallest keys with at most one per bucket (a better window
+// replaces its bucket's entry).  One thread at a time rewrites a list, under
+// a spin lock bounded by wait_ns (on timeout the offer is dropped, which only
+// loosens the bound, and DTWS_ETIMEOUT is recorded).  Readers take only the
+// k-th entry, which changes by one 64-bit store, from one valid bound to a
+// smaller valid one.  With `append` the window also joins the candidate
 // buffer (DTWS_EOVERFLOW when full).
-__device__ __forceinline__ void xz_offer(const QueryBufs &b, const QueryArgs &a, unsigned long long key, bool append) {
+static __device__ __noinline__ void xz_offer(const QueryBufs &b, const QueryArgs &a, unsigned long long key, bool append) {
     QueryState *st = b.st;
-    const unsigned idx = key_idx(key);
-    const unsigned bucket = idx / (unsigned)(2 * a.xz_z + 1);
-    if (atomicCAS(&b.xz_bkey[bucket], kEmptyKey, key) == kEmptyKey) list_insert(st->xz_keys[bucket & 1u], a.k, key);
     if (append) {
         const int i = atomicAdd(&st->xz_count, 1);
         if (i < b.xz_cap) b.xz_buf[i] = key;
         else atomicOr(b.status, kStOverflow);
     }
+    const int k = a.k;
+    const unsigned W = (unsigned)(2 * a.xz_z + 1);
+    const unsigned bk = key_idx(key) / W;
+    unsigned long long *Lp = st->xz_keys[bk & 1u];
+    if (key >= *((volatile unsigned long long *)&Lp[k - 1])) return;  // changes nothing
+    int *lock = &st->xz_lock[bk & 1u];
+    const long long t0 = global_ns();
+    while (atomicCAS(lock, 0, 1) != 0) {
+        if (global_ns() - t0 > b.wait_ns) {
+            atomicOr(b.status, kStTimeout);
+            return;
+        }
+        __nanosleep(64);
+    }
+    __threadfence();
+    unsigned long long v[kKMax];
+    int n = 0, same = -1;
+    for (int j = 0; j < k; ++j) {
+        v[j] = *((volatile unsigned long long *)&Lp[j]);
+        if (v[j] != kEmptyKey) {
+            ++n;
+            if (key_idx(v[j]) / W == bk) same = j;
+        }
+    }
+    bool changed = false;
+    if (same >= 0) {
+        if (key < v[same]) {  // the bucket's entry improves: drop it, insert below
+            for (int j = same; j + 1 < k; ++j) v[j] = v[j + 1];
+            v[k - 1] = kEmptyKey;
+            changed = true;
+        }
+    } else {
+        changed = key < v[k - 1];
+    }
+    if (changed) {
+        int pos = k - 1;
+        while (pos > 0 && v[pos - 1] > key) {
+            v[pos] = v[pos - 1];
+            --pos;
+        }
+        v[pos] = key;
+        for (int j = 0; j < k - 1; ++j) Lp[j] = v[j];
+        __threadfence();
+        *((volatile unsigned long long *)&Lp[k - 1]) = v[k - 1];
+    }
+    __threadfence();
+    atomicExch(lock, 0);
 }
+
+// A query of a batch whose survivor DTW runs in the persistent stage.
+struct PoolQuery {
+    QueryState *st;
+    float *qh32;
+    unsigned short *ord;
+    float *sq, *sU, *sL;
+    const float *U, *L;  // the exact envelope for its r, or null (block envelope)
+    QueryArgs a;
+};
+
+// The survivor pool of a batch: survivors (offset, bound) and their window
+// statistics, each query's run reserved from one cursor.
+struct SurvPool {
+    unsigned *idx;
+    float *lb, *mh, *is, *ls;
+    unsigned long long *cursor;
+    long long cap;
+};
 
 cudaError_t launch_query_reset(const QueryBufs &b, const QueryArgs &a, cudaStream_t s);
 cudaError_t launch_qprep(const float *Q, const QueryBufs &b, const QueryArgs &a, cudaStream_t s);
@@ -93,6 +164,16 @@ cudaError_t launch_order(const QueryBufs &b, const QueryArgs &a, cudaStream_t s)
 cudaError_t launch_dtw_survivors(const QueryBufs &b, const QueryArgs &a, cudaStream_t s);
 cudaError_t launch_finalize(const QueryBufs &b, const QueryArgs &a, int64_t *out_idx,
                             float *out_dist, cudaStream_t s);
+// persistent batch stage (dtw_pool.cu): the default anti-diagonal shape of a
+// band (false when the band takes another kernel), and the stage's launch
+// over the shape's queries list[0..nlist) of pq (device arrays); m_max,
+// r_max size its shared memory
+bool pool_shape(int r, int *L, int *K);
+cudaError_t launch_dtw_pool(const QueryBufs &base, const SurvPool &pool, const PoolQuery *pq, const int *list,
+                            int nlist, int L, int K, int m_max, int r_max, cudaStream_t s);
+// hand the ordered survivors of b's query to the pool (st->deferred = 1), or
+// leave them to the query's own survivor pass when the pool is full
+cudaError_t launch_defer(const QueryBufs &b, const SurvPool &pool, cudaStream_t s);
 // wide exclusion zone: the candidates within the final threshold,
 // re-scored, sorted, taken greedily (k results; -1 / +inf where missing)
 cudaError_t launch_xz_finalize(const QueryBufs &b, const QueryArgs &a, int64_t *out_idx, float *out_dist,
@@ -112,6 +193,8 @@ cudaError_t launch_lbs_at(const QueryBufs &b, const QueryArgs &a, const int64_t 
 
 // one bounded wait on an mbarrier nothing arrives on (records kStTimeout)
 cudaError_t launch_wait_selftest(int *status, long long wait_ns, cudaStream_t s);
+// the exclusion zone's list lock held while an offer waits (records kStTimeout)
+cudaError_t launch_lock_selftest(const QueryBufs &b, const QueryArgs &a, cudaStream_t s);
 
 // ---- learned proposal encoder (encoder.cu)
 // params -> packed blob; with `adam`, one Adam step first (c1, c2: bias corrections)

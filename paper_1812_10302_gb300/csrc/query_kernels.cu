@@ -52,6 +52,10 @@ __global__ void k_query_reset(QueryState *st) {
     if (threadIdx.x == 0) {
         st->xz_count = 0;
         st->xz_nsel = 0;
+        st->xz_lock[0] = 0;
+        st->xz_lock[1] = 0;
+        st->deferred = 0;
+        st->pool_off = 0;
         st->n_seeds = 0;
         st->n_cand = 0;
         st->work = 0;
@@ -806,6 +810,43 @@ __global__ void k_wait_selftest(int *status, long long wait_ns) {
     mbar_init(&bar, 1);
     mbar_fence_init();
     if (!mbar_wait_bounded(&bar, 0u, wait_ns)) atomicOr(status, kStTimeout);
+}
+
+// The bounded lock of the wide exclusion zone's bucket lists: one thread
+// holds list 0's lock while a second offers a key to that list, so the offer
+// waits out wait_ns, records the timeout and drops the key; the holder then
+// releases the lock.  Both lists and the lock are left as the query reset
+// makes them.  No spin here is unbounded: the holder waits only for the
+// offer to return.
+__global__ void k_lock_selftest(QueryBufs b, QueryArgs a) {
+    __shared__ int held, offered;
+    QueryState *st = b.st;
+    if (threadIdx.x == 0) {
+        for (int t = 0; t < 2 * kKMax; ++t) st->xz_keys[t / kKMax][t % kKMax] = kEmptyKey;
+        st->xz_lock[0] = 1;  // held by this thread
+        st->xz_lock[1] = 0;
+        st->xz_count = 0;
+        __threadfence();
+        held = 1;
+        offered = 0;
+    }
+    __syncthreads();
+    if (threadIdx.x == 32) {  // another warp: bucket 0 has parity 0
+        xz_offer(b, a, make_key(1.0f, 0u), false);
+        atomicExch(&offered, 1);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        atomicExch(&st->xz_lock[0], 0);
+        held = 0;
+    }
+    (void)offered;
+    (void)held;
+}
+
+cudaError_t launch_lock_selftest(const QueryBufs &b, const QueryArgs &a, cudaStream_t s) {
+    k_lock_selftest<<<1, 64, 0, s>>>(b, a);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_wait_selftest(int *status, long long wait_ns, cudaStream_t s) {

@@ -105,6 +105,7 @@ _SIGS = {
     "dtws_last_error_detail": (ctypes.c_char_p, []),
     "dtws_debug_fail_next_allocs": (None, [ctypes.c_int]),
     "dtws_debug_set_xz_capacity": (_S, [_P, _I32, _I32]),
+    "dtws_debug_set_pool_capacity": (_S, [_P, _I64]),
     "dtws_window_stats": (_S, [_P, _I32, _P, _P, _P, _P]),
     "dtws_series_envelope": (_S, [_P, _I32, _P, _P, _P]),
     "dtws_dtw_at": (_S, [_P, _P, _I32, _I32, _P, _I64, _P, _P]),
@@ -112,6 +113,7 @@ _SIGS = {
     "dtws_lower_bounds_at": (_S, [_P, _P, _I32, _I32, _P, _I64, _P, _P, _P, _P]),
     "dtws_dtw_at_noalloc": (_S, [_P, _I64, _P, _I32, _I32, _P, _I64, _P, _P]),
     "dtws_debug_wait_selftest": (_S, [_P, _I64, _P]),
+    "dtws_debug_lock_selftest": (_S, [_P, _I64, _P]),
     "dtws_autotune": (_S, [_P, _P, _P, _I32, _I32, _P]),
     "dtws_tune_entry": (_S, [_P, _I32, _I32, _P, _P]),
     "dtws_set_encoder": (_S, [_P, _P, _I32, _P]),
@@ -390,10 +392,18 @@ class Index:
                                          _stream_ptr(stream)), "dtws_dtw_at_f64")
         return out
 
+    def debug_set_pool_capacity(self, cap: int):
+        """Test hook: survivor pool capacity of the batch's persistent stage
+        (0: none, -1: default; see dtws.h)."""
+        _check(self._lib.dtws_debug_set_pool_capacity(self.h, cap), "dtws_debug_set_pool_capacity")
+
     def debug_set_xz_capacity(self, buf_cap: int, sel_cap: int):
         """Test hook: capacities of the wide exclusion zone's candidate buffer
         and re-score list (see dtws.h)."""
         _check(self._lib.dtws_debug_set_xz_capacity(self.h, buf_cap, sel_cap), "dtws_debug_set_xz_capacity")
+
+    def debug_lock_selftest(self, wait_ns: int, stream=None):
+        _check(self._lib.dtws_debug_lock_selftest(self.h, wait_ns, _stream_ptr(stream)), "dtws_debug_lock_selftest")
 
     def debug_wait_selftest(self, wait_ns: int, stream=None):
         _check(self._lib.dtws_debug_wait_selftest(self.h, wait_ns, _stream_ptr(stream)), "dtws_debug_wait_selftest")

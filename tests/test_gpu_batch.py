@@ -1,6 +1,7 @@
-"""Batched queries (lanes of concurrent queries, CUDA-graph capture and
-replay), the per-series block envelope and the learned ordering inside a
-batch: every variant returns the oracle's answers."""
+"""Batched queries (lanes of concurrent queries, the persistent survivor-DTW
+stage over the whole batch, CUDA-graph capture and replay), the per-series
+block envelope and the learned ordering inside a batch: every variant returns
+the oracle's answers."""
 import numpy as np
 import pytest
 
@@ -46,6 +47,54 @@ def test_lanes_and_graph_replay_match_the_oracle(walk):
             oi, od = fragments.search_fragments(walk, q, r, k)
             np.testing.assert_array_equal(bi[t], oi)
             _close(bd[t], od, len(q))
+
+
+def test_persistent_stage_pool_sizes_give_the_same_answers(walk):
+    """The batch's survivor DTW in the persistent per-shape launches (default
+    pool), on the lanes (no pool), and split between the two (a pool too small
+    for some queries' survivors, so those run on their lanes): the oracle's
+    answers every time, with and without a captured graph."""
+    qs, rs, _ = _queries(walk, 20, 8, m_range=(32, 700))
+    k = 4
+    want = [fragments.search_fragments(walk, q, r, k) for q, r in zip(qs, rs)]
+    with dtws.Index(walk) as ix:
+        for cap in (-1, 0, 3000, 1):
+            ix.debug_set_pool_capacity(cap)
+            for graph in (0, 1):
+                ix.set_options(batch_lanes=3, batch_graph=graph)
+                bi, bd = ix.query_batch(qs, rs, k=k)
+                assert ix.sync_status() == dtws.DTWS_OK
+                for t, (q, r) in enumerate(zip(qs, rs)):
+                    np.testing.assert_array_equal(bi[t], want[t][0], err_msg=f"cap {cap} graph {graph} query {t}")
+                    _close(bd[t], want[t][1], len(q))
+                st = ix.last_stats()
+                assert st["dtw_started"] >= st["dtw_abandoned"] >= 0
+        ix.debug_set_pool_capacity(-1)
+        with pytest.raises(dtws.DtwsError):
+            ix.debug_set_pool_capacity(-2)
+
+
+def test_exclusion_lock_wait_is_bounded(walk):
+    """The one lock of the library (the wide exclusion zone's bucket lists)
+    gives up after the handle's wait limit: held by one device thread while
+    another offers, the offer times out, DTWS_ETIMEOUT is reported, and the
+    handle answers correctly afterwards."""
+    import time
+    q, _ = synth.noisy_copy(walk, 128, 70, 71, noise=0.3)
+    with dtws.Index(walk) as ix:
+        t0 = time.perf_counter()
+        ix.debug_lock_selftest(2_000_000)  # 2 ms
+        assert ix.sync_status() == dtws.DTWS_ETIMEOUT
+        assert time.perf_counter() - t0 < 5.0
+        assert ix.sync_status() == dtws.DTWS_OK  # cleared
+        ix.set_options(exclusion_zone=64)
+        idx, dist = ix.query(q, 12, 3)
+        assert ix.sync_status() == dtws.DTWS_OK
+    import oracle
+    d = oracle.dtw_at(walk, q, 12, np.arange(walk.size - 127))
+    oi, od = oracle.exclusion_topk(d, 3, 64)
+    np.testing.assert_array_equal(idx, oi)
+    _close(dist, od, 128)
 
 
 def test_batch_with_device_queries_and_outputs(walk):

@@ -108,17 +108,18 @@ def test_wide_exclusion_zone_matches_oracle(m, r, k, z):
 
 
 def test_wide_exclusion_zone_with_decoys_inside_the_zone():
-    """An exact copy of the query, two close copies z samples on either side
-    of it (inside its zone, so the answer may not take them) and a noisier
-    copy far away: the answer is the exact copy and the far one.  The two
-    decoys are 2z apart, so a threshold from windows kept only z apart would
-    prune the far copy."""
+    """An exact copy of the query, two close copies 20 samples inside either
+    edge of its zone (so the answer may not take them, nor their neighbours
+    that DTW's band can still align) and a noisier copy far away: the answer
+    is the exact copy and the far one.  The two decoys are 2z - 40 > z apart,
+    so a threshold from windows kept only z apart would prune the far
+    copy."""
     m, r, z, k = 64, 6, 80, 2
     x = synth.random_walk(40_000, 610).astype(np.float64)
     rng = np.random.default_rng(611)
     P, F = 20_000, 33_000
     base = x[P:P + m].copy()
-    for o, noise in ((P - z, 0.02), (P + z, 0.02), (F, 0.4)):
+    for o, noise in ((P - z + 20, 0.02), (P + z - 20, 0.02), (F, 0.4)):
         x[o:o + m] = base + rng.normal(0, noise, m) + (x[o] - base[0])
     x = x.astype(np.float32)
     q = x[P:P + m].copy()

@@ -141,18 +141,20 @@ def test_separated_set_keeps_the_better_neighbour():
 
 
 def _bucket_kth(d, k, z, found):
-    """The lock-free form of the threshold: offsets cut into buckets of
-    2z + 1; windows in different buckets of the same parity are at least
-    2z + 2 apart.  Per parity, the first window found in each bucket enters a
-    list once; the k-th smallest of either list bounds the answer (each entry
-    is a real window's distance, the entries pairwise more than 2z apart)."""
+    """The bucket form of the threshold that the GPU path keeps: offsets cut
+    into buckets of 2z + 1; windows in different buckets of the same parity
+    are at least 2z + 2 apart.  Per parity, a list of the best window found
+    in each bucket; the k-th smallest of either list bounds the answer (each
+    entry is a real window's distance, the entries pairwise more than 2z
+    apart)."""
     W = 2 * z + 1
-    first = {}
+    best_in = {}
     for w in found:
-        first.setdefault(w // W, float(d[w]))
+        b = w // W
+        best_in[b] = min(best_in.get(b, np.inf), float(d[w]))
     best = np.inf
     for parity in (0, 1):
-        vals = sorted(v for b, v in first.items() if b % 2 == parity)
+        vals = sorted(v for b, v in best_in.items() if b % 2 == parity)
         if len(vals) >= k:
             best = min(best, vals[k - 1])
     return best

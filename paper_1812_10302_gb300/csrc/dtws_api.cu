@@ -98,6 +98,7 @@ struct dtws_ctx {
     int device = 0, num_sms = 0;
     int64_t n = 0, n_alloc = 0;
     float *x = nullptr;
+    float *x_even = nullptr;             // x[2j] for j < n_alloc/2, plus a zero tail
     float *pf = nullptr, *bf = nullptr;  // prefix sums as FP32 pairs, block totals and anchors
     int *pok = nullptr;                  // per-block flag: the pairs carry the block
     float *pscale = nullptr;             // [0]: the series' power-of-two scale; [1]: scratch
@@ -482,6 +483,7 @@ QueryBufs make_bufs(dtws_t h, const StatsEntry *se, const EnvEntry *ee) {
     memset(&b, 0, sizeof b);  // padding included: the bytes enter graph signatures
     b.st = h->st;
     b.x = h->x;
+    b.x_even = h->x_even;
     b.mu_hi = se ? se->mu_hi : nullptr;
     b.mu_lo = se ? se->mu_lo : nullptr;
     b.inv_sigma = se ? se->inv_sigma : nullptr;
@@ -1288,7 +1290,7 @@ dtws_status dtws_destroy(dtws_t h) {
     for (auto &l : h->lanes) free_lane(l);
     if (h->batch_fork) cudaEventDestroy(h->batch_fork);
     if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
-    void *ptrs[] = {h->x, h->pf, h->bf, h->pok, h->pscale, h->envst, h->absmax, h->st, h->status, h->qh32, h->Uq,
+    void *ptrs[] = {h->x, h->x_even, h->pf, h->bf, h->pok, h->pscale, h->envst, h->absmax, h->st, h->status, h->qh32, h->Uq,
                     h->Lq, h->sq, h->sU, h->sL, h->qh64, h->ord, h->cand_lb, h->sort_lb,
                     h->cand_idx, h->sort_idx, h->stage, h->xz_buf, h->xz_sel, h->xz_d64, h->bq_st, h->bq_f, h->bq_d, h->bq_o, h->pool.idx,
                     h->pool.lb, h->pool.mh, h->pool.is, h->pool.ls, h->pool.cursor, h->pq_dev, h->plist_dev};
@@ -1333,6 +1335,7 @@ dtws_status dtws_create(const float *series, int64_t n, void *stream, dtws_t *ou
     h->n_alloc = round_up(n, kProxyTile) + kMMax + 64;
     const int64_t nb = (n + kBlockB - 1) / kBlockB;
     CKF(dalloc(&h->x, h->n_alloc));
+    CKF(dalloc(&h->x_even, h->n_alloc / 2 + kProxyTile));
     CKF(dalloc(&h->pf, 4 * n));
     CKF(dalloc(&h->bf, 5 * nb));
     CKF(dalloc(&h->pok, nb));
@@ -1356,6 +1359,8 @@ dtws_status dtws_create(const float *series, int64_t n, void *stream, dtws_t *ou
         set_err("series contains NaN or Inf");
         return fail(DTWS_ENONFINITE);
     }
+    CKF(cudaMemsetAsync(h->x_even, 0, (h->n_alloc / 2 + kProxyTile) * 4, s));
+    CKF(launch_even(h->x, h->n_alloc / 2, h->x_even, h->num_sms, s));
     CKF(launch_prefix(h->x, n, h->pf, h->bf, h->pok, reinterpret_cast<unsigned *>(h->pscale + 1), h->pscale, s));
     CKF(launch_block_envelope(h->x, n, h->envst, h->nblk, s));
     CKF(cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking));

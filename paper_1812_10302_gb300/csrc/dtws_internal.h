@@ -16,6 +16,8 @@ void set_error_detail(const char *fmt, ...);
 // ---- series level (series_kernels.cu)
 cudaError_t launch_check_finite(const float *x, int64_t n, int *flag, unsigned *absmax, cudaStream_t s);
 cudaError_t launch_fill(float *p, int64_t count, float v, int num_sms, cudaStream_t s);
+// xe[j] = x[2j], j < count
+cudaError_t launch_even(const float *x, int64_t count, float *xe, int num_sms, cudaStream_t s);
 // pf: 4*n floats (P1 hi, P1 lo, P2 hi, P2 lo); bf: 5*nb floats (T1 hi, lo,
 // T2 hi, lo, anchors); ok: nb flags; nb = ceil(n / kBlockB); maxabs: one
 // word of scratch; scale: one float (the series' power-of-two scale)
@@ -32,6 +34,7 @@ cudaError_t launch_block_envelope(const float *x, int64_t n, float *st, int64_t 
 struct QueryBufs {
     QueryState *st;
     const float *x;              // padded series
+    const float *x_even;         // its even samples (the proxy scan's copy)
     const float *mu_hi, *mu_lo, *inv_sigma;  // window stats for m
     const float *smu_hi, *sinv_sigma;  // mean (high part) and 1/sigma of every kProxyStride-th window
     const float *U, *L;          // exact series envelope for r, or null:

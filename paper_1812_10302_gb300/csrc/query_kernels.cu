@@ -79,12 +79,14 @@ cudaError_t launch_query_reset(const QueryBufs &b, const QueryArgs &, cudaStream
 // ------------------------------------------------------------------ query prep
 // One CTA of 1024 threads.  Dynamic smem: q_hat FP32 [m] + sort keys u64 [P],
 // P = next power of two >= m.
+constexpr int kQBins = 1024;  // |q_hat| quantised to 1/256, up to 4
 __global__ void __launch_bounds__(1024) k_qprep(const float *__restrict__ Q, QueryBufs b, QueryArgs a) {
     extern __shared__ __align__(16) unsigned char smraw[];
     __shared__ int bad;
     const int m = a.m, r = a.r;
     int P = 1;
     while (P < m) P <<= 1;
+    if (P < kQBins / 2) P = kQBins / 2;  // (as launch_qprep sizes it)
     unsigned long long *keys = (unsigned long long *)smraw;
     float *qs = (float *)(keys + P);
 
@@ -154,47 +156,67 @@ __global__ void __launch_bounds__(1024) k_qprep(const float *__restrict__ Q, Que
         b.Lq[j] = l;
         b.qh32[j] = qs[j];
     }
-    // order by |q_hat| descending, ties by position ascending: bitonic sort of
-    // (|q| bits << 32 | ~j) descending; padding keys sort last
-    for (int j = threadIdx.x; j < P; j += blockDim.x) {
-        unsigned kb = j < m ? __float_as_uint(fabsf(qs[j])) : 0u;
-        keys[j] = ((unsigned long long)kb << 32) | (unsigned)(0xffffffffu - (unsigned)j);
-    }
+    // order by |q_hat| descending, quantised to 1/256 (the order only decides
+    // which terms the early-abandoning bounds take first: any order is
+    // admissible), ties by position ascending: a stable counting sort --
+    // histogram of the keys, exclusive scan from the largest key down, then
+    // one warp places the positions chunk by chunk, ranking equal keys
+    // within a chunk by lane
+    unsigned *cnt = reinterpret_cast<unsigned *>(keys);  // kQBins counters (reuses the key buffer)
+    for (int t = threadIdx.x; t < kQBins; t += blockDim.x) cnt[t] = 0u;
     __syncthreads();
-    for (int size = 2; size <= P; size <<= 1) {
-        for (int stride = size >> 1; stride > 0; stride >>= 1) {
-            for (int t = threadIdx.x; t < P / 2; t += blockDim.x) {
-                int lo = 2 * t - (t & (stride - 1));
-                int hi = lo + stride;
-                bool desc = ((lo & size) == 0);
-                unsigned long long x0 = keys[lo], x1 = keys[hi];
-                if ((x0 < x1) == desc) {
-                    keys[lo] = x1;
-                    keys[hi] = x0;
-                }
-            }
-            __syncthreads();
+    auto qkey = [&](int j) {
+        const int v = (int)(fabsf(qs[j]) * 256.0f);
+        return (kQBins - 1) - (v < kQBins - 1 ? v : kQBins - 1);  // 0 = the largest |q_hat|
+    };
+    for (int j = threadIdx.x; j < m; j += blockDim.x) atomicAdd(&cnt[qkey(j)], 1u);
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        const int lane = threadIdx.x;
+        constexpr int per = kQBins / 32;
+        unsigned run = 0;
+        for (int t = 0; t < per; ++t) run += cnt[lane * per + t];
+        unsigned incl = run;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned u = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += u;
         }
-    }
-    __syncthreads();
-    for (int t = threadIdx.x; t < m; t += blockDim.x) {
-        int j = (int)(0xffffffffu - (unsigned)(keys[t] & 0xffffffffu));
-        b.ord[t] = (unsigned short)j;
-        b.sq[t] = qs[j];
-        b.sU[t] = b.Uq[j];
-        b.sL[t] = b.Lq[j];
+        unsigned base = incl - run;
+        for (int t = 0; t < per; ++t) {
+            const unsigned c = cnt[lane * per + t];
+            cnt[lane * per + t] = base;
+            base += c;
+        }
+        __syncwarp();
+        for (int c0 = 0; c0 < m; c0 += 32) {
+            const int j = c0 + lane;
+            const bool in = j < m;
+            const int kk = in ? qkey(j) : -1 - lane;  // (out-of-range lanes match nobody)
+            const unsigned peers = __match_any_sync(0xffffffffu, kk);
+            const unsigned rank = __popc(peers & ((1u << lane) - 1u));
+            const unsigned slot = in ? cnt[kk] + rank : 0u;
+            __syncwarp();
+            if (in && rank == 0) cnt[kk] += __popc(peers);
+            if (in) {
+                b.ord[slot] = (unsigned short)j;
+                b.sq[slot] = qs[j];
+                b.sU[slot] = b.Uq[j];
+                b.sL[slot] = b.Lq[j];
+            }
+            __syncwarp();
+        }
     }
 }
 
 cudaError_t launch_qprep(const float *Q, const QueryBufs &b, const QueryArgs &a, cudaStream_t s) {
     int P = 1;
     while (P < a.m) P <<= 1;
+    if (P < kQBins / 2) P = kQBins / 2;  // (the key buffer also holds the sort's counters)
     size_t smem = (size_t)P * 8 + (size_t)a.m * 4;
     cudaError_t e = cudaFuncSetAttribute(k_qprep, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    // the sort's compare-exchange steps take P/2 threads; a smaller block
-    // makes each of its barriers cheaper
-    const int threads = P / 2 < 128 ? 128 : (P / 2 > 1024 ? 1024 : P / 2);
+    const int threads = a.m < 256 ? 128 : (a.m < 1024 ? 256 : 512);
     k_qprep<<<1, threads, smem, s>>>(Q, b, a);
     return cudaGetLastError();
 }
@@ -219,18 +241,21 @@ cudaError_t launch_qprep(const float *Q, const QueryBufs &b, const QueryArgs &a,
 // whose tile index is -1, completed without copies.
 //
 // Two stage layouts.  LbLayout<TW>: TW windows with the statistics (mean as
-// a hi + lo pair, 1/sigma) of every window (the lower-bound scan).
-// ProxyLayout: kProxyTile windows with the mean's high part and 1/sigma of
-// every kProxyStride-th window (the proxy scan; no ml array).
+// a hi + lo pair, 1/sigma) of every window and all their samples (the
+// lower-bound scan).  ProxyLayout: kProxyTile windows with the mean's high
+// part and 1/sigma of every kProxyStride-th window and only the even samples
+// (the proxy scan scores even windows at even term positions; no ml array).
 template <int TW>
 struct LbLayout {
-    static constexpr int W = TW, S = TW, kStride = 1, NS = 3;
+    static constexpr int W = TW, S = TW, kStride = 1, NS = 3, XDIV = 1;
+    __device__ static const float *xs(const QueryBufs &b) { return b.x; }
     __device__ static const float *mh(const QueryBufs &b) { return b.mu_hi; }
     __device__ static const float *ml(const QueryBufs &b) { return b.mu_lo; }
     __device__ static const float *is(const QueryBufs &b) { return b.inv_sigma; }
 };
 struct ProxyLayout {
-    static constexpr int W = kProxyTile, S = kProxyTile / kProxyStride, kStride = kProxyStride, NS = 2;
+    static constexpr int W = kProxyTile, S = kProxyTile / kProxyStride, kStride = kProxyStride, NS = 2, XDIV = 2;
+    __device__ static const float *xs(const QueryBufs &b) { return b.x_even; }
     __device__ static const float *mh(const QueryBufs &b) { return b.smu_hi; }
     __device__ static const float *ml(const QueryBufs &) { return nullptr; }
     __device__ static const float *is(const QueryBufs &b) { return b.sinv_sigma; }
@@ -244,9 +269,10 @@ struct Tile {
 
 constexpr int kStageHeader = 32;  // full, empty barriers and the tile index
 
+// samples staged per tile: W + m - 1, or the even ones of them
 template <class LY>
 __host__ __device__ __forceinline__ unsigned tile_x_floats(int m) {
-    return (unsigned)((LY::W + m - 1 + 3) & ~3);
+    return (unsigned)(((LY::W + m - 1 + LY::XDIV - 1) / LY::XDIV + 3) & ~3);
 }
 template <class LY>
 __host__ __device__ __forceinline__ size_t stage_bytes(int m) {
@@ -273,7 +299,7 @@ __device__ __forceinline__ void issue_tile(const Tile &t, const QueryBufs &b, in
     const int64_t s0 = i0 / LY::kStride;
     // the transaction count covers exactly the copies issued below
     mbar_arrive_expect_tx(t.full, xb + (unsigned)LY::NS * sb);
-    bulk_g2s(t.xs, b.x + i0, xb, t.full);
+    bulk_g2s(t.xs, LY::xs(b) + i0 / LY::XDIV, xb, t.full);
     bulk_g2s(t.mh, LY::mh(b) + s0, sb, t.full);
     if constexpr (LY::NS == 3) bulk_g2s(t.ml, LY::ml(b) + s0, sb, t.full);
     bulk_g2s(t.is, LY::is(b) + s0, sb, t.full);
@@ -391,11 +417,13 @@ static int scan_stages(const void *kernel, size_t stage_bytes, int min_stages, s
 // distances seed the best-so-far).  Spread-out positions make the terms
 // nearly independent, so a random window scores near 2*TERMS while a window
 // within a sample of a noisy copy scores far lower.  Each thread keeps its best window over
-// all the tiles it scans; each CTA proposes its best.  Reading the
-// statistics of one window in two cuts the scan's traffic from 16 to 10
-// bytes per window; the seed step then covers the neighbours of each
-// proposal.  (With one window in eight, a window four samples off a match
-// scored no better than lucky random windows and matches were lost.)
+// all the tiles it scans; each CTA proposes its best.  Scoring one window in
+// two, with the mean's high part and 1/sigma of those windows only, and with
+// every term position even so that only the series' even samples are read,
+// the scan moves 6 bytes per window (2 of samples, 4 of statistics) instead
+// of 16; the seed step then covers the neighbours of each proposal.  (With
+// one window in eight, a window four samples off a match scored no better
+// than lucky random windows and matches were lost.)
 // Packed FP32 pairs (sm_100 family): one instruction does the operation on
 // both halves, each half rounded exactly as the scalar operation would be.
 __device__ __forceinline__ unsigned long long x2_pack(float lo, float hi) {
@@ -438,14 +466,11 @@ __global__ void __launch_bounds__(kScanThreads) k_seed_scan(QueryBufs b, QueryAr
     __shared__ unsigned long long wbest[kScanConsumers + 1];
     if (!b.st->valid) return;
     const int m = a.m;
-    // Term positions, evenly spread; for m >= 4*TERMS each is moved by at
-    // most one sample so that even terms sit at even and odd terms at odd
-    // positions.  Lane l scores window 2l (+ const), so a load of one term
-    // would touch 16 banks twice; the upper half-warp takes the terms of
-    // each pair in the other order, so the two halves read opposite bank
-    // parities and every load is conflict-free.  Scores are identical in
-    // both halves: the pair sums are added in either order.
-    const int hsel = lane_id() >= 16 ? 1 : 0;
+    // Term positions, evenly spread, each rounded down to an even position
+    // (the scored windows are the even ones, so their term samples are all
+    // even: the stage holds only the series' even samples).  Lane l scores
+    // window 2l (+ const), whose term sample p sits at even sample l + p/2:
+    // consecutive words across the warp, so every load is conflict-free.
     unsigned poff[TERMS];
     unsigned long long qv2[TERMS / 2];
 #pragma unroll
@@ -455,31 +480,30 @@ __global__ void __launch_bounds__(kScanThreads) k_seed_scan(QueryBufs b, QueryAr
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
             const int u = 2 * j + h;
-            int pu = (int)(((2 * u + 1) * (long long)m) / (2 * TERMS));
-            if (m >= 4 * TERMS) pu ^= (pu ^ u) & 1;
+            const int pu = (int)(((2 * u + 1) * (long long)m) / (2 * TERMS)) & ~1;
             p[h] = pu;
             q[h] = b.qh32[pu];
         }
-        poff[2 * j] = 4u * (unsigned)(hsel ? p[1] : p[0]);
-        poff[2 * j + 1] = 4u * (unsigned)(hsel ? p[0] : p[1]);
-        qv2[j] = hsel ? x2_pack(q[1], q[0]) : x2_pack(q[0], q[1]);
+        poff[2 * j] = 2u * (unsigned)p[0];  // bytes: 4 * (p / 2)
+        poff[2 * j + 1] = 2u * (unsigned)p[1];
+        qv2[j] = x2_pack(q[0], q[1]);
     }
     unsigned long long best = kEmptyKey;
     const int64_t ntiles = (a.N + ProxyLayout::W - 1) / ProxyLayout::W;
     tile_pipeline<ProxyLayout>(smraw, b, m, ntiles, &b.st->tile_ctr[0], stages, [&](const Tile &t, int64_t i0) {
-        // window w = 2v, v = threadIdx.x + it * kPer: its samples at byte
-        // offset 8v in xs, its statistics at 4v in mh / ml / is.  Two
+        // window w = 2v, v = threadIdx.x + it * kPer: its (even) samples from
+        // byte offset 4v in xs, its statistics at 4v in mh / is.  Two
         // windows (it, it + kIt/2) at a time, each with two partial sums,
         // so four independent FMA chains are in flight.
-        const unsigned xa = smem_u32(t.xs) + 8u * threadIdx.x;
+        const unsigned xa = smem_u32(t.xs) + 4u * threadIdx.x;
         const unsigned sa = smem_u32(t.mh) + 4u * threadIdx.x;
         unsigned addr[TERMS];
 #pragma unroll
         for (int k = 0; k < TERMS; ++k) addr[k] = xa + poff[k];
         static_for<kIt / 2>([&](auto itc) {
             constexpr int itA = decltype(itc)::value, itB = itA + kIt / 2;
-            constexpr int soA = itA * kPer * 4, xoA = itA * kPer * 8;
-            constexpr int soB = itB * kPer * 4, xoB = itB * kPer * 8;
+            constexpr int soA = itA * kPer * 4, xoA = itA * kPer * 4;
+            constexpr int soB = itB * kPer * 4, xoB = itB * kPer * 4;
             const int64_t iA = i0 + (int64_t)kProxyStride * (threadIdx.x + itA * kPer);
             const int64_t iB = i0 + (int64_t)kProxyStride * (threadIdx.x + itB * kPer);
             const bool liveA = iA < a.N, liveB = iB < a.N;

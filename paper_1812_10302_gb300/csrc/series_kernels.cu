@@ -51,6 +51,21 @@ cudaError_t launch_fill(float *p, int64_t count, float v, int num_sms, cudaStrea
     return cudaGetLastError();
 }
 
+// The series' even samples, xe[j] = x[2 j] for j < count (the proxy scan
+// scores every second window at even term positions, so it reads only these).
+__global__ void k_even(const float *__restrict__ x, int64_t count, float *__restrict__ xe) {
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < count; j += (int64_t)gridDim.x * blockDim.x)
+        xe[j] = x[2 * j];
+}
+
+cudaError_t launch_even(const float *x, int64_t count, float *xe, int num_sms, cudaStream_t s) {
+    if (count <= 0) return cudaSuccess;
+    int64_t blocks = (count + 255) / 256;
+    if (blocks > 8LL * num_sms) blocks = 8LL * num_sms;
+    k_even<<<(int)blocks, 256, 0, s>>>(x, count, xe);
+    return cudaGetLastError();
+}
+
 // ------------------------------------------------------------------ prefix
 // One thread per block b of kBlockB samples.  The anchor a_b = x[b*B]; every
 // sum inside the block runs over d = x - a_b, in FP64, so no sum grows with

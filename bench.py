@@ -17,7 +17,11 @@ and the paper's random seeding, the speedups and whether the answers agree;
 ``batch`` -- the batched workload (n = 5e7, 256 queries of mixed m and r,
 top-10) through dtws_query_batch with a replayed CUDA graph; ``drift`` -- the
 precision-stress workload (n = 1e9 with drift and variance regimes, 32
-queries m = 1024): ms per query and the FP32 DTW's error at each answer.
+queries m = 1024): ms per query and, against the FP64 oracle at each answer,
+the error of the FP32 DTW and of the returned distance; ``wide`` -- bands of
+0.9 m (m = 1024 and 2048 on 2e7 samples): ms per query and phase times.
+``dtw_roofline`` times the DTW kernel's walk alone (dtws_dtw_at over 1e5
+windows of the workload, no pruning) against its ALU ceiling.
 
 Metric: subsequences/s per query (N windows / step time).  Also reported:
 brute-force-equivalent DTW cells/s (N * cells(m, r) / step time), the

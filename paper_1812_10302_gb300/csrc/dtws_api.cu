@@ -640,10 +640,9 @@ dtws_status enqueue_search(dtws_t h, const Exec &e, const QueryArgs &a, const fl
     auto rec = [&](int i) {
         if (e.timing) record(h, i, s);
     };
-    CK(launch_query_reset(b, a, s));
-    CK(launch_qprep(Qd, b, a, s));
+    CK(launch_qprep(Qd, b, a, s));  // (clears the query's state first)
     rec(0);
-    int half = kProxyStride / 2;
+    int half = kProxyHalf;
     if (P > 0 && e.le) {
         int c0 = 0, c1 = 0;
         CK(launch_enc_query(h->enc_blob, b, a, s));
@@ -691,14 +690,14 @@ dtws_status enqueue_search(dtws_t h, const Exec &e, const QueryArgs &a, const fl
     rec(4);
     if (a.prescore) CK(cudaStreamWaitEvent(s, e.ev_join, 0));
     if (e.stage == 1) {
-        launches += 2 + 2 + 1 + 3 + 1;  // reset, qprep, gather, ED seeds, scan, order x3, DTW
+        launches += 1 + 2 + 1 + 3 + 1;  // qprep, gather, ED seeds, scan, order x3, DTW
         *launches_out = launches;
         return DTWS_OK;
     }
     if (a.xz_z > 0) CK(launch_xz_finalize(b, a, idx_d, dist_d, s));
     else CK(launch_finalize(b, a, idx_d, dist_d, s));
     rec(5);
-    launches += 2 + 2 + 1 + 3 + 1 + 3;  // reset, qprep, gather, ED seeds, scan, order x3, DTW, final x3
+    launches += 1 + 2 + 1 + 3 + 1 + 3;  // qprep, gather, ED seeds, scan, order x3, DTW, final x3
     *launches_out = launches;
     return DTWS_OK;
 }

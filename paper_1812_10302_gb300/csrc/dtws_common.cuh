@@ -35,6 +35,12 @@ constexpr int kSeedMax = 128;       // random seeds + proxy proposals
 constexpr int kPropMax = 64;
 constexpr int kCtaSlots = 1024;     // per-CTA best windows of one proposal scan (at most this many CTAs)
 constexpr int kProxyStride = 2;     // the proxy scan looks at every other window
+// Euclidean seeds around each proxy proposal: offsets within +-kProxyHalf.
+// A match at an odd offset is never scored by the proxy itself; on a series
+// with strong per-sample noise the proxy can rank a window three samples off
+// above one sample off (one noisy copy of m = 1024 on the 2e7-sample walk
+// with bursts did), so the seeds reach three samples either side.
+constexpr int kProxyHalf = 3;
 // Euclidean seeds: random windows + the neighbourhoods of the proposals
 // (+-1 window for the proxy scan; +-b/2, b <= 128, for the learned scan with
 // at most kLearnPropMax proposals)

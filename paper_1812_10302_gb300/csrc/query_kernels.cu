@@ -41,7 +41,9 @@
 namespace dtws {
 
 // ------------------------------------------------------------------ reset
-__global__ void k_query_reset(QueryState *st) {
+// Clear a query's device state (by every thread of one block; the caller
+// synchronises the block before any of it is read).
+__device__ __forceinline__ void reset_state(QueryState *st) {
     for (int t = threadIdx.x; t < kListMax; t += blockDim.x) st->res_keys[t] = kEmptyKey;
     for (int t = threadIdx.x; t < kKMax; t += blockDim.x) st->seed_keys[t] = kEmptyKey;
     for (int t = threadIdx.x; t < kPropMax; t += blockDim.x) st->prop_keys[t] = kEmptyKey;
@@ -71,6 +73,8 @@ __global__ void k_query_reset(QueryState *st) {
     }
 }
 
+__global__ void k_query_reset(QueryState *st) { reset_state(st); }
+
 cudaError_t launch_query_reset(const QueryBufs &b, const QueryArgs &, cudaStream_t s) {
     k_query_reset<<<1, 1024, 0, s>>>(b.st);
     return cudaGetLastError();
@@ -90,6 +94,8 @@ __global__ void __launch_bounds__(1024) k_qprep(const float *__restrict__ Q, Que
     unsigned long long *keys = (unsigned long long *)smraw;
     float *qs = (float *)(keys + P);
 
+    // the query's state starts clear (this kernel opens every query)
+    reset_state(b.st);
     if (threadIdx.x == 0) bad = 0;
     __syncthreads();
     bool nf = false;
@@ -1099,15 +1105,17 @@ static cudaError_t dtw64_dispatch(const QueryBufs &b, const QueryArgs &a, const 
                                                                              count_for_grid, s);
         DTWS_MW(2) DTWS_MW(3) DTWS_MW(4) DTWS_MW(6) DTWS_MW(8) DTWS_MW(10) DTWS_MW(12) DTWS_MW(16)
 #undef DTWS_MW
-    } else if (a.r > kDiagRMax && a.r < 4 * 32 * 16) {
+    } else if (a.r > kDiagRMax && a.r < 8 * 32 * 8) {
         // bands past the one-warp walks (r > 511, up to 2047): the double-float
-        // walk over four warps with up to 16 cells per lane, instead of FP64
-        // arithmetic, which this part issues at a small fraction of its FP32 rate
-        const int k2 = (a.r + 1 + 127) / 128;
-        if (k2 <= 6) mw = dtw64_mw_launch<4, 6>(b, a, offsets, count, out, count_for_grid, s);
-        else if (k2 <= 8) mw = dtw64_mw_launch<4, 8>(b, a, offsets, count, out, count_for_grid, s);
-        else if (k2 <= 12) mw = dtw64_mw_launch<4, 12>(b, a, offsets, count, out, count_for_grid, s);
-        else mw = dtw64_mw_launch<4, 16>(b, a, offsets, count, out, count_for_grid, s);
+        // walk over four warps (r <= 1023) or eight (a window's walk is latency:
+        // more warps, fewer cells per lane per anti-diagonal) with up to 8
+        // cells per lane, instead of FP64 arithmetic, which this part issues
+        // at a small fraction of its FP32 rate
+        const int k4 = (a.r + 1 + 127) / 128, k8 = (a.r + 1 + 255) / 256;
+        if (k4 <= 6) mw = dtw64_mw_launch<4, 6>(b, a, offsets, count, out, count_for_grid, s);
+        else if (k4 <= 8) mw = dtw64_mw_launch<4, 8>(b, a, offsets, count, out, count_for_grid, s);
+        else if (k8 <= 6) mw = dtw64_mw_launch<8, 6>(b, a, offsets, count, out, count_for_grid, s);
+        else mw = dtw64_mw_launch<8, 8>(b, a, offsets, count, out, count_for_grid, s);
     }
     if (mw != cudaErrorNotSupported) return mw;
     // (the shared-memory copies do not fit: the one-group kernels below)

@@ -189,3 +189,43 @@ def test_trained_encoder_gains_over_random_seeding():
     assert seed_hit["trained"] >= seed_hit["untrained"]
     assert seed_hit["trained"] >= 0.9
     del offs
+
+
+@pytest.mark.skipif(not os.path.exists(train.DEFAULT_WEIGHTS), reason="no trained encoder weights committed")
+def test_seeding_by_proposal_count():
+    """How well each seeding finds the answer's neighbourhood as the number of
+    proposals shrinks: the trained encoder, an untrained (random) one and the
+    proxy scan, with 1, 2, 4 and 16 proposals, on 32 queries of the learned
+    workload's kind (8e6 samples).  A query counts when its best seed is no
+    worse than the answer window's own Euclidean distance.  The answers are
+    the same in every case; the counts are printed (they are the record of
+    what training buys), and at the default 16 proposals every seeding must
+    reach the answer for at least 90% of the queries and the trained encoder
+    must be no worse than the untrained one."""
+    w = synth.workload("learn", n=8_000_000)
+    x, qs = w["series"], w["queries"][:32]
+    r = w["rs"][0]
+    hits = {}
+    with dtws.Index(x) as ix:
+        ix.set_options(seed_proposals=0)
+        base = [ix.query(q, r, 1) for q in qs]
+        ed = np.array([oracle.dtw_at(x, q, 0, a[0])[0] for q, a in zip(qs, base)])
+        for P in (1, 2, 4, 16):
+            for name in ("proxy", "trained", "untrained"):
+                if name == "proxy":
+                    ix.set_options(ordering=dtws.DTWS_ORDER_PLAIN, seed_proposals=P)
+                else:
+                    ix.set_encoder(train.load_weights() if name == "trained" else train.init_params(0))
+                    ix.set_options(ordering=dtws.DTWS_ORDER_LEARNED, seed_proposals=P)
+                got = 0
+                for q, e, a in zip(qs, ed, base):
+                    idx, dist = ix.query(q, r, 1)
+                    assert ix.sync_status() == dtws.DTWS_OK
+                    np.testing.assert_array_equal(idx, a[0])
+                    got += ix.last_stats()["seed_bsf"] <= e * (1 + 1e-4) + 1e-6
+                hits[(P, name)] = got
+    print("queries (of 32) whose best seed reached the answer's Euclidean distance:",
+          {f"P={P} {n}": v for (P, n), v in hits.items()})
+    for name in ("proxy", "trained", "untrained"):
+        assert hits[(16, name)] >= 29
+    assert hits[(16, "trained")] >= hits[(16, "untrained")]

@@ -98,7 +98,7 @@ struct dtws_ctx {
     int device = 0, num_sms = 0;
     int64_t n = 0, n_alloc = 0;
     float *x = nullptr;
-    float *x_even = nullptr;             // x[2j] for j < n_alloc/2, plus a zero tail
+    float *x_sub = nullptr;              // x[kProxyStride j] for j < n_alloc/kProxyStride, plus a zero tail
     float *pf = nullptr, *bf = nullptr;  // prefix sums as FP32 pairs, block totals and anchors
     int *pok = nullptr;                  // per-block flag: the pairs carry the block
     float *pscale = nullptr;             // [0]: the series' power-of-two scale; [1]: scratch
@@ -483,7 +483,7 @@ QueryBufs make_bufs(dtws_t h, const StatsEntry *se, const EnvEntry *ee) {
     memset(&b, 0, sizeof b);  // padding included: the bytes enter graph signatures
     b.st = h->st;
     b.x = h->x;
-    b.x_even = h->x_even;
+    b.x_sub = h->x_sub;
     b.mu_hi = se ? se->mu_hi : nullptr;
     b.mu_lo = se ? se->mu_lo : nullptr;
     b.inv_sigma = se ? se->inv_sigma : nullptr;
@@ -654,13 +654,15 @@ dtws_status enqueue_search(dtws_t h, const Exec &e, const QueryArgs &a, const fl
         CK(launch_prop_merge(b, c0, c1, P, s));
         half = learn_half(m);
         launches += 3;
-    } else if (P > 0) {
-        int c0 = 0;
-        CK(launch_seed_scan(b, a, P, h->opt.proxy_terms, &c0, s));
-        CK(launch_prop_merge(b, c0, 0, P, s));
-        launches += 2;
     }
-    CK(launch_seed_gather(b, a, R, P, half, h->opt.rng_seed, s));
+    if (P > 0 && !e.le) {  // (the proxy scan merges its proposals and gathers the seeds itself)
+        int c0 = 0;
+        CK(launch_seed_scan(b, a, P, h->opt.proxy_terms, R, half, h->opt.rng_seed, &c0, s));
+        ++launches;
+    } else {
+        CK(launch_seed_gather(b, a, R, P, half, h->opt.rng_seed, s));
+        ++launches;
+    }
     CK(launch_seed_ed(b, a, s));
     if (k > 1 && a.xz_z == 0) {  // exact DTW seeds tighten a k-th bound the Euclidean seeds leave loose
         // (the neighbours of one match, which is all these seeds are, bound
@@ -690,14 +692,14 @@ dtws_status enqueue_search(dtws_t h, const Exec &e, const QueryArgs &a, const fl
     rec(4);
     if (a.prescore) CK(cudaStreamWaitEvent(s, e.ev_join, 0));
     if (e.stage == 1) {
-        launches += 1 + 2 + 1 + 3 + 1;  // qprep, gather, ED seeds, scan, order x3, DTW
+        launches += 1 + 1 + 1 + 2 + 1;  // qprep, ED seeds, scan, order x2, DTW
         *launches_out = launches;
         return DTWS_OK;
     }
     if (a.xz_z > 0) CK(launch_xz_finalize(b, a, idx_d, dist_d, s));
     else CK(launch_finalize(b, a, idx_d, dist_d, s));
     rec(5);
-    launches += 1 + 2 + 1 + 3 + 1 + 3;  // qprep, gather, ED seeds, scan, order x3, DTW, final x3
+    launches += 1 + 1 + 1 + 2 + 1 + 3;  // qprep, ED seeds, scan, order x2, DTW, final x3
     *launches_out = launches;
     return DTWS_OK;
 }
@@ -1289,7 +1291,7 @@ dtws_status dtws_destroy(dtws_t h) {
     for (auto &l : h->lanes) free_lane(l);
     if (h->batch_fork) cudaEventDestroy(h->batch_fork);
     if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
-    void *ptrs[] = {h->x, h->x_even, h->pf, h->bf, h->pok, h->pscale, h->envst, h->absmax, h->st, h->status, h->qh32, h->Uq,
+    void *ptrs[] = {h->x, h->x_sub, h->pf, h->bf, h->pok, h->pscale, h->envst, h->absmax, h->st, h->status, h->qh32, h->Uq,
                     h->Lq, h->sq, h->sU, h->sL, h->qh64, h->ord, h->cand_lb, h->sort_lb,
                     h->cand_idx, h->sort_idx, h->stage, h->xz_buf, h->xz_sel, h->xz_d64, h->bq_st, h->bq_f, h->bq_d, h->bq_o, h->pool.idx,
                     h->pool.lb, h->pool.mh, h->pool.is, h->pool.ls, h->pool.cursor, h->pq_dev, h->plist_dev};
@@ -1334,7 +1336,7 @@ dtws_status dtws_create(const float *series, int64_t n, void *stream, dtws_t *ou
     h->n_alloc = round_up(n, kProxyTile) + kMMax + 64;
     const int64_t nb = (n + kBlockB - 1) / kBlockB;
     CKF(dalloc(&h->x, h->n_alloc));
-    CKF(dalloc(&h->x_even, h->n_alloc / 2 + kProxyTile));
+    CKF(dalloc(&h->x_sub, h->n_alloc / kProxyStride + kProxyTile));
     CKF(dalloc(&h->pf, 4 * n));
     CKF(dalloc(&h->bf, 5 * nb));
     CKF(dalloc(&h->pok, nb));
@@ -1358,8 +1360,8 @@ dtws_status dtws_create(const float *series, int64_t n, void *stream, dtws_t *ou
         set_err("series contains NaN or Inf");
         return fail(DTWS_ENONFINITE);
     }
-    CKF(cudaMemsetAsync(h->x_even, 0, (h->n_alloc / 2 + kProxyTile) * 4, s));
-    CKF(launch_even(h->x, h->n_alloc / 2, h->x_even, h->num_sms, s));
+    CKF(cudaMemsetAsync(h->x_sub, 0, (h->n_alloc / kProxyStride + kProxyTile) * 4, s));
+    CKF(launch_subsample(h->x, h->n_alloc / kProxyStride, h->x_sub, h->num_sms, s));
     CKF(launch_prefix(h->x, n, h->pf, h->bf, h->pok, reinterpret_cast<unsigned *>(h->pscale + 1), h->pscale, s));
     CKF(launch_block_envelope(h->x, n, h->envst, h->nblk, s));
     CKF(cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking));

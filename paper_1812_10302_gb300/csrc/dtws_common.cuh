@@ -34,15 +34,17 @@ constexpr int kListMax = 128;       // result list capacity (k + near-tie margin
 constexpr int kSeedMax = 128;       // random seeds + proxy proposals
 constexpr int kPropMax = 64;
 constexpr int kCtaSlots = 1024;     // per-CTA best windows of one proposal scan (at most this many CTAs)
-constexpr int kProxyStride = 2;     // the proxy scan looks at every other window
+constexpr int kProxyStride = 4;     // the proxy scan looks at every fourth window
 // Euclidean seeds around each proxy proposal: offsets within +-kProxyHalf.
-// A match at an odd offset is never scored by the proxy itself; on a series
-// with strong per-sample noise the proxy can rank a window three samples off
-// above one sample off (one noisy copy of m = 1024 on the 2e7-sample walk
-// with bursts did), so the seeds reach three samples either side.
+// A match off the proxy's grid is never scored by the proxy itself; on a
+// series with strong per-sample noise the proxy can also rank a window a few
+// samples off above the nearest one (one noisy copy of m = 1024 on the
+// 2e7-sample walk with bursts did), so the seeds reach three samples either
+// side: with one window in four scored, every window lies within two of a
+// scored one.
 constexpr int kProxyHalf = 3;
 // Euclidean seeds: random windows + the neighbourhoods of the proposals
-// (+-1 window for the proxy scan; +-b/2, b <= 128, for the learned scan with
+// (+-kProxyHalf windows for the proxy scan; +-b/2, b <= 128, for the learned scan with
 // at most kLearnPropMax proposals)
 constexpr int kLearnPropMax = 64;
 // per-series block envelope: sparse table of max / min over blocks of
@@ -116,6 +118,9 @@ struct QueryState {
     // batch: the survivors went to the persistent stage's pool at pool_off
     int deferred;
     long long pool_off;
+    // CTAs of the proxy scan and of the survivor histogram that have
+    // finished: the last one of each takes the step that needs all of them
+    unsigned int prop_done, bin_done;
 };
 
 // Scalars of one query, passed by value to every kernel.

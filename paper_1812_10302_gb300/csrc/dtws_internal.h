@@ -17,7 +17,7 @@ void set_error_detail(const char *fmt, ...);
 cudaError_t launch_check_finite(const float *x, int64_t n, int *flag, unsigned *absmax, cudaStream_t s);
 cudaError_t launch_fill(float *p, int64_t count, float v, int num_sms, cudaStream_t s);
 // xe[j] = x[2j], j < count
-cudaError_t launch_even(const float *x, int64_t count, float *xe, int num_sms, cudaStream_t s);
+cudaError_t launch_subsample(const float *x, int64_t count, float *xs, int num_sms, cudaStream_t s);
 // pf: 4*n floats (P1 hi, P1 lo, P2 hi, P2 lo); bf: 5*nb floats (T1 hi, lo,
 // T2 hi, lo, anchors); ok: nb flags; nb = ceil(n / kBlockB); maxabs: one
 // word of scratch; scale: one float (the series' power-of-two scale)
@@ -34,7 +34,7 @@ cudaError_t launch_block_envelope(const float *x, int64_t n, float *st, int64_t 
 struct QueryBufs {
     QueryState *st;
     const float *x;              // padded series
-    const float *x_even;         // its even samples (the proxy scan's copy)
+    const float *x_sub;          // its every kProxyStride-th sample (the proxy scan's copy)
     const float *mu_hi, *mu_lo, *inv_sigma;  // window stats for m
     const float *smu_hi, *sinv_sigma;  // mean (high part) and 1/sigma of every kProxyStride-th window
     const float *U, *L;          // exact series envelope for r, or null:
@@ -151,9 +151,11 @@ struct SurvPool {
 cudaError_t launch_query_reset(const QueryBufs &b, const QueryArgs &a, cudaStream_t s);
 cudaError_t launch_qprep(const float *Q, const QueryBufs &b, const QueryArgs &a, cudaStream_t s);
 // proposal scans: each CTA writes its best window to cta_best[slot * kCtaSlots + cta];
-// *ctas receives the grid size; launch_prop_merge then keeps the best `proposals`
-cudaError_t launch_seed_scan(const QueryBufs &b, const QueryArgs &a, int proposals, int terms, int *ctas,
-                             cudaStream_t s);
+// *ctas receives the grid size; launch_prop_merge then keeps the best `proposals`.
+// The proxy scan does that merge itself, and the seed lists (launch_seed_gather
+// with n_random, H and rng), in the last of its CTAs to finish.
+cudaError_t launch_seed_scan(const QueryBufs &b, const QueryArgs &a, int proposals, int terms, int n_random, int H,
+                             unsigned long long rng, int *ctas, cudaStream_t s);
 // half: Euclidean seeds cover the proposals' offsets +-half
 cudaError_t launch_seed_gather(const QueryBufs &b, const QueryArgs &a, int n_random,
                                int proposals, int half, unsigned long long rng, cudaStream_t s);

@@ -58,6 +58,8 @@ __device__ __forceinline__ void reset_state(QueryState *st) {
         st->xz_lock[1] = 0;
         st->deferred = 0;
         st->pool_off = 0;
+        st->prop_done = 0;
+        st->bin_done = 0;
         st->n_seeds = 0;
         st->n_cand = 0;
         st->work = 0;
@@ -249,8 +251,9 @@ cudaError_t launch_qprep(const float *Q, const QueryBufs &b, const QueryArgs &a,
 // Two stage layouts.  LbLayout<TW>: TW windows with the statistics (mean as
 // a hi + lo pair, 1/sigma) of every window and all their samples (the
 // lower-bound scan).  ProxyLayout: kProxyTile windows with the mean's high
-// part and 1/sigma of every kProxyStride-th window and only the even samples
-// (the proxy scan scores even windows at even term positions; no ml array).
+// part and 1/sigma of every kProxyStride-th window and only every
+// kProxyStride-th sample (the proxy scan scores those windows at term
+// positions that are multiples of kProxyStride; no ml array).
 template <int TW>
 struct LbLayout {
     static constexpr int W = TW, S = TW, kStride = 1, NS = 3, XDIV = 1;
@@ -260,8 +263,9 @@ struct LbLayout {
     __device__ static const float *is(const QueryBufs &b) { return b.inv_sigma; }
 };
 struct ProxyLayout {
-    static constexpr int W = kProxyTile, S = kProxyTile / kProxyStride, kStride = kProxyStride, NS = 2, XDIV = 2;
-    __device__ static const float *xs(const QueryBufs &b) { return b.x_even; }
+    static constexpr int W = kProxyTile, S = kProxyTile / kProxyStride, kStride = kProxyStride, NS = 2,
+                         XDIV = kProxyStride;
+    __device__ static const float *xs(const QueryBufs &b) { return b.x_sub; }
     __device__ static const float *mh(const QueryBufs &b) { return b.smu_hi; }
     __device__ static const float *ml(const QueryBufs &) { return nullptr; }
     __device__ static const float *is(const QueryBufs &b) { return b.sinv_sigma; }
@@ -275,7 +279,7 @@ struct Tile {
 
 constexpr int kStageHeader = 32;  // full, empty barriers and the tile index
 
-// samples staged per tile: W + m - 1, or the even ones of them
+// samples staged per tile: W + m - 1, or every XDIV-th of them
 template <class LY>
 __host__ __device__ __forceinline__ unsigned tile_x_floats(int m) {
     return (unsigned)(((LY::W + m - 1 + LY::XDIV - 1) / LY::XDIV + 3) & ~3);
@@ -317,9 +321,10 @@ constexpr int kScanThreads = (kScanConsumers + 1) * 32;  // + one producer warp
 
 // Runs process(tile, i0) in every consumer warp for each tile this CTA takes
 // from *cursor.  A wait that runs past the bound records DTWS_ETIMEOUT and
-// ends the loop for that warp (the other warps' waits then run out too).
+// ends the loop for that warp (the other warps' waits then run out too);
+// the thread's return value is false then.
 template <class LY, typename F>
-__device__ void tile_pipeline(unsigned char *sm, const QueryBufs &b, int m, int64_t ntiles,
+__device__ bool tile_pipeline(unsigned char *sm, const QueryBufs &b, int m, int64_t ntiles,
                               unsigned long long *cursor, int kS, F &&process) {
     const int warp = threadIdx.x >> 5, lane = lane_id();
     if (threadIdx.x == 0) {
@@ -384,6 +389,7 @@ __device__ void tile_pipeline(unsigned char *sm, const QueryBufs &b, int m, int6
         }
     }
     if (!ok) atomicOr(b.status, kStTimeout);
+    return ok;
 }
 
 static int scan_grid(const void *kernel, int threads, size_t smem, int num_sms, int64_t ntiles) {
@@ -418,18 +424,19 @@ static int scan_stages(const void *kernel, size_t stage_bytes, int min_stages, s
 }
 
 // ------------------------------------------------------------------ proxy scan
-// For every other window: the squared distance on TERMS evenly spaced query
-// positions (not a lower bound: it only proposes windows whose exact
-// distances seed the best-so-far).  Spread-out positions make the terms
+// For every kProxyStride-th window: the squared distance on TERMS evenly
+// spaced query positions (not a lower bound: it only proposes windows whose
+// exact distances seed the best-so-far).  Spread-out positions make the terms
 // nearly independent, so a random window scores near 2*TERMS while a window
-// within a sample of a noisy copy scores far lower.  Each thread keeps its best window over
-// all the tiles it scans; each CTA proposes its best.  Scoring one window in
-// two, with the mean's high part and 1/sigma of those windows only, and with
-// every term position even so that only the series' even samples are read,
-// the scan moves 6 bytes per window (2 of samples, 4 of statistics) instead
-// of 16; the seed step then covers the neighbours of each proposal.  (With
-// one window in eight, a window four samples off a match scored no better
-// than lucky random windows and matches were lost.)
+// within a sample or two of a noisy copy scores far lower.  Each thread keeps
+// its best window over all the tiles it scans; each CTA proposes its best.
+// Scoring one window in four, with the mean's high part and 1/sigma of those
+// windows only, and with every term position a multiple of four so that only
+// every fourth sample of the series is read, the scan moves 3 bytes per
+// window (1 of samples, 2 of statistics) instead of 16; the seed step then
+// covers the neighbours of each proposal.  (With one window in eight, a
+// window four samples off a match scored no better than lucky random windows
+// and matches were lost.)
 // Packed FP32 pairs (sm_100 family): one instruction does the operation on
 // both halves, each half rounded exactly as the scalar operation would be.
 __device__ __forceinline__ unsigned long long x2_pack(float lo, float hi) {
@@ -462,8 +469,17 @@ __device__ __forceinline__ float lds_at(unsigned addr) {
     return v;
 }
 
+__device__ void prop_rank_select(QueryState *st, const unsigned long long *keys, int n, int first, int stride,
+                                 int proposals);
+__device__ void seed_lists(const QueryBufs &b, const QueryArgs &a, int n_random, int proposals, int H,
+                           unsigned long long rng, unsigned *cand, int *wcnt, int *total);
+
+// The last CTA of the scan to finish (a completion count; nothing waits)
+// then merges every CTA's best into the proposals and builds the seed
+// lists, the work of k_prop_merge and k_seed_gather without their launches.
 template <int TERMS>
-__global__ void __launch_bounds__(kScanThreads) k_seed_scan(QueryBufs b, QueryArgs a, int proposals, int stages) {
+__global__ void __launch_bounds__(kScanThreads) k_seed_scan(QueryBufs b, QueryArgs a, int proposals, int stages,
+                                                            int n_random, int H, unsigned long long rng) {
     static_assert(TERMS % 2 == 0, "terms are taken in pairs");
     constexpr int kPer = kScanConsumers * 32;           // scored windows per pass of the CTA
     constexpr int kIt = ProxyLayout::S / kPer;          // passes per tile
@@ -472,11 +488,12 @@ __global__ void __launch_bounds__(kScanThreads) k_seed_scan(QueryBufs b, QueryAr
     __shared__ unsigned long long wbest[kScanConsumers + 1];
     if (!b.st->valid) return;
     const int m = a.m;
-    // Term positions, evenly spread, each rounded down to an even position
-    // (the scored windows are the even ones, so their term samples are all
-    // even: the stage holds only the series' even samples).  Lane l scores
-    // window 2l (+ const), whose term sample p sits at even sample l + p/2:
-    // consecutive words across the warp, so every load is conflict-free.
+    // Term positions, evenly spread, each rounded down to a multiple of
+    // kProxyStride (the scored windows are those at multiples of kProxyStride,
+    // so their term samples are too: the stage holds only those samples).
+    // Lane l scores window kProxyStride*l (+ const), whose term sample p sits
+    // at staged sample l + p/kProxyStride: consecutive words across the warp,
+    // so every load is conflict-free.
     unsigned poff[TERMS];
     unsigned long long qv2[TERMS / 2];
 #pragma unroll
@@ -486,19 +503,19 @@ __global__ void __launch_bounds__(kScanThreads) k_seed_scan(QueryBufs b, QueryAr
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
             const int u = 2 * j + h;
-            const int pu = (int)(((2 * u + 1) * (long long)m) / (2 * TERMS)) & ~1;
+            const int pu = (int)(((2 * u + 1) * (long long)m) / (2 * TERMS)) & ~(kProxyStride - 1);
             p[h] = pu;
             q[h] = b.qh32[pu];
         }
-        poff[2 * j] = 2u * (unsigned)p[0];  // bytes: 4 * (p / 2)
-        poff[2 * j + 1] = 2u * (unsigned)p[1];
+        poff[2 * j] = 4u * (unsigned)(p[0] / kProxyStride);  // bytes
+        poff[2 * j + 1] = 4u * (unsigned)(p[1] / kProxyStride);
         qv2[j] = x2_pack(q[0], q[1]);
     }
     unsigned long long best = kEmptyKey;
     const int64_t ntiles = (a.N + ProxyLayout::W - 1) / ProxyLayout::W;
-    tile_pipeline<ProxyLayout>(smraw, b, m, ntiles, &b.st->tile_ctr[0], stages, [&](const Tile &t, int64_t i0) {
-        // window w = 2v, v = threadIdx.x + it * kPer: its (even) samples from
-        // byte offset 4v in xs, its statistics at 4v in mh / is.  Two
+    const bool piped = tile_pipeline<ProxyLayout>(smraw, b, m, ntiles, &b.st->tile_ctr[0], stages, [&](const Tile &t, int64_t i0) {
+        // window w = kProxyStride*v, v = threadIdx.x + it * kPer: its staged
+        // samples from byte offset 4v in xs, its statistics at 4v in mh / is.  Two
         // windows (it, it + kIt/2) at a time, each with two partial sums,
         // so four independent FMA chains are in flight.
         const unsigned xa = smem_u32(t.xs) + 4u * threadIdx.x;
@@ -572,38 +589,60 @@ __global__ void __launch_bounds__(kScanThreads) k_seed_scan(QueryBufs b, QueryAr
         best = v < best ? v : best;
     }
     if (lane_id() == 0) wbest[threadIdx.x >> 5] = best;
-    __syncthreads();
+    __shared__ int last, wcnt[kScanConsumers + 2], total;
+    // (every copy into the stages has landed unless a wait ran out)
+    const bool all_ok = __syncthreads_and(piped);
     if (threadIdx.x == 0) {
         for (int w = 1; w < (int)(blockDim.x >> 5); ++w) best = wbest[w] < best ? wbest[w] : best;
         b.st->cta_best[blockIdx.x] = best;
+        __threadfence();
+        last = atomicAdd(&b.st->prop_done, 1u) == gridDim.x - 1;
     }
-    (void)proposals;
+    __syncthreads();
+    if (!last || !all_ok) return;  // (a timed-out query ends with an error)
+    __threadfence();
+    // the stages are idle: the data part of stage 0 (past its barriers,
+    // which stay untouched) holds the keys, then the candidates
+    unsigned char *spare = smraw + kStageHeader;
+    unsigned long long *keys = reinterpret_cast<unsigned long long *>(spare);
+    const int n = (int)gridDim.x, n8 = (n + 7) & ~7;
+    for (int t = threadIdx.x; t < n8; t += blockDim.x) keys[t] = t < n ? __ldcg(&b.st->cta_best[t]) : kEmptyKey;
+    __syncthreads();
+    prop_rank_select(b.st, keys, n, threadIdx.x, blockDim.x, proposals);
+    __syncthreads();
+    seed_lists(b, a, n_random, proposals, H, rng, reinterpret_cast<unsigned *>(spare), wcnt, &total);
 }
 
 template <int TERMS>
-static cudaError_t launch_seed_scan_t(const QueryBufs &b, const QueryArgs &a, int proposals, int *ctas,
-                                      cudaStream_t s) {
+static cudaError_t launch_seed_scan_t(const QueryBufs &b, const QueryArgs &a, int proposals, int n_random, int H,
+                                      unsigned long long rng, int *ctas, cudaStream_t s) {
     size_t smem = 0;
     const int stages = scan_stages((const void *)k_seed_scan<TERMS>, stage_bytes<ProxyLayout>(a.m), 2, &smem);
+    // the last CTA's keys and candidates fit in the data part of stage 0
+    const size_t tail = (size_t)(kCtaSlots + 8) * 8 > (size_t)(n_random + proposals * (2 * H + 1)) * 4
+                            ? (size_t)(kCtaSlots + 8) * 8
+                            : (size_t)(n_random + proposals * (2 * H + 1)) * 4;
+    if (stage_bytes<ProxyLayout>(a.m) < kStageHeader + tail) return cudaErrorInvalidValue;
     cudaError_t e = cudaFuncSetAttribute(k_seed_scan<TERMS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     const int64_t tiles = (a.N + ProxyLayout::W - 1) / ProxyLayout::W;
     int grid = scan_grid((const void *)k_seed_scan<TERMS>, kScanThreads, smem, b.num_sms, tiles);
     if (grid > kCtaSlots) grid = kCtaSlots;
-    k_seed_scan<TERMS><<<grid, kScanThreads, smem, s>>>(b, a, proposals, stages);
+    k_seed_scan<TERMS><<<grid, kScanThreads, smem, s>>>(b, a, proposals, stages, n_random, H, rng);
     *ctas = grid;
     return cudaGetLastError();
 }
 
-cudaError_t launch_seed_scan(const QueryBufs &b, const QueryArgs &a, int proposals, int terms, int *ctas,
-                             cudaStream_t s) {
+cudaError_t launch_seed_scan(const QueryBufs &b, const QueryArgs &a, int proposals, int terms, int n_random, int H,
+                             unsigned long long rng, int *ctas, cudaStream_t s) {
     *ctas = 0;
-    if (proposals <= 0) return cudaSuccess;
+    if (proposals <= 0 || proposals > kPropMax || n_random + proposals * (2 * H + 1) > kEdMax)
+        return cudaErrorInvalidValue;
     // evenly spaced positions, so never more terms than m
-    if (terms >= 16 && a.m >= 16) return launch_seed_scan_t<16>(b, a, proposals, ctas, s);
-    if (terms >= 8 && a.m >= 8) return launch_seed_scan_t<8>(b, a, proposals, ctas, s);
-    if (terms >= 4 && a.m >= 4) return launch_seed_scan_t<4>(b, a, proposals, ctas, s);
-    return launch_seed_scan_t<2>(b, a, proposals, ctas, s);
+    if (terms >= 16 && a.m >= 16) return launch_seed_scan_t<16>(b, a, proposals, n_random, H, rng, ctas, s);
+    if (terms >= 8 && a.m >= 8) return launch_seed_scan_t<8>(b, a, proposals, n_random, H, rng, ctas, s);
+    if (terms >= 4 && a.m >= 4) return launch_seed_scan_t<4>(b, a, proposals, n_random, H, rng, ctas, s);
+    return launch_seed_scan_t<2>(b, a, proposals, n_random, H, rng, ctas, s);
 }
 
 // The proposals: the `proposals` smallest of the per-CTA best windows of one
@@ -611,9 +650,32 @@ cudaError_t launch_seed_scan(const QueryBufs &b, const QueryArgs &a, int proposa
 // ctas1-1), ascending.  The CTAs cover disjoint windows, so the keys other
 // than the empty key are distinct: each key's rank is the number of keys
 // below it, and a key of rank < proposals goes to that slot (the list was
-// emptied by the query reset; empty keys are not written).  128 keys per
-// CTA (one per thread), each CTA with its own copy of all the keys in shared
-// memory, eight keys per step in four independent 16-byte loads.
+// emptied by the query reset; empty keys are not written).  keys[0 .. n8)
+// in shared memory, n8 = n rounded up to 8 (the padding empty); this thread
+// ranks keys first, first + stride, ..., eight keys per step in four
+// independent 16-byte loads.
+__device__ void prop_rank_select(QueryState *st, const unsigned long long *keys, int n, int first, int stride,
+                                 int proposals) {
+    const int n8 = (n + 7) & ~7;
+    const ulonglong2 *k2 = reinterpret_cast<const ulonglong2 *>(keys);
+    for (int t = first; t < n; t += stride) {
+        const unsigned long long k = keys[t];
+        if (k == kEmptyKey) continue;
+        int r0 = 0, r1 = 0, r2 = 0, r3 = 0;
+        for (int u = 0; u < n8 / 2; u += 4) {
+            const ulonglong2 a = k2[u], c = k2[u + 1], d = k2[u + 2], e = k2[u + 3];
+            r0 += (a.x < k) + (a.y < k);
+            r1 += (c.x < k) + (c.y < k);
+            r2 += (d.x < k) + (d.y < k);
+            r3 += (e.x < k) + (e.y < k);
+        }
+        const int rank = r0 + r1 + r2 + r3;
+        if (rank < proposals) st->prop_keys[rank] = k;
+    }
+}
+
+// 128 keys per CTA (one per thread), each CTA with its own copy of all the
+// keys in shared memory.
 constexpr int kMergeThreads = 128;
 __global__ void __launch_bounds__(kMergeThreads) k_prop_merge(QueryBufs b, int n0, int n1, int proposals) {
     __shared__ __align__(16) unsigned long long keys[2 * kCtaSlots + 8];
@@ -624,20 +686,7 @@ __global__ void __launch_bounds__(kMergeThreads) k_prop_merge(QueryBufs b, int n
         keys[t] = t < n0 ? st->cta_best[t] : (t < n ? st->cta_best[kCtaSlots + (t - n0)] : kEmptyKey);
     __syncthreads();
     const int t = blockIdx.x * kMergeThreads + threadIdx.x;
-    if (t >= n) return;
-    const unsigned long long k = keys[t];
-    if (k == kEmptyKey) return;
-    int r0 = 0, r1 = 0, r2 = 0, r3 = 0;
-    const ulonglong2 *k2 = reinterpret_cast<const ulonglong2 *>(keys);
-    for (int u = 0; u < n8 / 2; u += 4) {
-        const ulonglong2 a = k2[u], c = k2[u + 1], d = k2[u + 2], e = k2[u + 3];
-        r0 += (a.x < k) + (a.y < k);
-        r1 += (c.x < k) + (c.y < k);
-        r2 += (d.x < k) + (d.y < k);
-        r3 += (e.x < k) + (e.y < k);
-    }
-    const int rank = r0 + r1 + r2 + r3;
-    if (rank < proposals) st->prop_keys[rank] = k;
+    if (t < n) prop_rank_select(st, keys, n, t, n, proposals);
 }
 
 cudaError_t launch_prop_merge(const QueryBufs &b, int ctas0, int ctas1, int proposals, cudaStream_t s) {
@@ -660,7 +709,7 @@ __device__ __forceinline__ unsigned long long splitmix64(unsigned long long z) {
 // Seed windows.  seed_off (exact DTW seeds, used when k > 1): the random
 // windows (the paper's random first bsf, Algorithm 1) and the proposals.
 // ed_off (Euclidean seeds): the random windows and, for each proposal, the
-// kProxyStride + 1 windows centred on it, since the proxy scan looked at
+// 2 * kProxyHalf + 1 windows centred on it, since the proxy scan looked at
 // every kProxyStride-th window only.  Both lists hold distinct offsets: a repeated seed
 // would fill two of the k slots with one window.
 // Append the distinct values of src[0..n) (0xffffffff: none) to dst after
@@ -714,11 +763,11 @@ __device__ int distinct_append(unsigned *dst, int cap, const unsigned *src, int 
     return *total < cap ? *total : cap;
 }
 
-__global__ void __launch_bounds__(1024) k_seed_gather(QueryBufs b, QueryArgs a, int n_random, int proposals, int H,
-                                                      unsigned long long rng) {
-    __shared__ __align__(16) unsigned cand[kEdMax];
-    __shared__ int wcnt[33], total;
-    if (!b.st->valid) return;
+// cand: room for n_random + proposals * (2H + 1) offsets (16-byte aligned);
+// wcnt: one int per warp of the block and one more.
+__device__ void seed_lists(const QueryBufs &b, const QueryArgs &a, int n_random, int proposals, int H,
+                           unsigned long long rng, unsigned *cand, int *wcnt, int *total_p) {
+    int &total = *total_p;
     // exact-DTW seeds: random windows + proposals
     for (int j = threadIdx.x; j < n_random; j += blockDim.x)
         cand[j] = (unsigned)(splitmix64(rng + (unsigned long long)j) % (unsigned long long)a.N);
@@ -749,6 +798,14 @@ __global__ void __launch_bounds__(1024) k_seed_gather(QueryBufs b, QueryArgs a, 
         b.st->n_ed = ne;
         b.st->work = 0;
     }
+}
+
+__global__ void __launch_bounds__(1024) k_seed_gather(QueryBufs b, QueryArgs a, int n_random, int proposals, int H,
+                                                      unsigned long long rng) {
+    __shared__ __align__(16) unsigned cand[kEdMax];
+    __shared__ int wcnt[33], total;
+    if (!b.st->valid) return;
+    seed_lists(b, a, n_random, proposals, H, rng, cand, wcnt, &total);
 }
 
 // Squared Euclidean distance of the normalised query and window (the
@@ -849,7 +906,6 @@ __global__ void k_wait_selftest(int *status, long long wait_ns) {
 // makes them.  No spin here is unbounded: the holder waits only for the
 // offer to return.
 __global__ void k_lock_selftest(QueryBufs b, QueryArgs a) {
-    __shared__ int held, offered;
     QueryState *st = b.st;
     if (threadIdx.x == 0) {
         for (int t = 0; t < 2 * kKMax; ++t) st->xz_keys[t / kKMax][t % kKMax] = kEmptyKey;
@@ -857,21 +913,11 @@ __global__ void k_lock_selftest(QueryBufs b, QueryArgs a) {
         st->xz_lock[1] = 0;
         st->xz_count = 0;
         __threadfence();
-        held = 1;
-        offered = 0;
     }
     __syncthreads();
-    if (threadIdx.x == 32) {  // another warp: bucket 0 has parity 0
-        xz_offer(b, a, make_key(1.0f, 0u), false);
-        atomicExch(&offered, 1);
-    }
+    if (threadIdx.x == 32) xz_offer(b, a, make_key(1.0f, 0u), false);  // another warp: bucket 0 has parity 0
     __syncthreads();
-    if (threadIdx.x == 0) {
-        atomicExch(&st->xz_lock[0], 0);
-        held = 0;
-    }
-    (void)offered;
-    (void)held;
+    if (threadIdx.x == 0) atomicExch(&st->xz_lock[0], 0);
 }
 
 cudaError_t launch_lock_selftest(const QueryBufs &b, const QueryArgs &a, cudaStream_t s) {
@@ -1349,8 +1395,13 @@ cudaError_t launch_lb_scan(const QueryBufs &b, const QueryArgs &a, cudaStream_t 
 // threshold the bins split [0, thr] evenly; otherwise they follow the
 // float's exponent and leading mantissa bits (monotone for lb >= 0).
 
-__global__ void k_bin_hist(QueryBufs b) {
+// The histogram over all CTAs; the last CTA to finish (a completion count,
+// nothing waits) turns it into each bin's first position.
+constexpr int kBinThreads = 512;
+__global__ void __launch_bounds__(kBinThreads) k_bin_hist(QueryBufs b) {
+    static_assert(kBins == 2 * kBinThreads, "two bins per thread in the prefix");
     __shared__ int h[kBins];
+    __shared__ int wsum[kBinThreads / 32], last;
     QueryState *st = b.st;
     for (int t = threadIdx.x; t < kBins; t += blockDim.x) h[t] = 0;
     __syncthreads();
@@ -1361,22 +1412,29 @@ __global__ void k_bin_hist(QueryBufs b) {
     __syncthreads();
     for (int t = threadIdx.x; t < kBins; t += blockDim.x)
         if (h[t]) atomicAdd(&st->hist[t], h[t]);
-}
-
-__global__ void __launch_bounds__(kBins) k_bin_scan(QueryState *st) {
-    __shared__ int wsum[kBins / 32];
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) last = atomicAdd(&st->bin_done, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    // exclusive prefix over the bins: thread t holds bins 2t and 2t + 1
     const int t = threadIdx.x, lane = t & 31, w = t >> 5;
-    int v = st->hist[t], inc = v;
+    const int v0 = __ldcg(&st->hist[2 * t]), v1 = __ldcg(&st->hist[2 * t + 1]);
+    const int v = v0 + v1;
+    int inc = v;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-        int u = __shfl_up_sync(0xffffffffu, inc, o);
+        const int u = __shfl_up_sync(0xffffffffu, inc, o);
         if (lane >= o) inc += u;
     }
     if (lane == 31) wsum[w] = inc;
     __syncthreads();
     int carry = 0;
     for (int q = 0; q < w; ++q) carry += wsum[q];
-    st->bin_off[t] = carry + inc - v;
+    const int base = carry + inc - v;
+    st->bin_off[2 * t] = base;
+    st->bin_off[2 * t + 1] = base + v0;
     if (t == 0) st->work2 = 0;
 }
 
@@ -1410,8 +1468,7 @@ __global__ void __launch_bounds__(512) k_bin_scatter(QueryBufs b) {
 
 cudaError_t launch_order(const QueryBufs &b, const QueryArgs &, cudaStream_t s) {
     int blocks = b.num_sms * 2;
-    k_bin_hist<<<blocks, 512, 0, s>>>(b);
-    k_bin_scan<<<1, kBins, 0, s>>>(b.st);
+    k_bin_hist<<<blocks, kBinThreads, 0, s>>>(b);
     k_bin_scatter<<<blocks, 512, 0, s>>>(b);
     return cudaGetLastError();
 }

@@ -51,18 +51,19 @@ cudaError_t launch_fill(float *p, int64_t count, float v, int num_sms, cudaStrea
     return cudaGetLastError();
 }
 
-// The series' even samples, xe[j] = x[2 j] for j < count (the proxy scan
-// scores every second window at even term positions, so it reads only these).
-__global__ void k_even(const float *__restrict__ x, int64_t count, float *__restrict__ xe) {
+// The series' every kProxyStride-th sample, xs[j] = x[kProxyStride j] for
+// j < count (the proxy scan scores every kProxyStride-th window at term
+// positions that are multiples of kProxyStride, so it reads only these).
+__global__ void k_subsample(const float *__restrict__ x, int64_t count, float *__restrict__ xs) {
     for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < count; j += (int64_t)gridDim.x * blockDim.x)
-        xe[j] = x[2 * j];
+        xs[j] = x[kProxyStride * j];
 }
 
-cudaError_t launch_even(const float *x, int64_t count, float *xe, int num_sms, cudaStream_t s) {
+cudaError_t launch_subsample(const float *x, int64_t count, float *xs, int num_sms, cudaStream_t s) {
     if (count <= 0) return cudaSuccess;
     int64_t blocks = (count + 255) / 256;
     if (blocks > 8LL * num_sms) blocks = 8LL * num_sms;
-    k_even<<<(int)blocks, 256, 0, s>>>(x, count, xe);
+    k_subsample<<<(int)blocks, 256, 0, s>>>(x, count, xs);
     return cudaGetLastError();
 }
 

@@ -118,9 +118,11 @@ struct dtws_ctx {
     float *cand_lb = nullptr, *sort_lb = nullptr;
     unsigned *cand_idx = nullptr, *sort_idx = nullptr;
     int64_t cand_cap = 0;
-    // staging of host arrays
+    // staging of host arrays: device side, and pinned host memory for results
     void *stage = nullptr;
     size_t stage_cap = 0;
+    void *hstage = nullptr;
+    size_t hstage_cap = 0;
     dtws_options opt;
     cudaStream_t last_stream = nullptr;
     QueryState *last_st = nullptr;  // the state the last query's counters are in
@@ -203,6 +205,36 @@ dtws_status ensure_stage(dtws_t h, size_t bytes) {
     CK(cudaMalloc(&p, cap));
     h->stage = p;
     h->stage_cap = cap;
+    return DTWS_OK;
+}
+
+// Host-bound results: one copy of the device region that holds them (in the
+// stage: offsets, then distances) into the pinned host stage, one wait, then
+// plain copies into the caller's arrays.  (Copies into pageable memory are
+// staged by the driver and wait on their own, once per array.)
+dtws_status read_back(dtws_t h, cudaStream_t s, const int64_t *idx_d, const float *dist_d, int64_t *out_idx,
+                      float *out_dist, size_t ib, size_t db, bool idev, bool ddev) {
+    if (idev && ddev) return DTWS_OK;
+    const char *lo = !idev ? (const char *)idx_d : (const char *)dist_d;
+    const char *hi = !ddev ? (const char *)dist_d + db : (const char *)idx_d + ib;
+    const size_t span = (size_t)(hi - lo);
+    if (h->hstage_cap < span) {
+        if (h->hstage) cudaFreeHost(h->hstage);
+        h->hstage = nullptr;
+        h->hstage_cap = 0;
+        const size_t cap = span < 4096 ? 4096 : span;
+        if (g_fail_allocs > 0) {
+            --g_fail_allocs;
+            return DTWS_ENOMEM;
+        }
+        CK(cudaMallocHost(&h->hstage, cap));
+        h->hstage_cap = cap;
+    }
+    CK(cudaMemcpyAsync(h->hstage, lo, span, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    const char *hs = (const char *)h->hstage;
+    if (!idev) memcpy(out_idx, hs + ((const char *)idx_d - lo), ib);
+    if (!ddev) memcpy(out_dist, hs + ((const char *)dist_d - lo), db);
     return DTWS_OK;
 }
 
@@ -1297,6 +1329,7 @@ dtws_status dtws_destroy(dtws_t h) {
                     h->pool.lb, h->pool.mh, h->pool.is, h->pool.ls, h->pool.cursor, h->pq_dev, h->plist_dev};
     for (void *p : ptrs)
         if (p) cudaFree(p);
+    if (h->hstage) cudaFreeHost(h->hstage);
     if (h->ev_ok)
         for (auto &e : h->ev) cudaEventDestroy(e);
     if (h->ev_fork) cudaEventDestroy(h->ev_fork);
@@ -1447,10 +1480,7 @@ dtws_status dtws_query(dtws_t h, const float *Q, int32_t m, int32_t r, int32_t k
     } else if ((st = run_query(h, Qd, m, r, k, idx_d, dist_d, s)) != DTWS_OK) {
         return st;
     }
-    if (!idev) CK(cudaMemcpyAsync(out_idx, idx_d, ib, cudaMemcpyDeviceToHost, s));
-    if (!ddev) CK(cudaMemcpyAsync(out_dist, dist_d, db, cudaMemcpyDeviceToHost, s));
-    if (!idev || !ddev) CK(cudaStreamSynchronize(s));
-    return DTWS_OK;
+    return read_back(h, s, idx_d, dist_d, out_idx, out_dist, ib, db, idev, ddev);
 }
 
 dtws_status dtws_query_batch(dtws_t h, const float *Q_cat, const int64_t *q_off, const int32_t *m_arr,
@@ -1483,10 +1513,7 @@ dtws_status dtws_query_batch(dtws_t h, const float *Q_cat, const int64_t *q_off,
     float *dist_d = ddev ? out_dist : (float *)(sp + round_up(qb, 256) + round_up(ib, 256));
     st = run_batch(h, Qd, q_off, m_arr, r_arr, nq, k, idx_d, dist_d, s);
     if (st != DTWS_OK) return st;
-    if (!idev) CK(cudaMemcpyAsync(out_idx, idx_d, ib, cudaMemcpyDeviceToHost, s));
-    if (!ddev) CK(cudaMemcpyAsync(out_dist, dist_d, db, cudaMemcpyDeviceToHost, s));
-    if (!idev || !ddev) CK(cudaStreamSynchronize(s));
-    return DTWS_OK;
+    return read_back(h, s, idx_d, dist_d, out_idx, out_dist, ib, db, idev, ddev);
 }
 
 dtws_status dtws_sync_status(dtws_t h, void *stream) {

@@ -83,8 +83,9 @@ cudaError_t launch_query_reset(const QueryBufs &b, const QueryArgs &, cudaStream
 }
 
 // ------------------------------------------------------------------ query prep
-// One CTA of 1024 threads.  Dynamic smem: q_hat FP32 [m] + sort keys u64 [P],
-// P = next power of two >= m.
+// One CTA.  Dynamic smem: sort keys u64 [P] (P = next power of two >= m, at
+// least kQBins / 2), then q_hat, its upper and its lower envelope, FP32 [m]
+// each.
 constexpr int kQBins = 1024;  // |q_hat| quantised to 1/256, up to 4
 __global__ void __launch_bounds__(1024) k_qprep(const float *__restrict__ Q, QueryBufs b, QueryArgs a) {
     extern __shared__ __align__(16) unsigned char smraw[];
@@ -95,6 +96,7 @@ __global__ void __launch_bounds__(1024) k_qprep(const float *__restrict__ Q, Que
     if (P < kQBins / 2) P = kQBins / 2;  // (as launch_qprep sizes it)
     unsigned long long *keys = (unsigned long long *)smraw;
     float *qs = (float *)(keys + P);
+    float *us = qs + m, *ls = us + m;
 
     // the query's state starts clear (this kernel opens every query)
     reset_state(b.st);
@@ -162,6 +164,8 @@ __global__ void __launch_bounds__(1024) k_qprep(const float *__restrict__ Q, Que
         }
         b.Uq[j] = u;
         b.Lq[j] = l;
+        us[j] = u;
+        ls[j] = l;
         b.qh32[j] = qs[j];
     }
     // order by |q_hat| descending, quantised to 1/256 (the order only decides
@@ -209,8 +213,8 @@ __global__ void __launch_bounds__(1024) k_qprep(const float *__restrict__ Q, Que
             if (in) {
                 b.ord[slot] = (unsigned short)j;
                 b.sq[slot] = qs[j];
-                b.sU[slot] = b.Uq[j];
-                b.sL[slot] = b.Lq[j];
+                b.sU[slot] = us[j];
+                b.sL[slot] = ls[j];
             }
             __syncwarp();
         }
@@ -221,7 +225,7 @@ cudaError_t launch_qprep(const float *Q, const QueryBufs &b, const QueryArgs &a,
     int P = 1;
     while (P < a.m) P <<= 1;
     if (P < kQBins / 2) P = kQBins / 2;  // (the key buffer also holds the sort's counters)
-    size_t smem = (size_t)P * 8 + (size_t)a.m * 4;
+    size_t smem = (size_t)P * 8 + (size_t)a.m * 12;
     cudaError_t e = cudaFuncSetAttribute(k_qprep, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     const int threads = a.m < 256 ? 128 : (a.m < 1024 ? 256 : 512);

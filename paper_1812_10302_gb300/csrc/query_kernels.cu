@@ -464,12 +464,26 @@ __device__ __forceinline__ unsigned long long x2_add(unsigned long long a, unsig
     asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
     return d;
 }
+__device__ __forceinline__ unsigned long long x2_mul(unsigned long long a, unsigned long long b) {
+    unsigned long long d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ void x2_unpack(unsigned long long v, float &lo, float &hi) {
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
 // Shared-memory load at a 32-bit shared address plus a constant byte offset
 // (volatile: it stays after the barrier wait that made the data visible).
 template <int OFF>
 __device__ __forceinline__ float lds_at(unsigned addr) {
     float v;
     asm volatile("ld.shared.f32 %0, [%1+%2];" : "=f"(v) : "r"(addr), "n"(OFF));
+    return v;
+}
+template <int OFF>
+__device__ __forceinline__ unsigned long long lds64_at(unsigned addr) {
+    unsigned long long v;
+    asm volatile("ld.shared.b64 %0, [%1+%2];" : "=l"(v) : "r"(addr), "n"(OFF));
     return v;
 }
 
@@ -484,77 +498,69 @@ __device__ void seed_lists(const QueryBufs &b, const QueryArgs &a, int n_random,
 template <int TERMS>
 __global__ void __launch_bounds__(kScanThreads) k_seed_scan(QueryBufs b, QueryArgs a, int proposals, int stages,
                                                             int n_random, int H, unsigned long long rng) {
-    static_assert(TERMS % 2 == 0, "terms are taken in pairs");
-    constexpr int kPer = kScanConsumers * 32;           // scored windows per pass of the CTA
+    constexpr int kPer = kScanConsumers * 64;           // scored windows per pass of the CTA (two per lane)
     constexpr int kIt = ProxyLayout::S / kPer;          // passes per tile
-    static_assert(ProxyLayout::S % kPer == 0, "whole passes per tile");
+    static_assert(ProxyLayout::S % kPer == 0 && kIt % 2 == 0, "whole pairs of passes per tile");
     extern __shared__ __align__(16) unsigned char smraw[];
     __shared__ unsigned long long wbest[kScanConsumers + 1];
     if (!b.st->valid) return;
     const int m = a.m;
     // Term positions, evenly spread, each rounded down to a multiple of
-    // kProxyStride (the scored windows are those at multiples of kProxyStride,
-    // so their term samples are too: the stage holds only those samples).
-    // Lane l scores window kProxyStride*l (+ const), whose term sample p sits
-    // at staged sample l + p/kProxyStride: consecutive words across the warp,
-    // so every load is conflict-free.
+    // 2 * kProxyStride.  Lane l scores the adjacent scored windows 2l and
+    // 2l + 1 (+ const; window offsets kProxyStride times those), whose term-p
+    // samples are the staged words 2l + p/kProxyStride and the next: one
+    // aligned 8-byte load (p/kProxyStride is even), consecutive across the
+    // warp (conflict-free), and one packed FP32x2 operation serves both.
     unsigned poff[TERMS];
-    unsigned long long qv2[TERMS / 2];
+    unsigned long long qq[TERMS];  // (q_p, q_p)
 #pragma unroll
-    for (int j = 0; j < TERMS / 2; ++j) {
-        int p[2];
-        float q[2];
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            const int u = 2 * j + h;
-            const int pu = (int)(((2 * u + 1) * (long long)m) / (2 * TERMS)) & ~(kProxyStride - 1);
-            p[h] = pu;
-            q[h] = b.qh32[pu];
-        }
-        poff[2 * j] = 4u * (unsigned)(p[0] / kProxyStride);  // bytes
-        poff[2 * j + 1] = 4u * (unsigned)(p[1] / kProxyStride);
-        qv2[j] = x2_pack(q[0], q[1]);
+    for (int u = 0; u < TERMS; ++u) {
+        const int pu = (int)(((2 * u + 1) * (long long)m) / (2 * TERMS)) & ~(2 * kProxyStride - 1);
+        poff[u] = 4u * (unsigned)(pu / kProxyStride);  // bytes
+        const float q = b.qh32[pu];
+        qq[u] = x2_pack(q, q);
     }
     unsigned long long best = kEmptyKey;
     const int64_t ntiles = (a.N + ProxyLayout::W - 1) / ProxyLayout::W;
     const bool piped = tile_pipeline<ProxyLayout>(smraw, b, m, ntiles, &b.st->tile_ctr[0], stages, [&](const Tile &t, int64_t i0) {
-        // window w = kProxyStride*v, v = threadIdx.x + it * kPer: its staged
-        // samples from byte offset 4v in xs, its statistics at 4v in mh / is.  Two
-        // windows (it, it + kIt/2) at a time, each with two partial sums,
-        // so four independent FMA chains are in flight.
-        const unsigned xa = smem_u32(t.xs) + 4u * threadIdx.x;
-        const unsigned sa = smem_u32(t.mh) + 4u * threadIdx.x;
-        unsigned addr[TERMS];
-#pragma unroll
-        for (int k = 0; k < TERMS; ++k) addr[k] = xa + poff[k];
+        // the pair (2v, 2v + 1), v = threadIdx.x + it * kPer / 2: its staged
+        // samples from byte offset 8v in xs, its statistics at 8v in mh / is.
+        // Two pairs (passes it, it + kIt/2) at a time, each with two partial
+        // sums, so four independent FMA chains are in flight.
+        const unsigned xa = smem_u32(t.xs) + 8u * threadIdx.x;
+        const unsigned sa = smem_u32(t.mh) + 8u * threadIdx.x;
         static_for<kIt / 2>([&](auto itc) {
             constexpr int itA = decltype(itc)::value, itB = itA + kIt / 2;
-            constexpr int soA = itA * kPer * 4, xoA = itA * kPer * 4;
-            constexpr int soB = itB * kPer * 4, xoB = itB * kPer * 4;
-            const int64_t iA = i0 + (int64_t)kProxyStride * (threadIdx.x + itA * kPer);
-            const int64_t iB = i0 + (int64_t)kProxyStride * (threadIdx.x + itB * kPer);
-            const bool liveA = iA < a.N, liveB = iB < a.N;
+            constexpr int oA = itA * kPer * 4, oB = itB * kPer * 4;  // bytes, in mh and in xs alike
+            const int64_t iA = i0 + (int64_t)kProxyStride * (2 * threadIdx.x + itA * kPer);
+            const int64_t iB = i0 + (int64_t)kProxyStride * (2 * threadIdx.x + itB * kPer);
+            const bool liveA0 = iA < a.N, liveA1 = iA + kProxyStride < a.N;
+            const bool liveB0 = iB < a.N, liveB1 = iB + kProxyStride < a.N;
             static_assert(ProxyLayout::NS == 2, "the proxy stage holds mh and is only");
-            const float mhA = lds_at<soA>(sa), isA = lds_at<soA + ProxyLayout::S * 4>(sa);
-            const float mhB = lds_at<soB>(sa), isB = lds_at<soB + ProxyLayout::S * 4>(sa);
+            const unsigned long long mhA = lds64_at<oA>(sa), isA = lds64_at<oA + ProxyLayout::S * 4>(sa);
+            const unsigned long long mhB = lds64_at<oB>(sa), isB = lds64_at<oB + ProxyLayout::S * 4>(sa);
             // q_hat - x_hat = (q + mh*is) - x*is, with the mean's high part
             // only (its low part moves every term of a window by the same
             // ~ulp(mu)/sigma: the proxy only ranks proposals)
-            const float kwA = mhA * isA, kwB = mhB * isB;
-            float accA, accB;
-            if (!__any_sync(0xffffffffu, (liveA && !(fabsf(kwA) < 4096.0f)) || (liveB && !(fabsf(kwB) < 4096.0f)))) {
+            const unsigned long long kwA = x2_mul(mhA, isA), kwB = x2_mul(mhB, isB);
+            float kA0, kA1, kB0, kB1;
+            x2_unpack(kwA, kA0, kA1);
+            x2_unpack(kwB, kB0, kB1);
+            float accA0, accA1, accB0, accB1;
+            if (!__any_sync(0xffffffffu, (liveA0 && !(fabsf(kA0) < 4096.0f)) || (liveA1 && !(fabsf(kA1) < 4096.0f)) ||
+                                             (liveB0 && !(fabsf(kB0) < 4096.0f)) || (liveB1 && !(fabsf(kB1) < 4096.0f)))) {
                 // one FMA per term; the absolute error stays below ~2^-11
                 // when |mu|/sigma < 2^12 (the proxy only ranks proposals)
-                const unsigned long long kw2A = x2_pack(kwA, kwA), nis2A = x2_pack(-isA, -isA);
-                const unsigned long long kw2B = x2_pack(kwB, kwB), nis2B = x2_pack(-isB, -isB);
+                const unsigned long long m1 = x2_pack(-1.0f, -1.0f);
+                const unsigned long long nisA = x2_mul(isA, m1), nisB = x2_mul(isB, m1);
                 unsigned long long sA0 = 0ull, sA1 = 0ull, sB0 = 0ull, sB1 = 0ull;  // (+0, +0)
 #pragma unroll
-                for (int j = 0; j < TERMS / 2; ++j) {
-                    const unsigned long long xA = x2_pack(lds_at<xoA>(addr[2 * j]), lds_at<xoA>(addr[2 * j + 1]));
-                    const unsigned long long xB = x2_pack(lds_at<xoB>(addr[2 * j]), lds_at<xoB>(addr[2 * j + 1]));
-                    const unsigned long long cA = x2_fma(xA, nis2A, x2_add(qv2[j], kw2A));
-                    const unsigned long long cB = x2_fma(xB, nis2B, x2_add(qv2[j], kw2B));
-                    if (j & 1) {
+                for (int u = 0; u < TERMS; ++u) {
+                    const unsigned long long xA = lds64_at<oA>(xa + poff[u]);
+                    const unsigned long long xB = lds64_at<oB>(xa + poff[u]);
+                    const unsigned long long cA = x2_fma(xA, nisA, x2_add(qq[u], kwA));
+                    const unsigned long long cB = x2_fma(xB, nisB, x2_add(qq[u], kwB));
+                    if (u & 1) {
                         sA1 = x2_fma(cA, cA, sA1);
                         sB1 = x2_fma(cB, cB, sB1);
                     } else {
@@ -562,29 +568,37 @@ __global__ void __launch_bounds__(kScanThreads) k_seed_scan(QueryBufs b, QueryAr
                         sB0 = x2_fma(cB, cB, sB0);
                     }
                 }
-                accA = x2_sum(x2_add(sA0, sA1));
-                accB = x2_sum(x2_add(sB0, sB1));
+                x2_unpack(x2_add(sA0, sA1), accA0, accA1);
+                x2_unpack(x2_add(sB0, sB1), accB0, accB1);
             } else {
-                float a0 = 0.0f, a1 = 0.0f, b0 = 0.0f, b1 = 0.0f;
+                float mA0, mA1, mB0, mB1, sA0, sA1, sB0, sB1;
+                x2_unpack(mhA, mA0, mA1);
+                x2_unpack(mhB, mB0, mB1);
+                x2_unpack(isA, sA0, sA1);
+                x2_unpack(isB, sB0, sB1);
+                accA0 = accA1 = accB0 = accB1 = 0.0f;
 #pragma unroll
-                for (int j = 0; j < TERMS / 2; ++j) {
-                    float q0, q1;
-                    asm("mov.b64 {%0, %1}, %2;" : "=f"(q0), "=f"(q1) : "l"(qv2[j]));
-                    const float cA0 = q0 - (lds_at<xoA>(addr[2 * j]) - mhA) * isA;
-                    const float cA1 = q1 - (lds_at<xoA>(addr[2 * j + 1]) - mhA) * isA;
-                    const float cB0 = q0 - (lds_at<xoB>(addr[2 * j]) - mhB) * isB;
-                    const float cB1 = q1 - (lds_at<xoB>(addr[2 * j + 1]) - mhB) * isB;
-                    a0 = fmaf(cA0, cA0, a0);
-                    a1 = fmaf(cA1, cA1, a1);
-                    b0 = fmaf(cB0, cB0, b0);
-                    b1 = fmaf(cB1, cB1, b1);
+                for (int u = 0; u < TERMS; ++u) {
+                    float q, q1, xA0, xA1, xB0, xB1;
+                    x2_unpack(qq[u], q, q1);
+                    x2_unpack(lds64_at<oA>(xa + poff[u]), xA0, xA1);
+                    x2_unpack(lds64_at<oB>(xa + poff[u]), xB0, xB1);
+                    const float cA0 = q - (xA0 - mA0) * sA0, cA1 = q - (xA1 - mA1) * sA1;
+                    const float cB0 = q - (xB0 - mB0) * sB0, cB1 = q - (xB1 - mB1) * sB1;
+                    accA0 = fmaf(cA0, cA0, accA0);
+                    accA1 = fmaf(cA1, cA1, accA1);
+                    accB0 = fmaf(cB0, cB0, accB0);
+                    accB1 = fmaf(cB1, cB1, accB1);
                 }
-                accA = a0 + a1;
-                accB = b0 + b1;
             }
-            const unsigned long long keyA = make_key(accA, (unsigned)iA), keyB = make_key(accB, (unsigned)iB);
-            best = liveA && keyA < best ? keyA : best;
-            best = liveB && keyB < best ? keyB : best;
+            const unsigned long long kyA0 = make_key(accA0, (unsigned)iA);
+            const unsigned long long kyA1 = make_key(accA1, (unsigned)(iA + kProxyStride));
+            const unsigned long long kyB0 = make_key(accB0, (unsigned)iB);
+            const unsigned long long kyB1 = make_key(accB1, (unsigned)(iB + kProxyStride));
+            best = liveA0 && kyA0 < best ? kyA0 : best;
+            best = liveA1 && kyA1 < best ? kyA1 : best;
+            best = liveB0 && kyB0 < best ? kyB0 : best;
+            best = liveB1 && kyB1 < best ? kyB1 : best;
         });
     });
 #pragma unroll
@@ -642,10 +656,12 @@ cudaError_t launch_seed_scan(const QueryBufs &b, const QueryArgs &a, int proposa
     *ctas = 0;
     if (proposals <= 0 || proposals > kPropMax || n_random + proposals * (2 * H + 1) > kEdMax)
         return cudaErrorInvalidValue;
-    // evenly spaced positions, so never more terms than m
-    if (terms >= 16 && a.m >= 16) return launch_seed_scan_t<16>(b, a, proposals, n_random, H, rng, ctas, s);
-    if (terms >= 8 && a.m >= 8) return launch_seed_scan_t<8>(b, a, proposals, n_random, H, rng, ctas, s);
-    if (terms >= 4 && a.m >= 4) return launch_seed_scan_t<4>(b, a, proposals, n_random, H, rng, ctas, s);
+    // evenly spaced positions at multiples of 2 * kProxyStride, so at most
+    // m / (2 * kProxyStride) distinct terms
+    constexpr int g = 2 * kProxyStride;
+    if (terms >= 16 && a.m >= 16 * g) return launch_seed_scan_t<16>(b, a, proposals, n_random, H, rng, ctas, s);
+    if (terms >= 8 && a.m >= 8 * g) return launch_seed_scan_t<8>(b, a, proposals, n_random, H, rng, ctas, s);
+    if (terms >= 4 && a.m >= 4 * g) return launch_seed_scan_t<4>(b, a, proposals, n_random, H, rng, ctas, s);
     return launch_seed_scan_t<2>(b, a, proposals, n_random, H, rng, ctas, s);
 }
 

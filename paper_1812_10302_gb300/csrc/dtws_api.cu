@@ -660,8 +660,9 @@ dtws_status enqueue_search(dtws_t h, const Exec &e, const QueryArgs &a, const fl
     cudaStream_t s = e.s;
     const int m = a.m, k = a.k;
     if (e.stage == 2) {  // the final stage of a batch query (after the persistent stage)
-        CK(launch_finalize(b, a, idx_d, dist_d, s));
-        *launches_out = 3;
+        int nf = 0;
+        CK(launch_finalize(b, a, idx_d, dist_d, s, &nf));
+        *launches_out = nf;
         return DTWS_OK;
     }
     // a wide exclusion zone needs k seeds in separate buckets of each parity
@@ -728,10 +729,11 @@ dtws_status enqueue_search(dtws_t h, const Exec &e, const QueryArgs &a, const fl
         *launches_out = launches;
         return DTWS_OK;
     }
+    int nf = 3;
     if (a.xz_z > 0) CK(launch_xz_finalize(b, a, idx_d, dist_d, s));
-    else CK(launch_finalize(b, a, idx_d, dist_d, s));
+    else CK(launch_finalize(b, a, idx_d, dist_d, s, &nf));
     rec(5);
-    launches += 1 + 1 + 1 + 2 + 1 + 3;  // qprep, ED seeds, scan, order x2, DTW, final x3
+    launches += 1 + 1 + 1 + 2 + 1 + nf;  // qprep, ED seeds, scan, order x2, DTW, final
     *launches_out = launches;
     return DTWS_OK;
 }

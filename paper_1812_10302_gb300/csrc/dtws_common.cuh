@@ -120,7 +120,7 @@ struct QueryState {
     long long pool_off;
     // CTAs of the proxy scan and of the survivor histogram that have
     // finished: the last one of each takes the step that needs all of them
-    unsigned int prop_done, bin_done;
+    unsigned int prop_done, bin_done, final_done;
 };
 
 // Scalars of one query, passed by value to every kernel.

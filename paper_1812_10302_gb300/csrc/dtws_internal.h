@@ -167,8 +167,9 @@ cudaError_t launch_prescore(const QueryBufs &b, const QueryArgs &a, cudaStream_t
 cudaError_t launch_lb_scan(const QueryBufs &b, const QueryArgs &a, cudaStream_t s);
 cudaError_t launch_order(const QueryBufs &b, const QueryArgs &a, cudaStream_t s);
 cudaError_t launch_dtw_survivors(const QueryBufs &b, const QueryArgs &a, cudaStream_t s);
+// the final stage: one launch, or three (*launches says which)
 cudaError_t launch_finalize(const QueryBufs &b, const QueryArgs &a, int64_t *out_idx,
-                            float *out_dist, cudaStream_t s);
+                            float *out_dist, cudaStream_t s, int *launches);
 // persistent batch stage (dtw_pool.cu): the default anti-diagonal shape of a
 // band (false when the band takes another kernel), and the stage's launch
 // over the shape's queries list[0..nlist) of pq (device arrays); m_max,

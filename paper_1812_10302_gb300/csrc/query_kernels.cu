@@ -60,6 +60,7 @@ __device__ __forceinline__ void reset_state(QueryState *st) {
         st->pool_off = 0;
         st->prop_done = 0;
         st->bin_done = 0;
+        st->final_done = 0;
         st->n_seeds = 0;
         st->n_cand = 0;
         st->work = 0;
@@ -1048,6 +1049,17 @@ __global__ void __launch_bounds__(256) k_dtw64(QueryBufs b, QueryArgs a, const i
     }
 }
 
+// Where the final stage writes the answer (the multi-warp re-score kernel
+// does the whole stage when idx is set).
+struct FinalOut {
+    int64_t *idx = nullptr;
+    float *dist = nullptr;
+};
+__device__ __forceinline__ int margin_select(const unsigned long long *keys, const QueryState *st, const QueryArgs &a,
+                             unsigned *idx, int *skip, bool *overflow);
+__device__ __forceinline__ void final_order(const unsigned *idx, const double *d64, int nm, const QueryArgs &a, int64_t *out_idx,
+                            float *out_dist, int tid, int nthreads);
+
 // The re-score with the anti-diagonal walk spread over W warps per window
 // (dtw_diag_df_mw): G = blockDim.x / (32 W) groups per CTA, group g owning
 // named barrier 1 + g; the query's double-float copy is shared, each group
@@ -1055,16 +1067,25 @@ __global__ void __launch_bounds__(256) k_dtw64(QueryBufs b, QueryArgs a, const i
 // cell per lane of one warp: per window it is the latency of the walk that
 // counts, and W warps cut the cells each lane steps through per
 // anti-diagonal by W.
+//
+// With fin set (the end of a search, no exclusion zone) the kernel is the
+// whole final stage: every CTA makes the margin list itself from the result
+// list (margin_select: the same list in every CTA), group gg of the grid
+// re-scores entries skip + gg, skip + gg + groups, ..., and the last CTA to
+// finish (a completion count; nothing waits) orders the list and writes the
+// output (final_order) -- k_final_select and k_final_sort without their
+// launches.
 template <int W, int K>
-__global__ void __launch_bounds__(256) k_dtw64_mw(QueryBufs b, QueryArgs a, const int64_t *offsets,
-                                                  int64_t count_host, double *out) {
+__global__ void __launch_bounds__(256, 1) k_dtw64_mw(QueryBufs b, QueryArgs a, const int64_t *offsets,
+                                                  int64_t count_host, double *out, FinalOut fin) {
     constexpr int GMAX = 8 / W;
     extern __shared__ __align__(16) unsigned char smraw[];
     __shared__ DfXchg xch[GMAX];
     __shared__ double bc[2 * GMAX];
     __shared__ int cur[GMAX];
     QueryState *st = b.st;
-    if (!st->valid) return;
+    const bool fused = fin.idx != nullptr;
+    if (!fused && !st->valid) return;
     const int m = a.m, r = a.r;
     const int G = (int)(blockDim.x / (32 * W));
     const int pad = diag_pad(r, 32 * W, K);
@@ -1078,17 +1099,48 @@ __global__ void __launch_bounds__(256) k_dtw64_mw(QueryBufs b, QueryArgs a, cons
     dfloat *cbase = (dfloat *)(smraw + span * 8 * (size_t)(1 + g));
     dfloat *cd = cbase + pad;
     if (g < G) fill_pads(cbase, m, pad, dfloat{-1e15f, 0.0f}, t, nthr);
+    __shared__ unsigned long long ms_keys[kListMax];
+    __shared__ unsigned ms_idx[kListMax];
+    __shared__ double ms_d[kListMax];
+    __shared__ int ms_n, ms_skip, last;
+    if (fused) {
+        const bool valid = st->valid != 0;
+        for (int j = threadIdx.x; j < a.list_cap; j += blockDim.x) ms_keys[j] = valid ? st->res_keys[j] : kEmptyKey;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int skip = 0;
+            bool ovf = false;
+            ms_n = valid ? margin_select(ms_keys, st, a, ms_idx, &skip, &ovf) : 0;
+            ms_skip = skip;
+            if (blockIdx.x == 0) {
+                st->n_margin = ms_n;
+                st->margin_skip = skip;
+                st->ctr[kCtrRescored] = (unsigned long long)ms_n;
+                if (ovf) atomicOr(b.status, kStOverflow);
+            }
+        }
+    }
     __syncthreads();
-    if (g >= G) return;
+    if (g >= G) {
+        if (!fused) return;
+    } else {
     const int64_t count = offsets ? count_host
+                        : fused ? (int64_t)ms_n
                         : a.xz_z > 0 ? (int64_t)min(st->xz_nsel, b.xz_sel_cap)
                                      : (int64_t)st->n_margin;
+    int c_next = fused ? ms_skip + (int)blockIdx.x * G + g : 0;
     while (true) {
-        // (the previous window's last barrier lies between every thread's
-        // read of cur[g] and this write)
-        if (t == 0) cur[g] = atomicAdd(&st->work, 1);
-        group_bar(bar, nthr);
-        const int c = cur[g];
+        int c;
+        if (fused) {
+            c = c_next;
+            c_next += (int)gridDim.x * G;
+        } else {
+            // (the previous window's last barrier lies between every thread's
+            // read of cur[g] and this write)
+            if (t == 0) cur[g] = atomicAdd(&st->work, 1);
+            group_bar(bar, nthr);
+            c = cur[g];
+        }
         if (c >= count) break;
         unsigned idx = 0;
         bool bad = false;
@@ -1097,7 +1149,7 @@ __global__ void __launch_bounds__(256) k_dtw64_mw(QueryBufs b, QueryArgs a, cons
             bad = o < 0 || o >= a.N;
             idx = bad ? 0u : (unsigned)o;
         } else {
-            idx = a.xz_z > 0 ? b.xz_sel[c] : st->margin_idx[c];
+            idx = fused ? ms_idx[c] : a.xz_z > 0 ? b.xz_sel[c] : st->margin_idx[c];
         }
         if (bad) {
             if (t == 0) out[c] = __longlong_as_double(0x7ff8000000000000ll);
@@ -1131,15 +1183,32 @@ __global__ void __launch_bounds__(256) k_dtw64_mw(QueryBufs b, QueryArgs a, cons
         const double d = dtw_diag_df_mw<W, K>(qd, cd, m, r, w, lane, xch[g], bar);
         if (t == 0) {
             if (offsets) out[c] = d;
-            else if (a.xz_z > 0) b.xz_d64[c] = d;
+            else if (a.xz_z > 0 && !fused) b.xz_d64[c] = d;
             else st->margin_d64[c] = d;
+            if (fused) __threadfence();  // (before this CTA counts itself done)
         }
+        // (in the fused form the next window's first barrier is this one:
+        // no thread of the group reuses cd or bc before all have passed it)
+        if (fused) group_bar(bar, nthr);
     }
+    }
+    if (!fused) return;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        last = atomicAdd(&st->final_done, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    for (int j = threadIdx.x; j < ms_n; j += blockDim.x) ms_d[j] = j < ms_skip ? st->pre_d64 : __ldcg(&st->margin_d64[j]);
+    __syncthreads();
+    final_order(ms_idx, ms_d, ms_n, a, fin.idx, fin.dist, threadIdx.x, blockDim.x);
 }
 
 template <int W, int K>
 static cudaError_t dtw64_mw_launch(const QueryBufs &b, const QueryArgs &a, const int64_t *offsets, int64_t count,
-                                   double *out, int64_t count_for_grid, cudaStream_t s) {
+                                   double *out, int64_t count_for_grid, cudaStream_t s, FinalOut fin) {
     // the query's copy plus one window copy per group (double-float: 8 B per element)
     const size_t span = (size_t)((a.m + 2 * diag_pad(a.r, 32 * W, K) + 3) & ~3), bytes = span * sizeof(dfloat);
     const size_t hard = (size_t)200 * 1024;
@@ -1153,12 +1222,15 @@ static cudaError_t dtw64_mw_launch(const QueryBufs &b, const QueryArgs &a, const
     const int blocks = (int)(want < cap ? want : cap);
     cudaError_t e = cudaFuncSetAttribute(k_dtw64_mw<W, K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k_dtw64_mw<W, K><<<blocks, groups * W * 32, smem, s>>>(b, a, offsets, count, out);
+    k_dtw64_mw<W, K><<<blocks, groups * W * 32, smem, s>>>(b, a, offsets, count, out, fin);
     return cudaGetLastError();
 }
 
+// fin set: the whole final stage in the multi-warp kernel, or nothing is
+// launched and the result is cudaErrorNotSupported.
 static cudaError_t dtw64_dispatch(const QueryBufs &b, const QueryArgs &a, const int64_t *offsets,
-                                  int64_t count, double *out, int64_t count_for_grid, cudaStream_t s) {
+                                  int64_t count, double *out, int64_t count_for_grid, cudaStream_t s,
+                                  FinalOut fin) {
     DtwPlan p;
     if (!plan_dtw<double>(a.m, a.r, false, &p)) return cudaErrorInvalidValue;
     // anti-diagonal with more than one cell per lane of a warp: the
@@ -1168,7 +1240,7 @@ static cudaError_t dtw64_dispatch(const QueryBufs &b, const QueryArgs &a, const 
 #define DTWS_MW(KK)                                                                                       \
         if (p.K == KK)                                                                                     \
             mw = dtw64_mw_launch<PreShape<32, KK>::W, PreShape<32, KK>::K2>(b, a, offsets, count, out,    \
-                                                                             count_for_grid, s);
+                                                                             count_for_grid, s, fin);
         DTWS_MW(2) DTWS_MW(3) DTWS_MW(4) DTWS_MW(6) DTWS_MW(8) DTWS_MW(10) DTWS_MW(12) DTWS_MW(16)
 #undef DTWS_MW
     } else if (a.r > kDiagRMax && a.r < 8 * 32 * 8) {
@@ -1178,12 +1250,12 @@ static cudaError_t dtw64_dispatch(const QueryBufs &b, const QueryArgs &a, const 
         // cells per lane, instead of FP64 arithmetic, which this part issues
         // at a small fraction of its FP32 rate
         const int k4 = (a.r + 1 + 127) / 128, k8 = (a.r + 1 + 255) / 256;
-        if (k4 <= 6) mw = dtw64_mw_launch<4, 6>(b, a, offsets, count, out, count_for_grid, s);
-        else if (k4 <= 8) mw = dtw64_mw_launch<4, 8>(b, a, offsets, count, out, count_for_grid, s);
-        else if (k8 <= 6) mw = dtw64_mw_launch<8, 6>(b, a, offsets, count, out, count_for_grid, s);
-        else mw = dtw64_mw_launch<8, 8>(b, a, offsets, count, out, count_for_grid, s);
+        if (k4 <= 6) mw = dtw64_mw_launch<4, 6>(b, a, offsets, count, out, count_for_grid, s, fin);
+        else if (k4 <= 8) mw = dtw64_mw_launch<4, 8>(b, a, offsets, count, out, count_for_grid, s, fin);
+        else if (k8 <= 6) mw = dtw64_mw_launch<8, 6>(b, a, offsets, count, out, count_for_grid, s, fin);
+        else mw = dtw64_mw_launch<8, 8>(b, a, offsets, count, out, count_for_grid, s, fin);
     }
-    if (mw != cudaErrorNotSupported) return mw;
+    if (mw != cudaErrorNotSupported || fin.idx) return mw;
     // (the shared-memory copies do not fit: the one-group kernels below)
     const int blocks = dtw_blocks(p, b.num_sms, count_for_grid);
 #define DTWS_CASE(LL, KK)                                                                                     \
@@ -1209,7 +1281,7 @@ __global__ void k_reset_cursor(QueryState *st) { st->work = 0; }
 cudaError_t launch_dtw_at_f64(const QueryBufs &b, const QueryArgs &a, const int64_t *offsets,
                               int64_t count, double *out, cudaStream_t s) {
     k_reset_cursor<<<1, 1, 0, s>>>(b.st);
-    return dtw64_dispatch(b, a, offsets, count, out, count, s);
+    return dtw64_dispatch(b, a, offsets, count, out, count, s, FinalOut{});
 }
 
 // ------------------------------------------------------------------ LB scan
@@ -1414,6 +1486,17 @@ cudaError_t launch_lb_scan(const QueryBufs &b, const QueryArgs &a, cudaStream_t 
 // stage meets the most promising windows first.  With a finite scan
 // threshold the bins split [0, thr] evenly; otherwise they follow the
 // float's exponent and leading mantissa bits (monotone for lb >= 0).
+// Each CTA takes a contiguous chunk of at least kBinChunk survivors (with
+// few survivors most CTAs have none and finish at once: fewer CTAs each pay
+// the bins' clearing and the per-bin global atomics).
+constexpr int kBinChunk = 4096;
+__device__ __forceinline__ void bin_chunk(int64_t n, int64_t *c0, int64_t *c1) {
+    int64_t per = (n + gridDim.x - 1) / gridDim.x;
+    if (per < kBinChunk) per = kBinChunk;
+    *c0 = (int64_t)blockIdx.x * per;
+    if (*c0 > n) *c0 = n;
+    *c1 = *c0 + per < n ? *c0 + per : n;
+}
 
 // The histogram over all CTAs; the last CTA to finish (a completion count,
 // nothing waits) turns it into each bin's first position.
@@ -1425,13 +1508,14 @@ __global__ void __launch_bounds__(kBinThreads) k_bin_hist(QueryBufs b) {
     QueryState *st = b.st;
     for (int t = threadIdx.x; t < kBins; t += blockDim.x) h[t] = 0;
     __syncthreads();
-    const int n = st->n_cand;
     const float thr = st->thr_scan;
-    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n; c += gridDim.x * blockDim.x)
-        atomicAdd(&h[bin_of(b.cand_lb[c], thr)], 1);
+    int64_t c0, c1;
+    bin_chunk(st->n_cand, &c0, &c1);
+    for (int64_t c = c0 + threadIdx.x; c < c1; c += blockDim.x) atomicAdd(&h[bin_of(b.cand_lb[c], thr)], 1);
     __syncthreads();
-    for (int t = threadIdx.x; t < kBins; t += blockDim.x)
-        if (h[t]) atomicAdd(&st->hist[t], h[t]);
+    if (c1 > c0)
+        for (int t = threadIdx.x; t < kBins; t += blockDim.x)
+            if (h[t]) atomicAdd(&st->hist[t], h[t]);
     __threadfence();
     __syncthreads();
     if (threadIdx.x == 0) last = atomicAdd(&st->bin_done, 1u) == gridDim.x - 1;
@@ -1467,10 +1551,10 @@ __global__ void __launch_bounds__(kBinThreads) k_bin_hist(QueryBufs b) {
 __global__ void __launch_bounds__(512) k_bin_scatter(QueryBufs b) {
     __shared__ int h[kBins];
     QueryState *st = b.st;
-    const int64_t n = st->n_cand;
     const float thr = st->thr_scan;
-    const int64_t per = (n + gridDim.x - 1) / gridDim.x;
-    const int64_t c0 = (int64_t)blockIdx.x * per, c1 = c0 + per < n ? c0 + per : n;
+    int64_t c0, c1;
+    bin_chunk(st->n_cand, &c0, &c1);
+    if (c1 <= c0) return;
     for (int t = threadIdx.x; t < kBins; t += blockDim.x) h[t] = 0;
     __syncthreads();
     for (int64_t c = c0 + threadIdx.x; c < c1; c += blockDim.x) atomicAdd(&h[bin_of(b.cand_lb[c], thr)], 1);
@@ -1500,32 +1584,71 @@ cudaError_t launch_order(const QueryBufs &b, const QueryArgs &, cudaStream_t s) 
 // within that margin are re-scored in FP64 and ordered by (FP64 distance,
 // offset).  If the list is full and its last entry is still inside the
 // margin, more near-ties may exist than it holds: DTWS_EOVERFLOW.
+// keys: the result list (a.list_cap slots, ascending, empty keys last).
+// Writes the windows to re-score to idx (the pre-scored window first: *skip
+// of them, 0 or 1, are re-scored already), returns their count and sets
+// *overflow when the list is full and its last entry is still inside the
+// margin.
+__device__ __forceinline__ int margin_select(const unsigned long long *keys, const QueryState *st, const QueryArgs &a,
+                             unsigned *idx, int *skip, bool *overflow) {
+    int count = 0;
+    while (count < a.list_cap && keys[count] != kEmptyKey) ++count;
+    *skip = 0;
+    *overflow = false;
+    if (count == 0) return 0;
+    const float dk = key_dist(keys[(count < a.k ? count : a.k) - 1]);
+    const float lim = fmaf(dk, 1.0f + a.delta, a.alpha);
+    // the pre-scored window (side stream) goes first with its re-score
+    const unsigned pre = st->pre_done ? prescored_window(st, a) : 0xffffffffu;
+    int nm = 0;
+    for (int j = 0; j < count; ++j)
+        if (key_dist(keys[j]) <= lim && key_idx(keys[j]) == pre) idx[nm++] = pre;
+    *skip = nm;
+    for (int j = 0; j < count; ++j) {
+        const unsigned w = key_idx(keys[j]);
+        if (key_dist(keys[j]) <= lim && w != pre) idx[nm++] = w;
+    }
+    *overflow = count == a.list_cap && key_dist(keys[count - 1]) <= lim;
+    return nm;
+}
+
+// The output: the k smallest (re-scored distance, offset) pairs of the nm
+// entries, ascending; slots past nm get offset -1, distance +inf.
+__device__ __forceinline__ void final_order(const unsigned *idx, const double *d64, int nm, const QueryArgs &a, int64_t *out_idx,
+                            float *out_dist, int tid, int nthreads) {
+    for (int t = tid; t < nm; t += nthreads) {
+        const double d = d64[t];
+        const unsigned w = idx[t];
+        int rank = 0;
+        for (int u = 0; u < nm; ++u) {
+            const double du = d64[u];
+            const unsigned iu = idx[u];
+            rank += (du < d) || (du == d && iu < w);
+        }
+        if (rank < a.k) {
+            out_idx[rank] = (int64_t)w;
+            out_dist[rank] = (float)d;
+        }
+    }
+    for (int u = nm + tid; u < a.k; u += nthreads) {
+        out_idx[u] = -1;
+        out_dist[u] = DINF;
+    }
+}
+
 __global__ void k_final_select(QueryBufs b, QueryArgs a) {
     QueryState *st = b.st;
     if (threadIdx.x != 0) return;
     st->work = 0;
     st->margin_skip = 0;
     if (!st->valid) { st->n_margin = 0; return; }
-    int count = 0;
-    while (count < a.list_cap && st->res_keys[count] != kEmptyKey) ++count;
-    if (count == 0) { st->n_margin = 0; return; }
-    const float dk = key_dist(st->res_keys[(count < a.k ? count : a.k) - 1]);
-    const float lim = fmaf(dk, 1.0f + a.delta, a.alpha);
-    // the pre-scored window (side stream) goes first with its re-score
-    const unsigned pre = st->pre_done ? prescored_window(st, a) : 0xffffffffu;
-    int nm = 0;
-    for (int j = 0; j < count; ++j)
-        if (key_dist(st->res_keys[j]) <= lim && key_idx(st->res_keys[j]) == pre) {
-            st->margin_idx[nm] = pre;
-            st->margin_d64[nm++] = st->pre_d64;
-        }
-    st->margin_skip = nm;
-    st->work = nm;
-    for (int j = 0; j < count; ++j) {
-        const unsigned idx = key_idx(st->res_keys[j]);
-        if (key_dist(st->res_keys[j]) <= lim && idx != pre) st->margin_idx[nm++] = idx;
-    }
-    if (count == a.list_cap && key_dist(st->res_keys[count - 1]) <= lim) atomicOr(b.status, kStOverflow);
+    int skip = 0;
+    bool ovf = false;
+    const int nm = margin_select(st->res_keys, st, a, st->margin_idx, &skip, &ovf);
+    for (int j = 0; j < skip; ++j) st->margin_d64[j] = st->pre_d64;
+    st->margin_skip = skip;
+    st->work = skip;
+    if (ovf) atomicOr(b.status, kStOverflow);
     st->n_margin = nm;
     st->ctr[kCtrRescored] = (unsigned long long)nm;
 }
@@ -1572,32 +1695,21 @@ cudaError_t launch_exclusion_select(const int64_t *idx, const float *dist, int K
 
 __global__ void k_final_sort(QueryBufs b, QueryArgs a, int64_t *out_idx, float *out_dist) {
     QueryState *st = b.st;
-    const int nm = st->valid ? st->n_margin : 0;
-    const int t = threadIdx.x;
-    if (t < nm) {
-        const double d = st->margin_d64[t];
-        const unsigned idx = st->margin_idx[t];
-        int rank = 0;
-        for (int u = 0; u < nm; ++u) {
-            const double du = st->margin_d64[u];
-            const unsigned iu = st->margin_idx[u];
-            rank += (du < d) || (du == d && iu < idx);
-        }
-        if (rank < a.k) {
-            out_idx[rank] = (int64_t)idx;
-            out_dist[rank] = (float)d;
-        }
-    }
-    for (int u = nm + t; u < a.k; u += blockDim.x) {
-        out_idx[u] = -1;
-        out_dist[u] = DINF;
-    }
+    final_order(st->margin_idx, st->margin_d64, st->valid ? st->n_margin : 0, a, out_idx, out_dist, threadIdx.x,
+                blockDim.x);
 }
 
+// One launch when the re-score takes the multi-warp walk (it then selects
+// and orders too); otherwise select, re-score, order.  *launches: how many.
 cudaError_t launch_finalize(const QueryBufs &b, const QueryArgs &a, int64_t *out_idx,
-                            float *out_dist, cudaStream_t s) {
+                            float *out_dist, cudaStream_t s, int *launches) {
+    *launches = 1;
+    cudaError_t e = dtw64_dispatch(b, a, nullptr, 0, nullptr, kListMax, s, FinalOut{out_idx, out_dist});
+    if (e != cudaErrorNotSupported) return e;
+    cudaGetLastError();
+    *launches = 3;
     k_final_select<<<1, 32, 0, s>>>(b, a);
-    cudaError_t e = dtw64_dispatch(b, a, nullptr, 0, nullptr, kListMax, s);
+    e = dtw64_dispatch(b, a, nullptr, 0, nullptr, kListMax, s, FinalOut{});
     if (e != cudaSuccess) return e;
     k_final_sort<<<1, kListMax, 0, s>>>(b, a, out_idx, out_dist);
     return cudaGetLastError();
@@ -1709,7 +1821,7 @@ cudaError_t launch_xz_finalize(const QueryBufs &b, const QueryArgs &a, int64_t *
     k_xz_compact<<<1, 1024, 0, s>>>(b, a);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    e = dtw64_dispatch(b, a, nullptr, 0, nullptr, b.xz_sel_cap, s);
+    e = dtw64_dispatch(b, a, nullptr, 0, nullptr, b.xz_sel_cap, s, FinalOut{});
     if (e != cudaSuccess) return e;
     int Pmax = 1;
     while (Pmax < b.xz_sel_cap) Pmax <<= 1;

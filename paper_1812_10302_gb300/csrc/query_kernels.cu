@@ -84,19 +84,18 @@ cudaError_t launch_query_reset(const QueryBufs &b, const QueryArgs &, cudaStream
 }
 
 // ------------------------------------------------------------------ query prep
-// One CTA.  Dynamic smem: sort keys u64 [P] (P = next power of two >= m, at
-// least kQBins / 2), then q_hat, its upper and its lower envelope, FP32 [m]
-// each.
+// One CTA of 128, 256 or 512 threads.  Dynamic smem: one row of kQBins
+// 16-bit counters per warp (the ordering's counting sort), then q_hat, its
+// upper and its lower envelope, FP32 [m] each.
 constexpr int kQBins = 1024;  // |q_hat| quantised to 1/256, up to 4
-__global__ void __launch_bounds__(1024) k_qprep(const float *__restrict__ Q, QueryBufs b, QueryArgs a) {
+__global__ void __launch_bounds__(512) k_qprep(const float *__restrict__ Q, QueryBufs b, QueryArgs a) {
     extern __shared__ __align__(16) unsigned char smraw[];
     __shared__ int bad;
+    __shared__ unsigned wsum[16];
     const int m = a.m, r = a.r;
-    int P = 1;
-    while (P < m) P <<= 1;
-    if (P < kQBins / 2) P = kQBins / 2;  // (as launch_qprep sizes it)
-    unsigned long long *keys = (unsigned long long *)smraw;
-    float *qs = (float *)(keys + P);
+    const int nw = (int)(blockDim.x >> 5), wid = (int)(threadIdx.x >> 5), lane = lane_id();
+    unsigned short *tab = reinterpret_cast<unsigned short *>(smraw);
+    float *qs = reinterpret_cast<float *>(tab + nw * kQBins);
     float *us = qs + m, *ls = us + m;
 
     // the query's state starts clear (this kernel opens every query)
@@ -171,65 +170,80 @@ __global__ void __launch_bounds__(1024) k_qprep(const float *__restrict__ Q, Que
     }
     // order by |q_hat| descending, quantised to 1/256 (the order only decides
     // which terms the early-abandoning bounds take first: any order is
-    // admissible), ties by position ascending: a stable counting sort --
-    // histogram of the keys, exclusive scan from the largest key down, then
-    // one warp places the positions chunk by chunk, ranking equal keys
-    // within a chunk by lane
-    unsigned *cnt = reinterpret_cast<unsigned *>(keys);  // kQBins counters (reuses the key buffer)
-    for (int t = threadIdx.x; t < kQBins; t += blockDim.x) cnt[t] = 0u;
+    // admissible), ties by position ascending: a stable counting sort over
+    // the warps.  Warp w owns positions [w C, (w + 1) C) and a row of
+    // counters: (1) each warp counts its keys, 32 positions at a time (equal
+    // keys found by a match, counted once by their lowest lane); (2) per key,
+    // from the largest |q_hat| down, the rows' counts become each row's first
+    // slot (a scan over the keys of the rows' totals, then down the rows);
+    // (3) each warp places its positions in order, ranking equal keys within
+    // 32 positions by lane.
+    for (int t = threadIdx.x; t < nw * kQBins; t += blockDim.x) tab[t] = 0;
     __syncthreads();
     auto qkey = [&](int j) {
         const int v = (int)(fabsf(qs[j]) * 256.0f);
         return (kQBins - 1) - (v < kQBins - 1 ? v : kQBins - 1);  // 0 = the largest |q_hat|
     };
-    for (int j = threadIdx.x; j < m; j += blockDim.x) atomicAdd(&cnt[qkey(j)], 1u);
+    const int C = ((m + nw - 1) / nw + 31) & ~31;
+    const int j0 = wid * C < m ? wid * C : m, j1 = j0 + C < m ? j0 + C : m;
+    unsigned short *row = tab + wid * kQBins;
+    for (int c0 = j0; c0 < j1; c0 += 32) {
+        const int j = c0 + lane;
+        const bool in = j < j1;
+        const int kk = in ? qkey(j) : -1 - lane;  // (out-of-range lanes match nobody)
+        const unsigned peers = __match_any_sync(0xffffffffu, kk);
+        if (in && (peers & ((1u << lane) - 1u)) == 0u) row[kk] = (unsigned short)(row[kk] + __popc(peers));
+        __syncwarp();
+    }
     __syncthreads();
-    if (threadIdx.x < 32) {
-        const int lane = threadIdx.x;
-        constexpr int per = kQBins / 32;
+    {
+        const int per = kQBins / (int)blockDim.x;  // 8, 4 or 2 keys per thread
+        const int k0 = (int)threadIdx.x * per;
         unsigned run = 0;
-        for (int t = 0; t < per; ++t) run += cnt[lane * per + t];
+        for (int u = 0; u < per; ++u)
+            for (int w = 0; w < nw; ++w) run += tab[w * kQBins + k0 + u];
         unsigned incl = run;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
-            const unsigned u = __shfl_up_sync(0xffffffffu, incl, o);
-            if (lane >= o) incl += u;
+            const unsigned v = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += v;
         }
-        unsigned base = incl - run;
-        for (int t = 0; t < per; ++t) {
-            const unsigned c = cnt[lane * per + t];
-            cnt[lane * per + t] = base;
-            base += c;
+        if (lane == 31) wsum[wid] = incl;
+        __syncthreads();
+        unsigned start = incl - run;
+        for (int w = 0; w < wid; ++w) start += wsum[w];
+        for (int u = 0; u < per; ++u)
+            for (int w = 0; w < nw; ++w) {
+                const unsigned v = tab[w * kQBins + k0 + u];
+                tab[w * kQBins + k0 + u] = (unsigned short)start;
+                start += v;
+            }
+    }
+    __syncthreads();
+    for (int c0 = j0; c0 < j1; c0 += 32) {
+        const int j = c0 + lane;
+        const bool in = j < j1;
+        const int kk = in ? qkey(j) : -1 - lane;
+        const unsigned peers = __match_any_sync(0xffffffffu, kk);
+        const unsigned rank = __popc(peers & ((1u << lane) - 1u));
+        const unsigned slot = in ? row[kk] + rank : 0u;
+        __syncwarp();
+        if (in && rank == 0) row[kk] = (unsigned short)(row[kk] + __popc(peers));
+        if (in) {
+            b.ord[slot] = (unsigned short)j;
+            b.sq[slot] = qs[j];
+            b.sU[slot] = us[j];
+            b.sL[slot] = ls[j];
         }
         __syncwarp();
-        for (int c0 = 0; c0 < m; c0 += 32) {
-            const int j = c0 + lane;
-            const bool in = j < m;
-            const int kk = in ? qkey(j) : -1 - lane;  // (out-of-range lanes match nobody)
-            const unsigned peers = __match_any_sync(0xffffffffu, kk);
-            const unsigned rank = __popc(peers & ((1u << lane) - 1u));
-            const unsigned slot = in ? cnt[kk] + rank : 0u;
-            __syncwarp();
-            if (in && rank == 0) cnt[kk] += __popc(peers);
-            if (in) {
-                b.ord[slot] = (unsigned short)j;
-                b.sq[slot] = qs[j];
-                b.sU[slot] = us[j];
-                b.sL[slot] = ls[j];
-            }
-            __syncwarp();
-        }
     }
 }
 
 cudaError_t launch_qprep(const float *Q, const QueryBufs &b, const QueryArgs &a, cudaStream_t s) {
-    int P = 1;
-    while (P < a.m) P <<= 1;
-    if (P < kQBins / 2) P = kQBins / 2;  // (the key buffer also holds the sort's counters)
-    size_t smem = (size_t)P * 8 + (size_t)a.m * 12;
+    const int threads = a.m < 256 ? 128 : (a.m < 1024 ? 256 : 512);
+    const size_t smem = (size_t)(threads / 32) * kQBins * 2 + (size_t)a.m * 12;
     cudaError_t e = cudaFuncSetAttribute(k_qprep, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    const int threads = a.m < 256 ? 128 : (a.m < 1024 ? 256 : 512);
     k_qprep<<<1, threads, smem, s>>>(Q, b, a);
     return cudaGetLastError();
 }
@@ -521,7 +535,9 @@ __global__ void __launch_bounds__(kScanThreads) k_seed_scan(QueryBufs b, QueryAr
         const float q = b.qh32[pu];
         qq[u] = x2_pack(q, q);
     }
-    unsigned long long best = kEmptyKey;
+    // this thread's best window so far: score, then offset on ties
+    float bs = DINF;
+    unsigned bi = 0xffffffffu;
     const int64_t ntiles = (a.N + ProxyLayout::W - 1) / ProxyLayout::W;
     const bool piped = tile_pipeline<ProxyLayout>(smraw, b, m, ntiles, &b.st->tile_ctr[0], stages, [&](const Tile &t, int64_t i0) {
         // the pair (2v, 2v + 1), v = threadIdx.x + it * kPer / 2: its staged
@@ -533,10 +549,12 @@ __global__ void __launch_bounds__(kScanThreads) k_seed_scan(QueryBufs b, QueryAr
         static_for<kIt / 2>([&](auto itc) {
             constexpr int itA = decltype(itc)::value, itB = itA + kIt / 2;
             constexpr int oA = itA * kPer * 4, oB = itB * kPer * 4;  // bytes, in mh and in xs alike
-            const int64_t iA = i0 + (int64_t)kProxyStride * (2 * threadIdx.x + itA * kPer);
-            const int64_t iB = i0 + (int64_t)kProxyStride * (2 * threadIdx.x + itB * kPer);
-            const bool liveA0 = iA < a.N, liveA1 = iA + kProxyStride < a.N;
-            const bool liveB0 = iB < a.N, liveB1 = iB + kProxyStride < a.N;
+            // window offsets within the tile, and the windows the tile has
+            const int wA = kProxyStride * (2 * (int)threadIdx.x + itA * kPer);
+            const int wB = kProxyStride * (2 * (int)threadIdx.x + itB * kPer);
+            const int rem = a.N - i0 < ProxyLayout::W ? (int)(a.N - i0) : ProxyLayout::W;
+            const bool liveA0 = wA < rem, liveA1 = wA + kProxyStride < rem;
+            const bool liveB0 = wB < rem, liveB1 = wB + kProxyStride < rem;
             static_assert(ProxyLayout::NS == 2, "the proxy stage holds mh and is only");
             const unsigned long long mhA = lds64_at<oA>(sa), isA = lds64_at<oA + ProxyLayout::S * 4>(sa);
             const unsigned long long mhB = lds64_at<oB>(sa), isB = lds64_at<oB + ProxyLayout::S * 4>(sa);
@@ -592,16 +610,19 @@ __global__ void __launch_bounds__(kScanThreads) k_seed_scan(QueryBufs b, QueryAr
                     accB1 = fmaf(cB1, cB1, accB1);
                 }
             }
-            const unsigned long long kyA0 = make_key(accA0, (unsigned)iA);
-            const unsigned long long kyA1 = make_key(accA1, (unsigned)(iA + kProxyStride));
-            const unsigned long long kyB0 = make_key(accB0, (unsigned)iB);
-            const unsigned long long kyB1 = make_key(accB1, (unsigned)(iB + kProxyStride));
-            best = liveA0 && kyA0 < best ? kyA0 : best;
-            best = liveA1 && kyA1 < best ? kyA1 : best;
-            best = liveB0 && kyB0 < best ? kyB0 : best;
-            best = liveB1 && kyB1 < best ? kyB1 : best;
+            const unsigned iA = (unsigned)i0 + (unsigned)wA, iB = (unsigned)i0 + (unsigned)wB;
+            auto take = [&](float sc, unsigned i, bool live) {
+                const bool better = live && (sc < bs || (sc == bs && i < bi));
+                bs = better ? sc : bs;
+                bi = better ? i : bi;
+            };
+            take(accA0, iA, liveA0);
+            take(accA1, iA + kProxyStride, liveA1);
+            take(accB0, iB, liveB0);
+            take(accB1, iB + kProxyStride, liveB1);
         });
     });
+    unsigned long long best = bi == 0xffffffffu ? kEmptyKey : make_key(bs, bi);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         const unsigned long long v = __shfl_xor_sync(0xffffffffu, best, o);

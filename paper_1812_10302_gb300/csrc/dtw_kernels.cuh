@@ -164,25 +164,17 @@ __device__ __forceinline__ void dtw_body(const QueryBufs &b, const QueryArgs &a,
     // cooperatively, L terms per step (shorter critical path when most of
     // them sit near the best match; measured on 1e8 windows, m = 512,
     // ~38,000 survivors over 4,864 groups: 54 us, against 117 us with each
-    // group's 8 survivors pre-checked lane by lane).  In that schedule group
-    // G of the grid takes survivors G, G + groups, ... (in ascending bins,
-    // as the cursor would hand them out), so the next one's offset and bound
-    // are loaded while the current one is checked: no atomic and no
-    // dependent load opens a candidate.
+    // group's 8 survivors pre-checked lane by lane, and 61 us with each group
+    // taking every groups-th survivor, the next one's offset loaded ahead:
+    // the cursor balances the groups).
     unsigned pend = 0, my_idx = 0;
     float my_mh = 0.0f, my_is = 0.0f, my_ls = 0.0f;
     bool stop = false;
     const unsigned lmask = L == 32 ? 0xffffffffu : ((1u << L) - 1u);
-    const int groups = (int)(gridDim.x * (blockDim.x / L));
-    const bool lanewise = MODE == kModeSurv && count > (int64_t)groups * 64;
-    // (survivor counts fit an int: n_cand is one)
-    int c_next = (int)(blockIdx.x * (blockDim.x / L)) + gid;
-    unsigned nx_idx = 0u;
-    float nx_lb = 0.0f;
-    if (MODE == kModeSurv && !lanewise && c_next < count) {
-        nx_idx = b.sort_idx[c_next];
-        nx_lb = b.sort_lb[c_next];
-    }
+    const bool lanewise = MODE == kModeSurv && count > (int64_t)gridDim.x * (blockDim.x / L) * 64;
+    // the ordering gathered the survivors' statistics in order
+    const bool sorted_stats = MODE == kModeSurv && !b.surv_mh && b.sort_mh && count <= kSortStatCap;
+    float smh = 0.0f, sis = 0.0f, sls = 0.0f;
     while (true) {
         int c = 0, psrc = 0;
         unsigned idx;
@@ -216,6 +208,10 @@ __device__ __forceinline__ void dtw_body(const QueryBufs &b, const QueryArgs &a,
                     pmh = b.surv_mh[cc];
                     pis = b.surv_is[cc];
                     pls = b.surv_ls[cc];
+                } else if (pass && sorted_stats) {
+                    pmh = b.sort_mh[cc];
+                    pis = b.sort_is[cc];
+                    pls = b.sort_ls[cc];
                 } else if (pass) {
                     pmh = b.mu_hi[id];
                     pis = b.inv_sigma[id];
@@ -284,21 +280,20 @@ __device__ __forceinline__ void dtw_body(const QueryBufs &b, const QueryArgs &a,
             psrc = __ffs(pend) - 1;
             pend &= pend - 1;
             idx = __shfl_sync(gmask, my_idx, psrc, L);
-        } else if (MODE == kModeSurv) {
-            if (c_next >= count) break;
-            c = c_next;
-            idx = nx_idx;
-            lb = nx_lb;
-            coop = true;
-            c_next += groups;
-            if (c_next < count) {
-                nx_idx = b.sort_idx[c_next];
-                nx_lb = b.sort_lb[c_next];
-            }
         } else {
             if (lane == 0) c = atomicAdd(cursor, 1);
             c = __shfl_sync(gmask, c, 0, L);
             if (c >= count) break;
+            if (MODE == kModeSurv) {
+                idx = b.sort_idx[c];
+                lb = b.sort_lb[c];
+                if (sorted_stats) {  // (loaded beside the offset)
+                    smh = b.sort_mh[c];
+                    sis = b.sort_is[c];
+                    sls = b.sort_ls[c];
+                }
+                coop = true;
+            }
         }
         if (MODE == kModeSeed) {
             idx = st->seed_off[c];
@@ -339,6 +334,10 @@ __device__ __forceinline__ void dtw_body(const QueryBufs &b, const QueryArgs &a,
             mh = b.surv_mh[c];
             is = b.surv_is[c];
             ls = b.surv_ls[c];
+        } else if (MODE == kModeSurv && sorted_stats) {
+            mh = smh;
+            is = sis;
+            ls = sls;
         } else {
             mh = b.mu_hi[idx];
             is = b.inv_sigma[idx];

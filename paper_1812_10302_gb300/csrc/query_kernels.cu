@@ -535,9 +535,7 @@ __global__ void __launch_bounds__(kScanThreads) k_seed_scan(QueryBufs b, QueryAr
         const float q = b.qh32[pu];
         qq[u] = x2_pack(q, q);
     }
-    // this thread's best window so far: score, then offset on ties
-    float bs = DINF;
-    unsigned bi = 0xffffffffu;
+    unsigned long long best = kEmptyKey;
     const int64_t ntiles = (a.N + ProxyLayout::W - 1) / ProxyLayout::W;
     const bool piped = tile_pipeline<ProxyLayout>(smraw, b, m, ntiles, &b.st->tile_ctr[0], stages, [&](const Tile &t, int64_t i0) {
         // the pair (2v, 2v + 1), v = threadIdx.x + it * kPer / 2: its staged
@@ -611,18 +609,14 @@ __global__ void __launch_bounds__(kScanThreads) k_seed_scan(QueryBufs b, QueryAr
                 }
             }
             const unsigned iA = (unsigned)i0 + (unsigned)wA, iB = (unsigned)i0 + (unsigned)wB;
-            auto take = [&](float sc, unsigned i, bool live) {
-                const bool better = live && (sc < bs || (sc == bs && i < bi));
-                bs = better ? sc : bs;
-                bi = better ? i : bi;
-            };
-            take(accA0, iA, liveA0);
-            take(accA1, iA + kProxyStride, liveA1);
-            take(accB0, iB, liveB0);
-            take(accB1, iB + kProxyStride, liveB1);
+            const unsigned long long kyA0 = make_key(accA0, iA), kyA1 = make_key(accA1, iA + kProxyStride);
+            const unsigned long long kyB0 = make_key(accB0, iB), kyB1 = make_key(accB1, iB + kProxyStride);
+            best = liveA0 && kyA0 < best ? kyA0 : best;
+            best = liveA1 && kyA1 < best ? kyA1 : best;
+            best = liveB0 && kyB0 < best ? kyB0 : best;
+            best = liveB1 && kyB1 < best ? kyB1 : best;
         });
     });
-    unsigned long long best = bi == 0xffffffffu ? kEmptyKey : make_key(bs, bi);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         const unsigned long long v = __shfl_xor_sync(0xffffffffu, best, o);
@@ -1583,11 +1577,19 @@ __global__ void __launch_bounds__(512) k_bin_scatter(QueryBufs b) {
     for (int t = threadIdx.x; t < kBins; t += blockDim.x)
         if (h[t]) h[t] = atomicAdd(&st->bin_off[t], h[t]);
     __syncthreads();
+    const bool with_stats = b.sort_mh != nullptr && st->n_cand <= kSortStatCap;
     for (int64_t c = c0 + threadIdx.x; c < c1; c += blockDim.x) {
         const float lb = b.cand_lb[c];
         const int pos = atomicAdd(&h[bin_of(lb, thr)], 1);
+        const unsigned idx = b.cand_idx[c];
         b.sort_lb[pos] = lb;
-        b.sort_idx[pos] = b.cand_idx[c];
+        b.sort_idx[pos] = idx;
+        if (with_stats) {
+            const float is = b.inv_sigma[idx];
+            b.sort_mh[pos] = b.mu_hi[idx];
+            b.sort_is[pos] = is;
+            b.sort_ls[pos] = b.mu_lo[idx] * is;
+        }
     }
 }
 

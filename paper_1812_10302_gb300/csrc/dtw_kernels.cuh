@@ -164,17 +164,15 @@ __device__ __forceinline__ void dtw_body(const QueryBufs &b, const QueryArgs &a,
     // cooperatively, L terms per step (shorter critical path when most of
     // them sit near the best match; measured on 1e8 windows, m = 512,
     // ~38,000 survivors over 4,864 groups: 54 us, against 117 us with each
-    // group's 8 survivors pre-checked lane by lane, and 61 us with each group
-    // taking every groups-th survivor, the next one's offset loaded ahead:
-    // the cursor balances the groups).
+    // group's 8 survivors pre-checked lane by lane, 61 us with each group
+    // taking every groups-th survivor, the next one's offset loaded ahead
+    // (the cursor balances the groups), and 56 us with the survivors'
+    // statistics gathered in order by the ordering kernel).
     unsigned pend = 0, my_idx = 0;
     float my_mh = 0.0f, my_is = 0.0f, my_ls = 0.0f;
     bool stop = false;
     const unsigned lmask = L == 32 ? 0xffffffffu : ((1u << L) - 1u);
     const bool lanewise = MODE == kModeSurv && count > (int64_t)gridDim.x * (blockDim.x / L) * 64;
-    // the ordering gathered the survivors' statistics in order
-    const bool sorted_stats = MODE == kModeSurv && !b.surv_mh && b.sort_mh && count <= kSortStatCap;
-    float smh = 0.0f, sis = 0.0f, sls = 0.0f;
     while (true) {
         int c = 0, psrc = 0;
         unsigned idx;
@@ -208,10 +206,6 @@ __device__ __forceinline__ void dtw_body(const QueryBufs &b, const QueryArgs &a,
                     pmh = b.surv_mh[cc];
                     pis = b.surv_is[cc];
                     pls = b.surv_ls[cc];
-                } else if (pass && sorted_stats) {
-                    pmh = b.sort_mh[cc];
-                    pis = b.sort_is[cc];
-                    pls = b.sort_ls[cc];
                 } else if (pass) {
                     pmh = b.mu_hi[id];
                     pis = b.inv_sigma[id];
@@ -287,11 +281,6 @@ __device__ __forceinline__ void dtw_body(const QueryBufs &b, const QueryArgs &a,
             if (MODE == kModeSurv) {
                 idx = b.sort_idx[c];
                 lb = b.sort_lb[c];
-                if (sorted_stats) {  // (loaded beside the offset)
-                    smh = b.sort_mh[c];
-                    sis = b.sort_is[c];
-                    sls = b.sort_ls[c];
-                }
                 coop = true;
             }
         }
@@ -334,10 +323,6 @@ __device__ __forceinline__ void dtw_body(const QueryBufs &b, const QueryArgs &a,
             mh = b.surv_mh[c];
             is = b.surv_is[c];
             ls = b.surv_ls[c];
-        } else if (MODE == kModeSurv && sorted_stats) {
-            mh = smh;
-            is = sis;
-            ls = sls;
         } else {
             mh = b.mu_hi[idx];
             is = b.inv_sigma[idx];

@@ -75,7 +75,6 @@ cudaError_t launch_dtw_pool(const QueryBufs &base_in, const SurvPool &pool, cons
     QueryBufs base = base_in;
     base.sort_idx = pool.idx;
     base.sort_lb = pool.lb;
-    base.sort_mh = base.sort_is = base.sort_ls = nullptr;  // (the pool holds them)
     base.surv_mh = pool.mh;
     base.surv_is = pool.is;
     base.surv_ls = pool.ls;

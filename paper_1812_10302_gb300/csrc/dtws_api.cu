@@ -79,8 +79,6 @@ struct Lane {
     unsigned short *ord = nullptr;
     float *cand_lb = nullptr, *sort_lb = nullptr;
     unsigned *cand_idx = nullptr, *sort_idx = nullptr;
-    float *sort_st = nullptr;  // sort_mh | sort_is | sort_ls, sort_cap each
-    int64_t sort_cap = 0;
     StatsEntry stats;  // slot sized for the batch's smallest m
     int64_t stats_cap = 0;
     cudaStream_t stream = nullptr, side = nullptr;
@@ -120,8 +118,6 @@ struct dtws_ctx {
     float *cand_lb = nullptr, *sort_lb = nullptr;
     unsigned *cand_idx = nullptr, *sort_idx = nullptr;
     int64_t cand_cap = 0;
-    float *sort_st = nullptr;  // sort_mh | sort_is | sort_ls, sort_cap each
-    int64_t sort_cap = 0;
     // staging of host arrays: device side, and pinned host memory for results
     void *stage = nullptr;
     size_t stage_cap = 0;
@@ -511,8 +507,6 @@ dtws_status ensure_candidates(dtws_t h) {
     CK(need(&h->cand_idx, cap));
     CK(need(&h->sort_idx, cap));
     h->cand_cap = cap;
-    h->sort_cap = cap < kSortStatCap ? cap : kSortStatCap;
-    CK(need(&h->sort_st, 3 * h->sort_cap));
     return DTWS_OK;
 }
 
@@ -543,11 +537,6 @@ QueryBufs make_bufs(dtws_t h, const StatsEntry *se, const EnvEntry *ee) {
     b.sL = h->sL;
     b.cand_lb = h->cand_lb;
     b.sort_lb = h->sort_lb;
-    if (h->sort_st) {
-        b.sort_mh = h->sort_st;
-        b.sort_is = h->sort_st + h->sort_cap;
-        b.sort_ls = h->sort_st + 2 * h->sort_cap;
-    }
     b.cand_idx = h->cand_idx;
     b.sort_idx = h->sort_idx;
     b.status = h->status;
@@ -839,7 +828,7 @@ dtws_status run_query(dtws_t h, const float *Qd, int m, int r, int k, int64_t *i
 
 void free_lane(Lane &l) {
     void *ptrs[] = {l.st, l.qh32, l.Uq, l.Lq, l.sq, l.sU, l.sL, l.qh64, l.ord, l.cand_lb, l.sort_lb, l.cand_idx,
-                    l.sort_idx, l.sort_st};
+                    l.sort_idx};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     free_stats(l.stats);
@@ -895,8 +884,6 @@ dtws_status ensure_lanes(dtws_t h, int count, int m_min) {
         al(dalloc(&l.sort_lb, cap));
         al(dalloc(&l.cand_idx, cap));
         al(dalloc(&l.sort_idx, cap));
-        l.sort_cap = cap < kSortStatCap ? cap : kSortStatCap;
-        al(dalloc(&l.sort_st, 3 * l.sort_cap));
         al(dalloc(&l.stats.mu_hi, need_cap));
         al(dalloc(&l.stats.mu_lo, need_cap));
         al(dalloc(&l.stats.inv_sigma, need_cap));
@@ -943,9 +930,6 @@ QueryBufs lane_bufs(dtws_t h, const Lane &l, const EnvEntry *ee) {
     b.sort_lb = l.sort_lb;
     b.cand_idx = l.cand_idx;
     b.sort_idx = l.sort_idx;
-    b.sort_mh = l.sort_st;
-    b.sort_is = l.sort_st + l.sort_cap;
-    b.sort_ls = l.sort_st + 2 * l.sort_cap;
     return b;
 }
 
@@ -1343,7 +1327,7 @@ dtws_status dtws_destroy(dtws_t h) {
     if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
     void *ptrs[] = {h->x, h->x_sub, h->pf, h->bf, h->pok, h->pscale, h->envst, h->absmax, h->st, h->status, h->qh32, h->Uq,
                     h->Lq, h->sq, h->sU, h->sL, h->qh64, h->ord, h->cand_lb, h->sort_lb,
-                    h->cand_idx, h->sort_idx, h->sort_st, h->stage, h->xz_buf, h->xz_sel, h->xz_d64, h->bq_st, h->bq_f, h->bq_d, h->bq_o, h->pool.idx,
+                    h->cand_idx, h->sort_idx, h->stage, h->xz_buf, h->xz_sel, h->xz_d64, h->bq_st, h->bq_f, h->bq_d, h->bq_o, h->pool.idx,
                     h->pool.lb, h->pool.mh, h->pool.is, h->pool.ls, h->pool.cursor, h->pq_dev, h->plist_dev};
     for (void *p : ptrs)
         if (p) cudaFree(p);

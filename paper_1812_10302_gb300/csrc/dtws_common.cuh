@@ -60,9 +60,6 @@ constexpr int kTile = 1024;         // windows per lower-bound tile
 constexpr int kProxyTile = 4096;    // windows per proxy-scan tile (a multiple of kTile)
 constexpr int kStages = 4;          // shared-memory stages of the scan pipeline
 constexpr int kBins = 1024;         // survivor ordering bins
-// survivors whose window statistics the ordering also gathers, in order, so
-// that the survivor pass reads them with the offset (one load step fewer)
-constexpr int kSortStatCap = 1 << 19;
 constexpr int kDiagRMax = 511;      // widest band of the anti-diagonal DTW kernels (all shapes)
 constexpr int kDiagRMaxF32 = 1023;  // widest band of the FP32 anti-diagonal kernels (24, 32 cells per lane)
 constexpr uint64_t kEmptyKey = ~0ull;

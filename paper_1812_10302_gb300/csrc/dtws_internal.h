@@ -47,10 +47,6 @@ struct QueryBufs {
     float *sq, *sU, *sL;         // q_hat, Uq, Lq in that order [m]
     float *cand_lb, *sort_lb;    // survivors [cap]
     unsigned int *cand_idx, *sort_idx;
-    // their statistics in sort order (mean high part, 1/sigma, mean low part
-    // * 1/sigma), written by the ordering when there are at most
-    // kSortStatCap survivors; null where unused
-    float *sort_mh, *sort_is, *sort_ls;
     int *status;
     long long wait_ns;
     int num_sms;

@@ -511,7 +511,7 @@ __device__ void seed_lists(const QueryBufs &b, const QueryArgs &a, int n_random,
 // then merges every CTA's best into the proposals and builds the seed
 // lists, the work of k_prop_merge and k_seed_gather without their launches.
 template <int TERMS>
-__global__ void __launch_bounds__(kScanThreads, 4) k_seed_scan(QueryBufs b, QueryArgs a, int proposals, int stages,
+__global__ void __launch_bounds__(kScanThreads) k_seed_scan(QueryBufs b, QueryArgs a, int proposals, int stages,
                                                             int n_random, int H, unsigned long long rng) {
     constexpr int kPer = kScanConsumers * 64;           // scored windows per pass of the CTA (two per lane)
     constexpr int kIt = ProxyLayout::S / kPer;          // passes per tile
@@ -526,18 +526,17 @@ __global__ void __launch_bounds__(kScanThreads, 4) k_seed_scan(QueryBufs b, Quer
     // samples are the staged words 2l + p/kProxyStride and the next: one
     // aligned 8-byte load (p/kProxyStride is even), consecutive across the
     // warp (conflict-free), and one packed FP32x2 operation serves both.
-    // (the pairs (q_p, q_p) in shared memory, read as broadcasts: registers
-    // for four CTAs per SM)
-    __shared__ __align__(8) unsigned long long qq[TERMS];
+    // (the pairs (q_p, q_p) stay in registers: with them in shared memory,
+    // 56 registers and four CTAs per SM, the scan was no faster, 89.3 against
+    // 87.7 us per 1e8 windows -- its FMA pipe is the busiest unit either way)
     unsigned poff[TERMS];
+    unsigned long long qq[TERMS];
 #pragma unroll
     for (int u = 0; u < TERMS; ++u) {
         const int pu = (int)(((2 * u + 1) * (long long)m) / (2 * TERMS)) & ~(2 * kProxyStride - 1);
         poff[u] = 4u * (unsigned)(pu / kProxyStride);  // bytes
-        if ((int)threadIdx.x == u) {
-            const float q = b.qh32[pu];
-            qq[u] = x2_pack(q, q);
-        }
+        const float q = b.qh32[pu];
+        qq[u] = x2_pack(q, q);
     }
     unsigned long long best = kEmptyKey;
     const int64_t ntiles = (a.N + ProxyLayout::W - 1) / ProxyLayout::W;
@@ -579,9 +578,8 @@ __global__ void __launch_bounds__(kScanThreads, 4) k_seed_scan(QueryBufs b, Quer
                 for (int u = 0; u < TERMS; ++u) {
                     const unsigned long long xA = lds64_at<oA>(xa + poff[u]);
                     const unsigned long long xB = lds64_at<oB>(xa + poff[u]);
-                    const unsigned long long q2 = qq[u];
-                    const unsigned long long cA = x2_fma(xA, nisA, x2_add(q2, kwA));
-                    const unsigned long long cB = x2_fma(xB, nisB, x2_add(q2, kwB));
+                    const unsigned long long cA = x2_fma(xA, nisA, x2_add(qq[u], kwA));
+                    const unsigned long long cB = x2_fma(xB, nisB, x2_add(qq[u], kwB));
                     if (u & 1) {
                         sA1 = x2_fma(cA, cA, sA1);
                         sB1 = x2_fma(cB, cB, sB1);
@@ -1345,9 +1343,17 @@ __device__ __forceinline__ float warp_sum(float v) {
 // (bound, offset) by one warp-aggregated atomic.  A dense row (a loose
 // bound) gives each passing lane its own window's terms; otherwise the warp
 // takes one window at a time, 32 terms per step.  Returns the survivors.
-__device__ __forceinline__ int lb_row_keogh(const Tile &t, const QueryBufs &b, QueryState *st, const int *o_s,
-                                         const float *u_s, const float *l_s, int m, float thr, unsigned bal,
-                                         int wrow, int lane, float kim, float mh, float is, float ls, int64_t i0) {
+// A window that passes Eq. 8 one at a time then takes the first 32 terms of
+// Eq. 10 (q_hat against the window's envelope, the same bound the survivor
+// pass's pre-check and tail use, from the exact or the block envelope) and
+// is dropped when they alone exceed thr: most windows that pass the
+// scan's Eq. 8 fail there, and the warp that holds the window's statistics
+// settles them for one load step instead of handing them to the survivor
+// pass's per-candidate chain.
+__device__ __forceinline__ int lb_row_keogh(const Tile &t, const QueryBufs &b, const QueryArgs &a, QueryState *st,
+                                         const int *o_s, const float *u_s, const float *l_s, const float *q_s,
+                                         int m, float thr, unsigned bal, int wrow, int lane, float kim, float mh,
+                                         float is, float ls, int64_t i0) {
     const int w = wrow + lane;
     unsigned keep = 0;   // windows of this row that survive Eq. 8
     float my_lb = 0.0f;  // lane t holds window t's bound when it survives
@@ -1400,6 +1406,28 @@ __device__ __forceinline__ int lb_row_keogh(const Tile &t, const QueryBufs &b, Q
                 if (s2 > thr) break;
             }
             if (s2 > thr) continue;
+            if (b.U || b.stmax) {
+                TailCtx tc;
+                tc.Uw = b.U ? b.U + (i0 + ws) : nullptr;
+                tc.Lw = b.L ? b.L + (i0 + ws) : nullptr;
+                tc.stmax = b.stmax;
+                tc.stmin = b.stmin;
+                tc.nblk = b.nblk;
+                tc.n = b.n;
+                tc.t0 = i0 + ws;
+                tc.r = a.r;
+                float term = 0.0f;
+                if (lane < m) {
+                    float U, Lo;
+                    env_at(tc, o_s[lane], U, Lo);
+                    const float u = fmaf(U - smh, sis, -sls), l = fmaf(Lo - smh, sis, -sls), q = q_s[lane];
+                    const float d = fmaxf(q - u, 0.0f) + fmaxf(l - q, 0.0f);
+                    term = d * d;
+                }
+                const float s3 = warp_sum(term);
+                if (s3 > thr) continue;
+                s2 = fmaxf(s2, s3);
+            }
             keep |= 1u << src;
             if (lane == src) my_lb = fmaxf(kim, s2);
         }
@@ -1431,11 +1459,12 @@ __global__ void __launch_bounds__(kScanThreads) k_lb_scan(QueryBufs b, QueryArgs
     constexpr int kPerWarp = TW / kScanConsumers;
     // the ordered query terms the scan uses, in shared memory
     __shared__ int o_s[kEqSmem * 32];
-    __shared__ float u_s[kEqSmem * 32], l_s[kEqSmem * 32];
+    __shared__ float u_s[kEqSmem * 32], l_s[kEqSmem * 32], q_s[32];
     for (int j = threadIdx.x; j < kEqSmem * 32; j += blockDim.x) {
         o_s[j] = j < m ? (int)b.ord[j] : 0;
         u_s[j] = j < m ? b.sU[j] : 0.0f;
         l_s[j] = j < m ? b.sL[j] : 0.0f;
+        if (j < 32) q_s[j] = j < m ? b.sq[j] : 0.0f;
     }
     unsigned long long c1 = 0, c2 = 0;
     const int64_t ntiles = (a.N + TW - 1) / TW;
@@ -1466,7 +1495,8 @@ __global__ void __launch_bounds__(kScanThreads) k_lb_scan(QueryBufs b, QueryArgs
             }
             const unsigned bal = __ballot_sync(0xffffffffu, pass);
             c1 += __popc(bal);
-            if (bal) c2 += lb_row_keogh(t, b, st, o_s, u_s, l_s, m, thr, bal, w - lane, lane, kim, mh, is, ls, i0);
+            if (bal)
+                c2 += lb_row_keogh(t, b, a, st, o_s, u_s, l_s, q_s, m, thr, bal, w - lane, lane, kim, mh, is, ls, i0);
         }
     });
     if (lane == 0) {

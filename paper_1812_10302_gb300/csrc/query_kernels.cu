@@ -1343,17 +1343,13 @@ __device__ __forceinline__ float warp_sum(float v) {
 // (bound, offset) by one warp-aggregated atomic.  A dense row (a loose
 // bound) gives each passing lane its own window's terms; otherwise the warp
 // takes one window at a time, 32 terms per step.  Returns the survivors.
-// A window that passes Eq. 8 one at a time then takes the first 32 terms of
-// Eq. 10 (q_hat against the window's envelope, the same bound the survivor
-// pass's pre-check and tail use, from the exact or the block envelope) and
-// is dropped when they alone exceed thr: most windows that pass the
-// scan's Eq. 8 fail there, and the warp that holds the window's statistics
-// settles them for one load step instead of handing them to the survivor
-// pass's per-candidate chain.
-__device__ __forceinline__ int lb_row_keogh(const Tile &t, const QueryBufs &b, const QueryArgs &a, QueryState *st,
-                                         const int *o_s, const float *u_s, const float *l_s, const float *q_s,
-                                         int m, float thr, unsigned bal, int wrow, int lane, float kim, float mh,
-                                         float is, float ls, int64_t i0) {
+// (Eq. 10's first 32 terms here as well, for each window past Eq. 8, halved
+// the survivors on 1e8 windows, m = 512 -- 38,000 to 21,000, the survivor
+// pass 55 -> 43 us -- but slowed the scan 278 -> 300 us: the random loads of
+// the series envelope stall the warps that feed the ring.)
+__device__ __forceinline__ int lb_row_keogh(const Tile &t, const QueryBufs &b, QueryState *st, const int *o_s,
+                                         const float *u_s, const float *l_s, int m, float thr, unsigned bal,
+                                         int wrow, int lane, float kim, float mh, float is, float ls, int64_t i0) {
     const int w = wrow + lane;
     unsigned keep = 0;   // windows of this row that survive Eq. 8
     float my_lb = 0.0f;  // lane t holds window t's bound when it survives
@@ -1406,28 +1402,6 @@ __device__ __forceinline__ int lb_row_keogh(const Tile &t, const QueryBufs &b, c
                 if (s2 > thr) break;
             }
             if (s2 > thr) continue;
-            if (b.U || b.stmax) {
-                TailCtx tc;
-                tc.Uw = b.U ? b.U + (i0 + ws) : nullptr;
-                tc.Lw = b.L ? b.L + (i0 + ws) : nullptr;
-                tc.stmax = b.stmax;
-                tc.stmin = b.stmin;
-                tc.nblk = b.nblk;
-                tc.n = b.n;
-                tc.t0 = i0 + ws;
-                tc.r = a.r;
-                float term = 0.0f;
-                if (lane < m) {
-                    float U, Lo;
-                    env_at(tc, o_s[lane], U, Lo);
-                    const float u = fmaf(U - smh, sis, -sls), l = fmaf(Lo - smh, sis, -sls), q = q_s[lane];
-                    const float d = fmaxf(q - u, 0.0f) + fmaxf(l - q, 0.0f);
-                    term = d * d;
-                }
-                const float s3 = warp_sum(term);
-                if (s3 > thr) continue;
-                s2 = fmaxf(s2, s3);
-            }
             keep |= 1u << src;
             if (lane == src) my_lb = fmaxf(kim, s2);
         }
@@ -1459,12 +1433,11 @@ __global__ void __launch_bounds__(kScanThreads) k_lb_scan(QueryBufs b, QueryArgs
     constexpr int kPerWarp = TW / kScanConsumers;
     // the ordered query terms the scan uses, in shared memory
     __shared__ int o_s[kEqSmem * 32];
-    __shared__ float u_s[kEqSmem * 32], l_s[kEqSmem * 32], q_s[32];
+    __shared__ float u_s[kEqSmem * 32], l_s[kEqSmem * 32];
     for (int j = threadIdx.x; j < kEqSmem * 32; j += blockDim.x) {
         o_s[j] = j < m ? (int)b.ord[j] : 0;
         u_s[j] = j < m ? b.sU[j] : 0.0f;
         l_s[j] = j < m ? b.sL[j] : 0.0f;
-        if (j < 32) q_s[j] = j < m ? b.sq[j] : 0.0f;
     }
     unsigned long long c1 = 0, c2 = 0;
     const int64_t ntiles = (a.N + TW - 1) / TW;
@@ -1495,8 +1468,7 @@ __global__ void __launch_bounds__(kScanThreads) k_lb_scan(QueryBufs b, QueryArgs
             }
             const unsigned bal = __ballot_sync(0xffffffffu, pass);
             c1 += __popc(bal);
-            if (bal)
-                c2 += lb_row_keogh(t, b, a, st, o_s, u_s, l_s, q_s, m, thr, bal, w - lane, lane, kim, mh, is, ls, i0);
+            if (bal) c2 += lb_row_keogh(t, b, st, o_s, u_s, l_s, m, thr, bal, w - lane, lane, kim, mh, is, ls, i0);
         }
     });
     if (lane == 0) {

@@ -714,7 +714,10 @@ __device__ __forceinline__ void diag_step_df(const dfloat (&qv)[K], const dfloat
         // (+/-1e15): a cell outside [0, m)^2 costs ~4e30, far above any DTW
         // and far below FP32 overflow over 2m steps, and never turns
         // TwoSum into NaN
-        const dfloat best = df_min(df_min(left, up), p2[t]);
+        // (the cell's own predecessor and the diagonal first: only the last
+        // minimum waits for the neighbour lane's value; the minimum of
+        // double-floats is exact, so the order does not change the result)
+        const dfloat best = ODD ? df_min(up, df_min(left, p2[t])) : df_min(left, df_min(up, p2[t]));
         dfloat v = df_add_pos(df_sqr(df_sub(qv[t], cv[t])), best);
         if (ODD ? (p >= r) : (p > r)) v = INF;  // past the band's cells
         cur[t] = v;
@@ -832,7 +835,7 @@ __device__ __forceinline__ void diag_step_df_mw(const dfloat (&qv)[K], const dfl
         const int p = gl * K + t;
         const dfloat left = ODD ? p1[t] : (t == 0 ? nb : p1[t > 0 ? t - 1 : 0]);
         const dfloat up = ODD ? (t == K - 1 ? nb : p1[t < K - 1 ? t + 1 : 0]) : p1[t];
-        const dfloat best = df_min(df_min(left, up), p2[t]);
+        const dfloat best = ODD ? df_min(up, df_min(left, p2[t])) : df_min(left, df_min(up, p2[t]));
         dfloat v = df_add_pos(df_sqr(df_sub(qv[t], cv[t])), best);
         if (ODD ? (p >= r) : (p > r)) v = INF;
         cur[t] = v;

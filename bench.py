@@ -405,7 +405,13 @@ def gpu_arm(args):
         got = n_off * cells(m, r) / (walk_ms * 1e-3)
         dtw_ms = float(phases[4])
         surv = st["dtw_cells"] / (dtw_ms * 1e-3) if dtw_ms > 0 else None
-        dtw_roof = {"kernel": "k_dtw (the walk: dtws_dtw_at, no pruning)", "bound": "alu", "achieved": got,
+        # the library's shape for DTW at offsets: four cells per lane on 8 or
+        # 16 lanes for bands of 9..64 cells, else the survivor pass's shape
+        need = r + 1
+        shape = (f"{8 if need <= 32 else 16} lanes x 4 cells per window" if 8 < need <= 64
+                 else "the survivor pass's shape")
+        dtw_roof = {"kernel": "k_dtw (the walk: dtws_dtw_at, no pruning)", "shape": shape,
+                    "bound": "alu", "achieved": got,
                     "peak": peak_cells, "unit": "cells/s", "frac": got / peak_cells, "ops_per_cell": 5,
                     "peak_source": f"{sms} SMs x 128 lanes x {mhz:.0f} MHz / 5",
                     "windows": n_off, "cells_per_window": cells(m, r), "ms_per_launch": walk_ms,

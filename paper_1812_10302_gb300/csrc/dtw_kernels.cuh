@@ -597,6 +597,33 @@ static cudaError_t dtw_dispatch(const QueryBufs &b, const QueryArgs &a, const in
     DtwPlan p;
     const bool tail = MODE == kModeSurv && (b.U != nullptr || b.stmax != nullptr);
     const bool tuned = a.tune_l > 0 && plan_shape<float>(a.m, a.r, tail, a.tune_l, a.tune_k, a.tune_w, &p);
+    if constexpr (MODE == kModeOut) {
+        // DTW at given offsets: every walk runs to its end, so the grid's
+        // throughput counts, not one walk's latency -- four cells per lane
+        // (half as many shuffles, rotations and band checks per cell as two)
+        // for bands of 9 to 64 cells; the same cells, the same values
+        const int need = a.r + 1;
+        if (!tuned && need > 8 && need <= 64) {
+            const bool fit = need <= 32 ? plan_fits<float, 8, 4>(a.m, a.r, false, &p)
+                                        : plan_fits<float, 16, 4>(a.m, a.r, false, &p);
+            if (fit) {
+                const int blocks = dtw_blocks(p, b.num_sms, count_for_grid);
+                cudaError_t e;
+                if (p.L == 8) {
+                    e = cudaFuncSetAttribute(k_dtw<8, 4, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)p.smem);
+                    if (e == cudaSuccess)
+                        k_dtw<8, 4, MODE><<<blocks, p.warps * 32, p.smem, s>>>(b, a, offsets, count, out, p.staged);
+                } else {
+                    e = cudaFuncSetAttribute(k_dtw<16, 4, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)p.smem);
+                    if (e == cudaSuccess)
+                        k_dtw<16, 4, MODE><<<blocks, p.warps * 32, p.smem, s>>>(b, a, offsets, count, out, p.staged);
+                }
+                return e != cudaSuccess ? e : cudaGetLastError();
+            }
+        }
+    }
     if (!tuned && a.r > kDiagRMax && a.r <= kWideRMax)
         return dtw_wide_launch<MODE>(b, a, offsets, count, out, count_for_grid, s);
     if (!tuned && !plan_dtw<float>(a.m, a.r, tail, &p)) return cudaErrorInvalidValue;

@@ -14,6 +14,15 @@ cudaError_t launch_dtw_at(const QueryBufs &b, const QueryArgs &a, const int64_t 
     return dtw_dispatch<kModeOut>(b, a, offsets, count, out, count, s);
 }
 
+bool dtw_default_shape(int m, int r, int *L, int *K, int *warps) {
+    DtwPlan p;
+    if (r > kDiagRMax || !plan_dtw<float>(m, r, false, &p)) return false;
+    *L = p.L;
+    *K = p.K;
+    *warps = p.warps;
+    return true;
+}
+
 bool dtw_shape_valid(int m, int r, int L, int K, int warps) {
     DtwPlan p;
     return plan_shape<float>(m, r, true, L, K, warps, &p) && plan_shape<float>(m, r, false, L, K, warps, &p);

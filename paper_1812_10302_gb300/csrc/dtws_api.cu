@@ -1677,8 +1677,12 @@ dtws_status dtws_autotune(dtws_t h, const int32_t *m_arr, const int32_t *r_arr, 
             *ms = best;
             return cudaSuccess;
         };
+        // the default is the survivor pass's own shape (DTW at offsets alone
+        // takes a four-cell shape for bands of 9 to 64 cells)
+        int dL = 0, dK = 0, dW = 0;
+        if (!dtw_default_shape(m, r, &dL, &dK, &dW)) dL = dK = dW = 0;
         float ms_def = 0.f;
-        CK(timed(0, 0, 0, ref_d, &ms_def));
+        CK(timed(dL, dK, dW, ref_d, &ms_def));
         CK(cudaMemcpy(ref.data(), ref_d, fb, cudaMemcpyDeviceToHost));
         TuneEntry best{m, r, 0, 0, 0, ms_def, ms_def};
         const int Ls[6] = {1, 2, 4, 8, 16, 32}, Ks[10] = {0, 1, 2, 3, 4, 6, 8, 10, 12, 16}, Ws[3] = {2, 4, 8};

@@ -188,7 +188,10 @@ cudaError_t launch_xz_finalize(const QueryBufs &b, const QueryArgs &a, int64_t *
 // element-wise building blocks
 cudaError_t launch_dtw_at(const QueryBufs &b, const QueryArgs &a, const int64_t *offsets,
                           int64_t count, float *out, cudaStream_t s);
-// the autotuner's probes: a shape (see plan_shape) and DTW at offsets with it
+// the autotuner's probes: a shape (see plan_shape) and DTW at offsets with it;
+// the survivor pass's default shape for (m, r) (false: the multi-warp or
+// row-systolic kernel, not a plan_shape shape)
+bool dtw_default_shape(int m, int r, int *L, int *K, int *warps);
 bool dtw_shape_valid(int m, int r, int L, int K, int warps);
 cudaError_t launch_dtw_at_shape(const QueryBufs &b, QueryArgs a, const int64_t *offsets, int64_t count, float *out,
                                 int L, int K, int warps, cudaStream_t s);

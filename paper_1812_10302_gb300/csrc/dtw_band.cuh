@@ -296,7 +296,9 @@ __device__ __forceinline__ void diag_step(const float (&qv)[K], const float (&cv
         const float d = qv[((t - QP) % K + K) % K] - cv[(t + CP) % K];
         float v = fmaf(d, d, min3f(left, up, p2[t]));
         if (ODD) {
-            if constexpr (K <= 8) v = fmaxf(v, pen[t]);
+            // pen is 0 or +inf and v >= 0: an add, which the FMA pipe takes,
+            // instead of a maximum on the ALU pipe, the walk's busiest
+            if constexpr (K <= 8) v = v + pen[t];
             else if (lane * K + t == r) v = INF;
         }
         cur[t] = v;
@@ -493,7 +495,7 @@ __device__ __forceinline__ void diag_step_mw(const float (&qv)[K], const float (
         const float d = qv[((t - QP) % K + K) % K] - cv[(t + CP) % K];
         float v = fmaf(d, d, min3f(left, up, p2[t]));
         if (ODD) {
-            if constexpr (K <= 8) v = fmaxf(v, pen[t]);
+            if constexpr (K <= 8) v = v + pen[t];  // (as in diag_step)
             else if (gl * K + t == r) v = INF;
         }
         cur[t] = v;

@@ -820,8 +820,18 @@ struct DfXchg {
 };
 
 
+// The cells' costs (q_hat_i - c_j)^2 of a step, from its register windows.
+template <int K>
+__device__ __forceinline__ void df_costs(const dfloat (&qv)[K], const dfloat (&cv)[K], dfloat (&cst)[K]) {
+#pragma unroll
+    for (int t = 0; t < K; ++t) cst[t] = df_sqr(df_sub(qv[t], cv[t]));
+}
+
+// A step of the multi-warp walk with its cells' costs given (computed while
+// the previous step's values were still on their way: only the minimum and
+// the addition wait for them).
 template <int W, int K, int ODD>
-__device__ __forceinline__ void diag_step_df_mw(const dfloat (&qv)[K], const dfloat (&cv)[K], dfloat (&p1)[K],
+__device__ __forceinline__ void diag_step_df_mw(const dfloat (&cst)[K], dfloat (&p1)[K],
                                                 dfloat (&p2)[K], int gl, int lane, int w, int r,
                                                 const DfXchg &x, int buf) {
     const dfloat INF = dfloat{1e30f, 0.0f};
@@ -838,7 +848,7 @@ __device__ __forceinline__ void diag_step_df_mw(const dfloat (&qv)[K], const dfl
         const dfloat left = ODD ? p1[t] : (t == 0 ? nb : p1[t > 0 ? t - 1 : 0]);
         const dfloat up = ODD ? (t == K - 1 ? nb : p1[t < K - 1 ? t + 1 : 0]) : p1[t];
         const dfloat best = ODD ? df_min(up, df_min(left, p2[t])) : df_min(left, df_min(up, p2[t]));
-        dfloat v = df_add_pos(df_sqr(df_sub(qv[t], cv[t])), best);
+        dfloat v = df_add_pos(cst[t], best);
         if (ODD ? (p >= r) : (p > r)) v = INF;
         cur[t] = v;
     }
@@ -902,6 +912,10 @@ __device__ double dtw_diag_df_mw(const dfloat *__restrict__ qs, const dfloat *__
     df_mw_publish<W, K>(p1, lane, w, x, buf, bar_id);  // buffer 0 := the all-inf anti-diagonal -1
     const int last = 2 * m - 2;
     int a = 0, bi, bj;
+    // each step's costs are formed before the previous step's exchange, so
+    // the chain from one step's values to the next holds only the minimum,
+    // the addition and the exchange
+    dfloat cst[K], cst2[K];
     if (r & 1) {
         const int qb = (r - 1) >> 1, cb = (1 - r) >> 1;
 #pragma unroll
@@ -909,10 +923,12 @@ __device__ double dtw_diag_df_mw(const dfloat *__restrict__ qs, const dfloat *__
             qv[t] = qs[qb - (gl * K + t)];
             cv[t] = cs[cb + (gl * K + t)];
         }
-        diag_step_df_mw<W, K, 1>(qv, cv, p1, p2, gl, lane, w, r, x, buf);
+        df_costs<K>(qv, cv, cst);
+        diag_step_df_mw<W, K, 1>(cst, p1, p2, gl, lane, w, r, x, buf);
+        shift_q_df_mw<K>(qv, qs, qb + 1, gl, lane);
+        df_costs<K>(qv, cv, cst);
         df_mw_publish<W, K>(p1, lane, w, x, buf, bar_id);
         a = 1;
-        shift_q_df_mw<K>(qv, qs, qb + 1, gl, lane);
     } else {
         const int qb = r >> 1, cb = -(r >> 1);
 #pragma unroll
@@ -920,18 +936,23 @@ __device__ double dtw_diag_df_mw(const dfloat *__restrict__ qs, const dfloat *__
             qv[t] = qs[qb - (gl * K + t)];
             cv[t] = cs[cb + (gl * K + t)];
         }
+        df_costs<K>(qv, cv, cst);
     }
     bi = (a + r) >> 1;
     bj = (a - r) >> 1;
     for (; a + 1 <= last; a += 2, ++bi, ++bj) {
-        diag_step_df_mw<W, K, 0>(qv, cv, p1, p2, gl, lane, w, r, x, buf);
-        df_mw_publish<W, K>(p1, lane, w, x, buf, bar_id);
+        // even step a (costs in cst); the odd step's operands and costs
         shift_c_df_mw<K>(cv, cs, bj + 1, gl, lane);
-        diag_step_df_mw<W, K, 1>(qv, cv, p1, p2, gl, lane, w, r, x, buf);
+        df_costs<K>(qv, cv, cst2);
+        diag_step_df_mw<W, K, 0>(cst, p1, p2, gl, lane, w, r, x, buf);
         df_mw_publish<W, K>(p1, lane, w, x, buf, bar_id);
+        // odd step a + 1 (costs in cst2); the next even step's
         shift_q_df_mw<K>(qv, qs, bi + 1, gl, lane);
+        df_costs<K>(qv, cv, cst);
+        diag_step_df_mw<W, K, 1>(cst2, p1, p2, gl, lane, w, r, x, buf);
+        df_mw_publish<W, K>(p1, lane, w, x, buf, bar_id);
     }
-    if (a == last) diag_step_df_mw<W, K, 0>(qv, cv, p1, p2, gl, lane, w, r, x, buf);
+    if (a == last) diag_step_df_mw<W, K, 0>(cst, p1, p2, gl, lane, w, r, x, buf);
     const int pe = (r - ((last + r) & 1)) >> 1;
 #pragma unroll
     for (int t = 0; t < K; ++t)

@@ -242,10 +242,16 @@ def _torch():
     return torch
 
 
+_CUDA_AVAILABLE = None  # torch.cuda.is_available(), asked once per process
+
+
 def _stream_ptr(stream) -> int:
+    global _CUDA_AVAILABLE
     if stream is None:
         torch = _torch()
-        return int(torch.cuda.current_stream().cuda_stream) if torch.cuda.is_available() else 0
+        if _CUDA_AVAILABLE is None:
+            _CUDA_AVAILABLE = bool(torch.cuda.is_available())
+        return int(torch.cuda.current_stream().cuda_stream) if _CUDA_AVAILABLE else 0
     if isinstance(stream, int):
         return stream
     return int(stream.cuda_stream)

@@ -541,7 +541,7 @@ static bool plan_shape(int m, int r, bool tail, int L, int K, int warps, DtwPlan
 #define DTWS_TRY(LL, KK) \
     if (!ok && L == LL && K == KK) ok = plan_fits<T, LL, KK>(m, r, tail, p);
     DTWS_TRY(1, 1) DTWS_TRY(2, 1) DTWS_TRY(4, 1) DTWS_TRY(8, 1) DTWS_TRY(16, 1)
-    DTWS_TRY(4, 2) DTWS_TRY(8, 2) DTWS_TRY(16, 2)
+    DTWS_TRY(4, 2) DTWS_TRY(8, 2) DTWS_TRY(16, 2) DTWS_TRY(8, 4) DTWS_TRY(16, 4)
     DTWS_TRY(32, 1) DTWS_TRY(32, 2) DTWS_TRY(32, 3) DTWS_TRY(32, 4) DTWS_TRY(32, 6) DTWS_TRY(32, 8) \
         DTWS_TRY(32, 10) DTWS_TRY(32, 12) DTWS_TRY(32, 16)
     DTWS_TRY(1, 0) DTWS_TRY(2, 0) DTWS_TRY(4, 0) DTWS_TRY(8, 0) DTWS_TRY(16, 0) DTWS_TRY(32, 0)
@@ -637,7 +637,7 @@ static cudaError_t dtw_dispatch(const QueryBufs &b, const QueryArgs &a, const in
         return cudaGetLastError();                                                                            \
     }
     DTWS_CASE(1, 1) DTWS_CASE(2, 1) DTWS_CASE(4, 1) DTWS_CASE(8, 1) DTWS_CASE(16, 1)
-    DTWS_CASE(4, 2) DTWS_CASE(8, 2) DTWS_CASE(16, 2)
+    DTWS_CASE(4, 2) DTWS_CASE(8, 2) DTWS_CASE(16, 2) DTWS_CASE(8, 4) DTWS_CASE(16, 4)
     DTWS_CASE(32, 1) DTWS_CASE(32, 2) DTWS_CASE(32, 3) DTWS_CASE(32, 4) DTWS_CASE(32, 6) DTWS_CASE(32, 8) \
     DTWS_CASE(32, 10) DTWS_CASE(32, 12) DTWS_CASE(32, 16)
     DTWS_CASE(1, 0) DTWS_CASE(2, 0) DTWS_CASE(4, 0) DTWS_CASE(8, 0) DTWS_CASE(16, 0) DTWS_CASE(32, 0)

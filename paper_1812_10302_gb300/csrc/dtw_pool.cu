@@ -81,7 +81,7 @@ cudaError_t launch_dtw_pool(const QueryBufs &base_in, const SurvPool &pool, cons
 #define DTWS_CASE(LL, KK) \
     if (L == LL && K == KK) return pool_launch<LL, KK>(base, pq, list, nlist, m_max, r_max, s);
     DTWS_CASE(1, 1) DTWS_CASE(2, 1) DTWS_CASE(4, 1) DTWS_CASE(8, 1) DTWS_CASE(16, 1)
-    DTWS_CASE(4, 2) DTWS_CASE(8, 2) DTWS_CASE(16, 2)
+    DTWS_CASE(4, 2) DTWS_CASE(8, 2) DTWS_CASE(16, 2) DTWS_CASE(8, 4) DTWS_CASE(16, 4)
     DTWS_CASE(32, 1) DTWS_CASE(32, 2) DTWS_CASE(32, 3) DTWS_CASE(32, 4) DTWS_CASE(32, 6) DTWS_CASE(32, 8)
     DTWS_CASE(32, 10) DTWS_CASE(32, 12) DTWS_CASE(32, 16)
 #undef DTWS_CASE

@@ -166,14 +166,14 @@ __device__ __forceinline__ void dtw_body(const QueryBufs &b, const QueryArgs &a,
     // ~38,000 survivors over 4,864 groups: 54 us, against 117 us with each
     // group's 8 survivors pre-checked lane by lane, 61 us with each group
     // taking every groups-th survivor, the next one's offset loaded ahead
-    // (the cursor balances the groups), and 56 us with the survivors'
-    // statistics gathered in order by the ordering kernel).
+    // (the cursor balances the groups), 56 us with the survivors'
+    // statistics gathered in order by the ordering kernel, and 59 us with
+    // each group taking its next slot one candidate ahead).
     unsigned pend = 0, my_idx = 0;
     float my_mh = 0.0f, my_is = 0.0f, my_ls = 0.0f;
     bool stop = false;
     const unsigned lmask = L == 32 ? 0xffffffffu : ((1u << L) - 1u);
     const bool lanewise = MODE == kModeSurv && count > (int64_t)gridDim.x * (blockDim.x / L) * 64;
-    int nxt = -1;  // (the cooperative survivor schedule, lane 0) the next slot, already taken
     while (true) {
         int c = 0, psrc = 0;
         unsigned idx;
@@ -275,22 +275,15 @@ __device__ __forceinline__ void dtw_body(const QueryBufs &b, const QueryArgs &a,
             psrc = __ffs(pend) - 1;
             pend &= pend - 1;
             idx = __shfl_sync(gmask, my_idx, psrc, L);
-        } else if (MODE == kModeSurv) {
-            // the slot taken a candidate ahead (lane 0), so the cursor's
-            // round trip overlaps the previous candidate's checks; a group
-            // that stops at a bin floor leaves its taken slot, which lies in
-            // a later bin and is pruned all the same
-            if (lane == 0) c = nxt >= 0 ? nxt : atomicAdd(cursor, 1);
-            c = __shfl_sync(gmask, c, 0, L);
-            if (c >= count) break;
-            if (lane == 0) nxt = atomicAdd(cursor, 1);
-            idx = b.sort_idx[c];
-            lb = b.sort_lb[c];
-            coop = true;
         } else {
             if (lane == 0) c = atomicAdd(cursor, 1);
             c = __shfl_sync(gmask, c, 0, L);
             if (c >= count) break;
+            if (MODE == kModeSurv) {
+                idx = b.sort_idx[c];
+                lb = b.sort_lb[c];
+                coop = true;
+            }
         }
         if (MODE == kModeSeed) {
             idx = st->seed_off[c];

@@ -862,6 +862,10 @@ __device__ __forceinline__ void diag_step_df_mw(const dfloat (&cst)[K], dfloat (
 template <int W, int K>
 __device__ __forceinline__ void df_mw_publish(const dfloat (&p1)[K], int lane, int w, DfXchg &x, int &buf,
                                               int bar_id) {
+    if constexpr (W == 1) {  // one warp: no other warp reads the boundary cells
+        buf ^= 1;
+        return;
+    }
     const int nbuf = buf ^ 1;
     if (lane == 0) x.first[nbuf][w] = p1[0];
     if (lane == 31) x.last[nbuf][w] = p1[K - 1];

@@ -494,10 +494,11 @@ __global__ void __launch_bounds__(256, dtw_min_blocks(K)) k_dtw_pool(QueryBufs b
 template <int L, int K>
 struct PreShape {
     // the double-float walk for the FP32 walk's shape (L lanes, K cells):
-    // as many warps as the FP32 walk has cells per lane (at most 4), the
-    // r+1 <= L*K cells spread over them
-    static constexpr int W = (L < 32) ? 1 : (K <= 4 ? K : 4);
-    static constexpr int K2 = (L < 32 || K <= 4) ? 1 : (K * 32 + 127) / 128;
+    // one warp with the same cells per lane up to 4 (no exchange between
+    // warps at each step), four warps beyond, the r+1 <= L*K cells spread
+    // over them
+    static constexpr int W = (L < 32 || K <= 4) ? 1 : 4;
+    static constexpr int K2 = (L < 32) ? 1 : (K <= 4 ? K : (K * 32 + 127) / 128);
 };
 __host__ __device__ inline size_t pre_span(int m, int r, int lanes, int k) {
     return (size_t)((m + 2 * diag_pad(r, lanes, k) + 3) & ~3);

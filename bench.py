@@ -358,7 +358,9 @@ def gpu_arm(args):
 
     hbm, peak_kind = load_peaks()
     lb_ms = float(phases[2])
-    lb_bytes = N * 16 + st["pass_keogh_q"] * 8  # the scan writes (bound, offset) per survivor
+    # 12 B read per window (sample, mean's high part, 1/sigma); the scan writes
+    # (bound, offset) per survivor
+    lb_bytes = N * 12 + st["pass_keogh_q"] * 8
     achieved = lb_bytes / (lb_ms * 1e-3) / 1e9 if lb_ms > 0 else None
     cpu = None
     if not args.no_cpu_baseline and world == 1:

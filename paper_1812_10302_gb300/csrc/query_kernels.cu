@@ -267,18 +267,18 @@ cudaError_t launch_qprep(const float *Q, const QueryBufs &b, const QueryArgs &a,
 // Use u of a stage waits for phase u & 1 of its barriers.  The end is a stage
 // whose tile index is -1, completed without copies.
 //
-// Two stage layouts.  LbLayout<TW>: TW windows with the statistics (mean as
-// a hi + lo pair, 1/sigma) of every window and all their samples (the
-// lower-bound scan).  ProxyLayout: kProxyTile windows with the mean's high
+// Two stage layouts.  LbLayout<TW>: TW windows with the mean's high part and
+// 1/sigma of every window and all their samples (the lower-bound scan; see
+// shift_bound for the mean's low part).  ProxyLayout: kProxyTile windows with the mean's high
 // part and 1/sigma of every kProxyStride-th window and only every
 // kProxyStride-th sample (the proxy scan scores those windows at term
 // positions that are multiples of kProxyStride; no ml array).
 template <int TW>
 struct LbLayout {
-    static constexpr int W = TW, S = TW, kStride = 1, NS = 3, XDIV = 1;
+    static constexpr int W = TW, S = TW, kStride = 1, NS = 2, XDIV = 1;
     __device__ static const float *xs(const QueryBufs &b) { return b.x; }
     __device__ static const float *mh(const QueryBufs &b) { return b.mu_hi; }
-    __device__ static const float *ml(const QueryBufs &b) { return b.mu_lo; }
+    __device__ static const float *ml(const QueryBufs &) { return nullptr; }
     __device__ static const float *is(const QueryBufs &b) { return b.inv_sigma; }
 };
 struct ProxyLayout {
@@ -1320,6 +1320,18 @@ cudaError_t launch_dtw_at_f64(const QueryBufs &b, const QueryArgs &a, const int6
 // after 2 and the survivor stage's pre-check takes over.
 constexpr int kEqChunks = 2, kEqSmem = 2;
 
+// The lower-bound scan normalises with the mean's high part alone: the
+// window's values then sit shifted by mu_lo / sigma, and |mu_lo| <= ulp(mu_hi)
+// / 2 <= |mu_hi| 2^-24 (the pair is normalised; 2^-149 covers a subnormal
+// mu_hi).  A value at most D from the true one is at least |d| - D from a
+// point the true one is d from, so each bound is taken on distances reduced
+// by D -- (|d| - D)+ for LB_KimFL's end points, the query envelope widened
+// by D for LB_Keogh -- and stays a lower bound; D is ~1e-7 of |mu| / sigma.
+// The scan then reads 12 bytes per window instead of 16.
+__device__ __forceinline__ float shift_bound(float mh, float is) {
+    return fmaf(fabsf(mh), 0x1p-24f, 0x1p-149f) * is;
+}
+
 __device__ __forceinline__ float keogh_term(float v, float u, float l) {
     const float d = fmaxf(v - u, 0.0f) + fmaxf(l - v, 0.0f);
     return d * d;
@@ -1349,7 +1361,7 @@ __device__ __forceinline__ float warp_sum(float v) {
 // the series envelope stall the warps that feed the ring.)
 __device__ __forceinline__ int lb_row_keogh(const Tile &t, const QueryBufs &b, QueryState *st, const int *o_s,
                                          const float *u_s, const float *l_s, int m, float thr, unsigned bal,
-                                         int wrow, int lane, float kim, float mh, float is, float ls, int64_t i0) {
+                                         int wrow, int lane, float kim, float mh, float is, float sd, int64_t i0) {
     const int w = wrow + lane;
     unsigned keep = 0;   // windows of this row that survive Eq. 8
     float my_lb = 0.0f;  // lane t holds window t's bound when it survives
@@ -1370,7 +1382,7 @@ __device__ __forceinline__ int lb_row_keogh(const Tile &t, const QueryBufs &b, Q
                         const bool sm = j < kEqSmem * 32;
                         const int o = sm ? o_s[j] : (int)__ldg(b.ord + j);
                         const float uq = sm ? u_s[j] : __ldg(b.sU + j), lq = sm ? l_s[j] : __ldg(b.sL + j);
-                        s2 += keogh_term(fmaf(t.xs[w + o] - mh, is, -ls), uq, lq);
+                        s2 += keogh_term((t.xs[w + o] - mh) * is, uq + sd, lq - sd);
                     }
                 }
                 alive = !(s2 > thr);
@@ -1383,7 +1395,7 @@ __device__ __forceinline__ int lb_row_keogh(const Tile &t, const QueryBufs &b, Q
             const int src = __ffs(bal) - 1;
             bal &= bal - 1;
             const int ws = wrow + src;
-            const float smh = t.mh[ws], sis = t.is[ws], sls = t.ml[ws] * sis;
+            const float smh = t.mh[ws], sis = t.is[ws], ssd = shift_bound(smh, sis);
             const float *xw = t.xs + ws;
             // a window that survives these chunks (the neighbourhood of a
             // match) goes to the DTW stage with the partial sum, itself a
@@ -1396,7 +1408,7 @@ __device__ __forceinline__ int lb_row_keogh(const Tile &t, const QueryBufs &b, Q
                     const bool sm = base < kEqSmem * 32;
                     const int o = sm ? o_s[j] : (int)__ldg(b.ord + j);
                     const float uq = sm ? u_s[j] : __ldg(b.sU + j), lq = sm ? l_s[j] : __ldg(b.sL + j);
-                    term = keogh_term(fmaf(xw[o] - smh, sis, -sls), uq, lq);
+                    term = keogh_term((xw[o] - smh) * sis, uq + ssd, lq - ssd);
                 }
                 s2 += warp_sum(term);
                 if (s2 > thr) break;
@@ -1454,21 +1466,20 @@ __global__ void __launch_bounds__(kScanThreads) k_lb_scan(QueryBufs b, QueryArgs
             const unsigned ro = (unsigned)u * 32u * 4u;
             const int w = (int)w0 + u * 32;
             bool pass = false;
-            float kim = 0.0f, mh = 0.0f, is = 0.0f, ls = 0.0f;
+            float kim = 0.0f, mh = 0.0f, is = 0.0f, sd = 0.0f;
             if (w < nrem) {
                 const unsigned su = sa + ro;
                 mh = lds_at<0>(su);
-                const float ml = lds_at<TW * 4>(su);
-                is = lds_at<TW * 8>(su);
-                ls = ml * is;
-                const float d0 = qf - fmaf(lds_at<0>(xa + ro) - mh, is, -ls);
-                const float d1 = ql - fmaf(lds_at<0>(xl + ro) - mh, is, -ls);
+                is = lds_at<TW * 4>(su);
+                sd = shift_bound(mh, is);
+                const float d0 = fmaxf(fabsf(fmaf(mh - lds_at<0>(xa + ro), is, qf)) - sd, 0.0f);
+                const float d1 = fmaxf(fabsf(fmaf(mh - lds_at<0>(xl + ro), is, ql)) - sd, 0.0f);
                 kim = fmaf(d0, d0, d1 * d1);
                 pass = !(kim > thr);
             }
             const unsigned bal = __ballot_sync(0xffffffffu, pass);
             c1 += __popc(bal);
-            if (bal) c2 += lb_row_keogh(t, b, st, o_s, u_s, l_s, m, thr, bal, w - lane, lane, kim, mh, is, ls, i0);
+            if (bal) c2 += lb_row_keogh(t, b, st, o_s, u_s, l_s, m, thr, bal, w - lane, lane, kim, mh, is, sd, i0);
         }
     });
     if (lane == 0) {

@@ -1433,7 +1433,7 @@ __device__ __forceinline__ int lb_row_keogh(const Tile &t, const QueryBufs &b, Q
 }
 
 template <int TW>
-__global__ void __launch_bounds__(kScanThreads) k_lb_scan(QueryBufs b, QueryArgs a, int stages) {
+__global__ void __launch_bounds__(kScanThreads, 5) k_lb_scan(QueryBufs b, QueryArgs a, int stages) {
     extern __shared__ __align__(16) unsigned char smraw[];
     QueryState *st = b.st;
     if (!st->valid) return;
@@ -1451,7 +1451,7 @@ __global__ void __launch_bounds__(kScanThreads) k_lb_scan(QueryBufs b, QueryArgs
         u_s[j] = j < m ? b.sU[j] : 0.0f;
         l_s[j] = j < m ? b.sL[j] : 0.0f;
     }
-    unsigned long long c1 = 0, c2 = 0;
+    unsigned c1 = 0, c2 = 0;  // (per lane: at most the windows its warp scans)
     const int64_t ntiles = (a.N + TW - 1) / TW;
     tile_pipeline<LbLayout<TW>>(smraw, b, m, ntiles, &st->tile_ctr[1], stages, [&](const Tile &t, int64_t i0) {
         // 32-bit shared addresses of this lane's first window (row 0); the
@@ -1459,32 +1459,58 @@ __global__ void __launch_bounds__(kScanThreads) k_lb_scan(QueryBufs b, QueryArgs
         const unsigned w0 = (unsigned)(warp * kPerWarp + lane);
         const unsigned sa = smem_u32(t.mh) + 4u * w0, xa = smem_u32(t.xs) + 4u * w0;
         const unsigned xl = xa + 4u * (unsigned)(m - 1);
-        const int64_t nrem = a.N - i0;  // windows of this tile that exist: w < nrem
-        // (one copy of the row body: the rare part below is inlined once)
-#pragma unroll 1
-        for (int u = 0; u < kPerWarp / 32; ++u) {
-            const unsigned ro = (unsigned)u * 32u * 4u;
-            const int w = (int)w0 + u * 32;
+        // windows of this tile that exist: w < rem
+        const int rem = a.N - i0 < TW ? (int)(a.N - i0) : TW;
+        constexpr int kRows = kPerWarp / 32;
+        // LB_KimFL for every row first (unrolled, constant offsets), then the
+        // rare part for the rows where some window passed (one copy of it)
+        unsigned bals[kRows];
+        float kims[kRows];
+        static_for<kRows>([&](auto uc) {
+            constexpr int u = decltype(uc)::value;
+            constexpr int RO = u * 32 * 4;
             bool pass = false;
-            float kim = 0.0f, mh = 0.0f, is = 0.0f, sd = 0.0f;
-            if (w < nrem) {
-                const unsigned su = sa + ro;
-                mh = lds_at<0>(su);
-                is = lds_at<TW * 4>(su);
-                sd = shift_bound(mh, is);
-                const float d0 = fmaxf(fabsf(fmaf(mh - lds_at<0>(xa + ro), is, qf)) - sd, 0.0f);
-                const float d1 = fmaxf(fabsf(fmaf(mh - lds_at<0>(xl + ro), is, ql)) - sd, 0.0f);
+            float kim = 0.0f;
+            if ((int)w0 + u * 32 < rem) {
+                const float mh = lds_at<RO>(sa), is = lds_at<RO + TW * 4>(sa);
+                const float sd = shift_bound(mh, is);
+                const float d0 = fmaxf(fabsf(fmaf(mh - lds_at<RO>(xa), is, qf)) - sd, 0.0f);
+                const float d1 = fmaxf(fabsf(fmaf(mh - lds_at<RO>(xl), is, ql)) - sd, 0.0f);
                 kim = fmaf(d0, d0, d1 * d1);
                 pass = !(kim > thr);
             }
-            const unsigned bal = __ballot_sync(0xffffffffu, pass);
-            c1 += __popc(bal);
-            if (bal) c2 += lb_row_keogh(t, b, st, o_s, u_s, l_s, m, thr, bal, w - lane, lane, kim, mh, is, sd, i0);
+            bals[u] = __ballot_sync(0xffffffffu, pass);
+            kims[u] = kim;
+        });
+        unsigned any = 0;
+#pragma unroll
+        for (int u = 0; u < kRows; ++u) {
+            c1 += (unsigned)__popc(bals[u]);
+            any |= bals[u];
+        }
+        if (any) {
+#pragma unroll 1
+            for (int u = 0; u < kRows; ++u) {
+                // (the row's ballot and bound picked by constant indices, so
+                // the arrays stay in registers)
+                unsigned bu = 0;
+                float ku = 0.0f;
+                static_for<kRows>([&](auto vc) {
+                    constexpr int v = decltype(vc)::value;
+                    bu = u == v ? bals[v] : bu;
+                    ku = u == v ? kims[v] : ku;
+                });
+                if (!bu) continue;
+                const int w = (int)w0 + u * 32;
+                const float mh = t.mh[w], is = t.is[w];
+                c2 += lb_row_keogh(t, b, st, o_s, u_s, l_s, m, thr, bu, w - lane, lane, ku, mh, is,
+                                   shift_bound(mh, is), i0);
+            }
         }
     });
     if (lane == 0) {
-        if (c1) atomicAdd(&st->ctr[kCtrKim], c1);
-        if (c2) atomicAdd(&st->ctr[kCtrKeoghQ], c2);
+        if (c1) atomicAdd(&st->ctr[kCtrKim], (unsigned long long)c1);
+        if (c2) atomicAdd(&st->ctr[kCtrKeoghQ], (unsigned long long)c2);
     }
 }
 

@@ -55,6 +55,25 @@ def test_window_stats_drifting_series():
                 assert abs(float(inv[i]) * sg - 1.0) <= 2.0 ** -22
 
 
+def test_mean_low_part_within_the_scan_shift_bound(series):
+    """The lower-bound scan normalises with the mean's high part alone and
+    takes each bound on distances reduced by (|mu_hi| 2^-24 + 2^-149) / sigma:
+    that holds only if every window's mean is stored as a normalised pair,
+    |mu_lo| <= |mu_hi| 2^-24 (+ the subnormal step), on the walk with its
+    constant stretch and spike, on a drifting series far from zero and on a
+    series with a large offset."""
+    walks = [series, synth.drifting_regimes(200_000, 4, drift=1e-2, regime=(2e4, 6e4)),
+             (synth.random_walk(50_000, 6) + 3.0e5).astype(np.float32)]
+    for x in walks:
+        with dtws.Index(x) as ix:
+            for m in (2, 64, 512, 2048):
+                if m > x.size:
+                    continue
+                mh, ml, _ = ix.window_stats(m)
+                bound = np.abs(mh.astype(np.float64)) * 2.0 ** -24 + 2.0 ** -149
+                assert np.all(np.abs(ml.astype(np.float64)) <= bound), m
+
+
 @pytest.mark.parametrize("r", [0, 1, 6, 51, 409, 2047])
 def test_series_envelope_exact(series, index, r):
     U, L = index.series_envelope(r)

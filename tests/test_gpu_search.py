@@ -42,6 +42,23 @@ def test_query_matches_oracle(walk, index, m, w, k, noise):
     _close(dist, od, m)
 
 
+@pytest.mark.parametrize("offset", [3.0e5, -7.5e6])
+def test_query_far_from_zero_matches_oracle(offset):
+    """A series far from zero: |mu| / sigma of ~1e4 to ~1e6, so the lower-bound
+    scan's shift bound (the mean's low part left out) is as large as it gets
+    relative to the distances; the answers and the near-tie order must still
+    be the oracle's (an undersized bound would prune a true match)."""
+    x = (synth.random_walk(60_001, 23) + offset).astype(np.float32)
+    with dtws.Index(x) as ix:
+        for m, r, k, noise in ((128, 12, 5, 0.3), (512, 51, 1, 0.1), (300, 30, 10, 1.0)):
+            q, _ = synth.noisy_copy(x, m, 31 + m, 41 + k, noise=noise)
+            idx, dist = ix.query(q, r, k)
+            assert ix.sync_status() == dtws.DTWS_OK
+            oi, od = fragments.search_fragments(x, q, r, k)
+            np.testing.assert_array_equal(idx, oi)
+            _close(dist, od, m)
+
+
 @pytest.mark.parametrize("m,r", [(64, 5), (128, 17), (300, 70), (512, 51), (1024, 102), (700, 200),
                                  (2048, 409), (1024, 921)])
 def test_distances_are_the_extended_rescore(walk, index, m, r):

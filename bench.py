@@ -79,9 +79,9 @@ def cells(m: int, r: int) -> int:
 
 
 # DRAM bytes (read + write) per window of k_lb_scan, from one ncu --set full capture of the
-# current kernel on the n=3e7, m=512, r=51 case (480.06 + 3.36 MB over 29,999,489 windows);
-# the bytes are dominated by the 16 B read per window, so they scale with the window count.
-LB_SCAN_DRAM_BYTES_PER_WINDOW = 483.41e6 / 29_999_489
+# current kernel on the n=3e7, m=512, r=51 case (360.05 + 3.35 MB over 29,999,489 windows);
+# the bytes are dominated by the 12 B read per window, so they scale with the window count.
+LB_SCAN_DRAM_BYTES_PER_WINDOW = 363.40e6 / 29_999_489
 
 
 def load_peaks():

@@ -359,9 +359,6 @@ __device__ bool tile_pipeline(unsigned char *sm, const QueryBufs &b, int m, int6
     if (warp == kScanConsumers) {
         if (lane == 0) {
             int64_t u = 0;
-            // the next tile's index is taken a tile ahead, so the cursor's
-            // round trip overlaps the wait for a free stage
-            long long next = (long long)atomicAdd(cursor, 1ull);
             for (;; ++u) {
                 const Tile t = carve_stage<LY>(sm, m, (int)(u % kS));
                 if (u >= kS &&
@@ -369,8 +366,7 @@ __device__ bool tile_pipeline(unsigned char *sm, const QueryBufs &b, int m, int6
                     ok = false;
                     break;
                 }
-                const long long tile = next;
-                if (tile < ntiles) next = (long long)atomicAdd(cursor, 1ull);
+                const long long tile = (long long)atomicAdd(cursor, 1ull);
                 if (tile >= ntiles) {
                     *t.tile = -1;
                     mbar_arrive(t.full);  // completes the phase with no copies

@@ -807,7 +807,7 @@ __device__ double dtw_diag_df(const dfloat *__restrict__ qs, const dfloat *__res
 
 // ------------------------------------------------------------------ multi-warp double-float walk
 // The same walk with the r+1 cells of an anti-diagonal spread over W warps
-// (32*W lanes, K cells each; W <= 16).  Inside a warp the neighbour arrives by
+// (32*W lanes, K cells each; W <= 8).  Inside a warp the neighbour arrives by
 // shuffle as in dtw_diag_df; across a warp boundary it goes through shared
 // memory: after each step every warp's first and last lane publish their
 // newest cell into the other half of a double buffer and the W warps meet at
@@ -815,7 +815,7 @@ __device__ double dtw_diag_df(const dfloat *__restrict__ qs, const dfloat *__res
 // step's writes (the other half).  The register windows' boundary lanes load
 // their fresh value from the padded arrays instead of a neighbour warp.
 struct DfXchg {
-    dfloat first[2][16], last[2][16];  // [buffer][warp]: lane 0's p1[0], lane 31's p1[K-1]
+    dfloat first[2][8], last[2][8];  // [buffer][warp]: lane 0's p1[0], lane 31's p1[K-1]
     dfloat res;
 };
 
@@ -901,7 +901,7 @@ __device__ __forceinline__ void shift_q_df_mw(dfloat (&qv)[K], const dfloat *qs,
 template <int W, int K>
 __device__ double dtw_diag_df_mw(const dfloat *__restrict__ qs, const dfloat *__restrict__ cs, int m, int r, int w,
                                  int lane, DfXchg &x, int bar_id) {
-    static_assert(W >= 1 && W <= 16, "at most sixteen warps");
+    static_assert(W >= 1 && W <= 8, "at most eight warps");
     const dfloat INF = dfloat{1e30f, 0.0f};
     const int gl = w * 32 + lane;
     const int p0 = (r - (r & 1)) >> 1;

@@ -1094,10 +1094,9 @@ __device__ __forceinline__ void final_order(const unsigned *idx, const double *d
 // output (final_order) -- k_final_select and k_final_sort without their
 // launches.
 template <int W, int K>
-__global__ void __launch_bounds__((W > 8 ? W : 8) * 32, 1) k_dtw64_mw(QueryBufs b, QueryArgs a,
-                                                                      const int64_t *offsets, int64_t count_host,
-                                                                      double *out, FinalOut fin) {
-    constexpr int GMAX = W > 8 ? 1 : 8 / W;
+__global__ void __launch_bounds__(256, 1) k_dtw64_mw(QueryBufs b, QueryArgs a, const int64_t *offsets,
+                                                  int64_t count_host, double *out, FinalOut fin) {
+    constexpr int GMAX = 8 / W;
     extern __shared__ __align__(16) unsigned char smraw[];
     __shared__ DfXchg xch[GMAX];
     __shared__ double bc[2 * GMAX];
@@ -1231,7 +1230,7 @@ static cudaError_t dtw64_mw_launch(const QueryBufs &b, const QueryArgs &a, const
     // the query's copy plus one window copy per group (double-float: 8 B per element)
     const size_t span = (size_t)((a.m + 2 * diag_pad(a.r, 32 * W, K) + 3) & ~3), bytes = span * sizeof(dfloat);
     const size_t hard = (size_t)200 * 1024;
-    int groups = W > 8 ? 1 : 8 / W;
+    int groups = 8 / W;
     while (groups > 1 && bytes * (size_t)(1 + groups) > hard) --groups;
     if (bytes * (size_t)(1 + groups) > hard) return cudaErrorNotSupported;  // the caller falls back
     const size_t smem = bytes * (size_t)(1 + groups);
@@ -1264,15 +1263,15 @@ static cudaError_t dtw64_dispatch(const QueryBufs &b, const QueryArgs &a, const 
 #undef DTWS_MW
     } else if (a.r > kDiagRMax && a.r < 8 * 32 * 8) {
         // bands past the one-warp walks (r > 511, up to 2047): the double-float
-        // walk over four warps (r <= 1023) or sixteen (a window's walk is
-        // latency: more warps, fewer cells per lane per anti-diagonal), instead
-        // of FP64 arithmetic, which this part issues at a small fraction of
-        // its FP32 rate (one window of m = 2048, r = 1843: 2.25 ms on eight
-        // warps of 8 cells, 3.0 ms on four of 16)
-        const int k4 = (a.r + 1 + 127) / 128;
+        // walk over four warps (r <= 1023) or eight (a window's walk is latency:
+        // more warps, fewer cells per lane per anti-diagonal) with up to 8
+        // cells per lane, instead of FP64 arithmetic, which this part issues
+        // at a small fraction of its FP32 rate
+        const int k4 = (a.r + 1 + 127) / 128, k8 = (a.r + 1 + 255) / 256;
         if (k4 <= 6) mw = dtw64_mw_launch<4, 6>(b, a, offsets, count, out, count_for_grid, s, fin);
         else if (k4 <= 8) mw = dtw64_mw_launch<4, 8>(b, a, offsets, count, out, count_for_grid, s, fin);
-        else mw = dtw64_mw_launch<16, 4>(b, a, offsets, count, out, count_for_grid, s, fin);
+        else if (k8 <= 6) mw = dtw64_mw_launch<8, 6>(b, a, offsets, count, out, count_for_grid, s, fin);
+        else mw = dtw64_mw_launch<8, 8>(b, a, offsets, count, out, count_for_grid, s, fin);
     }
     if (mw != cudaErrorNotSupported || fin.idx) return mw;
     // (the shared-memory copies do not fit: the one-group kernels below)

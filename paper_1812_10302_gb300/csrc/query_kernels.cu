@@ -267,31 +267,30 @@ cudaError_t launch_qprep(const float *Q, const QueryBufs &b, const QueryArgs &a,
 // Use u of a stage waits for phase u & 1 of its barriers.  The end is a stage
 // whose tile index is -1, completed without copies.
 //
-// Two stage layouts.  LbLayout<TW>: TW windows with the mean's high part and
-// 1/sigma of every window and all their samples (the lower-bound scan; see
-// shift_bound for the mean's low part).  ProxyLayout: kProxyTile windows with the mean's high
-// part and 1/sigma of every kProxyStride-th window and only every
-// kProxyStride-th sample (the proxy scan scores those windows at term
-// positions that are multiples of kProxyStride; no ml array).
+// Two stage layouts, each a tile's mean (high part) and 1/sigma arrays and
+// its samples.  LbLayout<TW>: TW windows, every window's statistics and all
+// their samples (the lower-bound scan; see shift_bound for the mean's low
+// part).  ProxyLayout: kProxyTile windows, the statistics of every
+// kProxyStride-th window and only every kProxyStride-th sample (the proxy
+// scan scores those windows at term positions that are multiples of
+// kProxyStride).
 template <int TW>
 struct LbLayout {
-    static constexpr int W = TW, S = TW, kStride = 1, NS = 2, XDIV = 1;
+    static constexpr int W = TW, S = TW, kStride = 1, XDIV = 1;
     __device__ static const float *xs(const QueryBufs &b) { return b.x; }
     __device__ static const float *mh(const QueryBufs &b) { return b.mu_hi; }
-    __device__ static const float *ml(const QueryBufs &) { return nullptr; }
     __device__ static const float *is(const QueryBufs &b) { return b.inv_sigma; }
 };
 struct ProxyLayout {
-    static constexpr int W = kProxyTile, S = kProxyTile / kProxyStride, kStride = kProxyStride, NS = 2,
+    static constexpr int W = kProxyTile, S = kProxyTile / kProxyStride, kStride = kProxyStride,
                          XDIV = kProxyStride;
     __device__ static const float *xs(const QueryBufs &b) { return b.x_sub; }
     __device__ static const float *mh(const QueryBufs &b) { return b.smu_hi; }
-    __device__ static const float *ml(const QueryBufs &) { return nullptr; }
     __device__ static const float *is(const QueryBufs &b) { return b.sinv_sigma; }
 };
 
 struct Tile {
-    float *xs, *mh, *ml, *is;
+    float *xs, *mh, *is;
     uint64_t *full, *empty;
     long long *tile;
 };
@@ -305,7 +304,7 @@ __host__ __device__ __forceinline__ unsigned tile_x_floats(int m) {
 }
 template <class LY>
 __host__ __device__ __forceinline__ size_t stage_bytes(int m) {
-    return kStageHeader + (size_t)LY::NS * LY::S * 4 + (size_t)tile_x_floats<LY>(m) * 4;
+    return kStageHeader + (size_t)2 * LY::S * 4 + (size_t)tile_x_floats<LY>(m) * 4;
 }
 
 template <class LY>
@@ -316,8 +315,7 @@ __device__ __forceinline__ Tile carve_stage(unsigned char *sm, int m, int stage)
     t.empty = (uint64_t *)(base + 8);
     t.tile = (long long *)(base + 16);
     t.mh = (float *)(base + kStageHeader);
-    t.ml = LY::NS == 3 ? t.mh + LY::S : nullptr;
-    t.is = t.mh + (LY::NS - 1) * LY::S;
+    t.is = t.mh + LY::S;
     t.xs = t.is + LY::S;
     return t;
 }
@@ -327,10 +325,9 @@ __device__ __forceinline__ void issue_tile(const Tile &t, const QueryBufs &b, in
     const unsigned xb = tile_x_floats<LY>(m) * 4u, sb = LY::S * 4u;
     const int64_t s0 = i0 / LY::kStride;
     // the transaction count covers exactly the copies issued below
-    mbar_arrive_expect_tx(t.full, xb + (unsigned)LY::NS * sb);
+    mbar_arrive_expect_tx(t.full, xb + 2u * sb);
     bulk_g2s(t.xs, LY::xs(b) + i0 / LY::XDIV, xb, t.full);
     bulk_g2s(t.mh, LY::mh(b) + s0, sb, t.full);
-    if constexpr (LY::NS == 3) bulk_g2s(t.ml, LY::ml(b) + s0, sb, t.full);
     bulk_g2s(t.is, LY::is(b) + s0, sb, t.full);
 }
 
@@ -556,7 +553,6 @@ __global__ void __launch_bounds__(kScanThreads) k_seed_scan(QueryBufs b, QueryAr
             const int rem = a.N - i0 < ProxyLayout::W ? (int)(a.N - i0) : ProxyLayout::W;
             const bool liveA0 = wA < rem, liveA1 = wA + kProxyStride < rem;
             const bool liveB0 = wB < rem, liveB1 = wB + kProxyStride < rem;
-            static_assert(ProxyLayout::NS == 2, "the proxy stage holds mh and is only");
             const unsigned long long mhA = lds64_at<oA>(sa), isA = lds64_at<oA + ProxyLayout::S * 4>(sa);
             const unsigned long long mhB = lds64_at<oB>(sa), isB = lds64_at<oB + ProxyLayout::S * 4>(sa);
             // q_hat - x_hat = (q + mh*is) - x*is, with the mean's high part

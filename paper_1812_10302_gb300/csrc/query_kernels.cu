@@ -1105,14 +1105,11 @@ __global__ void __launch_bounds__(256, 1) k_dtw64_mw(QueryBufs b, QueryArgs a, c
     const int pad = diag_pad(r, 32 * W, K);
     const size_t span = (size_t)((m + 2 * pad + 3) & ~3);
     dfloat *qd = (dfloat *)smraw + pad;
-    for (int t = threadIdx.x; t < m; t += blockDim.x) qd[t] = df_from(b.qh64[t]);
-    fill_pads((dfloat *)smraw, m, pad, dfloat{1e15f, 0.0f}, threadIdx.x, blockDim.x);
     const int warp = threadIdx.x >> 5, lane = lane_id();
     const int g = warp / W, w = warp % W, t = w * 32 + lane;
     const int nthr = 32 * W, bar = 1 + g;
     dfloat *cbase = (dfloat *)(smraw + span * 8 * (size_t)(1 + g));
     dfloat *cd = cbase + pad;
-    if (g < G) fill_pads(cbase, m, pad, dfloat{-1e15f, 0.0f}, t, nthr);
     __shared__ unsigned long long ms_keys[kListMax];
     __shared__ unsigned ms_idx[kListMax];
     __shared__ double ms_d[kListMax];
@@ -1135,7 +1132,16 @@ __global__ void __launch_bounds__(256, 1) k_dtw64_mw(QueryBufs b, QueryArgs a, c
         }
     }
     __syncthreads();
-    if (g >= G) {
+    // (a CTA of the fused final stage with no window to re-score skips the
+    // copies: usually all but the first, the best window being pre-scored)
+    const bool work = !fused || ms_skip + (int)blockIdx.x * G < ms_n;
+    if (work) {
+        for (int j = threadIdx.x; j < m; j += blockDim.x) qd[j] = df_from(b.qh64[j]);
+        fill_pads((dfloat *)smraw, m, pad, dfloat{1e15f, 0.0f}, threadIdx.x, blockDim.x);
+        if (g < G) fill_pads(cbase, m, pad, dfloat{-1e15f, 0.0f}, t, nthr);
+    }
+    __syncthreads();
+    if (g >= G || !work) {
         if (!fused) return;
     } else {
     const int64_t count = offsets ? count_host

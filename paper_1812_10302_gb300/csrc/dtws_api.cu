@@ -696,7 +696,7 @@ dtws_status enqueue_search(dtws_t h, const Exec &e, const QueryArgs &a, const fl
         CK(launch_seed_gather(b, a, R, P, half, h->opt.rng_seed, s));
         ++launches;
     }
-    CK(launch_seed_ed(b, a, s));
+    CK(launch_seed_ed(b, a, R + P * (2 * half + 1), s));
     if (k > 1 && a.xz_z == 0) {  // exact DTW seeds tighten a k-th bound the Euclidean seeds leave loose
         // (the neighbours of one match, which is all these seeds are, bound
         // nothing with an exclusion zone)

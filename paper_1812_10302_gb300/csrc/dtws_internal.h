@@ -159,7 +159,8 @@ cudaError_t launch_seed_scan(const QueryBufs &b, const QueryArgs &a, int proposa
 // half: Euclidean seeds cover the proposals' offsets +-half
 cudaError_t launch_seed_gather(const QueryBufs &b, const QueryArgs &a, int n_random,
                                int proposals, int half, unsigned long long rng, cudaStream_t s);
-cudaError_t launch_seed_ed(const QueryBufs &b, const QueryArgs &a, cudaStream_t s);
+// max_seeds: an upper bound on the Euclidean seed list's length (grid size)
+cudaError_t launch_seed_ed(const QueryBufs &b, const QueryArgs &a, int max_seeds, cudaStream_t s);
 // k > 1: offsets within +-k of the two best Euclidean seeds join the DTW seeds
 cudaError_t launch_seed_expand(const QueryBufs &b, const QueryArgs &a, cudaStream_t s);
 cudaError_t launch_dtw_seeds(const QueryBufs &b, const QueryArgs &a, cudaStream_t s);

@@ -907,8 +907,11 @@ cudaError_t launch_seed_expand(const QueryBufs &b, const QueryArgs &a, cudaStrea
     return cudaGetLastError();
 }
 
-cudaError_t launch_seed_ed(const QueryBufs &b, const QueryArgs &a, cudaStream_t s) {
-    k_seed_ed<<<(kEdMax * 32 + 255) / 256, 256, 0, s>>>(b, a);
+cudaError_t launch_seed_ed(const QueryBufs &b, const QueryArgs &a, int max_seeds, cudaStream_t s) {
+    // one warp per seed, for at most max_seeds seeds (the lists' bound)
+    if (max_seeds < 1) max_seeds = 1;
+    if (max_seeds > kEdMax) max_seeds = kEdMax;
+    k_seed_ed<<<(max_seeds * 32 + 255) / 256, 256, 0, s>>>(b, a);
     return cudaGetLastError();
 }
 
